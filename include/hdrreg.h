@@ -1,0 +1,271 @@
+/*
+ * hdrreg.h -- C ABI of the B300 (sm_103a) library for locally non-rigid HDR
+ * registration and merging of exposure stacks, after Gallo, Troccoli, Hu,
+ * Pulli and Kautz, "Locally Non-rigid Registration for Mobile HDR
+ * Photography" (arXiv 1504.01441).
+ *
+ * The source frame of a stack is brought to the reference frame's exposure,
+ * matched to the reference on a pyramid (per-tile corners and an SSD search
+ * around a per-level homography, Sec. 2.2), its matches weeded (Sec. 2.3),
+ * the sparse displacements spread into a dense flow by an edge-aware filter
+ * (Sec. 2.4), the source resampled onto the reference, and the frames merged
+ * into an irradiance map weighted by well-exposedness and an SSIM
+ * consistency mask (Sec. 2.5, Sec. 3.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every image / array pointer is a DEVICE pointer owned by the caller,
+ *    unless the parameter says "host". Planes are row-major and tightly
+ *    packed: luma is w x h bytes, YUV420 chroma (U, V) is (w/2) x (h/2).
+ *  - Pixel centres are at integer coordinates. "Normalized" coordinates are
+ *    those of Sec. 2.2 (Eq. 3): x_n = (2x - (w-1)) / w, y_n = (2y - (h-1)) / w.
+ *    A homography is double[9] in device memory, row-major, H[8] = 1, mapping
+ *    reference -> source in normalized coordinates.
+ *  - Step calls never allocate. They are asynchronous on `stream` (a
+ *    cudaStream_t; NULL = legacy default stream), never synchronize the host,
+ *    and can be captured into a CUDA graph. Scratch memory, where needed, is
+ *    passed in as `workspace` of at least the size the matching *_workspace_size
+ *    call returns (256-byte aligned).
+ *  - Arguments are validated on the host before anything is launched; an
+ *    invalid argument returns HDRREG_E_INVALID_ARG and launches nothing. A
+ *    launch failure returns HDRREG_E_CUDA. hdrreg_last_error() returns a
+ *    thread-local text for the last failure of the calling thread.
+ *  - Conditions found on the device (a level with too few matches, a singular
+ *    fit) do not fail the call; they are written to the optional device
+ *    status words / diagnostics named below.
+ */
+#ifndef HDRREG_H
+#define HDRREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HDRREG_ABI_VERSION 1
+
+typedef enum hdrreg_status {
+    HDRREG_OK = 0,
+    HDRREG_E_INVALID_ARG = 1,
+    HDRREG_E_CUDA = 2,
+    HDRREG_E_DEGENERATE = 3,
+    HDRREG_E_TIMEOUT = 4,
+    HDRREG_E_UNSUPPORTED = 5,
+    HDRREG_E_WORKSPACE = 6
+} hdrreg_status;
+
+/* Exposure normalization modes (row a1). */
+#define HDRREG_NORM_RATIO 0   /* brighten the darker frame by the known ratio, clip at 255 */
+#define HDRREG_NORM_HISTEQ 1  /* equalize each frame's histogram (Sec. 3)                  */
+
+/*
+ * Method parameters. hdrreg_params_default() fills the paper's values where
+ * the paper gives them (Sec. 2.6: 21x21 patches, search radius 10, up to 5
+ * levels, levels >= 100 px, candidate grid spacing T/16, sigma_s = 400) and
+ * this library's readings of its silences elsewhere.
+ */
+typedef struct hdrreg_params {
+    int tile;             /* T: tile side in pixels of the level, 8..128, even          */
+    int radius;           /* R: SSD search radius, 1..15                                */
+    int patch_half;       /* SSD patch is (2*patch_half+1)^2; 1..15                     */
+    int levels_max;       /* maximum pyramid levels, 1..8                               */
+    int min_level_size;   /* a level is kept only if both sides >= this                 */
+    int grid_half;        /* K: corner candidates c + s*(i,j), i,j in [-K,K], 0..8      */
+    int quad;             /* q: quadrant side of the cornerness measure, 1..32          */
+    int corner_thresh;    /* T of Eq. 2 as a mean difference in DN (sum thr T*q*q)      */
+    int weed_iters;       /* iterations of the Eq. 4 filter per level, 0..65536         */
+    int weed_delta_min;   /* delta = max(delta_min, ceil(n_valid / delta_div))         */
+    int weed_delta_div;
+    int norm_mode;        /* HDRREG_NORM_RATIO or HDRREG_NORM_HISTEQ                    */
+    int dt_iters;         /* domain-transform iterations, 1..8                          */
+    int ssim_radius;      /* SSIM Gaussian window radius; must be 5                     */
+    int propagate_full;   /* 0: flow = residual to H0 (dense map H0+F); 1: q - p (H ignored) */
+    int reserved0;
+    double weed_eps;      /* inlier distance, pixels of the level                       */
+    double sigma_s;       /* domain-transform spatial sigma                             */
+    double sigma_r;       /* domain-transform range sigma, on a [0,1] intensity scale   */
+    double ssim_sigma;    /* SSIM Gaussian window sigma                                 */
+    double we_sigma;      /* well-exposedness sigma                                     */
+    double flow_eps;      /* F = 0 where the filtered normalization map is below this   */
+    uint64_t weed_seed;   /* stream of the counter-based sampler (level l uses seed+l)  */
+} hdrreg_params;
+
+/* A YUV420 (or luma-only: u = v = NULL) 8-bit frame, device pointers. */
+typedef struct hdrreg_frame {
+    const uint8_t* y;
+    const uint8_t* u;
+    const uint8_t* v;
+} hdrreg_frame;
+
+/* FP32 output planes (device). u, v may be NULL for luma-only stacks. */
+typedef struct hdrreg_planes_f32 {
+    float* y;
+    float* u;
+    float* v;
+} hdrreg_planes_f32;
+
+/* One warped source as the merge consumes it (row a10-a11). */
+typedef struct hdrreg_merge_src {
+    const float* y;          /* warped source luma, w x h                                  */
+    const float* u;          /* warped source chroma, (w/2) x (h/2), or NULL               */
+    const float* v;
+    const uint8_t* ref_n;    /* reference normalized for this source's registration        */
+    const uint8_t* src_lut;  /* HISTEQ only: the source frame's 256-entry LUT (device)     */
+    int ratio_num;           /* exposure ratio t_src / t_ref = num / den, both > 0          */
+    int ratio_den;
+} hdrreg_merge_src;
+
+/* Per-source diagnostics written on the device by hdrreg_register_merge. */
+typedef struct hdrreg_diag {
+    double H0[9];            /* level-0 homography                                          */
+    int32_t levels;          /* pyramid levels used                                         */
+    int32_t tiles;           /* level-0 tiles                                               */
+    int32_t valid;           /* level-0 tiles with a corner                                 */
+    int32_t kept;            /* level-0 matches kept by the weeding                         */
+    int32_t fit_status;      /* bit l set: level l kept the coarser homography              */
+    int32_t reserved[3];
+} hdrreg_diag;
+
+/* ---------------------------------------------------------------- misc */
+void hdrreg_params_default(hdrreg_params* p);
+const char* hdrreg_last_error(void);
+const char* hdrreg_version(void);
+/* Number of pyramid levels for a w x h frame under p (host computation, Sec. 2.6). */
+int hdrreg_num_levels(int w, int h, const hdrreg_params* p);
+/* Check p; returns HDRREG_OK or HDRREG_E_INVALID_ARG (message in hdrreg_last_error). */
+hdrreg_status hdrreg_validate_params(const hdrreg_params* p);
+
+/* ------------------------------------------------------ a1: normalization
+ * Bring both luma planes into one 8-bit domain (Sec. 2.1, Sec. 3). RATIO: the
+ * exposure ratio r = ratio_num / ratio_den = t_src / t_ref is known; the darker
+ * frame is multiplied by max(r, 1/r), rounded to nearest (halves up) and
+ * clipped at 255; the other is copied. HISTEQ: each frame is mapped through its
+ * own histogram-equalization LUT (ratio ignored). `luts` (optional, 512 bytes:
+ * reference LUT then source LUT) receives the maps applied. Workspace:
+ * hdrreg_normalize_workspace_size(mode) bytes (0 for RATIO).
+ */
+size_t hdrreg_normalize_workspace_size(int mode);
+hdrreg_status hdrreg_normalize_exposure(const uint8_t* ref_y, const uint8_t* src_y, int w, int h,
+                                        int mode, int ratio_num, int ratio_den, uint8_t* ref_n,
+                                        uint8_t* src_n, uint8_t* luts, void* workspace,
+                                        size_t ws_bytes, void* stream);
+
+/* --------------------------------------------------------- a2: pyramid
+ * Levels 1..levels-1 of a 2x2 box pyramid ((a+b+c+d+2)>>2, odd last row /
+ * column dropped; Sec. 2.2, Sec. 2.6) of the w x h plane `level0`, written one
+ * after the other into `pyr` (level l is (w>>l) x (h>>l) bytes).
+ * hdrreg_pyramid_bytes gives the size of `pyr`.
+ */
+size_t hdrreg_pyramid_bytes(int w, int h, int levels);
+hdrreg_status hdrreg_build_pyramid(const uint8_t* level0, int w, int h, int levels, uint8_t* pyr,
+                                   void* stream);
+
+/* ---------------------------------------------- a3-a5: local search (one level)
+ * For every full tile (floor(w/T) x floor(h/T), row-major) of the normalized
+ * reference: pick the corner of highest cornerness (Eq. 1) among the
+ * candidate grid that passes the minimum-activity test (Eq. 2); project it by
+ * H (Eq. 3, `H` = the coarser level's homography, device) to the rounded
+ * search centre c; and find the integer displacement d in [-R, R]^2 of least
+ * SSD between the (2h+1)^2 patches (ties: lowest row-major index of d).
+ * Outputs per tile (device, n = tiles): corner_xy[2n] (tile centre if no
+ * corner), match_xy[2n] = c + d, cost[n] (0xFFFFFFFF if no corner), valid[n].
+ * Reads outside the level clamp to the edge.
+ */
+int hdrreg_num_tiles(int w, int h, int tile);
+hdrreg_status hdrreg_local_search(const uint8_t* ref_n, const uint8_t* src_n, int w, int h,
+                                  const double* H, const hdrreg_params* p, int32_t* corner_xy,
+                                  int32_t* match_xy, uint32_t* cost, uint8_t* valid,
+                                  void* stream);
+
+/* ---------------------------------------------------------- a6: weeding
+ * Iterations [iter_begin, iter_end) of the union-of-inliers filter of Eq. 4
+ * (Sec. 2.3) over the n tiles' matches: each iteration draws 4 distinct valid
+ * matches from the counter-based SplitMix64 stream `seed`, fits the
+ * homography through them exactly, and if more than delta matches reproject
+ * within eps pixels of their match, ORs those matches into mask_bits (bit t of
+ * word t/32 = tile t; the caller zeroes it before the first range). Disjoint
+ * ranges compose by union: running the ranges in any order equals one run
+ * (Sec. 2.3). Workspace: hdrreg_weed_workspace_size(n).
+ */
+size_t hdrreg_weed_workspace_size(int n);
+hdrreg_status hdrreg_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* valid,
+                          int n, int w, int h, const hdrreg_params* p, uint64_t seed,
+                          int iter_begin, int iter_end, uint32_t* mask_bits, void* workspace,
+                          size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------- a7: level fit
+ * Least-squares homography (DLT, h22 = 1, normalized coordinates) over the
+ * matches set in mask_bits (Sec. 2.2: H^l from the level's corners and
+ * matches). Normal equations are accumulated exactly in integers. If fewer
+ * than 4 matches are set or the system is singular, H_out = H_prev and the
+ * optional device word *status is set to 1 (too few) or 2 (singular), else 0.
+ * H_prev and H_out may alias.
+ */
+hdrreg_status hdrreg_fit_homography(const int32_t* corner_xy, const int32_t* match_xy,
+                                    const uint32_t* mask_bits, int n, int w, int h,
+                                    const double* H_prev, double* H_out, int32_t* status,
+                                    void* stream);
+
+/* -------------------------------------------------- a8: sparse-to-dense flow
+ * Dense flow from the weeded matches (Sec. 2.4, Eq. 5-6): the maps P_u, P_v
+ * hold the residual q - H(p) of every kept match at its corner p (or q - p
+ * when p->propagate_full), N holds 1 there; all three are filtered by the
+ * recursive domain transform guided by `guide_n` (the normalized reference),
+ * and flow = P~ / N~ (0 where N~ < flow_eps). Outputs flow_u, flow_v: w x h
+ * FP32. Workspace: hdrreg_flow_workspace_size(w, h).
+ */
+size_t hdrreg_flow_workspace_size(int w, int h);
+hdrreg_status hdrreg_flow_upsample(const uint8_t* guide_n, int w, int h, const int32_t* corner_xy,
+                                   const int32_t* match_xy, const uint32_t* mask_bits, int n,
+                                   const double* H, const hdrreg_params* p, float* flow_u,
+                                   float* flow_v, void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------- a9: warp
+ * Resample the source onto the reference grid: reference pixel p reads the
+ * source at H(p) + flow(p), bilinear with clamp-to-edge taps. Chroma (when
+ * src->u, src->v and out->u, out->v are all set; w, h even) samples at
+ * (Mbar - 0.5) / 2 with Mbar the mean of the four luma positions of its 2x2
+ * block. Outputs FP32 planes.
+ */
+hdrreg_status hdrreg_warp(const hdrreg_frame* src, int w, int h, const double* H,
+                          const float* flow_u, const float* flow_v, const hdrreg_planes_f32* out,
+                          void* stream);
+
+/* ------------------------------------------------ a10-a11: ghost mask + merge
+ * Irradiance merge of the reference with nsrc warped sources (host array of
+ * descriptors): E = sum_k w_k Z_k / r_k / sum_k w_k with r_ref = 1,
+ * w_ref = WE(Z_ref), w_k = WE(Z_k) * max(0, SSIM(ref_n_k, N_k(Z_k))) and w_k = 0
+ * where Z_k is exactly 0 or 255. WE is the well-exposedness weight of exposure
+ * fusion; SSIM uses a Gaussian window (ssim_sigma, radius 5) with clamp-to-edge;
+ * N_k maps the warped source into the registration's normalized domain (RATIO:
+ * min(255, g z) with g the gain its frame received; HISTEQ: its LUT,
+ * interpolated). Chroma: U-128, V-128 merged with the mean luma weight of each
+ * 2x2 block. out->y (w x h) and, for YUV420, out->u, out->v ((w/2) x (h/2))
+ * are FP32. q_out (optional): nsrc consecutive w x h FP32 masks.
+ */
+hdrreg_status hdrreg_merge(const hdrreg_frame* ref, int w, int h, int nsrc,
+                           const hdrreg_merge_src* srcs, const hdrreg_params* p,
+                           const hdrreg_planes_f32* out, float* q_out, void* stream);
+
+/* ------------------------------------------------ a1-a11 fused, one stack
+ * The whole path for one stack: each of the nsrc sources (host array) is
+ * registered to the reference independently (Sec. 2: n-1 runs) -- a1..a9 --
+ * then all are merged (a10-a11). ratio_num / ratio_den (host arrays) give
+ * t_src / t_ref per source. Everything stays on the device; diag (optional,
+ * device, nsrc entries) receives per-source diagnostics. Workspace:
+ * hdrreg_register_merge_workspace_size(w, h, nsrc, p).
+ */
+size_t hdrreg_register_merge_workspace_size(int w, int h, int nsrc, const hdrreg_params* p);
+hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int nsrc,
+                                    const hdrreg_frame* srcs, const int* ratio_num,
+                                    const int* ratio_den, const hdrreg_params* p,
+                                    void* workspace, size_t ws_bytes,
+                                    const hdrreg_planes_f32* out, hdrreg_diag* diag,
+                                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDRREG_H */

@@ -379,3 +379,9 @@ def register_merge(ref, srcs, ratios, cfg, want_intermediates=False):
     out = dict(y=oy, u=ou, v=ov, H0=H0.reshape(k, 3, 3))
     out.update(inter)
     return out
+
+
+def is_inlier(H, p, q, w, h, eps):
+    H = _f64(H).reshape(9)
+    return bool(lib().orc_is_inlier(_p(H), int(p[0]), int(p[1]), int(q[0]), int(q[1]), w, h,
+                                    C.c_double(eps)))

@@ -337,11 +337,36 @@ static double norm_x(int x, int w) { return (double)(2 * x - (w - 1)) / (double)
 static double norm_y(int y, int w, int h) { return (double)(2 * y - (h - 1)) / (double)w; }
 
 /*
+ * Inlier test of the weeding filter: the match q of corner p is an inlier of H
+ * if H(p) lands within eps pixels of q (Sec. 2.3). With x_s = (X/D w + (w-1))/2
+ * this is (X w - x_qc D)^2 + (Y w - y_qc D)^2 <= (2 eps D)^2 for D > 0, where
+ * (X, Y, D) = H (x_n, y_n, 1) and x_qc = 2 q_x - (w-1), y_qc = 2 q_y - (h-1):
+ * the same predicate multiplied through by (2D)^2, evaluated without division
+ * in the written order.
+ */
+int orc_is_inlier(const double H[9], int px, int py, int qx, int qy, int w, int h, double eps)
+{
+    double W = (double)w;
+    double xn = (double)(2 * px - (w - 1)) / W;
+    double yn = (double)(2 * py - (h - 1)) / W;
+    double X = (H[0] * xn + H[1] * yn) + H[2];
+    double Y = (H[3] * xn + H[4] * yn) + H[5];
+    double D = (H[6] * xn + H[7] * yn) + H[8];
+    double qxc = (double)(2 * qx - (w - 1));
+    double qyc = (double)(2 * qy - (h - 1));
+    double ex = X * W - qxc * D;
+    double ey = Y * W - qyc * D;
+    double lhs = ex * ex + ey * ey;
+    double t = (2.0 * eps) * D;
+    return D > 0.0 && lhs <= t * t;
+}
+
+/*
  * Weeding filter of Sec. 2.3, Eq. 4, iterations [iter_begin, iter_end): for
  * each iteration sample 4 distinct valid matches, fit the homography H^i
  * through them exactly (8x8 DLT in normalized coordinates, h22 = 1; skipped if
  * singular), collect the inliers I^i = matches whose projection lands within
- * eps pixels of their match, and if |I^i| > delta set M |= I^i. Inliers are
+ * eps pixels of their match (orc_is_inlier), and if |I^i| > delta set M |= I^i. Inliers are
  * not removed from the pool. mask_bits (bit t = tile t) is OR-ed into, so that
  * runs over disjoint iteration ranges compose by union (Sec. 2.3, last
  * paragraph). delta = max(delta_min, ceil(n_valid / delta_div)).
@@ -358,7 +383,6 @@ void orc_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* 
     if (nv >= 4) {
         int delta = (nv + p->weed_delta_div - 1) / p->weed_delta_div;
         if (delta < p->weed_delta_min) delta = p->weed_delta_min;
-        double eps2 = p->weed_eps * p->weed_eps;
         for (int it = iter_begin; it < iter_end; it++) {
             int pick[4];
             if (!orc_weed_sample(seed, it, nv, pick)) continue;
@@ -380,11 +404,8 @@ void orc_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* 
             int cnt = 0;
             for (int k = 0; k < nv; k++) {
                 int t = V[k];
-                double xs, ys;
-                int ok = orc_project(H, corner_xy[2 * t], corner_xy[2 * t + 1], w, h, &xs, &ys);
-                double dx = xs - (double)match_xy[2 * t];
-                double dy = ys - (double)match_xy[2 * t + 1];
-                inl[k] = ok && (dx * dx + dy * dy <= eps2);
+                inl[k] = orc_is_inlier(H, corner_xy[2 * t], corner_xy[2 * t + 1],
+                                       match_xy[2 * t], match_xy[2 * t + 1], w, h, p->weed_eps);
                 cnt += inl[k];
             }
             if (cnt > delta) {

@@ -635,3 +635,22 @@ def test_register_merge_improves_on_homography(orc, vga_stack):
     epe_h = np.hypot(hx - gx, hy - gy).mean()
     epe = np.hypot(hx + out["flow_u"][0] - gx, hy + out["flow_v"][0] - gy).mean()
     assert epe < epe_h and epe < 1.0
+
+
+def test_inlier_test_matches_reprojection_distance(orc):
+    # the division-free predicate equals "projection within eps pixels" (Sec. 2.3)
+    rng = np.random.default_rng(18)
+    w, h = 320, 240
+    from paper_1504_01441_b300 import synth
+    n_checked = 0
+    for _ in range(3000):
+        H = synth.random_homography(rng, scale=0.05, shift_n=0.05, persp=0.01)
+        p = (int(rng.integers(0, w)), int(rng.integers(0, h)))
+        xs, ys, ok = orc.project(H, p[0], p[1], w, h)
+        q = (int(round(xs + rng.uniform(-3, 3))), int(round(ys + rng.uniform(-3, 3))))
+        d2 = (xs - q[0]) ** 2 + (ys - q[1]) ** 2
+        if abs(d2 - 1.5 ** 2) < 1e-9:
+            continue                         # on the boundary: rounding decides either way
+        assert orc.is_inlier(H, p, q, w, h, 1.5) == (ok and d2 <= 1.5 ** 2)
+        n_checked += 1
+    assert n_checked > 2900
