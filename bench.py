@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the registration + merge path on seeded synthetic 5 MP pairs.
+
+One step = the whole path (a1..a11: normalization, pyramid matcher, weeding,
+level homographies, domain-transform flow, warp, SSIM mask, irradiance merge)
+over a batch of 2592x1944 YUV420 two-frame stacks resident in HBM, replayed as
+one CUDA graph. Prints one JSON line (see the keys below).
+
+  python bench.py --gpus N --steps K --warmup W [--impl reference]
+
+Under torchrun each rank (one GPU) registers its own batch of stacks: stacks
+are independent, so the ranks are replicas with no data-path collective; the
+reported value is all ranks' pixels / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "registered+merged Mpix/s per B300 (5 MP pairs), learned vs plain at ≤0.5 px EPE"
+WORKLOAD = "5mp_yuv420_pair"
+W, H = 2592, 1944
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pairs", type=int, default=16, help="stacks per step (inputs > L2)")
+    ap.add_argument("--distinct", type=int, default=2, help="distinct generated stacks")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="short run for a profiler")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def make_inputs(n_distinct):
+    from paper_1504_01441_b300 import synth
+    stacks = [synth.make_stack(synth.FIVE_MP, synth.stack_seed(2, i)) for i in range(n_distinct)]
+    return stacks
+
+
+def flow_algorithmic_bytes(w, h, iters=3):
+    """Compulsory bytes of the flow stage: the first row pass reads the guide and writes 3
+    FP32 planes; every later pass reads 3 planes + guide and writes 3 planes; the last column
+    pass writes the 2 flow planes instead."""
+    px = w * h
+    first = px * (1 + 12)
+    middle = px * (12 + 1 + 12)
+    last = px * (12 + 1 + 8)
+    return first + (2 * iters - 2) * middle + last
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1504_01441_b300 import hdrreg, synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stacks = make_inputs(args.distinct)
+    p = hdrreg.params_from_dict(synth.method_params(32, 6))
+    P = args.pairs
+    # resident inputs: P distinct device buffers (contents cycle over the generated stacks)
+    frames = []
+    for i in range(P):
+        s = stacks[i % len(stacks)]
+        ref = tuple(torch.from_numpy(a).to(dev) for a in (s.ref.y, s.ref.u, s.ref.v))
+        src = tuple(torch.from_numpy(a).to(dev) for a in (s.srcs[0].y, s.srcs[0].u, s.srcs[0].v))
+        frames.append((ref, [src], s.ratios))
+    runner = hdrreg.RegisterMerge(W, H, 1, p, True, device=dev)
+    outs = [(torch.empty((H, W), dtype=torch.float32, device=dev),
+             torch.empty((H // 2, W // 2), dtype=torch.float32, device=dev),
+             torch.empty((H // 2, W // 2), dtype=torch.float32, device=dev)) for _ in range(P)]
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        for i, (ref, srcs, ratios) in enumerate(frames):
+            ey, eu, ev = runner(ref, srcs, ratios)
+            outs[i][0].copy_(ey, non_blocking=True)
+            outs[i][1].copy_(eu, non_blocking=True)
+            outs[i][2].copy_(ev, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        step()  # warm the library (smem attributes) before capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    n0 = hdrreg.launch_count()
+    with torch.cuda.graph(graph, stream=stream):
+        step()
+    launches_per_step = hdrreg.launch_count() - n0
+    for _ in range(max(args.warmup, 0)):
+        graph.replay()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    K = args.steps
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(K):
+            graph.replay()
+        end.record(stream)
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_step = ms / K
+    mpix_step = P * W * H / 1e6
+    value = ws * mpix_step / (ms_step / 1e3)
+
+    # -- dominant stage: the flow (6 domain-transform passes), timed alone on its stream
+    roof = None
+    if rank == 0:
+        roof = measure_flow_roofline(torch, hdrreg, synth, p, stacks[0], dev, args)
+    # -- end to end through the C ABI with host buffers (pinned), copies inside the timing
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        e2e = measure_e2e(torch, hdrreg, runner, stacks, dev, max(2, min(P, 8)), args)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.profile:
+        cpu = measure_cpu_baseline(synth, stacks[0])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/i32 match, f64 fit, f32 flow/warp/merge", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": W, "height": H, "format": "YUV420",
+                       "frames": 2, "exposure_ratio": 4, "pairs_per_step": P,
+                       "distinct_stacks": len(stacks), "tile": 32, "radius": 6,
+                       "path": "plain (a1-a11)", "graph": True,
+                       "l2": f"inputs larger than L2: {P} resident pairs x 15.1 MB per step",
+                       "parallelism": f"replicas x{ws}"},
+            "gpu_launches": launches_per_step * K,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _flow_inputs(torch, hdrreg, p, stack, dev):
+    ref = torch.from_numpy(stack.ref.y).to(dev)
+    src = torch.from_numpy(stack.srcs[0].y).to(dev)
+    rn, sn, _ = hdrreg.normalize_exposure(ref, src, hdrreg.NORM_RATIO, stack.ratios[0])
+    # the level-0 matches of the registration itself (pyramid matcher on the GPU)
+    L = hdrreg.num_levels(W, H, p)
+    pr = hdrreg.build_pyramid(rn, L)
+    ps = hdrreg.build_pyramid(sn, L)
+    Hc = torch.tensor([1, 0, 0, 0, 1, 0, 0, 0, 1], dtype=torch.float64, device=dev)
+    for l in range(L - 1, -1, -1):
+        lh, lw = pr[l].shape
+        cxy, mxy, cost, valid = hdrreg.local_search(pr[l], ps[l], Hc, p)
+        mask = hdrreg.weed(cxy, mxy, valid, lw, lh, p, p.weed_seed + l)
+        Hc, _ = hdrreg.fit_homography(cxy, mxy, mask, lw, lh, Hc)
+    return rn, cxy, mxy, mask, Hc
+
+
+def measure_flow_roofline(torch, hdrreg, synth, p, stack, dev, args):
+    rn, cxy, mxy, mask, Hc = _flow_inputs(torch, hdrreg, p, stack, dev)
+    s = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        hdrreg.flow_upsample(rn, cxy, mxy, mask, Hc, p)
+    reps = 5 if args.profile else 30
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(s)
+    for _ in range(reps):
+        hdrreg.flow_upsample(rn, cxy, mxy, mask, Hc, p)
+    b.record(s)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / reps / 1e3
+    peak, src = peaks()
+    algo = flow_algorithmic_bytes(W, H, p.dt_iters)
+    ach = algo / sec / 1e9
+    return {"kernel": "flow: 6 domain-transform passes (k_dt_rows + k_dt_cols)", "bound": "hbm",
+            "achieved": round(ach, 1), "peak": peak, "peak_source": src, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "traffic": None,
+            "algorithmic_bytes_per_launch": algo, "us_per_launch": round(sec * 1e6, 2)}
+
+
+def measure_e2e(torch, hdrreg, runner, stacks, dev, P, args):
+    """Host (pinned) inputs -> device -> fused call -> device -> host outputs, per step."""
+    hin = []
+    for i in range(P):
+        s = stacks[i % len(stacks)]
+        planes = [s.ref.y, s.ref.u, s.ref.v, s.srcs[0].y, s.srcs[0].u, s.srcs[0].v]
+        hin.append([torch.from_numpy(a).pin_memory() for a in planes])
+    din = [[torch.empty(t.shape, dtype=t.dtype, device=dev) for t in h] for h in hin[:1]]
+    hout = [[torch.empty((H, W), dtype=torch.float32).pin_memory(),
+             torch.empty((H // 2, W // 2), dtype=torch.float32).pin_memory(),
+             torch.empty((H // 2, W // 2), dtype=torch.float32).pin_memory()] for _ in range(P)]
+    s = torch.cuda.current_stream(dev)
+    ratios = stacks[0].ratios
+
+    def step():
+        for i in range(P):
+            d = din[0]
+            for k in range(6):
+                d[k].copy_(hin[i][k], non_blocking=True)
+            ey, eu, ev = runner((d[0], d[1], d[2]), [(d[3], d[4], d[5])], ratios)
+            hout[i][0].copy_(ey, non_blocking=True)
+            hout[i][1].copy_(eu, non_blocking=True)
+            hout[i][2].copy_(ev, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    K = 3 if args.profile else 10
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(K):
+        step()
+    b.record(s)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    h2d = sum(t.numel() * t.element_size() for t in hin[0]) * P
+    d2h = sum(t.numel() * t.element_size() for t in hout[0]) * P
+    return {"value": round(P * W * H / 1e6 / (ms / 1e3), 2), "unit": "Mpix/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "pairs_per_step": P,
+            "ms_per_step": round(ms, 3)}
+
+
+def measure_cpu_baseline(synth, stack, runs=3):
+    import oracle
+    oracle.build()
+    cfg = synth.method_params(32, 6)
+    t0 = time.perf_counter()
+    for _ in range(runs):
+        oracle.register_merge(stack.ref, stack.srcs, stack.ratios, cfg)
+    sec = (time.perf_counter() - t0) / runs
+    return {"value": round(W * H / 1e6 / sec, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": f"{runs} runs of the oracle's whole path (a1-a11) on one 2592x1944 YUV420 pair"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1504_01441_b300 import synth
+    import oracle
+    oracle.build()
+    stack = make_inputs(1)[0]
+    cfg = synth.method_params(32, 6)
+    for _ in range(max(args.warmup, 0)):
+        oracle.register_merge(stack.ref, stack.srcs, stack.ratios, cfg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.register_merge(stack.ref, stack.srcs, stack.ratios, cfg)
+    sec = time.perf_counter() - t0
+    ms_step = sec * 1e3 / args.steps
+    value = W * H / 1e6 / (ms_step / 1e3)
+    sample = "one 2592x1944 YUV420 two-frame stack per step through the oracle's whole path"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64/int64 (CPU oracle)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": W, "height": H, "format": "YUV420", "frames": 2,
+                   "exposure_ratio": 4, "tile": 32, "radius": 6, "path": "plain (a1-a11)"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -132,6 +132,10 @@ typedef struct hdrreg_diag {
 void hdrreg_params_default(hdrreg_params* p);
 const char* hdrreg_last_error(void);
 const char* hdrreg_version(void);
+/* Number of kernels this library has enqueued in this process (host counter,
+ * incremented at every launch; a graph captured from library calls replays the
+ * launches counted while it was captured). */
+unsigned long long hdrreg_launch_count(void);
 /* Number of pyramid levels for a w x h frame under p (host computation, Sec. 2.6). */
 int hdrreg_num_levels(int w, int h, const hdrreg_params* p);
 /* Check p; returns HDRREG_OK or HDRREG_E_INVALID_ARG (message in hdrreg_last_error). */
@@ -236,8 +240,9 @@ hdrreg_status hdrreg_warp(const hdrreg_frame* src, int w, int h, const double* H
 /* ------------------------------------------------ a10-a11: ghost mask + merge
  * Irradiance merge of the reference with nsrc warped sources (host array of
  * descriptors): E = sum_k w_k Z_k / r_k / sum_k w_k with r_ref = 1,
- * w_ref = WE(Z_ref), w_k = WE(Z_k) * max(0, SSIM(ref_n_k, N_k(Z_k))) and w_k = 0
- * where Z_k is exactly 0 or 255. WE is the well-exposedness weight of exposure
+ * w_ref = WE(Z_ref), w_k = WE(Z_k) * max(0, SSIM(ref_n_k, N_k(Z_k))) * c(Z_k), where
+ * c is 0 at 0 and 255 and rises linearly to 1 over the 2 DN next to either end
+ * (clipped samples carry no irradiance). WE is the well-exposedness weight of exposure
  * fusion; SSIM uses a Gaussian window (ssim_sigma, radius 5) with clamp-to-edge;
  * N_k maps the warped source into the registration's normalized domain (RATIO:
  * min(255, g z) with g the gain its frame received; HISTEQ: its LUT,

@@ -832,11 +832,22 @@ double orc_well_exposedness(double z, double sigma)
 }
 
 /*
+ * Clipping taper of a resampled source value: 0 at 0 and 255, rising linearly
+ * to 1 over the 2 DN next to either end. A clipped sample carries no
+ * irradiance; the ramp keeps the weight continuous in the sample value.
+ */
+double orc_clip_taper(double z)
+{
+    double d = fmin(z, 255.0 - z) / 2.0;
+    return d <= 0.0 ? 0.0 : (d >= 1.0 ? 1.0 : d);
+}
+
+/*
  * Weighted irradiance merge (Sec. 2.5 weights; Sec. 3.1 irradiance map):
  * E(p) = sum_k w_k Z_k / r_k / sum_k w_k with r_ref = 1, w_ref = WE(Z_ref) and
- * for every warped source w_k = WE(Z_k) * Q_k, except w_k = 0 where Z_k is 0 or
- * 255 (clipped samples carry no irradiance). Chroma U-128, V-128 is merged with
- * the mean of the four luma weights of its 2x2 block and the same 1/r_k.
+ * for every warped source w_k = WE(Z_k) * Q_k * taper(Z_k) (orc_clip_taper).
+ * Chroma U-128, V-128 is merged with the mean of the four luma weights of its
+ * 2x2 block and the same 1/r_k.
  */
 void orc_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v,
                int nsrc, const double* const* wy, const double* const* wu,
@@ -852,8 +863,7 @@ void orc_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u, const u
         wts[i] = w0;
         for (int k = 0; k < nsrc; k++) {
             double z = wy[k][i];
-            double wk = (z == 0.0 || z == 255.0) ? 0.0
-                                                 : orc_well_exposedness(z, we_sigma) * q[k][i];
+            double wk = orc_well_exposedness(z, we_sigma) * q[k][i] * orc_clip_taper(z);
             wts[(long)(k + 1) * np + i] = wk;
             num += wk * (z / ratio[k]);
             den += wk;

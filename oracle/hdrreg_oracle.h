@@ -120,6 +120,7 @@ void orc_ghost_mask(const uint8_t* ref_n, const double* warped_y, int w, int h, 
 
 /* ---- a11: weighted irradiance merge --------------------------------------- */
 double orc_well_exposedness(double z, double sigma);
+double orc_clip_taper(double z);
 void orc_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v,
                int nsrc, const double* const* wy, const double* const* wu,
                const double* const* wv, const double* const* q, const double* ratio,

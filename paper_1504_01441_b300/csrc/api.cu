@@ -1,0 +1,635 @@
+// C ABI of the hdrreg library: argument validation, workspace layout, the step
+// calls and the fused per-stack pipeline (rows a1-a11), all stream-ordered and
+// free of host synchronization so a whole call can be captured in a CUDA graph.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "hdrreg_internal.cuh"
+
+namespace hdrreg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+hdrreg_status fail(hdrreg_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// cudaFuncSetAttribute is a host-side setting per device; do it once per
+// (device, kernel) and size so that calls made during stream capture only enqueue.
+void ensure_smem(const void* kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = done[{dev, kernel}];
+    if (bytes > cur) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cur = bytes;
+    }
+}
+
+hdrreg_status launch_status(const char* what)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HDRREG_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return HDRREG_OK;
+}
+
+static int num_levels(int w, int h, int levels_max, int min_size)
+{
+    int L = 1;
+    while (L < levels_max) {
+        const int lw = w >> L, lh = h >> L;
+        if (lw < min_size || lh < min_size) break;
+        L++;
+    }
+    return L;
+}
+
+static bool bad_dims(int w, int h) { return w < 1 || h < 1 || w > 16384 || h > 16384; }
+
+static SearchGeom make_geom(int w, int h, const hdrreg_params* p)
+{
+    SearchGeom g;
+    g.w = w;
+    g.h = h;
+    g.tile = p->tile;
+    g.radius = p->radius;
+    g.patch_half = p->patch_half;
+    g.grid_half = p->grid_half;
+    g.quad = p->quad;
+    g.step = p->tile / 16 > 1 ? p->tile / 16 : 1;
+    g.ntx = w / p->tile;
+    g.nty = h / p->tile;
+    g.corner_thr = (long long)p->corner_thresh * p->quad * p->quad;
+    return g;
+}
+
+// ------------------------------------------------------- fused workspace
+struct Layout {
+    size_t total = 0;
+    size_t add(size_t bytes)
+    {
+        const size_t o = total;
+        total += align_up(bytes > 0 ? bytes : 1, 256);
+        return o;
+    }
+};
+
+struct FusedLayout {
+    int L = 1, n0 = 0, nsrc = 1;
+    size_t ref_lv[kMaxLevels], src_lv[kMaxLevels];
+    size_t corner, match, cost, valid, mask, H, fit_st, weed, hist, luts, flow, fu, fv;
+    size_t wy[kMaxSources], wu[kMaxSources], wv[kMaxSources], refn[kMaxSources];
+    size_t total;
+    FusedLayout(int w, int h, int ns, const hdrreg_params* p)
+    {
+        Layout lay;
+        nsrc = ns;
+        L = num_levels(w, h, p->levels_max, p->min_level_size);
+        n0 = (w / p->tile) * (h / p->tile);
+        for (int l = 0; l < kMaxLevels; l++) ref_lv[l] = src_lv[l] = 0;
+        for (int l = 0; l < L; l++) {
+            ref_lv[l] = lay.add((size_t)(w >> l) * (h >> l));
+            src_lv[l] = lay.add((size_t)(w >> l) * (h >> l));
+        }
+        const size_t nn = n0 > 0 ? n0 : 1;
+        corner = lay.add(nn * 8);
+        match = lay.add(nn * 8);
+        cost = lay.add(nn * 4);
+        valid = lay.add(nn);
+        mask = lay.add((nn / 32 + 1) * 4);
+        H = lay.add((size_t)(kMaxLevels + 2) * 9 * 8);
+        fit_st = lay.add(kMaxLevels * 4);
+        weed = lay.add(weed_ws_bytes(n0));
+        hist = lay.add(2 * 256 * 4);
+        luts = lay.add((size_t)kMaxSources * 512);
+        flow = lay.add(flow_ws_bytes(w, h));
+        fu = lay.add((size_t)w * h * 4);
+        fv = lay.add((size_t)w * h * 4);
+        for (int k = 0; k < ns; k++) {
+            wy[k] = lay.add((size_t)w * h * 4);
+            wu[k] = lay.add((size_t)(w / 2) * (h / 2) * 4);
+            wv[k] = lay.add((size_t)(w / 2) * (h / 2) * 4);
+            refn[k] = lay.add((size_t)w * h);
+        }
+        total = lay.total;
+    }
+};
+
+__global__ void k_diag(const double* H0, const uint8_t* valid, const uint32_t* mask, int n,
+                       const int32_t* fit_st, int levels, hdrreg_diag* d)
+{
+    __shared__ int sv, sk;
+    if (threadIdx.x == 0) {
+        sv = 0;
+        sk = 0;
+    }
+    __syncthreads();
+    int v = 0, k = 0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        v += valid[t];
+        k += (mask[t >> 5] >> (t & 31)) & 1u;
+    }
+    atomicAdd(&sv, v);
+    atomicAdd(&sk, k);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 9; i++) d->H0[i] = H0[i];
+        d->levels = levels;
+        d->tiles = n;
+        d->valid = sv;
+        d->kept = sk;
+        int bits = 0;
+        for (int l = 0; l < levels; l++) bits |= (fit_st[l] != 0) << l;
+        d->fit_status = bits;
+        d->reserved[0] = d->reserved[1] = d->reserved[2] = 0;
+    }
+}
+
+}  // namespace hdrreg
+
+using namespace hdrreg;
+
+extern "C" {
+
+const char* hdrreg_last_error(void) { return g_last_error.c_str(); }
+
+const char* hdrreg_version(void) { return "hdrreg 0.1 (sm_103a)"; }
+
+unsigned long long hdrreg_launch_count(void) { return g_launches.load(); }
+
+void hdrreg_params_default(hdrreg_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->tile = 32;
+    p->radius = 10;
+    p->patch_half = 10;
+    p->levels_max = 5;
+    p->min_level_size = 100;
+    p->grid_half = 4;
+    p->quad = 10;
+    p->corner_thresh = 2;
+    p->weed_iters = 512;
+    p->weed_delta_min = 8;
+    p->weed_delta_div = 20;
+    p->norm_mode = HDRREG_NORM_RATIO;
+    p->dt_iters = 3;
+    p->ssim_radius = 5;
+    p->propagate_full = 0;
+    p->weed_eps = 1.5;
+    p->sigma_s = 400.0;
+    p->sigma_r = 0.5;
+    p->ssim_sigma = 1.5;
+    p->we_sigma = 0.2;
+    p->flow_eps = 1e-20;
+    p->weed_seed = 0x1504014410ull;
+}
+
+hdrreg_status hdrreg_validate_params(const hdrreg_params* p)
+{
+    if (!p) return fail(HDRREG_E_INVALID_ARG, "params is NULL");
+    if (p->tile < 8 || p->tile > 128 || (p->tile & 1))
+        return fail(HDRREG_E_INVALID_ARG, "tile must be even and in [8, 128] (got %d)", p->tile);
+    if (p->radius < 1 || p->radius > 15)
+        return fail(HDRREG_E_INVALID_ARG, "radius must be in [1, 15] (got %d)", p->radius);
+    if (p->patch_half < 1 || p->patch_half > 15)
+        return fail(HDRREG_E_INVALID_ARG, "patch_half must be in [1, 15] (got %d)", p->patch_half);
+    if (p->levels_max < 1 || p->levels_max > kMaxLevels)
+        return fail(HDRREG_E_INVALID_ARG, "levels_max must be in [1, %d]", kMaxLevels);
+    if (p->min_level_size < 1) return fail(HDRREG_E_INVALID_ARG, "min_level_size must be >= 1");
+    const int step = p->tile / 16 > 1 ? p->tile / 16 : 1;
+    if (p->grid_half < 0 || p->grid_half > 8 || p->grid_half * step > p->tile / 2 - 1)
+        return fail(HDRREG_E_INVALID_ARG,
+                    "grid_half must be in [0, 8] with grid_half*max(1,T/16) < T/2 (got %d)",
+                    p->grid_half);
+    if (p->quad < 1 || p->quad > 32) return fail(HDRREG_E_INVALID_ARG, "quad must be in [1, 32]");
+    if (p->corner_thresh < 0) return fail(HDRREG_E_INVALID_ARG, "corner_thresh must be >= 0");
+    if (p->weed_iters < 0 || p->weed_iters > 65536)
+        return fail(HDRREG_E_INVALID_ARG, "weed_iters must be in [0, 65536]");
+    if (p->weed_delta_min < 0 || p->weed_delta_div < 1)
+        return fail(HDRREG_E_INVALID_ARG, "weed_delta_min >= 0 and weed_delta_div >= 1 required");
+    if (p->norm_mode != HDRREG_NORM_RATIO && p->norm_mode != HDRREG_NORM_HISTEQ)
+        return fail(HDRREG_E_INVALID_ARG, "unknown norm_mode %d", p->norm_mode);
+    if (p->dt_iters < 1 || p->dt_iters > 8)
+        return fail(HDRREG_E_INVALID_ARG, "dt_iters must be in [1, 8]");
+    if (p->ssim_radius != kSsimRadius)
+        return fail(HDRREG_E_INVALID_ARG, "ssim_radius must be %d", kSsimRadius);
+    if (p->propagate_full != 0 && p->propagate_full != 1)
+        return fail(HDRREG_E_INVALID_ARG, "propagate_full must be 0 or 1");
+    if (!(p->weed_eps > 0) || !(p->sigma_s > 0) || !(p->sigma_r > 0) || !(p->ssim_sigma > 0) ||
+        !(p->we_sigma > 0) || !(p->flow_eps >= 0))
+        return fail(HDRREG_E_INVALID_ARG,
+                    "weed_eps, sigma_s, sigma_r, ssim_sigma, we_sigma must be > 0, flow_eps >= 0");
+    return HDRREG_OK;
+}
+
+int hdrreg_num_levels(int w, int h, const hdrreg_params* p)
+{
+    if (!p || bad_dims(w, h)) return 0;
+    return num_levels(w, h, p->levels_max, p->min_level_size);
+}
+
+int hdrreg_num_tiles(int w, int h, int tile)
+{
+    if (tile < 1 || w < 0 || h < 0) return 0;
+    return (w / tile) * (h / tile);
+}
+
+// ------------------------------------------------------------------- a1
+size_t hdrreg_normalize_workspace_size(int mode)
+{
+    return mode == HDRREG_NORM_HISTEQ ? 2 * 256 * 4 : 0;
+}
+
+hdrreg_status hdrreg_normalize_exposure(const uint8_t* ref_y, const uint8_t* src_y, int w, int h,
+                                        int mode, int ratio_num, int ratio_den, uint8_t* ref_n,
+                                        uint8_t* src_n, uint8_t* luts, void* workspace,
+                                        size_t ws_bytes, void* stream)
+{
+    if (!ref_y || !src_y || !ref_n || !src_n)
+        return fail(HDRREG_E_INVALID_ARG, "normalize: NULL plane");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "normalize: bad size %dx%d", w, h);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)w * h;
+    if (mode == HDRREG_NORM_RATIO) {
+        if (ratio_num < 1 || ratio_den < 1)
+            return fail(HDRREG_E_INVALID_ARG, "normalize: ratio must be positive (%d/%d)",
+                        ratio_num, ratio_den);
+        const bool ref_darker = ratio_num >= ratio_den;
+        LutSpec la{nullptr, 1, 1}, lb{nullptr, 1, 1};
+        if (ref_darker) la = LutSpec{nullptr, ratio_num, ratio_den};
+        else lb = LutSpec{nullptr, ratio_den, ratio_num};
+        launch_lut2(ref_y, src_y, ref_n, src_n, n, la, lb, s);
+        if (luts) launch_write_luts(la, lb, luts, s);
+        return launch_status("normalize(ratio)");
+    }
+    if (mode != HDRREG_NORM_HISTEQ) return fail(HDRREG_E_INVALID_ARG, "normalize: unknown mode");
+    if (!workspace || ws_bytes < hdrreg_normalize_workspace_size(mode))
+        return fail(HDRREG_E_WORKSPACE, "normalize(histeq): workspace of %zu bytes required",
+                    hdrreg_normalize_workspace_size(mode));
+    if (!luts) return fail(HDRREG_E_INVALID_ARG, "normalize(histeq): luts buffer required");
+    uint32_t* hist = static_cast<uint32_t*>(workspace);
+    cudaMemsetAsync(hist, 0, 2 * 256 * 4, s);
+    launch_histograms(ref_y, src_y, n, hist, s);
+    launch_histeq_luts(hist, n, luts, s);
+    launch_lut2(ref_y, src_y, ref_n, src_n, n, LutSpec{luts, 1, 1}, LutSpec{luts + 256, 1, 1}, s);
+    return launch_status("normalize(histeq)");
+}
+
+// ------------------------------------------------------------------- a2
+size_t hdrreg_pyramid_bytes(int w, int h, int levels)
+{
+    size_t b = 0;
+    for (int l = 1; l < levels; l++) b += (size_t)(w >> l) * (h >> l);
+    return b;
+}
+
+hdrreg_status hdrreg_build_pyramid(const uint8_t* level0, int w, int h, int levels, uint8_t* pyr,
+                                   void* stream)
+{
+    if (!level0 || (levels > 1 && !pyr)) return fail(HDRREG_E_INVALID_ARG, "pyramid: NULL");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "pyramid: bad size");
+    if (levels < 1 || levels > kMaxLevels)
+        return fail(HDRREG_E_INVALID_ARG, "pyramid: levels must be in [1, %d]", kMaxLevels);
+    if (levels == 1) return HDRREG_OK;
+    uint8_t* lv[kMaxLevels] = {nullptr};
+    size_t off = 0;
+    for (int l = 1; l < levels; l++) {
+        lv[l] = pyr + off;
+        off += (size_t)(w >> l) * (h >> l);
+    }
+    launch_pyramid(level0, w, h, levels, LutSpec{nullptr, 1, 1}, nullptr, lv,
+                   static_cast<cudaStream_t>(stream));
+    return launch_status("pyramid");
+}
+
+// ---------------------------------------------------------------- a3-a5
+hdrreg_status hdrreg_local_search(const uint8_t* ref_n, const uint8_t* src_n, int w, int h,
+                                  const double* H, const hdrreg_params* p, int32_t* corner_xy,
+                                  int32_t* match_xy, uint32_t* cost, uint8_t* valid, void* stream)
+{
+    hdrreg_status st = hdrreg_validate_params(p);
+    if (st) return st;
+    if (!ref_n || !src_n || !H || !corner_xy || !match_xy || !cost || !valid)
+        return fail(HDRREG_E_INVALID_ARG, "local_search: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "local_search: bad size %dx%d", w, h);
+    const SearchGeom g = make_geom(w, h, p);
+    launch_local_search(ref_n, src_n, H, g, corner_xy, match_xy, cost, valid,
+                        static_cast<cudaStream_t>(stream));
+    return launch_status("local_search");
+}
+
+// -------------------------------------------------------------------- a6
+size_t hdrreg_weed_workspace_size(int n) { return weed_ws_bytes(n); }
+
+hdrreg_status hdrreg_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* valid,
+                          int n, int w, int h, const hdrreg_params* p, uint64_t seed,
+                          int iter_begin, int iter_end, uint32_t* mask_bits, void* workspace,
+                          size_t ws_bytes, void* stream)
+{
+    hdrreg_status st = hdrreg_validate_params(p);
+    if (st) return st;
+    if (n < 0 || n > (1 << 20)) return fail(HDRREG_E_INVALID_ARG, "weed: n out of range");
+    if (n > 0 && (!corner_xy || !match_xy || !valid || !mask_bits))
+        return fail(HDRREG_E_INVALID_ARG, "weed: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "weed: bad size");
+    if (iter_begin < 0 || iter_end < iter_begin)
+        return fail(HDRREG_E_INVALID_ARG, "weed: bad iteration range [%d, %d)", iter_begin,
+                    iter_end);
+    if (n == 0) return HDRREG_OK;
+    if (!workspace || ws_bytes < weed_ws_bytes(n))
+        return fail(HDRREG_E_WORKSPACE, "weed: workspace of %zu bytes required", weed_ws_bytes(n));
+    launch_weed(corner_xy, match_xy, valid, n, w, h, p->weed_eps, p->weed_delta_min,
+                p->weed_delta_div, seed, iter_begin, iter_end, mask_bits,
+                weed_ws_carve(workspace, n), static_cast<cudaStream_t>(stream));
+    return launch_status("weed");
+}
+
+// -------------------------------------------------------------------- a7
+hdrreg_status hdrreg_fit_homography(const int32_t* corner_xy, const int32_t* match_xy,
+                                    const uint32_t* mask_bits, int n, int w, int h,
+                                    const double* H_prev, double* H_out, int32_t* status,
+                                    void* stream)
+{
+    if (n < 0 || n > (1 << 20)) return fail(HDRREG_E_INVALID_ARG, "fit: n out of range");
+    if (!H_prev || !H_out || (n > 0 && (!corner_xy || !match_xy || !mask_bits)))
+        return fail(HDRREG_E_INVALID_ARG, "fit: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "fit: bad size");
+    launch_fit(corner_xy, match_xy, mask_bits, n, w, h, H_prev, H_out, status,
+               static_cast<cudaStream_t>(stream));
+    return launch_status("fit");
+}
+
+// -------------------------------------------------------------------- a8
+size_t hdrreg_flow_workspace_size(int w, int h)
+{
+    if (bad_dims(w, h)) return 0;
+    return flow_ws_bytes(w, h);
+}
+
+hdrreg_status hdrreg_flow_upsample(const uint8_t* guide_n, int w, int h, const int32_t* corner_xy,
+                                   const int32_t* match_xy, const uint32_t* mask_bits, int n,
+                                   const double* H, const hdrreg_params* p, float* flow_u,
+                                   float* flow_v, void* workspace, size_t ws_bytes, void* stream)
+{
+    hdrreg_status st = hdrreg_validate_params(p);
+    if (st) return st;
+    if (!guide_n || !flow_u || !flow_v || (!p->propagate_full && !H))
+        return fail(HDRREG_E_INVALID_ARG, "flow: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "flow: bad size");
+    if (n != (w / p->tile) * (h / p->tile))
+        return fail(HDRREG_E_INVALID_ARG, "flow: n (%d) must equal the tile count %d", n,
+                    (w / p->tile) * (h / p->tile));
+    if (n > 0 && (!corner_xy || !match_xy || !mask_bits))
+        return fail(HDRREG_E_INVALID_ARG, "flow: NULL match arrays");
+    if (!flow_supported(w, h))
+        return fail(HDRREG_E_UNSUPPORTED, "flow: %dx%d exceeds the on-chip strip capacity", w, h);
+    if (!workspace || ws_bytes < flow_ws_bytes(w, h))
+        return fail(HDRREG_E_WORKSPACE, "flow: workspace of %zu bytes required",
+                    flow_ws_bytes(w, h));
+    FlowCorners fc{corner_xy, match_xy, mask_bits, H, w / p->tile, h / p->tile, p->tile,
+                   p->propagate_full};
+    launch_flow(guide_n, w, h, fc, p->sigma_s, p->sigma_r, p->dt_iters, p->flow_eps, flow_u,
+                flow_v, workspace, static_cast<cudaStream_t>(stream));
+    return launch_status("flow");
+}
+
+// -------------------------------------------------------------------- a9
+hdrreg_status hdrreg_warp(const hdrreg_frame* src, int w, int h, const double* H,
+                          const float* flow_u, const float* flow_v, const hdrreg_planes_f32* out,
+                          void* stream)
+{
+    if (!src || !src->y || !H || !flow_u || !flow_v || !out || !out->y)
+        return fail(HDRREG_E_INVALID_ARG, "warp: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "warp: bad size");
+    const bool chroma = src->u && src->v && out->u && out->v;
+    if (chroma && ((w & 1) || (h & 1)))
+        return fail(HDRREG_E_INVALID_ARG, "warp: YUV420 needs even width and height");
+    launch_warp(src->y, chroma ? src->u : nullptr, chroma ? src->v : nullptr, w, h, H, flow_u,
+                flow_v, out->y, chroma ? out->u : nullptr, chroma ? out->v : nullptr,
+                static_cast<cudaStream_t>(stream));
+    return launch_status("warp");
+}
+
+// ---------------------------------------------------------------- a10-a11
+static hdrreg_status merge_src_dev(const hdrreg_merge_src& m, int mode, bool chroma,
+                                   MergeSrcDev& d)
+{
+    if (!m.y || !m.ref_n) return fail(HDRREG_E_INVALID_ARG, "merge: NULL source plane");
+    if (chroma && (!m.u || !m.v)) return fail(HDRREG_E_INVALID_ARG, "merge: NULL chroma plane");
+    if (m.ratio_num < 1 || m.ratio_den < 1)
+        return fail(HDRREG_E_INVALID_ARG, "merge: ratio must be positive");
+    if (mode == HDRREG_NORM_HISTEQ && !m.src_lut)
+        return fail(HDRREG_E_INVALID_ARG, "merge: HISTEQ needs the source LUT");
+    d.y = m.y;
+    d.u = m.u;
+    d.v = m.v;
+    d.ref_n = m.ref_n;
+    d.lut = m.src_lut;
+    d.inv_ratio = (float)((double)m.ratio_den / (double)m.ratio_num);
+    d.gain = m.ratio_num < m.ratio_den ? (float)((double)m.ratio_den / (double)m.ratio_num) : 1.f;
+    d.mode = mode;
+    return HDRREG_OK;
+}
+
+hdrreg_status hdrreg_merge(const hdrreg_frame* ref, int w, int h, int nsrc,
+                           const hdrreg_merge_src* srcs, const hdrreg_params* p,
+                           const hdrreg_planes_f32* out, float* q_out, void* stream)
+{
+    hdrreg_status st = hdrreg_validate_params(p);
+    if (st) return st;
+    if (!ref || !ref->y || !out || !out->y || !srcs)
+        return fail(HDRREG_E_INVALID_ARG, "merge: NULL pointer");
+    if (nsrc < 1 || nsrc > kMaxSources)
+        return fail(HDRREG_E_INVALID_ARG, "merge: nsrc must be in [1, %d]", kMaxSources);
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "merge: bad size");
+    const bool chroma = ref->u && ref->v && out->u && out->v;
+    if (chroma && ((w & 1) || (h & 1)))
+        return fail(HDRREG_E_INVALID_ARG, "merge: YUV420 needs even width and height");
+    MergeSrcDev d[kMaxSources];
+    for (int k = 0; k < nsrc; k++)
+        if ((st = merge_src_dev(srcs[k], p->norm_mode, chroma, d[k]))) return st;
+    launch_merge(ref->y, chroma ? ref->u : nullptr, chroma ? ref->v : nullptr, w, h, nsrc, d,
+                 p->ssim_sigma, p->we_sigma, out->y, chroma ? out->u : nullptr,
+                 chroma ? out->v : nullptr, q_out, static_cast<cudaStream_t>(stream));
+    return launch_status("merge");
+}
+
+// ------------------------------------------------------------ fused a1-a11
+size_t hdrreg_register_merge_workspace_size(int w, int h, int nsrc, const hdrreg_params* p)
+{
+    if (!p || bad_dims(w, h) || nsrc < 1 || nsrc > kMaxSources) return 0;
+    return FusedLayout(w, h, nsrc, p).total;
+}
+
+hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int nsrc,
+                                    const hdrreg_frame* srcs, const int* ratio_num,
+                                    const int* ratio_den, const hdrreg_params* p,
+                                    void* workspace, size_t ws_bytes,
+                                    const hdrreg_planes_f32* out, hdrreg_diag* diag,
+                                    void* stream)
+{
+    hdrreg_status st = hdrreg_validate_params(p);
+    if (st) return st;
+    if (!ref || !ref->y || !srcs || !ratio_num || !ratio_den || !out || !out->y)
+        return fail(HDRREG_E_INVALID_ARG, "register_merge: NULL pointer");
+    if (nsrc < 1 || nsrc > kMaxSources)
+        return fail(HDRREG_E_INVALID_ARG, "register_merge: nsrc must be in [1, %d]", kMaxSources);
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "register_merge: bad size %dx%d", w, h);
+    const bool chroma = ref->u && ref->v && out->u && out->v;
+    if (chroma && ((w & 1) || (h & 1)))
+        return fail(HDRREG_E_INVALID_ARG, "register_merge: YUV420 needs even width and height");
+    for (int k = 0; k < nsrc; k++) {
+        if (!srcs[k].y || (chroma && (!srcs[k].u || !srcs[k].v)))
+            return fail(HDRREG_E_INVALID_ARG, "register_merge: NULL source %d plane", k);
+        if (ratio_num[k] < 1 || ratio_den[k] < 1)
+            return fail(HDRREG_E_INVALID_ARG, "register_merge: ratio %d must be positive", k);
+    }
+    if (!flow_supported(w, h))
+        return fail(HDRREG_E_UNSUPPORTED, "register_merge: %dx%d exceeds the flow strip capacity",
+                    w, h);
+    const FusedLayout lay(w, h, nsrc, p);
+    if (!workspace || ws_bytes < lay.total)
+        return fail(HDRREG_E_WORKSPACE, "register_merge: workspace of %zu bytes required",
+                    lay.total);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* base = static_cast<uint8_t*>(workspace);
+    auto at = [&](size_t off) { return base + off; };
+    int32_t* corner = reinterpret_cast<int32_t*>(at(lay.corner));
+    int32_t* match = reinterpret_cast<int32_t*>(at(lay.match));
+    uint32_t* cost = reinterpret_cast<uint32_t*>(at(lay.cost));
+    uint8_t* valid = at(lay.valid);
+    uint32_t* mask = reinterpret_cast<uint32_t*>(at(lay.mask));
+    double* Hs = reinterpret_cast<double*>(at(lay.H));
+    int32_t* fit_st = reinterpret_cast<int32_t*>(at(lay.fit_st));
+    const WeedWs wws = weed_ws_carve(at(lay.weed), lay.n0);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(at(lay.hist));
+    float* fu = reinterpret_cast<float*>(at(lay.fu));
+    float* fv = reinterpret_cast<float*>(at(lay.fv));
+    const int L = lay.L;
+    const size_t npx = (size_t)w * h;
+    MergeSrcDev md[kMaxSources];
+
+    for (int k = 0; k < nsrc; k++) {
+        // ---- a1 + a2: normalized level 0 (or an alias of the input) and the pyramids
+        LutSpec lr{nullptr, 1, 1}, ls{nullptr, 1, 1};
+        uint8_t* luts_k = at(lay.luts) + 512 * k;
+        bool ref_identity = true, src_identity = true;
+        float gain = 1.f;
+        if (p->norm_mode == HDRREG_NORM_RATIO) {
+            if (ratio_num[k] > ratio_den[k]) {
+                lr = LutSpec{nullptr, ratio_num[k], ratio_den[k]};
+                ref_identity = false;
+            } else if (ratio_num[k] < ratio_den[k]) {
+                ls = LutSpec{nullptr, ratio_den[k], ratio_num[k]};
+                src_identity = false;
+                gain = (float)((double)ratio_den[k] / (double)ratio_num[k]);
+            }
+        } else {
+            cudaMemsetAsync(hist, 0, 2 * 256 * 4, s);
+            launch_histograms(ref->y, srcs[k].y, npx, hist, s);
+            launch_histeq_luts(hist, npx, luts_k, s);
+            lr = LutSpec{luts_k, 1, 1};
+            ls = LutSpec{luts_k + 256, 1, 1};
+            ref_identity = src_identity = false;
+        }
+        const uint8_t* ref0 = ref_identity ? ref->y : at(lay.refn[k]);
+        const uint8_t* src0 = src_identity ? srcs[k].y : at(lay.src_lv[0]);
+        {
+            uint8_t* rl[kMaxLevels] = {nullptr};
+            uint8_t* sl[kMaxLevels] = {nullptr};
+            for (int l = 1; l < L; l++) {
+                rl[l] = at(lay.ref_lv[l]);
+                sl[l] = at(lay.src_lv[l]);
+            }
+            const uint8_t* ins[2] = {ref->y, srcs[k].y};
+            const LutSpec luts[2] = {lr, ls};
+            uint8_t* outs0[2] = {ref_identity ? nullptr : at(lay.refn[k]),
+                                 src_identity ? nullptr : at(lay.src_lv[0])};
+            uint8_t* const* lvs[2] = {rl, sl};
+            launch_pyramid2(ins, w, h, L, luts, outs0, lvs, 2, s);
+        }
+        // ---- a3..a7 from the coarsest level to level 0
+        launch_set_identity(Hs + 9 * L, s);
+        for (int l = L - 1; l >= 0; l--) {
+            const int lw = w >> l, lh = h >> l;
+            const uint8_t* rl = l == 0 ? ref0 : at(lay.ref_lv[l]);
+            const uint8_t* sl = l == 0 ? src0 : at(lay.src_lv[l]);
+            const SearchGeom g = make_geom(lw, lh, p);
+            const int n = g.ntx * g.nty;
+            launch_local_search(rl, sl, Hs + 9 * (l + 1), g, corner, match, cost, valid, s);
+            cudaMemsetAsync(mask, 0, (size_t)(n / 32 + 1) * 4, s);
+            launch_weed(corner, match, valid, n, lw, lh, p->weed_eps, p->weed_delta_min,
+                        p->weed_delta_div, p->weed_seed + (uint64_t)l, 0, p->weed_iters, mask,
+                        wws, s);
+            launch_fit(corner, match, mask, n, lw, lh, Hs + 9 * (l + 1), Hs + 9 * l, fit_st + l, s);
+        }
+        // ---- a8: dense flow guided by the normalized reference
+        const double* Hw = Hs;
+        if (p->propagate_full) {
+            launch_set_identity(Hs + 9 * (kMaxLevels + 1), s);
+            Hw = Hs + 9 * (kMaxLevels + 1);
+        }
+        FlowCorners fc{corner, match, mask, Hs, w / p->tile, h / p->tile, p->tile,
+                       p->propagate_full};
+        launch_flow(ref0, w, h, fc, p->sigma_s, p->sigma_r, p->dt_iters, p->flow_eps, fu, fv,
+                    at(lay.flow), s);
+        // ---- a9: warp the source frame
+        float* wy = reinterpret_cast<float*>(at(lay.wy[k]));
+        float* wu = reinterpret_cast<float*>(at(lay.wu[k]));
+        float* wv = reinterpret_cast<float*>(at(lay.wv[k]));
+        launch_warp(srcs[k].y, chroma ? srcs[k].u : nullptr, chroma ? srcs[k].v : nullptr, w, h,
+                    Hw, fu, fv, wy, chroma ? wu : nullptr, chroma ? wv : nullptr, s);
+        if (diag) {
+            note_launch();
+            k_diag<<<1, 256, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L, diag + k);
+        }
+        md[k].y = wy;
+        md[k].u = chroma ? wu : nullptr;
+        md[k].v = chroma ? wv : nullptr;
+        md[k].ref_n = ref0;
+        md[k].lut = p->norm_mode == HDRREG_NORM_HISTEQ ? luts_k + 256 : nullptr;
+        md[k].inv_ratio = (float)((double)ratio_den[k] / (double)ratio_num[k]);
+        md[k].gain = gain;
+        md[k].mode = p->norm_mode;
+        if ((st = launch_status("register_merge(register)"))) return st;
+    }
+    // ---- a10 + a11
+    launch_merge(ref->y, chroma ? ref->u : nullptr, chroma ? ref->v : nullptr, w, h, nsrc, md,
+                 p->ssim_sigma, p->we_sigma, out->y, chroma ? out->u : nullptr,
+                 chroma ? out->v : nullptr, nullptr, s);
+    return launch_status("register_merge(merge)");
+}
+
+}  // extern "C"

@@ -1,0 +1,309 @@
+// Rows a6-a7: the union-of-inliers weeding filter (Sec. 2.3, Eq. 4) and the
+// least-squares level homography (Sec. 2.2).
+//
+// Weeding: one warp per iteration. Lane 0 draws the 4 samples from the
+// counter-based stream (so iterations are independent and the union over any
+// split of the iteration range equals one run, Sec. 2.3) and solves the 4-point
+// system; all lanes test the valid matches with the division-free FP64
+// predicate (bit-identical to the oracle's written order) and accumulate the
+// count with ballots; accepted iterations OR their inlier bits into the mask.
+// Fit: one CTA reduces the exact integer normal equations (int128) and one
+// thread solves the 8x8 system in the prescribed FP64 order.
+#include "hdrreg_internal.cuh"
+
+namespace hdrreg {
+
+size_t weed_ws_bytes(int n)
+{
+    const size_t nn = n > 0 ? (size_t)n : 1;
+    return align_up(nn * 4, 256) + 256 + align_up(nn * 32, 256);
+}
+
+WeedWs weed_ws_carve(void* base, int n)
+{
+    const size_t nn = n > 0 ? (size_t)n : 1;
+    uint8_t* p = static_cast<uint8_t*>(base);
+    WeedWs w;
+    w.list = reinterpret_cast<int32_t*>(p);
+    p += align_up(nn * 4, 256);
+    w.count = reinterpret_cast<int32_t*>(p);
+    p += 256;
+    w.coords = reinterpret_cast<double*>(p);
+    return w;
+}
+
+// Order-preserving compaction of valid tiles + per-match FP64 coordinates.
+__global__ void __launch_bounds__(1024) k_weed_compact(const int32_t* __restrict__ corner_xy,
+                                                       const int32_t* __restrict__ match_xy,
+                                                       const uint8_t* __restrict__ valid, int n,
+                                                       int w, int h, WeedWs ws)
+{
+    __shared__ int warp_cnt[32];
+    __shared__ int base_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) base_s = 0;
+    __syncthreads();
+    const double W = (double)w;
+    for (int start = 0; start < n; start += 1024) {
+        const int t = start + tid;
+        const bool f = t < n && valid[t];
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) warp_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = base_s;
+        for (int k = 0; k < warp; k++) off += warp_cnt[k];
+        off += __popc(bal & ((1u << lane) - 1u));
+        if (f) {
+            ws.list[off] = t;
+            ws.coords[4 * off + 0] = norm_coord(corner_xy[2 * t], w, W);
+            ws.coords[4 * off + 1] = norm_coord(corner_xy[2 * t + 1], h, W);
+            ws.coords[4 * off + 2] = (double)(2 * match_xy[2 * t] - (w - 1));
+            ws.coords[4 * off + 3] = (double)(2 * match_xy[2 * t + 1] - (h - 1));
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int tot = 0;
+            for (int k = 0; k < 32; k++) tot += warp_cnt[k];
+            base_s += tot;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *ws.count = base_s;
+}
+
+constexpr int kWeedWarps = 4;
+
+__global__ void __launch_bounds__(kWeedWarps * 32) k_weed_iters(
+    const int32_t* __restrict__ corner_xy, const int32_t* __restrict__ match_xy, int n, int w,
+    int h, double eps, int delta_min, int delta_div, uint64_t seed, int it0, int it1,
+    uint32_t* __restrict__ mask, WeedWs ws)
+{
+    extern __shared__ uint32_t bal_words[];  // [kWeedWarps][ceil(n/32)]
+    __shared__ double Hs[kWeedWarps][9];
+    __shared__ int ok_s[kWeedWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long it = (long long)it0 + (long long)blockIdx.x * kWeedWarps + warp;
+    if (it >= it1) return;
+    const int nv = *ws.count;
+    if (nv < 4) return;
+    const double W = (double)w;
+    if (lane == 0) {
+        int pick[4];
+        int ok = weed_sample(seed, it, nv, pick);
+        if (ok) {
+            double A[8][8], b[8], x[8];
+            for (int r = 0; r < 8; r++)
+                for (int c = 0; c < 8; c++) A[r][c] = 0.0;
+            for (int k = 0; k < 4; k++) {
+                const double* cc = ws.coords + 4 * pick[k];
+                const int t = ws.list[pick[k]];
+                const double xx = cc[0], yy = cc[1];
+                const double u = norm_coord(match_xy[2 * t], w, W);
+                const double v = norm_coord(match_xy[2 * t + 1], h, W);
+                A[2 * k][0] = xx;
+                A[2 * k][1] = yy;
+                A[2 * k][2] = 1.0;
+                A[2 * k][6] = -dmul(xx, u);
+                A[2 * k][7] = -dmul(yy, u);
+                A[2 * k + 1][3] = xx;
+                A[2 * k + 1][4] = yy;
+                A[2 * k + 1][5] = 1.0;
+                A[2 * k + 1][6] = -dmul(xx, v);
+                A[2 * k + 1][7] = -dmul(yy, v);
+                b[2 * k] = u;
+                b[2 * k + 1] = v;
+            }
+            ok = solve8(A, b, x, 1e-12) == 0;
+            if (ok) {
+                for (int k = 0; k < 8; k++) Hs[warp][k] = x[k];
+                Hs[warp][8] = 1.0;
+            }
+        }
+        ok_s[warp] = ok;
+    }
+    __syncwarp();
+    if (!ok_s[warp]) return;
+    double Hr[9];
+    for (int k = 0; k < 9; k++) Hr[k] = Hs[warp][k];
+    const double eps2x = dmul(2.0, eps);
+    const int nw = (nv + 31) / 32;
+    uint32_t* bw = bal_words + warp * ((n + 31) / 32);
+    int cnt = 0;
+    for (int j = 0; j < nw; j++) {
+        const int k = 32 * j + lane;
+        bool in = false;
+        if (k < nv) {
+            const double* cc = ws.coords + 4 * k;
+            in = is_inlier(Hr, cc[0], cc[1], cc[2], cc[3], W, eps2x);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, in);
+        cnt += __popc(b);
+        if (lane == 0) bw[j] = b;
+    }
+    __syncwarp();
+    int delta = (nv + delta_div - 1) / delta_div;
+    if (delta < delta_min) delta = delta_min;
+    if (cnt <= delta) return;
+    for (int j = lane; j < nw; j += 32) {
+        uint32_t b = bw[j];
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            const int t = ws.list[32 * j + bit];
+            atomicOr(&mask[t >> 5], 1u << (t & 31));
+        }
+    }
+}
+
+void launch_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* valid, int n,
+                 int w, int h, double eps, int delta_min, int delta_div, uint64_t seed, int it0,
+                 int it1, uint32_t* mask, const WeedWs& ws, cudaStream_t s)
+{
+    if (n <= 0) return;
+    note_launch();
+    k_weed_compact<<<1, 1024, 0, s>>>(corner_xy, match_xy, valid, n, w, h, ws);
+    if (it1 <= it0) return;
+    const int iters = it1 - it0;
+    const int blocks = (iters + kWeedWarps - 1) / kWeedWarps;
+    const size_t smem = (size_t)kWeedWarps * ((n + 31) / 32) * 4;
+    if (smem > 48 * 1024)
+        ensure_smem((const void*)k_weed_iters, smem);
+    note_launch();
+    k_weed_iters<<<blocks, kWeedWarps * 32, smem, s>>>(corner_xy, match_xy, n, w, h, eps,
+                                                        delta_min, delta_div, seed, it0, it1,
+                                                        mask, ws);
+}
+
+// ---------------------------------------------------------------- level fit
+// The 44 distinct entries of A^T A and A^T b of the DLT rows
+//   a1 = [x, y, 1, 0, 0, 0, -x u, -y u], b1 = u ;  a2 = [0, 0, 0, x, y, 1, -x v, -y v], b2 = v
+// in centred integer coordinates (x = 2 p_x - (w-1), u = 2 q_x - (w-1), ...)
+// reduce to 23 distinct sums, accumulated exactly in __int128.
+constexpr int kFitSums = 23;
+
+__device__ __forceinline__ void fit_terms(long long x, long long y, long long u, long long v,
+                                          long long (&s)[kFitSums])
+{
+    const long long x2 = x * x, xy = x * y, y2 = y * y, r2 = u * u + v * v;
+    s[0] = x2;          s[1] = xy;          s[2] = x;           s[3] = y2;
+    s[4] = y;           s[5] = 1;           s[6] = x2 * u;      s[7] = xy * u;
+    s[8] = y2 * u;      s[9] = x * u;       s[10] = y * u;      s[11] = x2 * v;
+    s[12] = xy * v;     s[13] = y2 * v;     s[14] = x * v;      s[15] = y * v;
+    s[16] = x2 * r2;    s[17] = xy * r2;    s[18] = y2 * r2;    s[19] = u;
+    s[20] = v;          s[21] = x * r2;     s[22] = y * r2;
+}
+
+__device__ __forceinline__ double i128_to_double(__int128 s)
+{
+    const long long hi = (long long)(s >> 32);
+    const unsigned long long lo = (unsigned long long)(s & (__int128)0xFFFFFFFFu);
+    return dadd(dmul((double)hi, 4294967296.0), (double)lo);
+}
+
+__global__ void __launch_bounds__(256) k_fit(const int32_t* __restrict__ corner_xy,
+                                             const int32_t* __restrict__ match_xy,
+                                             const uint32_t* __restrict__ mask, int n, int w,
+                                             int h, const double* H_prev, double* H_out,
+                                             int32_t* status)
+{
+    __shared__ __int128 part[8][kFitSums];
+    __shared__ int cnt_s[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __int128 acc[kFitSums];
+    for (int k = 0; k < kFitSums; k++) acc[k] = 0;
+    int cnt = 0;
+    for (int t = tid; t < n; t += 256) {
+        if (!((mask[t >> 5] >> (t & 31)) & 1u)) continue;
+        long long s[kFitSums];
+        fit_terms(2LL * corner_xy[2 * t] - (w - 1), 2LL * corner_xy[2 * t + 1] - (h - 1),
+                  2LL * match_xy[2 * t] - (w - 1), 2LL * match_xy[2 * t + 1] - (h - 1), s);
+        for (int k = 0; k < kFitSums; k++) acc[k] += (__int128)s[k];
+        cnt++;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        for (int k = 0; k < kFitSums; k++) {
+            const unsigned long long lo = (unsigned long long)acc[k];
+            const long long hi = (long long)(acc[k] >> 64);
+            const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            const long long hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            acc[k] += ((__int128)hi2 << 64) | (__int128)lo2;
+        }
+    }
+    if (lane == 0) {
+        cnt_s[warp] = cnt;
+        for (int k = 0; k < kFitSums; k++) part[warp][k] = acc[k];
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    double Hp[9];
+    for (int k = 0; k < 9; k++) Hp[k] = H_prev[k];
+    int total = 0;
+    __int128 S[kFitSums];
+    for (int k = 0; k < kFitSums; k++) S[k] = 0;
+    for (int wv = 0; wv < 8; wv++) {
+        total += cnt_s[wv];
+        for (int k = 0; k < kFitSums; k++) S[k] += part[wv][k];
+    }
+    int st = 0;
+    if (total < 4) {
+        st = 1;
+    } else {
+        // assemble A^T A (8x8) and A^T b from the distinct sums
+        const __int128 Sx2 = S[0], Sxy = S[1], Sx = S[2], Sy2 = S[3], Sy = S[4], S1 = S[5];
+        const __int128 Sx2u = S[6], Sxyu = S[7], Sy2u = S[8], Sxu = S[9], Syu = S[10];
+        const __int128 Sx2v = S[11], Sxyv = S[12], Sy2v = S[13], Sxv = S[14], Syv = S[15];
+        const __int128 Sx2r = S[16], Sxyr = S[17], Sy2r = S[18], Su = S[19], Sv = S[20];
+        const __int128 Sxr = S[21], Syr = S[22];
+        __int128 M[8][8];
+        const __int128 z = 0;
+        const __int128 rows[8][8] = {
+            {Sx2, Sxy, Sx, z, z, z, -Sx2u, -Sxyu},
+            {Sxy, Sy2, Sy, z, z, z, -Sxyu, -Sy2u},
+            {Sx, Sy, S1, z, z, z, -Sxu, -Syu},
+            {z, z, z, Sx2, Sxy, Sx, -Sx2v, -Sxyv},
+            {z, z, z, Sxy, Sy2, Sy, -Sxyv, -Sy2v},
+            {z, z, z, Sx, Sy, S1, -Sxv, -Syv},
+            {-Sx2u, -Sxyu, -Sxu, -Sx2v, -Sxyv, -Sxv, Sx2r, Sxyr},
+            {-Sxyu, -Sy2u, -Syu, -Sxyv, -Sy2v, -Syv, Sxyr, Sy2r}};
+        for (int r = 0; r < 8; r++)
+            for (int c = 0; c < 8; c++) M[r][c] = rows[r][c];
+        const __int128 rhs[8] = {Sxu, Syu, Su, Sxv, Syv, Sv, -Sxr, -Syr};
+        const int e[8] = {1, 1, 0, 1, 1, 0, 2, 2};
+        double Wp[6];
+        Wp[0] = 1.0;
+        for (int k = 1; k < 6; k++) Wp[k] = dmul(Wp[k - 1], (double)w);
+        double A[8][8], b[8], x[8];
+        for (int r = 0; r < 8; r++) {
+            for (int c = 0; c < 8; c++) A[r][c] = ddiv(i128_to_double(M[r][c]), Wp[e[r] + e[c]]);
+            b[r] = ddiv(i128_to_double(rhs[r]), Wp[e[r] + 1]);
+        }
+        if (solve8(A, b, x, 1e-12)) {
+            st = 2;
+        } else {
+            for (int k = 0; k < 8; k++) H_out[k] = x[k];
+            H_out[8] = 1.0;
+        }
+    }
+    if (st) {
+        for (int k = 0; k < 9; k++) H_out[k] = Hp[k];
+    }
+    if (status) *status = st;
+}
+
+void launch_fit(const int32_t* corner_xy, const int32_t* match_xy, const uint32_t* mask, int n,
+                int w, int h, const double* H_prev, double* H_out, int32_t* status,
+                cudaStream_t s)
+{
+    note_launch();
+    k_fit<<<1, 256, 0, s>>>(corner_xy, match_xy, mask, n, w, h, H_prev, H_out, status);
+}
+
+__global__ void k_set_identity(double* H)
+{
+    if (threadIdx.x < 9) H[threadIdx.x] = (threadIdx.x % 4 == 0) ? 1.0 : 0.0;
+}
+
+void launch_set_identity(double* H, cudaStream_t s) { k_set_identity<<<1, 32, 0, s>>>(H); }
+
+}  // namespace hdrreg

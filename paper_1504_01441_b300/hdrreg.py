@@ -1,0 +1,361 @@
+"""Python binding of the hdrreg C ABI (include/hdrreg.h).
+
+Argument marshalling only: every step runs in the CUDA kernels of
+libhdrreg.so. PyTorch provides device memory and the current stream. If the
+library is missing or cannot be loaded this module raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, List, Optional, Sequence, Tuple
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhdrreg.so")
+
+NORM_RATIO = 0
+NORM_HISTEQ = 1
+
+STATUS = {0: "OK", 1: "E_INVALID_ARG", 2: "E_CUDA", 3: "E_DEGENERATE", 4: "E_TIMEOUT",
+          5: "E_UNSUPPORTED", 6: "E_WORKSPACE"}
+
+EXPORTS = [
+    "hdrreg_params_default", "hdrreg_last_error", "hdrreg_version", "hdrreg_launch_count",
+    "hdrreg_num_levels",
+    "hdrreg_validate_params", "hdrreg_num_tiles", "hdrreg_normalize_workspace_size",
+    "hdrreg_normalize_exposure", "hdrreg_pyramid_bytes", "hdrreg_build_pyramid",
+    "hdrreg_local_search", "hdrreg_weed_workspace_size", "hdrreg_weed", "hdrreg_fit_homography",
+    "hdrreg_flow_workspace_size", "hdrreg_flow_upsample", "hdrreg_warp", "hdrreg_merge",
+    "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
+]
+
+
+class HdrregError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hdrreg {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("tile", C.c_int), ("radius", C.c_int), ("patch_half", C.c_int),
+        ("levels_max", C.c_int), ("min_level_size", C.c_int), ("grid_half", C.c_int),
+        ("quad", C.c_int), ("corner_thresh", C.c_int), ("weed_iters", C.c_int),
+        ("weed_delta_min", C.c_int), ("weed_delta_div", C.c_int), ("norm_mode", C.c_int),
+        ("dt_iters", C.c_int), ("ssim_radius", C.c_int), ("propagate_full", C.c_int),
+        ("reserved0", C.c_int),
+        ("weed_eps", C.c_double), ("sigma_s", C.c_double), ("sigma_r", C.c_double),
+        ("ssim_sigma", C.c_double), ("we_sigma", C.c_double), ("flow_eps", C.c_double),
+        ("weed_seed", C.c_uint64),
+    ]
+
+    def as_dict(self) -> Dict:
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved0"}
+
+
+class Frame(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("u", C.c_void_p), ("v", C.c_void_p)]
+
+
+class PlanesF32(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("u", C.c_void_p), ("v", C.c_void_p)]
+
+
+class MergeSrc(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("u", C.c_void_p), ("v", C.c_void_p), ("ref_n", C.c_void_p),
+                ("src_lut", C.c_void_p), ("ratio_num", C.c_int), ("ratio_den", C.c_int)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("H0", C.c_double * 9), ("levels", C.c_int32), ("tiles", C.c_int32),
+                ("valid", C.c_int32), ("kept", C.c_int32), ("fit_status", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libhdrreg.so (built in-tree by build.py); raise if it is not there."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"hdrreg CUDA library not built: {LIB_PATH} (run build.py)")
+        L = C.CDLL(LIB_PATH)
+        sz = C.c_size_t
+        vp = C.c_void_p
+        i = C.c_int
+        L.hdrreg_last_error.restype = C.c_char_p
+        L.hdrreg_version.restype = C.c_char_p
+        L.hdrreg_launch_count.restype = C.c_ulonglong
+        L.hdrreg_params_default.argtypes = [C.POINTER(Params)]
+        L.hdrreg_validate_params.argtypes = [C.POINTER(Params)]
+        L.hdrreg_num_levels.argtypes = [i, i, C.POINTER(Params)]
+        L.hdrreg_num_tiles.argtypes = [i, i, i]
+        L.hdrreg_normalize_workspace_size.restype = sz
+        L.hdrreg_normalize_workspace_size.argtypes = [i]
+        L.hdrreg_normalize_exposure.argtypes = [vp, vp, i, i, i, i, i, vp, vp, vp, vp, sz, vp]
+        L.hdrreg_pyramid_bytes.restype = sz
+        L.hdrreg_pyramid_bytes.argtypes = [i, i, i]
+        L.hdrreg_build_pyramid.argtypes = [vp, i, i, i, vp, vp]
+        L.hdrreg_local_search.argtypes = [vp, vp, i, i, vp, C.POINTER(Params), vp, vp, vp, vp, vp]
+        L.hdrreg_weed_workspace_size.restype = sz
+        L.hdrreg_weed_workspace_size.argtypes = [i]
+        L.hdrreg_weed.argtypes = [vp, vp, vp, i, i, i, C.POINTER(Params), C.c_uint64, i, i, vp,
+                                  vp, sz, vp]
+        L.hdrreg_fit_homography.argtypes = [vp, vp, vp, i, i, i, vp, vp, vp, vp]
+        L.hdrreg_flow_workspace_size.restype = sz
+        L.hdrreg_flow_workspace_size.argtypes = [i, i]
+        L.hdrreg_flow_upsample.argtypes = [vp, i, i, vp, vp, vp, i, vp, C.POINTER(Params), vp,
+                                           vp, vp, sz, vp]
+        L.hdrreg_warp.argtypes = [C.POINTER(Frame), i, i, vp, vp, vp, C.POINTER(PlanesF32), vp]
+        L.hdrreg_merge.argtypes = [C.POINTER(Frame), i, i, i, C.POINTER(MergeSrc),
+                                   C.POINTER(Params), C.POINTER(PlanesF32), vp, vp]
+        L.hdrreg_register_merge_workspace_size.restype = sz
+        L.hdrreg_register_merge_workspace_size.argtypes = [i, i, i, C.POINTER(Params)]
+        L.hdrreg_register_merge.argtypes = [C.POINTER(Frame), i, i, i, C.POINTER(Frame),
+                                            C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                            C.POINTER(Params), vp, sz, C.POINTER(PlanesF32),
+                                            vp, vp]
+        for name in EXPORTS:
+            if not hasattr(L, name):
+                raise ImportError(f"libhdrreg.so does not export {name}")
+        _lib = L
+    return _lib
+
+
+def version() -> str:
+    return lib().hdrreg_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels enqueued by the library so far in this process."""
+    return int(lib().hdrreg_launch_count())
+
+
+def params(**over) -> Params:
+    """Library defaults (the paper's values where it gives them), with overrides."""
+    p = Params()
+    lib().hdrreg_params_default(C.byref(p))
+    for k, v in over.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def params_from_dict(d: Dict) -> Params:
+    return params(**{k: v for k, v in d.items() if k != "pad_"})
+
+
+def _check(st: int):
+    if st != 0:
+        raise HdrregError(st, lib().hdrreg_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("hdrreg expects CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("hdrreg expects contiguous tensors")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _empty(shape, dtype, like):
+    import torch
+    return torch.empty(shape, dtype=dtype, device=like.device)
+
+
+def num_levels(w: int, h: int, p: Params) -> int:
+    return lib().hdrreg_num_levels(w, h, C.byref(p))
+
+
+def num_tiles(w: int, h: int, tile: int) -> int:
+    return lib().hdrreg_num_tiles(w, h, tile)
+
+
+# ---------------------------------------------------------------- a1
+def normalize_exposure(ref_y, src_y, mode=NORM_RATIO, ratio=(1, 1), stream=None):
+    """-> (ref_n, src_n, luts[2, 256])"""
+    import torch
+    h, w = ref_y.shape
+    ref_n, src_n = torch.empty_like(ref_y), torch.empty_like(src_y)
+    luts = _empty((2, 256), torch.uint8, ref_y)
+    ws_n = lib().hdrreg_normalize_workspace_size(mode)
+    ws = _empty((max(ws_n, 1),), torch.uint8, ref_y)
+    _check(lib().hdrreg_normalize_exposure(_ptr(ref_y), _ptr(src_y), w, h, mode, ratio[0],
+                                           ratio[1], _ptr(ref_n), _ptr(src_n), _ptr(luts),
+                                           _ptr(ws), ws_n, _stream(stream)))
+    return ref_n, src_n, luts
+
+
+# ---------------------------------------------------------------- a2
+def build_pyramid(level0, levels: int, stream=None) -> List:
+    import torch
+    h, w = level0.shape
+    nb = lib().hdrreg_pyramid_bytes(w, h, levels)
+    buf = _empty((max(nb, 1),), torch.uint8, level0)
+    _check(lib().hdrreg_build_pyramid(_ptr(level0), w, h, levels, _ptr(buf), _stream(stream)))
+    out, off = [level0], 0
+    for l in range(1, levels):
+        lw, lh = w >> l, h >> l
+        out.append(buf[off:off + lw * lh].view(lh, lw))
+        off += lw * lh
+    return out
+
+
+# ---------------------------------------------------------------- a3-a5
+def local_search(ref_n, src_n, H, p: Params, stream=None):
+    """-> corner_xy [n,2] int32, match_xy [n,2] int32, cost [n] int32 (uint32 bits), valid [n] u8"""
+    import torch
+    h, w = ref_n.shape
+    n = num_tiles(w, h, p.tile)
+    corner = _empty((max(n, 1), 2), torch.int32, ref_n)
+    match = _empty((max(n, 1), 2), torch.int32, ref_n)
+    cost = _empty((max(n, 1),), torch.int32, ref_n)
+    valid = _empty((max(n, 1),), torch.uint8, ref_n)
+    _check(lib().hdrreg_local_search(_ptr(ref_n), _ptr(src_n), w, h, _ptr(H), C.byref(p),
+                                     _ptr(corner), _ptr(match), _ptr(cost), _ptr(valid),
+                                     _stream(stream)))
+    return corner[:n], match[:n], cost[:n], valid[:n]
+
+
+# ---------------------------------------------------------------- a6
+def weed(corner_xy, match_xy, valid, w: int, h: int, p: Params, seed: int, iter_begin=0,
+         iter_end=None, mask=None, stream=None):
+    """OR the inliers of iterations [iter_begin, iter_end) into mask (int32 words); -> mask"""
+    import torch
+    n = valid.numel()
+    if iter_end is None:
+        iter_end = p.weed_iters
+    if mask is None:
+        mask = torch.zeros((n // 32 + 1,), dtype=torch.int32, device=valid.device)
+    ws_n = lib().hdrreg_weed_workspace_size(n)
+    ws = _empty((ws_n,), torch.uint8, valid)
+    _check(lib().hdrreg_weed(_ptr(corner_xy), _ptr(match_xy), _ptr(valid), n, w, h, C.byref(p),
+                             C.c_uint64(seed), iter_begin, iter_end, _ptr(mask), _ptr(ws), ws_n,
+                             _stream(stream)))
+    return mask
+
+
+# ---------------------------------------------------------------- a7
+def fit_homography(corner_xy, match_xy, mask, w: int, h: int, H_prev, stream=None):
+    """-> (H [9] float64 device, status [1] int32 device)"""
+    import torch
+    n = corner_xy.shape[0]
+    H = _empty((9,), torch.float64, H_prev)
+    st = _empty((1,), torch.int32, H_prev)
+    _check(lib().hdrreg_fit_homography(_ptr(corner_xy), _ptr(match_xy), _ptr(mask), n, w, h,
+                                       _ptr(H_prev), _ptr(H), _ptr(st), _stream(stream)))
+    return H, st
+
+
+# ---------------------------------------------------------------- a8
+def flow_upsample(guide_n, corner_xy, match_xy, mask, H, p: Params, stream=None):
+    import torch
+    h, w = guide_n.shape
+    n = corner_xy.shape[0]
+    fu = _empty((h, w), torch.float32, guide_n)
+    fv = _empty((h, w), torch.float32, guide_n)
+    ws_n = lib().hdrreg_flow_workspace_size(w, h)
+    ws = _empty((ws_n,), torch.uint8, guide_n)
+    _check(lib().hdrreg_flow_upsample(_ptr(guide_n), w, h, _ptr(corner_xy), _ptr(match_xy),
+                                      _ptr(mask), n, _ptr(H), C.byref(p), _ptr(fu), _ptr(fv),
+                                      _ptr(ws), ws_n, _stream(stream)))
+    return fu, fv
+
+
+# ---------------------------------------------------------------- a9
+def warp(src_y, src_u, src_v, H, flow_u, flow_v, stream=None):
+    import torch
+    h, w = src_y.shape
+    oy = _empty((h, w), torch.float32, src_y)
+    chroma = src_u is not None
+    ou = _empty((h // 2, w // 2), torch.float32, src_y) if chroma else None
+    ov = _empty((h // 2, w // 2), torch.float32, src_y) if chroma else None
+    f = Frame(_ptr(src_y), _ptr(src_u), _ptr(src_v))
+    o = PlanesF32(_ptr(oy), _ptr(ou), _ptr(ov))
+    _check(lib().hdrreg_warp(C.byref(f), w, h, _ptr(H), _ptr(flow_u), _ptr(flow_v), C.byref(o),
+                             _stream(stream)))
+    return oy, ou, ov
+
+
+# ---------------------------------------------------------------- a10-a11
+def merge(ref_y, ref_u, ref_v, sources: Sequence[Dict], p: Params, want_q=False, stream=None):
+    """sources: dicts with y, u, v (warped FP32), ref_n (u8), ratio (num, den), lut (HISTEQ)."""
+    import torch
+    h, w = ref_y.shape
+    chroma = ref_u is not None
+    k = len(sources)
+    arr = (MergeSrc * k)()
+    for i, s in enumerate(sources):
+        arr[i] = MergeSrc(_ptr(s["y"]), _ptr(s.get("u")), _ptr(s.get("v")), _ptr(s["ref_n"]),
+                          _ptr(s.get("lut")), s["ratio"][0], s["ratio"][1])
+    oy = _empty((h, w), torch.float32, ref_y)
+    ou = _empty((h // 2, w // 2), torch.float32, ref_y) if chroma else None
+    ov = _empty((h // 2, w // 2), torch.float32, ref_y) if chroma else None
+    q = _empty((k, h, w), torch.float32, ref_y) if want_q else None
+    f = Frame(_ptr(ref_y), _ptr(ref_u), _ptr(ref_v))
+    o = PlanesF32(_ptr(oy), _ptr(ou), _ptr(ov))
+    _check(lib().hdrreg_merge(C.byref(f), w, h, k, arr, C.byref(p), C.byref(o), _ptr(q),
+                              _stream(stream)))
+    return oy, ou, ov, q
+
+
+# ---------------------------------------------------------------- fused
+def register_merge_workspace_size(w: int, h: int, nsrc: int, p: Params) -> int:
+    return lib().hdrreg_register_merge_workspace_size(w, h, nsrc, C.byref(p))
+
+
+class RegisterMerge:
+    """Reusable fused call for one stack shape: owns the workspace and output planes."""
+
+    def __init__(self, w: int, h: int, nsrc: int, p: Params, chroma: bool, device="cuda"):
+        import torch
+        self.w, self.h, self.nsrc, self.p, self.chroma = w, h, nsrc, p, chroma
+        n = register_merge_workspace_size(w, h, nsrc, p)
+        if n == 0:
+            raise HdrregError(1, "bad shape or parameters for register_merge")
+        self.ws = torch.empty((n,), dtype=torch.uint8, device=device)
+        self.out_y = torch.empty((h, w), dtype=torch.float32, device=device)
+        self.out_u = torch.empty((h // 2, w // 2), dtype=torch.float32, device=device) if chroma else None
+        self.out_v = torch.empty((h // 2, w // 2), dtype=torch.float32, device=device) if chroma else None
+        self.diag = torch.zeros((nsrc, C.sizeof(Diag)), dtype=torch.uint8, device=device)
+
+    def __call__(self, ref, srcs, ratios, stream=None):
+        """ref, srcs[k]: (y, u, v) uint8 CUDA tensors (u = v = None for luma-only)."""
+        k = len(srcs)
+        if k != self.nsrc:
+            raise ValueError("number of sources differs from the one this call was built for")
+        fr = Frame(_ptr(ref[0]), _ptr(ref[1]) if self.chroma else None,
+                   _ptr(ref[2]) if self.chroma else None)
+        fs = (Frame * k)(*[Frame(_ptr(s[0]), _ptr(s[1]) if self.chroma else None,
+                                 _ptr(s[2]) if self.chroma else None) for s in srcs])
+        num = (C.c_int * k)(*[r[0] for r in ratios])
+        den = (C.c_int * k)(*[r[1] for r in ratios])
+        o = PlanesF32(_ptr(self.out_y), _ptr(self.out_u), _ptr(self.out_v))
+        _check(lib().hdrreg_register_merge(C.byref(fr), self.w, self.h, k, fs, num, den,
+                                           C.byref(self.p), _ptr(self.ws), self.ws.numel(),
+                                           C.byref(o), _ptr(self.diag), _stream(stream)))
+        return self.out_y, self.out_u, self.out_v
+
+    def diagnostics(self) -> List[Diag]:
+        raw = self.diag.cpu().numpy().tobytes()
+        n = C.sizeof(Diag)
+        return [Diag.from_buffer_copy(raw[i * n:(i + 1) * n]) for i in range(self.nsrc)]
+
+
+def register_merge(ref, srcs, ratios, p: Params, stream=None):
+    h, w = ref[0].shape
+    rm = RegisterMerge(w, h, len(srcs), p, ref[1] is not None, device=ref[0].device)
+    out = rm(ref, srcs, ratios, stream)
+    return out, rm

@@ -1,0 +1,108 @@
+"""The C-ABI library loads and exports everything include/hdrreg.h declares; host
+logic (defaults, validation, sizes) works without a GPU. No call here reaches a
+kernel launch: every invalid argument is rejected on the host first.
+"""
+import ctypes as C
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hd():
+    from paper_1504_01441_b300 import build, hdrreg
+    build.build()
+    return hdrreg
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "hdrreg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hdrreg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(hd):
+    lib = hd.lib()
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(hd.EXPORTS)
+
+
+def test_version_and_defaults_follow_the_paper(hd):
+    assert "sm_103a" in hd.version()
+    p = hd.params()
+    c = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    assert p.levels_max == c["levels_max"] and p.min_level_size == c["min_level_size_px"]
+    assert 2 * p.patch_half + 1 == c["patch_side"] and p.radius == c["max_search_radius"]
+    assert p.sigma_s == c["sigma_s"]
+    assert hd.lib().hdrreg_validate_params(C.byref(p)) == 0
+
+
+def test_param_fields_match_the_workload_parameter_sets(hd):
+    from paper_1504_01441_b300 import synth
+    d = synth.method_params(32, 6)
+    p = hd.params_from_dict(d)
+    assert p.as_dict() == {k: v for k, v in d.items()}
+
+
+@pytest.mark.parametrize("field,value", [("tile", 7), ("tile", 130), ("radius", 0), ("radius", 16),
+                                         ("patch_half", 0), ("levels_max", 9), ("grid_half", 9),
+                                         ("quad", 0), ("corner_thresh", -1), ("dt_iters", 0),
+                                         ("ssim_radius", 4), ("norm_mode", 2), ("sigma_r", 0.0),
+                                         ("weed_delta_div", 0), ("weed_iters", -1)])
+def test_invalid_params_rejected(hd, field, value):
+    p = hd.params(**{field: value})
+    assert hd.lib().hdrreg_validate_params(C.byref(p)) == 1
+    assert hd.lib().hdrreg_last_error()
+
+
+def test_grid_must_stay_inside_the_tile(hd):
+    # T=16 -> step 1, K=8 reaches the tile border: rejected; K=7 fine
+    assert hd.lib().hdrreg_validate_params(C.byref(hd.params(tile=16, grid_half=8))) == 1
+    assert hd.lib().hdrreg_validate_params(C.byref(hd.params(tile=16, grid_half=7))) == 0
+
+
+@pytest.mark.parametrize("w,h,L", [(2592, 1944, 5), (640, 480, 3), (199, 400, 1), (4000, 3000, 5)])
+def test_levels_match_oracle_rule(hd, w, h, L):
+    assert hd.num_levels(w, h, hd.params()) == L
+
+
+def test_sizes(hd):
+    lib = hd.lib()
+    assert hd.num_tiles(2592, 1944, 32) == 81 * 60
+    assert lib.hdrreg_pyramid_bytes(2592, 1944, 5) == sum((2592 >> l) * (1944 >> l) for l in range(1, 5))
+    assert lib.hdrreg_flow_workspace_size(2592, 1944) >= 3 * 2592 * 1944 * 4
+    assert lib.hdrreg_flow_workspace_size(0, 10) == 0
+    p = hd.params(tile=32, radius=6)
+    ws = hd.register_merge_workspace_size(2592, 1944, 1, p)
+    assert ws > 5 * 2592 * 1944 * 4
+    assert hd.register_merge_workspace_size(2592, 1944, 5, p) == 0      # too many sources
+    assert lib.hdrreg_normalize_workspace_size(0) == 0 and lib.hdrreg_normalize_workspace_size(1) > 0
+
+
+def test_null_and_size_errors_return_before_any_launch(hd):
+    lib = hd.lib()
+    p = hd.params()
+    assert lib.hdrreg_local_search(None, None, 64, 64, None, C.byref(p), None, None, None, None,
+                                   None) == 1
+    assert lib.hdrreg_normalize_exposure(None, None, 64, 64, 0, 4, 1, None, None, None, None, 0,
+                                         None) == 1
+    f = hd.Frame(None, None, None)
+    o = hd.PlanesF32(None, None, None)
+    assert lib.hdrreg_warp(C.byref(f), 64, 64, None, None, None, C.byref(o), None) == 1
+    assert lib.hdrreg_register_merge(C.byref(f), 64, 64, 1, None, None, None, C.byref(p), None, 0,
+                                     C.byref(o), None, None) == 1
+    assert lib.hdrreg_fit_homography(None, None, None, -1, 10, 10, None, None, None, None) == 1
+    assert b"NULL" in lib.hdrreg_last_error() or b"range" in lib.hdrreg_last_error()
+
+
+def test_python_binding_refuses_cpu_tensors(hd):
+    import torch
+    with pytest.raises(ValueError):
+        hd._ptr(torch.zeros(4))

@@ -1,0 +1,366 @@
+"""GPU parity: every C-ABI step against the CPU oracle on the same seeded inputs.
+
+Integer / index / FP64-decided outputs (normalized images, pyramids, corners,
+matches, SSD costs, weeding masks, level homographies) must be bit-exact. FP32
+outputs (flow, warp, SSIM mask, merge) must satisfy the tolerance of the
+spec: relative error <= 1e-4, measured in the max norm of each output
+plane, |gpu - oracle|_inf <= 1e-4 * max(|oracle|_inf, 1).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_01441_b300 import build, hdrreg
+    build.build()
+    return hdrreg
+
+
+def cfg(tile=16, radius=4, **kw):
+    from paper_1504_01441_b300 import synth
+    return synth.method_params(tile, radius, **kw)
+
+
+def dev(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel_err(gpu, orc):
+    g = np.asarray(gpu, np.float64)
+    o = np.asarray(orc, np.float64)
+    return float(np.abs(g - o).max() / max(np.abs(o).max(), 1.0))
+
+
+def assert_rel(gpu, orc, what, rel=REL):
+    g = np.asarray(gpu, np.float64)
+    o = np.asarray(orc, np.float64)
+    d = np.abs(g - o)
+    e = rel_err(g, o)
+    idx = np.unravel_index(int(np.argmax(d)), d.shape)
+    elem = d > rel * np.maximum(np.abs(o), 1.0)
+    msg = (f"{what}: max-norm relative error {e:.3e} (limit {rel:.0e}) at {idx}: gpu {g[idx]!r} "
+           f"oracle {o[idx]!r}; elements above {rel:.0e}*max(|oracle|,1): {int(elem.sum())} "
+           f"of {d.size}")
+    print(msg)
+    assert e <= rel, msg
+    return e
+
+
+def mask_bool(words, n):
+    from oracle import mask_to_bool
+    return mask_to_bool(np.asarray(words).view(np.uint32), n)
+
+
+@pytest.fixture(scope="module")
+def vga(vga_stack):
+    return vga_stack
+
+
+@pytest.fixture(scope="module")
+def five_mp():
+    from paper_1504_01441_b300 import synth
+    return synth.make_stack(synth.FIVE_MP, synth.stack_seed(2))
+
+
+def random_img(rng, h, w):
+    base = rng.integers(0, 256, (h // 4 + 2, w // 4 + 2)).astype(np.float64)
+    img = np.kron(base, np.ones((4, 4)))[:h, :w] + rng.normal(0, 6, (h, w))
+    return np.clip(img, 0, 255).astype(np.uint8)
+
+
+# --------------------------------------------------------------------- a1
+@pytest.mark.parametrize("ratio", [(4, 1), (1, 4), (3, 2), (1, 1), (8, 1)])
+def test_normalize_ratio_bit_exact(hd, orc, ratio):
+    rng = np.random.default_rng(1)
+    ref, src = random_img(rng, 97, 131), random_img(rng, 97, 131)
+    rn, sn, luts = hd.normalize_exposure(dev(ref), dev(src), hd.NORM_RATIO, ratio)
+    orn, osn = orc.normalize_ratio(ref, src, *ratio)
+    assert np.array_equal(host(rn), orn) and np.array_equal(host(sn), osn)
+    lut = host(luts)
+    assert np.array_equal(lut[0][ref], orn) and np.array_equal(lut[1][src], osn)
+
+
+def test_normalize_histeq_bit_exact(hd, orc):
+    rng = np.random.default_rng(2)
+    ref = np.clip(rng.normal(40, 20, (123, 211)), 0, 255).astype(np.uint8)
+    src = np.clip(rng.normal(150, 40, (123, 211)), 0, 255).astype(np.uint8)
+    rn, sn, luts = hd.normalize_exposure(dev(ref), dev(src), hd.NORM_HISTEQ)
+    lr, ls = orc.histeq_lut(ref), orc.histeq_lut(src)
+    assert np.array_equal(host(luts)[0], lr) and np.array_equal(host(luts)[1], ls)
+    assert np.array_equal(host(rn), lr[ref]) and np.array_equal(host(sn), ls[src])
+
+
+# --------------------------------------------------------------------- a2
+@pytest.mark.parametrize("shape,levels", [((480, 640), 3), ((1944, 2592), 5), ((101, 333), 4),
+                                          ((7, 9), 2)])
+def test_pyramid_bit_exact(hd, orc, shape, levels):
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 256, shape).astype(np.uint8)
+    got = hd.build_pyramid(dev(img), levels)
+    want = orc.pyramid(img, levels)
+    for l in range(levels):
+        assert np.array_equal(host(got[l]), want[l]), f"level {l}"
+
+
+# --------------------------------------------------------------------- a3-a5
+def _search_case(hd, orc, ref_n, src_n, H, c):
+    p = hd.params_from_dict(c)
+    cxy, mxy, cost, valid = hd.local_search(dev(ref_n), dev(src_n), dev(H.reshape(9)), p)
+    ocxy, ovalid, _ = orc.pick_corners(ref_n, c)
+    octr, omxy, ocost = orc.search(ref_n, src_n, H, c, ocxy, ovalid)
+    assert np.array_equal(host(valid), ovalid)
+    assert np.array_equal(host(cxy), ocxy)
+    assert np.array_equal(host(mxy), omxy)
+    assert np.array_equal(host(cost).view(np.uint32), ocost)
+    return int(ovalid.sum())
+
+
+@pytest.mark.parametrize("tile,radius,shape", [(16, 4, (480, 640)), (32, 6, (300, 410)),
+                                               (16, 10, (121, 162)), (48, 3, (250, 250)),
+                                               (8, 1, (60, 70))])
+def test_local_search_bit_exact(hd, orc, vga, tile, radius, shape):
+    from paper_1504_01441_b300 import synth
+    rng = np.random.default_rng(4)
+    c = cfg(tile, radius, grid_half=min(4, tile // 2 // max(1, tile // 16) - 1))
+    rn, sn = orc.normalize_ratio(vga.ref.y, vga.srcs[0].y, 4, 1)
+    h, w = shape
+    ref_n, src_n = np.ascontiguousarray(rn[:h, :w]), np.ascontiguousarray(sn[:h, :w])
+    H = synth.random_homography(rng)
+    assert _search_case(hd, orc, ref_n, src_n, H, c) > 0
+
+
+def test_local_search_full_size_bit_exact(hd, orc, five_mp):
+    from paper_1504_01441_b300 import synth
+    rng = np.random.default_rng(5)
+    rn, sn = orc.normalize_ratio(five_mp.ref.y, five_mp.srcs[0].y, 4, 1)
+    assert _search_case(hd, orc, rn, sn, synth.random_homography(rng), cfg(32, 6)) > 1000
+
+
+def test_local_search_flat_and_identity(hd, orc):
+    flat = np.full((128, 128), 77, np.uint8)
+    assert _search_case(hd, orc, flat, flat, np.eye(3), cfg(32, 6)) == 0
+    rng = np.random.default_rng(6)
+    img = random_img(rng, 128, 160)
+    _search_case(hd, orc, img, img, np.eye(3), cfg(16, 4))
+
+
+# --------------------------------------------------------------------- a6-a7
+def _level_matches(orc, vga, c):
+    rn, sn = orc.normalize_ratio(vga.ref.y, vga.srcs[0].y, 4, 1)
+    cxy, valid, _ = orc.pick_corners(rn, c)
+    _, mxy, _ = orc.search(rn, sn, np.eye(3), c, cxy, valid)
+    return rn.shape, cxy, mxy, valid
+
+
+@pytest.mark.parametrize("seed", [1, 99])
+def test_weed_bit_exact(hd, orc, vga, seed):
+    c = cfg()
+    (h, w), cxy, mxy, valid = _level_matches(orc, vga, c)
+    p = hd.params_from_dict(c)
+    mask = hd.weed(dev(cxy), dev(mxy), dev(valid), w, h, p, seed)
+    obits, _ = orc.weed(cxy, mxy, valid, w, h, c, seed)
+    assert np.array_equal(host(mask).view(np.uint32), obits)
+
+
+def test_weed_split_ranges_union_on_gpu(hd, orc, vga):
+    c = cfg(weed_iters=300)
+    (h, w), cxy, mxy, valid = _level_matches(orc, vga, c)
+    p = hd.params_from_dict(c)
+    one = host(hd.weed(dev(cxy), dev(mxy), dev(valid), w, h, p, 7))
+    mask = torch.zeros_like(torch.as_tensor(one)).cuda()
+    for a, b in [(200, 300), (0, 13), (13, 200)]:
+        hd.weed(dev(cxy), dev(mxy), dev(valid), w, h, p, 7, a, b, mask=mask)
+    assert np.array_equal(host(mask), one)
+
+
+def test_weed_two_plane_toy_scene_matches_oracle(hd, orc):
+    import test_oracle_pins as pins
+    rng = np.random.default_rng(6)
+    p_xy, q_xy, lab = pins._two_plane_scene(rng)
+    c = cfg(weed_delta_div=3)
+    valid = np.ones(len(p_xy), np.uint8)
+    mask = hd.weed(dev(p_xy), dev(q_xy), dev(valid), 640, 480, hd.params_from_dict(c), 99)
+    obits, _ = orc.weed(p_xy, q_xy, valid, 640, 480, c, 99)
+    assert np.array_equal(host(mask).view(np.uint32), obits)
+
+
+def test_fit_bit_exact(hd, orc, vga):
+    c = cfg()
+    (h, w), cxy, mxy, valid = _level_matches(orc, vga, c)
+    obits, _ = orc.weed(cxy, mxy, valid, w, h, c, 3)
+    Hprev = np.array([[1.0, 0.01, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    H, st = hd.fit_homography(dev(cxy), dev(mxy), dev(obits.view(np.int32)), w, h,
+                              dev(Hprev.reshape(9)))
+    oH, ost = orc.fit_homography(cxy, mxy, obits, w, h, Hprev)
+    assert host(st)[0] == ost == 0
+    assert np.array_equal(host(H).view(np.uint64), oH.reshape(9).view(np.uint64))
+    # fewer than 4 kept -> previous homography, status 1
+    few = np.zeros_like(obits)
+    few[0] = 0b101
+    H, st = hd.fit_homography(dev(cxy), dev(mxy), dev(few.view(np.int32)), w, h,
+                              dev(Hprev.reshape(9)))
+    assert host(st)[0] == 1 and np.array_equal(host(H), Hprev.reshape(9))
+
+
+# --------------------------------------------------------------------- a8
+def _flow_case(hd, orc, stack, c):
+    rn, sn = orc.normalize_ratio(stack.ref.y, stack.srcs[0].y, *stack.ratios[0])
+    m = orc.match(rn, sn, c)
+    p = hd.params_from_dict(c)
+    fu, fv = hd.flow_upsample(dev(rn), dev(m["corner_xy"]), dev(m["match_xy"]),
+                              dev(m["bits"].view(np.int32)), dev(m["H0"].reshape(9)), p)
+    ofu, ofv, ont = orc.flow(rn, m["corner_xy"], m["match_xy"], m["bits"], m["H0"], c)
+    eu = assert_rel(host(fu), ofu, "flow u")
+    ev = assert_rel(host(fv), ofv, "flow v")
+    return eu, ev
+
+
+def test_flow_vga(hd, orc, vga):
+    _flow_case(hd, orc, vga, cfg())
+
+
+def test_flow_ragged_size(hd, orc):
+    from paper_1504_01441_b300 import synth
+    spec = synth.StackSpec(333, 211, ratios=((4, 1),), noise_sigma=1.0, field_amp=3.0, movers=1,
+                           chroma=False, n_blobs=40, n_rects=10)
+    _flow_case(hd, orc, synth.make_stack(spec, 21), cfg())
+
+
+def test_flow_full_size(hd, orc, five_mp):
+    _flow_case(hd, orc, five_mp, cfg(32, 6))
+
+
+def test_flow_propagate_full_mode(hd, orc, vga):
+    _flow_case(hd, orc, vga, cfg(propagate_full=1))
+
+
+# --------------------------------------------------------------------- a9
+@pytest.mark.parametrize("chroma", [True, False])
+def test_warp(hd, orc, small_yuv_stack, chroma):
+    from paper_1504_01441_b300 import synth
+    rng = np.random.default_rng(7)
+    s = small_yuv_stack.srcs[0]
+    h, w = s.y.shape
+    H = synth.random_homography(rng)
+    fu, fv = synth.random_flow(rng, w, h, 4.0)
+    u = dev(s.u) if chroma else None
+    v = dev(s.v) if chroma else None
+    oy, ou, ov = hd.warp(dev(s.y), u, v, dev(H.reshape(9)), dev(fu), dev(fv))
+    wy, wu, wv = orc.warp(s.y, s.u if chroma else None, s.v if chroma else None, H, fu, fv)
+    assert_rel(host(oy), wy, "warp y")
+    if chroma:
+        assert_rel(host(ou), wu, "warp u")
+        assert_rel(host(ov), wv, "warp v")
+
+
+def test_warp_identity_exact(hd, small_yuv_stack):
+    s = small_yuv_stack.srcs[0]
+    h, w = s.y.shape
+    z = torch.zeros((h, w), dtype=torch.float32, device="cuda")
+    oy, ou, ov = hd.warp(dev(s.y), dev(s.u), dev(s.v), dev(np.eye(3).reshape(9)), z, z)
+    assert np.array_equal(host(oy), s.y.astype(np.float32))
+    assert np.array_equal(host(ou), s.u.astype(np.float32))
+
+
+# --------------------------------------------------------------------- a10-a11
+def _merge_case(hd, orc, stack, c, ratios):
+    from paper_1504_01441_b300 import synth
+    rng = np.random.default_rng(8)
+    h, w = stack.ref.y.shape
+    chroma = stack.ref.u is not None
+    srcs, osrcs, qs = [], [], []
+    for k, s in enumerate(stack.srcs):
+        rn, _ = orc.normalize_ratio(stack.ref.y, s.y, *ratios[k])
+        H = synth.random_homography(rng, scale=0.002, shift_n=0.002, persp=0.0001)
+        fu, fv = synth.random_flow(rng, w, h, 1.0)
+        wy, wu, wv = orc.warp(s.y, s.u, s.v, H, fu, fv)
+        wy, wu, wv = [None if a is None else a.astype(np.float32) for a in (wy, wu, wv)]
+        gain = ratios[k][1] / ratios[k][0] if ratios[k][0] < ratios[k][1] else 1.0
+        qs.append(orc.ghost_mask(rn, wy, 0, gain))
+        osrcs.append((wy, wu, wv))
+        srcs.append(dict(y=dev(wy), u=dev(wu) if chroma else None, v=dev(wv) if chroma else None,
+                         ref_n=dev(rn), ratio=ratios[k]))
+    p = hd.params_from_dict(c)
+    ey, eu, ev, q = hd.merge(dev(stack.ref.y), dev(stack.ref.u) if chroma else None,
+                             dev(stack.ref.v) if chroma else None, srcs, p, want_q=True)
+    oy, ou, ov = orc.merge(stack.ref.y, stack.ref.u, stack.ref.v, osrcs, qs,
+                           [r[0] / r[1] for r in ratios])
+    for k in range(len(srcs)):
+        assert_rel(host(q)[k], qs[k], f"ssim mask {k}")
+    assert_rel(host(ey), oy, "merge y")
+    if chroma:
+        assert_rel(host(eu), ou, "merge u")
+        assert_rel(host(ev), ov, "merge v")
+
+
+def test_merge_two_frames(hd, orc, small_yuv_stack):
+    _merge_case(hd, orc, small_yuv_stack, cfg(), [(4, 1)])
+
+
+def test_merge_three_frames(hd, orc):
+    from paper_1504_01441_b300 import synth
+    spec = synth.StackSpec(256, 192, ratios=((1, 4), (4, 1)), noise_sigma=1.0, field_amp=2.0,
+                           movers=1, chroma=True, n_blobs=40, n_rects=10)
+    st = synth.make_stack(spec, 33)
+    _merge_case(hd, orc, st, cfg(), [(1, 4), (4, 1)])
+
+
+# --------------------------------------------------------------------- fused
+def _fused_case(hd, orc, stack, c):
+    p = hd.params_from_dict(c)
+    chroma = stack.ref.u is not None
+    ref = (dev(stack.ref.y), dev(stack.ref.u) if chroma else None,
+           dev(stack.ref.v) if chroma else None)
+    srcs = [(dev(s.y), dev(s.u) if chroma else None, dev(s.v) if chroma else None)
+            for s in stack.srcs]
+    (ey, eu, ev), rm = hd.register_merge(ref, srcs, stack.ratios, p)
+    out = orc.register_merge(stack.ref, stack.srcs, stack.ratios, c)
+    diags = rm.diagnostics()
+    for k, d in enumerate(diags):
+        assert np.array_equal(np.array(d.H0[:]).view(np.uint64),
+                              out["H0"][k].reshape(9).view(np.uint64)), f"H0 of source {k}"
+    e = assert_rel(host(ey), out["y"], "fused merge y")
+    if chroma:
+        assert_rel(host(eu), out["u"], "fused merge u")
+        assert_rel(host(ev), out["v"], "fused merge v")
+    return e, diags
+
+
+def test_fused_vga_luma(hd, orc, vga):
+    _, diags = _fused_case(hd, orc, vga, cfg())
+    assert diags[0].levels == 3 and diags[0].valid > 300
+
+
+def test_fused_three_frame_yuv(hd, orc):
+    from paper_1504_01441_b300 import synth
+    spec = synth.StackSpec(480, 320, ratios=((1, 4), (4, 1)), noise_sigma=1.5, field_amp=4.0,
+                           movers=2, chroma=True)
+    _fused_case(hd, orc, synth.make_stack(spec, 44), cfg(16, 5))
+
+
+def test_fused_five_mp(hd, orc, five_mp):
+    _, diags = _fused_case(hd, orc, five_mp, cfg(32, 6))
+    assert diags[0].levels == 5 and diags[0].tiles == 81 * 60
+
+
+def test_fused_histeq_mode(hd, orc, small_yuv_stack):
+    _fused_case(hd, orc, small_yuv_stack, cfg(norm_mode=1))

@@ -654,3 +654,20 @@ def test_inlier_test_matches_reprojection_distance(orc):
         assert orc.is_inlier(H, p, q, w, h, 1.5) == (ok and d2 <= 1.5 ** 2)
         n_checked += 1
     assert n_checked > 2900
+
+
+@pytest.mark.parametrize("z,taper", [(254.0, 0.5), (253.0, 1.0), (255.0, 0.0), (1.0, 0.5),
+                                     (0.0, 0.0), (128.0, 1.0), (254.5, 0.25)])
+def test_merge_source_weight_closed_form(orc, z, taper):
+    # one pixel, Q = 1: E = (w0 Z0 + w1 Z1/r) / (w0 + w1) -> w1 = w0 (Z0 - E) / (E - Z1/r)
+    z0, r = 100, 2.0
+    oy, _, _ = orc.merge(np.array([[z0]], np.uint8), None, None, [(np.array([[z]]), None, None)],
+                         [np.ones((1, 1))], [r])
+    e = oy[0, 0]
+    w0 = orc.well_exposedness(float(z0))
+    want = orc.well_exposedness(z) * taper
+    if want == 0.0:
+        assert abs(e - z0) < 1e-12
+    else:
+        w1 = w0 * (z0 - e) / (e - z / r)
+        assert abs(w1 - want) < 1e-9 * max(want, 1e-3)
