@@ -385,3 +385,19 @@ def is_inlier(H, p, q, w, h, eps):
     H = _f64(H).reshape(9)
     return bool(lib().orc_is_inlier(_p(H), int(p[0]), int(p[1]), int(q[0]), int(q[1]), w, h,
                                     C.c_double(eps)))
+
+
+def pow2_scale(w):
+    return lib().orc_pow2_scale(int(w))
+
+
+def to_scaled(H, w):
+    """A homography in Eq. 3's normalized coordinates rewritten for the S-scaled ones."""
+    H = np.asarray(H, np.float64).reshape(3, 3)
+    r = pow2_scale(w) / w
+    T = H.copy()
+    T[0, 2] /= r
+    T[1, 2] /= r
+    T[2, 0] *= r
+    T[2, 1] *= r
+    return T

@@ -298,13 +298,15 @@ int orc_weed_sample(uint64_t seed, long iter, int nv, int pick[4])
 
 /*
  * Solve the 8x8 system A x = b by Gaussian elimination with partial pivoting
- * (pivot = first row of largest |a_ik|), then back substitution, each operation
- * rounded in the written order. Returns 0 on success, 1 if a pivot magnitude is
- * below tol.
+ * (pivot = first row of largest |a_ik|): each pivot is inverted once, the
+ * elimination factors are a_ik * (1 / a_kk), back substitution subtracts in
+ * increasing column order and multiplies by the stored reciprocal. Every
+ * operation is rounded in the written order. Returns 0 on success, 1 if a pivot
+ * magnitude is below tol.
  */
 int orc_solve8(const double A_in[64], const double b_in[8], double x[8], double tol)
 {
-    double A[8][8], b[8];
+    double A[8][8], b[8], inv[8];
     for (int i = 0; i < 8; i++) {
         for (int j = 0; j < 8; j++) A[i][j] = A_in[i * 8 + j];
         b[i] = b_in[i];
@@ -319,8 +321,9 @@ int orc_solve8(const double A_in[64], const double b_in[8], double x[8], double 
             for (int j = 0; j < 8; j++) { double t = A[k][j]; A[k][j] = A[piv][j]; A[piv][j] = t; }
             double t = b[k]; b[k] = b[piv]; b[piv] = t;
         }
+        inv[k] = 1.0 / A[k][k];
         for (int i = k + 1; i < 8; i++) {
-            double f = A[i][k] / A[k][k];
+            double f = A[i][k] * inv[k];
             for (int j = k + 1; j < 8; j++) A[i][j] = A[i][j] - f * A[k][j];
             b[i] = b[i] - f * b[k];
         }
@@ -328,34 +331,47 @@ int orc_solve8(const double A_in[64], const double b_in[8], double x[8], double 
     for (int k = 7; k >= 0; k--) {
         double s = b[k];
         for (int j = k + 1; j < 8; j++) s = s - A[k][j] * x[j];
-        x[k] = s / A[k][k];
+        x[k] = s * inv[k];
     }
     return 0;
 }
 
-static double norm_x(int x, int w) { return (double)(2 * x - (w - 1)) / (double)w; }
-static double norm_y(int y, int w, int h) { return (double)(2 * y - (h - 1)) / (double)w; }
+/*
+ * Coordinates in which the weeding and level-fit systems are solved: the
+ * centred integers x_c = 2x - (w-1), y_c = 2y - (h-1) divided by S, the smallest
+ * power of two >= w. The division is exact, so these are the same numbers on
+ * every machine; x_n = x_c / w of Eq. 3 is (S / w) times them.
+ */
+int orc_pow2_scale(int w)
+{
+    int s = 1;
+    while (s < w) s <<= 1;
+    return s;
+}
+
+static double tilde(int v, int extent, double S) { return (double)(2 * v - (extent - 1)) / S; }
 
 /*
- * Inlier test of the weeding filter: the match q of corner p is an inlier of H
- * if H(p) lands within eps pixels of q (Sec. 2.3). With x_s = (X/D w + (w-1))/2
- * this is (X w - x_qc D)^2 + (Y w - y_qc D)^2 <= (2 eps D)^2 for D > 0, where
- * (X, Y, D) = H (x_n, y_n, 1) and x_qc = 2 q_x - (w-1), y_qc = 2 q_y - (h-1):
- * the same predicate multiplied through by (2D)^2, evaluated without division
- * in the written order.
+ * Inlier test of the weeding filter: the match q of corner p is an inlier of
+ * the homography Ht (written in the S-scaled coordinates above) if it maps p
+ * within eps pixels of q (Sec. 2.3). With the source pixel x_s =
+ * (S X/D + (w-1)) / 2 this is (X S - x_qc D)^2 + (Y S - y_qc D)^2 <= (2 eps D)^2
+ * for D > 0, where (X, Y, D) = Ht (x~, y~, 1) and x_qc = 2 q_x - (w-1), y_qc =
+ * 2 q_y - (h-1): the same predicate multiplied through by (2D)^2, evaluated
+ * without division in the written order.
  */
-int orc_is_inlier(const double H[9], int px, int py, int qx, int qy, int w, int h, double eps)
+int orc_is_inlier(const double Ht[9], int px, int py, int qx, int qy, int w, int h, double eps)
 {
-    double W = (double)w;
-    double xn = (double)(2 * px - (w - 1)) / W;
-    double yn = (double)(2 * py - (h - 1)) / W;
-    double X = (H[0] * xn + H[1] * yn) + H[2];
-    double Y = (H[3] * xn + H[4] * yn) + H[5];
-    double D = (H[6] * xn + H[7] * yn) + H[8];
+    double S = (double)orc_pow2_scale(w);
+    double x = tilde(px, w, S);
+    double y = tilde(py, h, S);
+    double X = (Ht[0] * x + Ht[1] * y) + Ht[2];
+    double Y = (Ht[3] * x + Ht[4] * y) + Ht[5];
+    double D = (Ht[6] * x + Ht[7] * y) + Ht[8];
     double qxc = (double)(2 * qx - (w - 1));
     double qyc = (double)(2 * qy - (h - 1));
-    double ex = X * W - qxc * D;
-    double ey = Y * W - qyc * D;
+    double ex = X * S - qxc * D;
+    double ey = Y * S - qyc * D;
     double lhs = ex * ex + ey * ey;
     double t = (2.0 * eps) * D;
     return D > 0.0 && lhs <= t * t;
@@ -364,8 +380,8 @@ int orc_is_inlier(const double H[9], int px, int py, int qx, int qy, int w, int 
 /*
  * Weeding filter of Sec. 2.3, Eq. 4, iterations [iter_begin, iter_end): for
  * each iteration sample 4 distinct valid matches, fit the homography H^i
- * through them exactly (8x8 DLT in normalized coordinates, h22 = 1; skipped if
- * singular), collect the inliers I^i = matches whose projection lands within
+ * through them exactly (8x8 DLT in the S-scaled coordinates of orc_pow2_scale,
+ * h22 = 1; skipped if singular), collect the inliers I^i = matches whose projection lands within
  * eps pixels of their match (orc_is_inlier), and if |I^i| > delta set M |= I^i. Inliers are
  * not removed from the pool. mask_bits (bit t = tile t) is OR-ed into, so that
  * runs over disjoint iteration ranges compose by union (Sec. 2.3, last
@@ -383,6 +399,7 @@ void orc_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* 
     if (nv >= 4) {
         int delta = (nv + p->weed_delta_div - 1) / p->weed_delta_div;
         if (delta < p->weed_delta_min) delta = p->weed_delta_min;
+        double S = (double)orc_pow2_scale(w);
         for (int it = iter_begin; it < iter_end; it++) {
             int pick[4];
             if (!orc_weed_sample(seed, it, nv, pick)) continue;
@@ -390,8 +407,8 @@ void orc_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* 
             memset(A, 0, sizeof(A));
             for (int k = 0; k < 4; k++) {
                 int t = V[pick[k]];
-                double x = norm_x(corner_xy[2 * t], w), y = norm_y(corner_xy[2 * t + 1], w, h);
-                double u = norm_x(match_xy[2 * t], w), v = norm_y(match_xy[2 * t + 1], w, h);
+                double x = tilde(corner_xy[2 * t], w, S), y = tilde(corner_xy[2 * t + 1], h, S);
+                double u = tilde(match_xy[2 * t], w, S), v = tilde(match_xy[2 * t + 1], h, S);
                 double* r1 = &A[(2 * k) * 8];
                 double* r2 = &A[(2 * k + 1) * 8];
                 r1[0] = x; r1[1] = y; r1[2] = 1.0; r1[6] = -(x * u); r1[7] = -(y * u);
@@ -432,20 +449,22 @@ static double i128_to_double(__int128 s)
 /*
  * Homography H^l of one pyramid level (Sec. 2.2: computed from the level's
  * corners and matches; used to initialize the next finer level): linear least
- * squares (DLT with h22 = 1) over the weeded set M, in the normalized
- * coordinates of Eq. 3. The normal equations are accumulated exactly in
- * integers over the centred coordinates x_c = 2x - (w-1) (x_n = x_c / w), then
- * each entry is converted once to binary64 and divided by the power of w that
- * the normalization puts on its row and column, and the 8x8 system is solved
- * as in orc_solve8. Fewer than 4 matches or a singular system keep H_prev.
- * Returns 0 (fitted), 1 (too few matches) or 2 (singular).
+ * squares (DLT with h22 = 1) over the weeded set M. The normal equations are
+ * accumulated exactly in integers over the centred coordinates x_c = 2x - (w-1),
+ * each entry is converted once to binary64 and scaled exactly by the power of
+ * S (orc_pow2_scale) that the S-scaled coordinates put on its row and column,
+ * and the 8x8 system is solved as in orc_solve8. The solution Ht is returned in
+ * the normalized coordinates of Eq. 3 (x_n = (S/w) x~): h2 = (t2 S) / w,
+ * h5 = (t5 S) / w, h6 = t6 (w / S), h7 = t7 (w / S), the rest unchanged. Fewer than
+ * 4 matches or a singular system keep H_prev. Returns 0 (fitted), 1 (too few
+ * matches) or 2 (singular).
  */
 int orc_fit_homography(const int32_t* corner_xy, const int32_t* match_xy,
                        const uint32_t* mask_bits, int n, int w, int h,
                        const double H_prev[9], double H_out[9])
 {
-    __int128 S[8][8], Rv[8];
-    memset(S, 0, sizeof(S));
+    __int128 Sm[8][8], Rv[8];
+    memset(Sm, 0, sizeof(Sm));
     memset(Rv, 0, sizeof(Rv));
     long cnt = 0;
     for (int t = 0; t < n; t++) {
@@ -458,24 +477,32 @@ int orc_fit_homography(const int32_t* corner_xy, const int32_t* match_xy,
         int64_t a2[8] = {0, 0, 0, x, y, 1, -x * v, -y * v};
         for (int j = 0; j < 8; j++) {
             for (int k = 0; k < 8; k++)
-                S[j][k] += (__int128)a1[j] * a1[k] + (__int128)a2[j] * a2[k];
+                Sm[j][k] += (__int128)a1[j] * a1[k] + (__int128)a2[j] * a2[k];
             Rv[j] += (__int128)a1[j] * u + (__int128)a2[j] * v;
         }
         cnt++;
     }
     if (cnt < 4) { memcpy(H_out, H_prev, sizeof(double) * 9); return 1; }
-    /* normalized row: a_n[j] = a_c[j] / w^e[j], b_n = b_c / w */
+    /* S-scaled row: a~[j] = a_c[j] / S^e[j], b~ = b_c / S (exact power-of-two scaling) */
     static const int e[8] = {1, 1, 0, 1, 1, 0, 2, 2};
-    double Wp[6];
-    Wp[0] = 1.0;
-    for (int k = 1; k < 6; k++) Wp[k] = Wp[k - 1] * (double)w;
+    int s = orc_pow2_scale(w), lg = 0;
+    while ((1 << lg) < s) lg++;
     double A[64], b[8], hv[8];
     for (int j = 0; j < 8; j++) {
-        for (int k = 0; k < 8; k++) A[j * 8 + k] = i128_to_double(S[j][k]) / Wp[e[j] + e[k]];
-        b[j] = i128_to_double(Rv[j]) / Wp[e[j] + 1];
+        for (int k = 0; k < 8; k++) A[j * 8 + k] = ldexp(i128_to_double(Sm[j][k]), -lg * (e[j] + e[k]));
+        b[j] = ldexp(i128_to_double(Rv[j]), -lg * (e[j] + 1));
     }
     if (orc_solve8(A, b, hv, 1e-12)) { memcpy(H_out, H_prev, sizeof(double) * 9); return 2; }
-    for (int k = 0; k < 8; k++) H_out[k] = hv[k];
+    double S = (double)s, W = (double)w;
+    double WS = W / S; /* exact */
+    H_out[0] = hv[0];
+    H_out[1] = hv[1];
+    H_out[2] = (hv[2] * S) / W;
+    H_out[3] = hv[3];
+    H_out[4] = hv[4];
+    H_out[5] = (hv[5] * S) / W;
+    H_out[6] = hv[6] * WS;
+    H_out[7] = hv[7] * WS;
     H_out[8] = 1.0;
     return 0;
 }

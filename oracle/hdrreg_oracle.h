@@ -82,7 +82,8 @@ void orc_search(const uint8_t* ref_n, const uint8_t* src_n, int w, int h, const 
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k);
 int  orc_weed_sample(uint64_t seed, long iter, int nv, int pick[4]);
 int  orc_solve8(const double A[64], const double b[8], double x[8], double tol);
-int  orc_is_inlier(const double H[9], int px, int py, int qx, int qy, int w, int h, double eps);
+int  orc_pow2_scale(int w);
+int  orc_is_inlier(const double Ht[9], int px, int py, int qx, int qy, int w, int h, double eps);
 void orc_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* valid, int n,
               int w, int h, const orc_params* p, uint64_t seed, int iter_begin, int iter_end,
               uint32_t* mask_bits, int32_t* accepted_out);

@@ -11,8 +11,9 @@
 // every thread runs its segment with a zero carry while recording the segment's
 // map (A, B), the maps are scanned across threads, and a second sweep adds
 // A_prefix * carry. Rows: one CTA per row (256 segments, warp-shuffle scan).
-// Columns: one CTA per strip of SW adjacent columns holding the whole strip in
-// shared memory (SW x NSEG segments). Each pass therefore reads and writes the
+// Columns: one CTA per strip of SW (4, or 2 for tall frames) adjacent columns
+// holding the whole strip in shared memory (SW x NSEG segments), sized so that
+// two CTAs share an SM. Staging uses cp.async so all copies are in flight at once. Each pass therefore reads and writes the
 // planes exactly once; the first row pass builds its input from the corner
 // list (no dense zero planes are read) and the last column pass writes
 // F = P~ / N~ directly.
@@ -81,7 +82,7 @@ template <bool kSparse>
 __global__ void __launch_bounds__(kNT) k_dt_rows(float* __restrict__ P0, float* __restrict__ P1,
                                                  float* __restrict__ P2,
                                                  const uint8_t* __restrict__ guide, int w, int h,
-                                                 int L, DtLut lut_in, FlowCorners fc)
+                                                 int L, int gmode, DtLut lut_in, FlowCorners fc)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ float lut[256];
@@ -94,7 +95,14 @@ __global__ void __launch_bounds__(kNT) k_dt_rows(float* __restrict__ P0, float* 
     const int y = blockIdx.x, tid = threadIdx.x;
     lut[tid] = lut_in.w[tid];
     const size_t row = (size_t)y * w;
-    for (int x = tid; x < w; x += kNT) g[x] = guide[row + x];
+    // guide row: 16-byte, 4-byte or byte copies depending on alignment (gmode 2/1/0)
+    if (gmode == 2) {
+        for (int i = tid; i < w / 16; i += kNT) cp_async16(g + 16 * i, guide + row + 16 * i);
+    } else if (gmode == 1) {
+        for (int i = tid; i < w / 4; i += kNT) cp_async4(g + 4 * i, guide + row + 4 * i);
+    } else {
+        for (int x = tid; x < w; x += kNT) g[x] = guide[row + x];
+    }
     if (kSparse) {
         for (int x = tid; x < w; x += kNT) {
             s0[x] = 0.f;
@@ -121,24 +129,20 @@ __global__ void __launch_bounds__(kNT) k_dt_rows(float* __restrict__ P0, float* 
                 s2[cx] = 1.f;
             }
         }
+    } else if ((w & 3) == 0) {
+        for (int i = tid; i < w / 4; i += kNT) {
+            cp_async16(s0 + 4 * i, P0 + row + 4 * i);
+            cp_async16(s1 + 4 * i, P1 + row + 4 * i);
+            cp_async16(s2 + 4 * i, P2 + row + 4 * i);
+        }
     } else {
-        if ((w & 3) == 0) {
-            const float4* a = reinterpret_cast<const float4*>(P0 + row);
-            const float4* b = reinterpret_cast<const float4*>(P1 + row);
-            const float4* c = reinterpret_cast<const float4*>(P2 + row);
-            for (int i = tid; i < w / 4; i += kNT) {
-                reinterpret_cast<float4*>(s0)[i] = a[i];
-                reinterpret_cast<float4*>(s1)[i] = b[i];
-                reinterpret_cast<float4*>(s2)[i] = c[i];
-            }
-        } else {
-            for (int x = tid; x < w; x += kNT) {
-                s0[x] = P0[row + x];
-                s1[x] = P1[row + x];
-                s2[x] = P2[row + x];
-            }
+        for (int x = tid; x < w; x += kNT) {
+            cp_async4(s0 + x, P0 + row + x);
+            cp_async4(s1 + x, P1 + row + x);
+            cp_async4(s2 + x, P2 + row + x);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     const int x0 = tid * L, x1 = min(x0 + L, w);
@@ -233,7 +237,7 @@ template <int SW>
 __global__ void __launch_bounds__(kNT) k_dt_cols(float* __restrict__ P0, float* __restrict__ P1,
                                                  float* __restrict__ P2,
                                                  const uint8_t* __restrict__ guide, int w, int h,
-                                                 int L, DtLut lut_in, int final_pass,
+                                                 int L, int vec, DtLut lut_in, int final_pass,
                                                  float flow_eps, float* __restrict__ Fu,
                                                  float* __restrict__ Fv)
 {
@@ -250,31 +254,36 @@ __global__ void __launch_bounds__(kNT) k_dt_cols(float* __restrict__ P0, float* 
     const int xs0 = blockIdx.x * SW;
     const int ncols = min(SW, w - xs0);
     lut[tid] = lut_in.w[tid];
-    // load the strip
-    if (ncols == SW && (w & 3) == 0 && (SW % 4) == 0) {
-        constexpr int V = SW >= 4 ? SW / 4 : 1;
-        for (int i = tid; i < h * V; i += kNT) {
-            const int r = i / V, v = i % V;
-            const size_t off = (size_t)r * w + xs0 + 4 * v;
-            reinterpret_cast<float4*>(s0 + r * SW)[v] = *reinterpret_cast<const float4*>(P0 + off);
-            reinterpret_cast<float4*>(s1 + r * SW)[v] = *reinterpret_cast<const float4*>(P1 + off);
-            reinterpret_cast<float4*>(s2 + r * SW)[v] = *reinterpret_cast<const float4*>(P2 + off);
+    // stage the strip: SW floats per row and plane, SW guide bytes per row
+    if (ncols == SW && vec) {
+        for (int r = tid; r < h; r += kNT) {
+            const size_t off = (size_t)r * w + xs0;
+            if (SW == 4) {
+                cp_async16(s0 + r * SW, P0 + off);
+                cp_async16(s1 + r * SW, P1 + off);
+                cp_async16(s2 + r * SW, P2 + off);
+                cp_async4(g + r * SW, guide + off);
+            } else {
+                cp_async8(s0 + r * SW, P0 + off);
+                cp_async8(s1 + r * SW, P1 + off);
+                cp_async8(s2 + r * SW, P2 + off);
+                g[r * SW] = guide[off];
+                g[r * SW + 1] = guide[off + 1];
+            }
         }
     } else {
         for (int i = tid; i < h * SW; i += kNT) {
             const int r = i / SW, cc = i % SW;
             if (cc < ncols) {
                 const size_t off = (size_t)r * w + xs0 + cc;
-                s0[r * SW + cc] = P0[off];
-                s1[r * SW + cc] = P1[off];
-                s2[r * SW + cc] = P2[off];
+                cp_async4(s0 + r * SW + cc, P0 + off);
+                cp_async4(s1 + r * SW + cc, P1 + off);
+                cp_async4(s2 + r * SW + cc, P2 + off);
             }
+            g[r * SW + cc] = cc < ncols ? guide[(size_t)r * w + xs0 + cc] : 0;
         }
     }
-    for (int i = tid; i < h * SW; i += kNT) {
-        const int r = i / SW, cc = i % SW;
-        g[r * SW + cc] = cc < ncols ? guide[(size_t)r * w + xs0 + cc] : 0;
-    }
+    cp_async_wait_all();
     __syncthreads();
 
     const int c = tid % SW, s = tid / SW;
@@ -367,7 +376,25 @@ __global__ void __launch_bounds__(kNT) k_dt_cols(float* __restrict__ P0, float* 
     }
     __syncthreads();
     // store
-    if (final_pass) {
+    if (final_pass && ncols == SW && vec && SW == 4) {
+        for (int r = tid; r < h; r += kNT) {
+            const float4 a = *reinterpret_cast<const float4*>(s0 + r * SW);
+            const float4 b = *reinterpret_cast<const float4*>(s1 + r * SW);
+            const float4 n = *reinterpret_cast<const float4*>(s2 + r * SW);
+            float4 u, v;
+            u.x = n.x >= flow_eps ? a.x / n.x : 0.f;
+            u.y = n.y >= flow_eps ? a.y / n.y : 0.f;
+            u.z = n.z >= flow_eps ? a.z / n.z : 0.f;
+            u.w = n.w >= flow_eps ? a.w / n.w : 0.f;
+            v.x = n.x >= flow_eps ? b.x / n.x : 0.f;
+            v.y = n.y >= flow_eps ? b.y / n.y : 0.f;
+            v.z = n.z >= flow_eps ? b.z / n.z : 0.f;
+            v.w = n.w >= flow_eps ? b.w / n.w : 0.f;
+            const size_t off = (size_t)r * w + xs0;
+            *reinterpret_cast<float4*>(Fu + off) = u;
+            *reinterpret_cast<float4*>(Fv + off) = v;
+        }
+    } else if (final_pass) {
         for (int i = tid; i < h * SW; i += kNT) {
             const int r = i / SW, cc = i % SW;
             if (cc < ncols) {
@@ -378,14 +405,12 @@ __global__ void __launch_bounds__(kNT) k_dt_cols(float* __restrict__ P0, float* 
                 Fv[off] = ok ? s1[r * SW + cc] / n : 0.f;
             }
         }
-    } else if (ncols == SW && (w & 3) == 0 && (SW % 4) == 0) {
-        constexpr int V = SW >= 4 ? SW / 4 : 1;
-        for (int i = tid; i < h * V; i += kNT) {
-            const int r = i / V, v = i % V;
-            const size_t off = (size_t)r * w + xs0 + 4 * v;
-            *reinterpret_cast<float4*>(P0 + off) = reinterpret_cast<const float4*>(s0 + r * SW)[v];
-            *reinterpret_cast<float4*>(P1 + off) = reinterpret_cast<const float4*>(s1 + r * SW)[v];
-            *reinterpret_cast<float4*>(P2 + off) = reinterpret_cast<const float4*>(s2 + r * SW)[v];
+    } else if (ncols == SW && vec && SW == 4) {
+        for (int r = tid; r < h; r += kNT) {
+            const size_t off = (size_t)r * w + xs0;
+            *reinterpret_cast<float4*>(P0 + off) = *reinterpret_cast<const float4*>(s0 + r * SW);
+            *reinterpret_cast<float4*>(P1 + off) = *reinterpret_cast<const float4*>(s1 + r * SW);
+            *reinterpret_cast<float4*>(P2 + off) = *reinterpret_cast<const float4*>(s2 + r * SW);
         }
     } else {
         for (int i = tid; i < h * SW; i += kNT) {
@@ -402,6 +427,9 @@ __global__ void __launch_bounds__(kNT) k_dt_cols(float* __restrict__ P0, float* 
 
 int odd_up(int v) { return (v & 1) ? v : v + 1; }
 
+// Two CTAs per SM need <= ~110 KB of dynamic shared memory each; one CTA per SM
+// can take up to 220 KB (the static part of the column kernel is ~5 KB).
+constexpr size_t kSmemTwoPerSm = 110 * 1024;
 constexpr size_t kSmemBudget = 220 * 1024;
 
 size_t col_smem(int h, int sw)
@@ -414,7 +442,9 @@ size_t col_smem(int h, int sw)
 
 int pick_sw(int h)
 {
-    for (int sw : {8, 4, 2})
+    for (int sw : {4, 2})
+        if (col_smem(h, sw) <= kSmemTwoPerSm) return sw;
+    for (int sw : {4, 2})
         if (col_smem(h, sw) <= kSmemBudget) return sw;
     return 0;
 }
@@ -449,9 +479,14 @@ void launch_cols(float* P0, float* P1, float* P2, const uint8_t* guide, int w, i
     const size_t smem = col_smem(h, SW);
     ensure_smem((const void*)k_dt_cols<SW>, smem);
     const int grid = (w + SW - 1) / SW;
+    // vector staging needs every strip row start aligned: planes (workspace) and the
+    // caller's guide / flow planes
+    const uintptr_t al = (uintptr_t)guide | (uintptr_t)Fu | (uintptr_t)Fv;
+    const int vec = (w % SW == 0) && (w % 4 == 0) && (al % 4 == 0) &&
+                    (((uintptr_t)Fu | (uintptr_t)Fv) % 16 == 0);
     note_launch();
-    k_dt_cols<SW><<<grid, kNT, smem, s>>>(P0, P1, P2, guide, w, h, L, lut, final_pass, eps, Fu,
-                                          Fv);
+    k_dt_cols<SW><<<grid, kNT, smem, s>>>(P0, P1, P2, guide, w, h, L, vec, lut, final_pass, eps,
+                                          Fu, Fv);
 }
 
 }  // namespace
@@ -476,17 +511,17 @@ void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, doub
     ensure_smem((const void*)k_dt_rows<true>, rs);
     ensure_smem((const void*)k_dt_rows<false>, rs);
     const int sw = pick_sw(h);
+    const int gmode = ((uintptr_t)guide % 16 == 0 && w % 16 == 0) ? 2
+                      : (((uintptr_t)guide % 4 == 0 && w % 4 == 0) ? 1 : 0);
     for (int i = 0; i < iters; i++) {
         const DtLut lut = make_lut(sigma_s, sigma_r, iters, i);
         note_launch();
         if (i == 0)
-            k_dt_rows<true><<<h, kNT, rs, s>>>(P0, P1, P2, guide, w, h, Lr, lut, fc);
+            k_dt_rows<true><<<h, kNT, rs, s>>>(P0, P1, P2, guide, w, h, Lr, gmode, lut, fc);
         else
-            k_dt_rows<false><<<h, kNT, rs, s>>>(P0, P1, P2, guide, w, h, Lr, lut, fc);
+            k_dt_rows<false><<<h, kNT, rs, s>>>(P0, P1, P2, guide, w, h, Lr, gmode, lut, fc);
         const int fin = i == iters - 1;
-        if (sw == 8)
-            launch_cols<8>(P0, P1, P2, guide, w, h, lut, fin, (float)flow_eps, flow_u, flow_v, s);
-        else if (sw == 4)
+        if (sw == 4)
             launch_cols<4>(P0, P1, P2, guide, w, h, lut, fin, (float)flow_eps, flow_u, flow_v, s);
         else
             launch_cols<2>(P0, P1, P2, guide, w, h, lut, fin, (float)flow_eps, flow_u, flow_v, s);

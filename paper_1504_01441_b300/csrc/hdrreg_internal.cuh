@@ -97,10 +97,13 @@ __device__ inline bool weed_sample(uint64_t seed, long long it, int nv, int pick
 }
 
 // Gaussian elimination with partial pivoting on an 8x8 system (first row of
-// largest |a_ik| is the pivot), then back substitution; each operation one
-// binary64 rounding. Returns 0, or 1 if a pivot magnitude is below tol.
+// largest |a_ik| is the pivot); each pivot is inverted once, factors are
+// a_ik * (1/a_kk), back substitution subtracts in increasing column order and
+// multiplies by the stored reciprocal; each operation one binary64 rounding.
+// Returns 0, or 1 if a pivot magnitude is below tol.
 __device__ inline int solve8(double (&A)[8][8], double (&b)[8], double (&x)[8], double tol)
 {
+    double inv[8];
     for (int k = 0; k < 8; k++) {
         int piv = k;
         double best = fabs(A[k][k]);
@@ -122,8 +125,9 @@ __device__ inline int solve8(double (&A)[8][8], double (&b)[8], double (&x)[8], 
             b[k] = b[piv];
             b[piv] = t;
         }
+        inv[k] = ddiv(1.0, A[k][k]);
         for (int i = k + 1; i < 8; i++) {
-            const double f = ddiv(A[i][k], A[k][k]);
+            const double f = dmul(A[i][k], inv[k]);
             for (int j = k + 1; j < 8; j++) A[i][j] = dsub(A[i][j], dmul(f, A[k][j]));
             b[i] = dsub(b[i], dmul(f, b[k]));
         }
@@ -131,25 +135,57 @@ __device__ inline int solve8(double (&A)[8][8], double (&b)[8], double (&x)[8], 
     for (int k = 7; k >= 0; k--) {
         double s = b[k];
         for (int j = k + 1; j < 8; j++) s = dsub(s, dmul(A[k][j], x[j]));
-        x[k] = ddiv(s, A[k][k]);
+        x[k] = dmul(s, inv[k]);
     }
     return 0;
 }
 
-// Division-free inlier predicate of the weeding filter (reprojection of p by H
-// within eps pixels of q, multiplied through by (2D)^2, D > 0). xn, yn are the
-// normalized corner coordinates, qxc = 2 q_x - (w-1), qyc = 2 q_y - (h-1).
-__device__ __forceinline__ bool is_inlier(const double* H, double xn, double yn, double qxc,
-                                          double qyc, double W, double eps2x)
+// Smallest power of two >= w: the scale S of the coordinates x~ = (2x - (w-1)) / S
+// in which the weeding and level-fit systems are solved (the division is exact).
+__host__ __device__ inline int pow2_scale(int w)
 {
-    const double X = dadd(dadd(dmul(H[0], xn), dmul(H[1], yn)), H[2]);
-    const double Y = dadd(dadd(dmul(H[3], xn), dmul(H[4], yn)), H[5]);
-    const double D = dadd(dadd(dmul(H[6], xn), dmul(H[7], yn)), H[8]);
-    const double ex = dsub(dmul(X, W), dmul(qxc, D));
-    const double ey = dsub(dmul(Y, W), dmul(qyc, D));
+    int s = 1;
+    while (s < w) s <<= 1;
+    return s;
+}
+
+// Division-free inlier predicate of the weeding filter for a homography written in
+// the S-scaled coordinates: reprojection of p within eps pixels of q, multiplied
+// through by (2D)^2 with D > 0. x, y: S-scaled corner; qxc = 2 q_x - (w-1), qyc.
+__device__ __forceinline__ bool is_inlier(const double* H, double x, double y, double qxc,
+                                          double qyc, double S, double eps2x)
+{
+    const double X = dadd(dadd(dmul(H[0], x), dmul(H[1], y)), H[2]);
+    const double Y = dadd(dadd(dmul(H[3], x), dmul(H[4], y)), H[5]);
+    const double D = dadd(dadd(dmul(H[6], x), dmul(H[7], y)), H[8]);
+    const double ex = dsub(dmul(X, S), dmul(qxc, D));
+    const double ey = dsub(dmul(Y, S), dmul(qyc, D));
     const double lhs = dadd(dmul(ex, ex), dmul(ey, ey));
     const double t = dmul(eps2x, D);
     return D > 0.0 && lhs <= dmul(t, t);
+}
+
+// ------------------------------------------------- asynchronous global->shared
+// cp.async copies land in shared memory without a register round trip, so a
+// thread can keep all of its staging copies in flight at once.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // ----------------------------------------------------------------- launchers
@@ -182,7 +218,8 @@ void launch_local_search(const uint8_t* ref, const uint8_t* src, const double* H
 struct WeedWs {  // workspace of the weeding step
     int32_t* list;      // n: valid tile indices in tile order
     int32_t* count;     // 1: number of valid tiles
-    double* coords;     // 4n: x_n, y_n, x_qc, y_qc per valid match
+    double* coords;     // 4n: x~, y~, x_qc, y_qc per valid match (binary64, exact)
+    float4* coords32;   // n: x~, y~, x_qc / S, y_qc / S (FP32, exact for w < 2^23)
 };
 size_t weed_ws_bytes(int n);
 WeedWs weed_ws_carve(void* base, int n);

@@ -4,9 +4,11 @@
 // Weeding: one warp per iteration. Lane 0 draws the 4 samples from the
 // counter-based stream (so iterations are independent and the union over any
 // split of the iteration range equals one run, Sec. 2.3) and solves the 4-point
-// system; all lanes test the valid matches with the division-free FP64
-// predicate (bit-identical to the oracle's written order) and accumulate the
-// count with ballots; accepted iterations OR their inlier bits into the mask.
+// system in binary64; all lanes test the valid matches with an FP32 filter whose
+// forward error bound certifies the decision, falling back to the division-free
+// binary64 predicate (the oracle's written order) only where the interval
+// straddles the threshold, so the mask is bit-identical while the FP64 units
+// (a small fraction of the FP32 rate on this part) are almost never used.
 // Fit: one CTA reduces the exact integer normal equations (int128) and one
 // thread solves the 8x8 system in the prescribed FP64 order.
 #include "hdrreg_internal.cuh"
@@ -16,7 +18,7 @@ namespace hdrreg {
 size_t weed_ws_bytes(int n)
 {
     const size_t nn = n > 0 ? (size_t)n : 1;
-    return align_up(nn * 4, 256) + 256 + align_up(nn * 32, 256);
+    return align_up(nn * 4, 256) + 256 + align_up(nn * 32, 256) + align_up(nn * 16, 256);
 }
 
 WeedWs weed_ws_carve(void* base, int n)
@@ -29,6 +31,8 @@ WeedWs weed_ws_carve(void* base, int n)
     w.count = reinterpret_cast<int32_t*>(p);
     p += 256;
     w.coords = reinterpret_cast<double*>(p);
+    p += align_up(nn * 32, 256);
+    w.coords32 = reinterpret_cast<float4*>(p);
     return w;
 }
 
@@ -43,7 +47,8 @@ __global__ void __launch_bounds__(1024) k_weed_compact(const int32_t* __restrict
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) base_s = 0;
     __syncthreads();
-    const double W = (double)w;
+    const double S = (double)pow2_scale(w);
+    const float Sf = (float)S;
     for (int start = 0; start < n; start += 1024) {
         const int t = start + tid;
         const bool f = t < n && valid[t];
@@ -55,10 +60,14 @@ __global__ void __launch_bounds__(1024) k_weed_compact(const int32_t* __restrict
         off += __popc(bal & ((1u << lane) - 1u));
         if (f) {
             ws.list[off] = t;
-            ws.coords[4 * off + 0] = norm_coord(corner_xy[2 * t], w, W);
-            ws.coords[4 * off + 1] = norm_coord(corner_xy[2 * t + 1], h, W);
-            ws.coords[4 * off + 2] = (double)(2 * match_xy[2 * t] - (w - 1));
-            ws.coords[4 * off + 3] = (double)(2 * match_xy[2 * t + 1] - (h - 1));
+            const int xc = 2 * corner_xy[2 * t] - (w - 1), yc = 2 * corner_xy[2 * t + 1] - (h - 1);
+            const int qx = 2 * match_xy[2 * t] - (w - 1), qy = 2 * match_xy[2 * t + 1] - (h - 1);
+            ws.coords[4 * off + 0] = ddiv((double)xc, S);
+            ws.coords[4 * off + 1] = ddiv((double)yc, S);
+            ws.coords[4 * off + 2] = (double)qx;
+            ws.coords[4 * off + 3] = (double)qy;
+            ws.coords32[off] = make_float4((float)xc / Sf, (float)yc / Sf, (float)qx / Sf,
+                                           (float)qy / Sf);
         }
         __syncthreads();
         if (tid == 0) {
@@ -86,7 +95,7 @@ __global__ void __launch_bounds__(kWeedWarps * 32) k_weed_iters(
     if (it >= it1) return;
     const int nv = *ws.count;
     if (nv < 4) return;
-    const double W = (double)w;
+    const double S = (double)pow2_scale(w);
     if (lane == 0) {
         int pick[4];
         int ok = weed_sample(seed, it, nv, pick);
@@ -96,10 +105,8 @@ __global__ void __launch_bounds__(kWeedWarps * 32) k_weed_iters(
                 for (int c = 0; c < 8; c++) A[r][c] = 0.0;
             for (int k = 0; k < 4; k++) {
                 const double* cc = ws.coords + 4 * pick[k];
-                const int t = ws.list[pick[k]];
                 const double xx = cc[0], yy = cc[1];
-                const double u = norm_coord(match_xy[2 * t], w, W);
-                const double v = norm_coord(match_xy[2 * t + 1], h, W);
+                const double u = ddiv(cc[2], S), v = ddiv(cc[3], S);
                 A[2 * k][0] = xx;
                 A[2 * k][1] = yy;
                 A[2 * k][2] = 1.0;
@@ -124,8 +131,22 @@ __global__ void __launch_bounds__(kWeedWarps * 32) k_weed_iters(
     __syncwarp();
     if (!ok_s[warp]) return;
     double Hr[9];
-    for (int k = 0; k < 9; k++) Hr[k] = Hs[warp][k];
+    float hf[9], ha[9];
+    for (int k = 0; k < 9; k++) {
+        Hr[k] = Hs[warp][k];
+        hf[k] = (float)Hr[k];
+        ha[k] = fabsf(hf[k]);
+    }
     const double eps2x = dmul(2.0, eps);
+    // FP32 filter with a forward error bound (u = 2^-24): the values X, Y, D of the
+    // predicate, computed from FP32-rounded H and exact FP32 coordinates, are within
+    // 4u * (|h0 x| + |h1 y| + |h2|) of the exact ones; the residual interval follows.
+    // Decisions whose interval does not straddle the threshold equal the exact
+    // predicate and hence the binary64 one; the rest are evaluated in binary64.
+    const float kB = 4.0f * 5.9604645e-8f;
+    const float u1 = 1.01f * 5.9604645e-8f;
+    const float cth = (float)(((2.0 * eps) / S) * ((2.0 * eps) / S));
+    const float lo_f = 1.0f - 6.0f * 5.9604645e-8f, hi_f = 1.0f + 6.0f * 5.9604645e-8f;
     const int nw = (nv + 31) / 32;
     uint32_t* bw = bal_words + warp * ((n + 31) / 32);
     int cnt = 0;
@@ -133,8 +154,30 @@ __global__ void __launch_bounds__(kWeedWarps * 32) k_weed_iters(
         const int k = 32 * j + lane;
         bool in = false;
         if (k < nv) {
-            const double* cc = ws.coords + 4 * k;
-            in = is_inlier(Hr, cc[0], cc[1], cc[2], cc[3], W, eps2x);
+            const float4 c = ws.coords32[k];
+            const float ax = fabsf(c.x), ay = fabsf(c.y);
+            const float X = fmaf(hf[0], c.x, fmaf(hf[1], c.y, hf[2]));
+            const float Y = fmaf(hf[3], c.x, fmaf(hf[4], c.y, hf[5]));
+            const float D = fmaf(hf[6], c.x, fmaf(hf[7], c.y, hf[8]));
+            const float BX = kB * fmaf(ha[0], ax, fmaf(ha[1], ay, ha[2]));
+            const float BY = kB * fmaf(ha[3], ax, fmaf(ha[4], ay, ha[5]));
+            const float BD = kB * fmaf(ha[6], ax, fmaf(ha[7], ay, ha[8]));
+            const float ex = fmaf(-c.z, D, X), ey = fmaf(-c.w, D, Y);
+            const float Ex = fmaf(fabsf(c.z), BD, BX) + u1 * fabsf(ex);
+            const float Ey = fmaf(fabsf(c.w), BD, BY) + u1 * fabsf(ey);
+            const float hx = fabsf(ex) + Ex, hy = fabsf(ey) + Ey;
+            const float lx = fmaxf(fabsf(ex) - Ex, 0.f), ly = fmaxf(fabsf(ey) - Ey, 0.f);
+            const float Lhi = fmaf(hx, hx, hy * hy) * hi_f;
+            const float Llo = fmaf(lx, lx, ly * ly) * lo_f;
+            const float Dlo = D - BD, Dhi = fabsf(D) + BD;
+            const bool sure_in = Dlo > 0.f && Lhi < cth * (Dlo * Dlo) * lo_f;
+            const bool sure_out = (D + BD <= 0.f) || Llo > cth * (Dhi * Dhi) * hi_f;
+            if (sure_in) {
+                in = true;
+            } else if (!sure_out) {
+                const double* cc = ws.coords + 4 * k;
+                in = is_inlier(Hr, cc[0], cc[1], cc[2], cc[3], S, eps2x);
+            }
         }
         const unsigned b = __ballot_sync(0xffffffffu, in);
         cnt += __popc(b);
@@ -212,13 +255,27 @@ __global__ void __launch_bounds__(256) k_fit(const int32_t* __restrict__ corner_
     __int128 acc[kFitSums];
     for (int k = 0; k < kFitSums; k++) acc[k] = 0;
     int cnt = 0;
-    for (int t = tid; t < n; t += 256) {
-        if (!((mask[t >> 5] >> (t & 31)) & 1u)) continue;
-        long long s[kFitSums];
-        fit_terms(2LL * corner_xy[2 * t] - (w - 1), 2LL * corner_xy[2 * t + 1] - (h - 1),
-                  2LL * match_xy[2 * t] - (w - 1), 2LL * match_xy[2 * t + 1] - (h - 1), s);
-        for (int k = 0; k < kFitSums; k++) acc[k] += (__int128)s[k];
-        cnt++;
+    // 4 tiles per round: the mask words and coordinates are independent loads
+    for (int t0 = tid; t0 < n; t0 += 4 * 256) {
+        int2 pc[4], qc[4];
+        bool on[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int t = t0 + k * 256;
+            on[k] = t < n && ((__ldg(mask + (t >> 5)) >> (t & 31)) & 1u);
+            const int tt = t < n ? t : 0;
+            pc[k] = make_int2(__ldg(corner_xy + 2 * tt), __ldg(corner_xy + 2 * tt + 1));
+            qc[k] = make_int2(__ldg(match_xy + 2 * tt), __ldg(match_xy + 2 * tt + 1));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (!on[k]) continue;
+            long long s[kFitSums];
+            fit_terms(2LL * pc[k].x - (w - 1), 2LL * pc[k].y - (h - 1), 2LL * qc[k].x - (w - 1),
+                      2LL * qc[k].y - (h - 1), s);
+            for (int j = 0; j < kFitSums; j++) acc[j] += (__int128)s[j];
+            cnt++;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -270,18 +327,29 @@ __global__ void __launch_bounds__(256) k_fit(const int32_t* __restrict__ corner_
             for (int c = 0; c < 8; c++) M[r][c] = rows[r][c];
         const __int128 rhs[8] = {Sxu, Syu, Su, Sxv, Syv, Sv, -Sxr, -Syr};
         const int e[8] = {1, 1, 0, 1, 1, 0, 2, 2};
-        double Wp[6];
-        Wp[0] = 1.0;
-        for (int k = 1; k < 6; k++) Wp[k] = dmul(Wp[k - 1], (double)w);
+        const int s2 = pow2_scale(w);
+        int lg = 0;
+        while ((1 << lg) < s2) lg++;
+        double pw[6];
+        for (int k = 0; k < 6; k++) pw[k] = ldexp(1.0, -lg * k);  // exact powers of two
         double A[8][8], b[8], x[8];
         for (int r = 0; r < 8; r++) {
-            for (int c = 0; c < 8; c++) A[r][c] = ddiv(i128_to_double(M[r][c]), Wp[e[r] + e[c]]);
-            b[r] = ddiv(i128_to_double(rhs[r]), Wp[e[r] + 1]);
+            for (int c = 0; c < 8; c++) A[r][c] = dmul(i128_to_double(M[r][c]), pw[e[r] + e[c]]);
+            b[r] = dmul(i128_to_double(rhs[r]), pw[e[r] + 1]);
         }
         if (solve8(A, b, x, 1e-12)) {
             st = 2;
         } else {
-            for (int k = 0; k < 8; k++) H_out[k] = x[k];
+            const double S = (double)s2, W = (double)w;
+            const double WS = ddiv(W, S);  // exact
+            H_out[0] = x[0];
+            H_out[1] = x[1];
+            H_out[2] = ddiv(dmul(x[2], S), W);
+            H_out[3] = x[3];
+            H_out[4] = x[4];
+            H_out[5] = ddiv(dmul(x[5], S), W);
+            H_out[6] = dmul(x[6], WS);
+            H_out[7] = dmul(x[7], WS);
             H_out[8] = 1.0;
         }
     }

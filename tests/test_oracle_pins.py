@@ -651,7 +651,7 @@ def test_inlier_test_matches_reprojection_distance(orc):
         d2 = (xs - q[0]) ** 2 + (ys - q[1]) ** 2
         if abs(d2 - 1.5 ** 2) < 1e-9:
             continue                         # on the boundary: rounding decides either way
-        assert orc.is_inlier(H, p, q, w, h, 1.5) == (ok and d2 <= 1.5 ** 2)
+        assert orc.is_inlier(orc.to_scaled(H, w), p, q, w, h, 1.5) == (ok and d2 <= 1.5 ** 2)
         n_checked += 1
     assert n_checked > 2900
 
