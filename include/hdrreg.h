@@ -199,6 +199,28 @@ hdrreg_status hdrreg_weed(const int32_t* corner_xy, const int32_t* match_xy, con
                           int iter_begin, int iter_end, uint32_t* mask_bits, void* workspace,
                           size_t ws_bytes, void* stream);
 
+/* ------------------------------------ a6 without caller-provided scratch
+ * The paper has no counterpart: this is hdrreg_weed for callers that cannot
+ * allocate device memory and therefore have no workspace to pass -- code that
+ * runs while a stream is being captured in a mode that forbids cudaMalloc,
+ * real-time pipelines that allow no allocation after start-up, or plugins
+ * whose host owns all device memory. Same inputs, output and result as
+ * hdrreg_weed; it allocates nothing and calls no allocating routine.
+ * Its scratch is a fixed array inside this library (about 416 KB on every GPU
+ * that loads the library, kept until the process exits), so n must not exceed
+ * HDRREG_WEED_STATIC_MAX_TILES (larger n returns HDRREG_E_INVALID_ARG and
+ * launches nothing). The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture. All calls share the array: calls whose kernels overlap on the GPU
+ * (other streams or host threads on the same device) race and must be
+ * serialized by the caller.
+ */
+#define HDRREG_WEED_STATIC_MAX_TILES 8192
+hdrreg_status hdrreg_weed_static(const int32_t* corner_xy, const int32_t* match_xy,
+                                 const uint8_t* valid, int n, int w, int h,
+                                 const hdrreg_params* p, uint64_t seed, int iter_begin,
+                                 int iter_end, uint32_t* mask_bits, void* stream);
+
 /* ---------------------------------------------------------- a7: level fit
  * Least-squares homography (DLT, h22 = 1, normalized coordinates) over the
  * matches set in mask_bits (Sec. 2.2: H^l from the level's corners and

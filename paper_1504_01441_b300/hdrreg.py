@@ -25,7 +25,8 @@ EXPORTS = [
     "hdrreg_num_levels",
     "hdrreg_validate_params", "hdrreg_num_tiles", "hdrreg_normalize_workspace_size",
     "hdrreg_normalize_exposure", "hdrreg_pyramid_bytes", "hdrreg_build_pyramid",
-    "hdrreg_local_search", "hdrreg_weed_workspace_size", "hdrreg_weed", "hdrreg_fit_homography",
+    "hdrreg_local_search", "hdrreg_weed_workspace_size", "hdrreg_weed", "hdrreg_weed_static",
+    "hdrreg_fit_homography",
     "hdrreg_flow_workspace_size", "hdrreg_flow_upsample", "hdrreg_warp", "hdrreg_merge",
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
 ]
@@ -104,6 +105,8 @@ def lib():
         L.hdrreg_weed_workspace_size.argtypes = [i]
         L.hdrreg_weed.argtypes = [vp, vp, vp, i, i, i, C.POINTER(Params), C.c_uint64, i, i, vp,
                                   vp, sz, vp]
+        L.hdrreg_weed_static.argtypes = [vp, vp, vp, i, i, i, C.POINTER(Params), C.c_uint64, i,
+                                         i, vp, vp]
         L.hdrreg_fit_homography.argtypes = [vp, vp, vp, i, i, i, vp, vp, vp, vp]
         L.hdrreg_flow_workspace_size.restype = sz
         L.hdrreg_flow_workspace_size.argtypes = [i, i]
