@@ -1,0 +1,790 @@
+// Row a8, fast path: the domain-transform passes with register-resident
+// segments and TMA staging (Sec. 2.4; Gastal and Oliveira 2011).
+//
+// Both passes run the same chunked scan as the basic kernels in flow.cu, but
+// every thread keeps its whole segment of the three planes (P_u, P_v, N) and
+// the segment's link weights in registers, so the four sweeps (forward local,
+// forward carry, backward local, backward carry) are pure FMA chains.
+//  * Row pass: persistent CTAs walk the rows with two buffers; rows are staged
+//    with 1D bulk copies (cp.async.bulk, mbarrier completion) and written back
+//    the same way; the first pass builds its planes from the corner list.
+//  * Column pass: tiles of 32 columns x 64 rows in three phases (tile maps,
+//    per-column carry chain, tile apply); tiles move with 2D tensor copies
+//    (cp.async.bulk.tensor, 32 x 64 boxes of 128-byte rows).
+// Link weights: w_link(r) = a_i^(1 + (sigma_s/sigma_r)|g_r - g_{r-1}|/255) from the
+// 256-entry table, and 0 across the frame ends, so J[0] = x[0] and K[n-1] = J[n-1]
+// without branches. Every wait on a barrier is bounded; a timeout sets the
+// error word and the kernel drains its copies and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "hdrreg_internal.cuh"
+
+namespace hdrreg {
+
+namespace {
+
+constexpr int kRowNT = 256;
+constexpr uint32_t kWaitIters = 1u << 22;
+
+struct Aff {  // y -> A y + B, shared A for the three planes
+    float A, B0, B1, B2;
+};
+
+__device__ __forceinline__ Aff compose(const Aff& first, const Aff& second)
+{
+    return Aff{second.A * first.A, fmaf(second.A, first.B0, second.B0),
+               fmaf(second.A, first.B1, second.B1), fmaf(second.A, first.B2, second.B2)};
+}
+
+template <bool kUp>
+__device__ __forceinline__ Aff shfl_aff(const Aff& a, int d)
+{
+    if (kUp)
+        return Aff{__shfl_up_sync(0xffffffffu, a.A, d), __shfl_up_sync(0xffffffffu, a.B0, d),
+                   __shfl_up_sync(0xffffffffu, a.B1, d), __shfl_up_sync(0xffffffffu, a.B2, d)};
+    return Aff{__shfl_down_sync(0xffffffffu, a.A, d), __shfl_down_sync(0xffffffffu, a.B0, d),
+               __shfl_down_sync(0xffffffffu, a.B1, d), __shfl_down_sync(0xffffffffu, a.B2, d)};
+}
+
+__device__ __forceinline__ int absdiff(int a, int b) { return a > b ? a - b : b - a; }
+
+// ---------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false after kWaitIters polls (about a second at most)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kWaitIters; i++) {
+        if (mbar_try(bar, parity)) return true;
+        if (i > 16) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(su32(src)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     map),
+                 "r"(x), "r"(y), "r"(su32(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ------------------------------------------------ register-resident sweeps
+// v[k][i]: element i of the thread's segment in plane k; wl[i]: weight of the link
+// into element i (from i-1); wl[L]: link from the segment's last element to the
+// next segment's first. The local sweeps start from a zero carry and return the
+// segment's affine map; the carry sweeps add prefix (suffix) products times the
+// scanned carry.
+template <int LM>
+__device__ __forceinline__ Aff sweep_fwd(float (&v)[3][LM], const float (&wl)[LM + 1], int L)
+{
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f, A = 1.f;
+#pragma unroll
+    for (int i = 0; i < LM; i++) {
+        if (i < L) {
+            const float wt = wl[i];
+            y0 = fmaf(wt, y0 - v[0][i], v[0][i]);
+            y1 = fmaf(wt, y1 - v[1][i], v[1][i]);
+            y2 = fmaf(wt, y2 - v[2][i], v[2][i]);
+            A *= wt;
+            v[0][i] = y0;
+            v[1][i] = y1;
+            v[2][i] = y2;
+        }
+    }
+    return Aff{A, y0, y1, y2};
+}
+
+template <int LM>
+__device__ __forceinline__ void carry_fwd(float (&v)[3][LM], const float (&wl)[LM + 1], int L,
+                                          const Aff& c)
+{
+    float P = 1.f;
+#pragma unroll
+    for (int i = 0; i < LM; i++) {
+        if (i < L) {
+            P *= wl[i];
+            v[0][i] = fmaf(P, c.B0, v[0][i]);
+            v[1][i] = fmaf(P, c.B1, v[1][i]);
+            v[2][i] = fmaf(P, c.B2, v[2][i]);
+        }
+    }
+}
+
+template <int LM>
+__device__ __forceinline__ Aff sweep_bwd(float (&v)[3][LM], const float (&wl)[LM + 1], int L)
+{
+    float k0 = 0.f, k1 = 0.f, k2 = 0.f, A = 1.f;
+#pragma unroll
+    for (int i = LM - 1; i >= 0; i--) {
+        if (i < L) {
+            const float wt = (i == L - 1) ? wl[LM] : wl[i + 1];
+            k0 = fmaf(wt, k0 - v[0][i], v[0][i]);
+            k1 = fmaf(wt, k1 - v[1][i], v[1][i]);
+            k2 = fmaf(wt, k2 - v[2][i], v[2][i]);
+            A *= wt;
+            v[0][i] = k0;
+            v[1][i] = k1;
+            v[2][i] = k2;
+        }
+    }
+    return Aff{A, k0, k1, k2};
+}
+
+template <int LM>
+__device__ __forceinline__ void carry_bwd(float (&v)[3][LM], const float (&wl)[LM + 1], int L,
+                                          const Aff& c)
+{
+    float S = 1.f;
+#pragma unroll
+    for (int i = LM - 1; i >= 0; i--) {
+        if (i < L) {
+            S *= (i == L - 1) ? wl[LM] : wl[i + 1];
+            v[0][i] = fmaf(S, c.B0, v[0][i]);
+            v[1][i] = fmaf(S, c.B1, v[1][i]);
+            v[2][i] = fmaf(S, c.B2, v[2][i]);
+        }
+    }
+}
+
+// Exclusive scan over segments ordered by lane (stride `st` lanes within a warp),
+// then by warp; kUp = forward order, otherwise reverse order. `tot` holds one map
+// per (warp, column). Returns the composed map of all earlier segments.
+template <bool kUp, int kWarps, int kCols>
+__device__ __forceinline__ Aff seg_scan(Aff mine, Aff (*tot)[kCols], int col)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int st = kCols;            // lanes between consecutive segments of one column
+    constexpr int nseg = 32 / kCols;     // segments per warp
+    const int sl = lane / kCols;
+    Aff inc = mine;
+#pragma unroll
+    for (int d = 1; d < nseg; d <<= 1) {
+        const Aff o = shfl_aff<kUp>(inc, d * st);
+        if (kUp ? (sl >= d) : (sl + d < nseg)) inc = compose(o, inc);
+    }
+    Aff exc = shfl_aff<kUp>(inc, st);
+    if (kUp ? (sl == 0) : (sl == nseg - 1)) exc = Aff{1.f, 0.f, 0.f, 0.f};
+    if (kUp ? (sl == nseg - 1) : (sl == 0)) tot[warp][col] = inc;
+    __syncthreads();
+    Aff pre{1.f, 0.f, 0.f, 0.f};
+    if (kUp) {
+        for (int k = 0; k < warp; k++) pre = compose(pre, tot[k][col]);
+    } else {
+        for (int k = kWarps - 1; k > warp; k--) pre = compose(pre, tot[k][col]);
+    }
+    __syncthreads();
+    return compose(pre, exc);
+}
+
+// ---------------------------------------------------------------- row pass
+// Persistent, double-buffered row pass: each CTA walks
+// rows y = blockIdx.x + k * gridDim.x; while row k computes, row k+1 is loading
+// into the other buffer and row k-1 is storing.
+template <int LM, bool kSparse>
+__global__ void __launch_bounds__(kRowNT, 3) k_dt_rows_pipe(float* __restrict__ P0,
+                                                         float* __restrict__ P1,
+                                                         float* __restrict__ P2,
+                                                         const uint8_t* __restrict__ guide,
+                                                         int w, int h, DtLut lut_in,
+                                                         FlowCorners fc, int* err)
+{
+    extern __shared__ __align__(128) float sm[];
+    __shared__ float lut[256];
+    __shared__ Aff tot[kRowNT / 32][1];
+    __shared__ __align__(8) uint64_t bar[2];
+    constexpr int Wp = kRowNT * LM;          // floats per plane buffer
+    constexpr int kBuf = 3 * Wp + Wp / 4;    // floats per buffer (3 planes + guide bytes)
+    const int tid = threadIdx.x;
+    lut[tid] = lut_in.w[tid];
+    if (tid == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+    }
+    __syncthreads();
+    const uint32_t bytes = (kSparse ? 0u : 3u * (uint32_t)w * 4u) + (uint32_t)w;
+    auto issue = [&](int y, int b) {
+        if (tid == 0) {
+            float* B = sm + b * kBuf;
+            const size_t row = (size_t)y * w;
+            mbar_expect(&bar[b], bytes);
+            if (!kSparse) {
+                bulk_load(B, P0 + row, w * 4, &bar[b]);
+                bulk_load(B + Wp, P1 + row, w * 4, &bar[b]);
+                bulk_load(B + 2 * Wp, P2 + row, w * 4, &bar[b]);
+            }
+            bulk_load(B + 3 * Wp, guide + row, w, &bar[b]);
+        }
+    };
+    uint32_t ph0 = 0, ph1 = 0;
+    int y = blockIdx.x;
+    if (y < h) issue(y, 0);
+    for (int k = 0; y < h; y += gridDim.x, k++) {
+        const int b = k & 1;
+        const int yn = y + gridDim.x;
+        if (yn < h) {
+            if (tid == 0) bulk_wait_read();  // the store of row k-1 has left buffer 1-b
+            issue(yn, 1 - b);
+        }
+        const bool ok = __syncthreads_and(mbar_wait(&bar[b], b ? ph1 : ph0));
+        if (b) ph1 ^= 1u; else ph0 ^= 1u;
+        if (!ok) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait(&bar[1 - b], b ? ph0 : ph1);
+                bulk_wait_read();
+            }
+            return;
+        }
+        float* s0 = sm + b * kBuf;
+        float* s1 = s0 + Wp;
+        float* s2 = s0 + 2 * Wp;
+        const uint8_t* g = reinterpret_cast<const uint8_t*>(s0 + 3 * Wp);
+        const int x0 = tid * LM;
+        if (kSparse) {  // the planes of the first pass: residuals at this row's corners, else 0
+#pragma unroll
+            for (int i = 0; i < LM; i++) {
+                s0[x0 + i] = 0.f;
+                s1[x0 + i] = 0.f;
+                s2[x0 + i] = 0.f;
+            }
+            __syncthreads();
+            const int ty = y / fc.tile;
+            if (ty < fc.nty) {
+                for (int tx = tid; tx < fc.ntx; tx += kRowNT) {
+                    const int t = ty * fc.ntx + tx;
+                    if (!((fc.mask[t >> 5] >> (t & 31)) & 1u)) continue;
+                    if (fc.corner_xy[2 * t + 1] != y) continue;
+                    const int cx = fc.corner_xy[2 * t];
+                    double bx = (double)cx, by = (double)y;
+                    if (!fc.full) {
+                        double xs, ys;
+                        if (!project_px(fc.H, cx, y, w, h, xs, ys)) continue;
+                        bx = xs;
+                        by = ys;
+                    }
+                    s0[cx] = (float)((double)fc.match_xy[2 * t] - bx);
+                    s1[cx] = (float)((double)fc.match_xy[2 * t + 1] - by);
+                    s2[cx] = 1.f;
+                }
+            }
+            __syncthreads();
+        }
+        float v[3][LM];
+        float wl[LM + 1];
+#pragma unroll
+        for (int i = 0; i < LM; i++) {
+            const int x = x0 + i;
+            const bool in = x < w;
+            v[0][i] = in ? s0[x] : 0.f;
+            v[1][i] = in ? s1[x] : 0.f;
+            v[2][i] = in ? s2[x] : 0.f;
+            wl[i] = (in && x > 0) ? lut[absdiff(g[x], g[x - 1])] : 0.f;
+        }
+        {
+            const int x = x0 + LM;
+            wl[LM] = (x < w) ? lut[absdiff(g[x], g[x - 1])] : 0.f;
+        }
+        Aff m = sweep_fwd<LM>(v, wl, LM);
+        Aff c = seg_scan<true, kRowNT / 32, 1>(m, tot, 0);
+        carry_fwd<LM>(v, wl, LM, c);
+        m = sweep_bwd<LM>(v, wl, LM);
+        c = seg_scan<false, kRowNT / 32, 1>(m, tot, 0);
+        carry_bwd<LM>(v, wl, LM, c);
+#pragma unroll
+        for (int i = 0; i < LM; i++) {
+            const int x = x0 + i;
+            if (x < w) {
+                s0[x] = v[0][i];
+                s1[x] = v[1][i];
+                s2[x] = v[2][i];
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            const size_t row = (size_t)y * w;
+            bulk_store(P0 + row, s0, w * 4);
+            bulk_store(P1 + row, s1, w * 4);
+            bulk_store(P2 + row, s2, w * 4);
+            bulk_commit();
+        }
+    }
+    if (tid == 0) bulk_wait_read();
+}
+
+// ------------------------------------------------------------- column pass
+// Three phases over tiles of 32 columns x 64 rows (one lane per column, eight
+// 8-row segments = eight warps per tile):
+//  A) per tile, the forward map (J_bottom = A_f c + B_f) and the backward value
+//     at the tile's top row as a function of both carries,
+//     K_top = K0 + Q c + S c' (c: forward carry entering at the top, c': backward
+//     carry entering at the bottom; Q because the backward pass is linear in J =
+//     J0 + P c);
+//  B) one thread per column chains the carries down and up the tiles;
+//  C) every tile recomputes its sweeps with the exact carries and stores.
+// Tiles never wait on one another; phase C re-reads the tile from L2.
+constexpr int kTW = 32;
+constexpr int kTSeg = 8;
+constexpr int kTLS = 8;
+constexpr int kTR = kTSeg * kTLS;  // 64 rows per tile
+constexpr int kTNT = kTSeg * 32;   // 256 threads
+constexpr int kAgg = 9;            // per (tile, column): A_f, B_f[3], K0[3], Q, S
+constexpr int kCar = 6;            // per (tile, column): c[3], c'[3]
+
+struct ColMaps {
+    CUtensorMap in[3];   // planes, FP32 {w, h}, box {32, 64}
+    CUtensorMap out[3];  // planes, or the flow planes (out[0], out[1]) for the final pass
+    CUtensorMap guide;   // guide, u8 {w, h}, box {32, 66}: the tile plus a row above and below
+};
+
+constexpr int kGRows = kTR + 2;
+constexpr int kTileBuf = (3 * kTR * kTW * 4 + kGRows * kTW + 1023) / 1024 * 1024;  // bytes
+
+struct Aff4 {
+    float A, B0, B1, B2, B3;
+};
+
+__device__ __forceinline__ Aff4 compose4(const Aff4& f, const Aff4& s)
+{
+    return Aff4{s.A * f.A, fmaf(s.A, f.B0, s.B0), fmaf(s.A, f.B1, s.B1), fmaf(s.A, f.B2, s.B2),
+                fmaf(s.A, f.B3, s.B3)};
+}
+
+// Persistent, double-buffered tile pass over items i = tile * ntx + strip.
+// kApply = false: phase A (tile maps to agg_out); true: phase C (apply carries, store).
+template <bool kApply>
+__global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMaps maps, int w,
+                                                   int h, int ntx, int ntile, DtLut lut_in,
+                                                   float* __restrict__ agg_out,
+                                                   const float* __restrict__ car, int final_pass,
+                                                   float flow_eps, int* err)
+{
+    extern __shared__ __align__(1024) uint8_t smt[];
+    __shared__ float lut[256];
+    __shared__ Aff4 agg[kTSeg][kTW];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x, lane = tid & 31, sg = tid >> 5;
+    lut[tid] = lut_in.w[tid];
+    if (tid == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+    }
+    __syncthreads();
+    const int nitems = ntx * ntile;
+    auto issue = [&](int item, int b) {
+        if (tid == 0) {
+            float* P = reinterpret_cast<float*>(smt + b * kTileBuf);
+            uint8_t* G = smt + b * kTileBuf + 3 * kTR * kTW * 4;
+            const int x0 = (item % ntx) * kTW, r0 = (item / ntx) * kTR;
+            mbar_expect(&bar[b], 3u * kTR * kTW * 4u + kGRows * kTW);
+            for (int k = 0; k < 3; k++) tma_load_2d(P + k * kTR * kTW, &maps.in[k], x0, r0, &bar[b]);
+            tma_load_2d(G, &maps.guide, x0, r0 - 1, &bar[b]);
+        }
+    };
+    uint32_t ph0 = 0, ph1 = 0;
+    int item = blockIdx.x;
+    if (item < nitems) issue(item, 0);
+    for (int k = 0; item < nitems; item += gridDim.x, k++) {
+        const int b = k & 1;
+        const int nx = item + gridDim.x;
+        if (nx < nitems) {
+            if (kApply && tid == 0) bulk_wait_read();  // the store of item k-1 left buffer 1-b
+            if (!kApply) __syncthreads();             // all threads are done reading buffer 1-b
+            issue(nx, 1 - b);
+        }
+        const bool ok = __syncthreads_and(mbar_wait(&bar[b], b ? ph1 : ph0));
+        if (b) ph1 ^= 1u; else ph0 ^= 1u;
+        if (!ok) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait(&bar[1 - b], b ? ph0 : ph1);
+                bulk_wait_read();
+            }
+            return;
+        }
+        float* P = reinterpret_cast<float*>(smt + b * kTileBuf);
+        const uint8_t* G = smt + b * kTileBuf + 3 * kTR * kTW * 4;
+        const int x0 = (item % ntx) * kTW, tile = item / ntx, r0 = tile * kTR;
+        // registers: rows r0 + sg*8 + i of column x0 + lane; G row j is global row r0-1+j
+        float v[3][kTLS], wl[kTLS + 1];
+#pragma unroll
+        for (int i = 0; i < kTLS; i++) {
+            const int rr = sg * kTLS + i, r = r0 + rr;
+            const bool in = r < h;
+            v[0][i] = in ? P[(0 * kTR + rr) * kTW + lane] : 0.f;
+            v[1][i] = in ? P[(1 * kTR + rr) * kTW + lane] : 0.f;
+            v[2][i] = in ? P[(2 * kTR + rr) * kTW + lane] : 0.f;
+            wl[i] = (r > 0 && r < h) ? lut[absdiff(G[(rr + 1) * kTW + lane], G[rr * kTW + lane])] : 0.f;
+        }
+        {
+            const int rr = sg * kTLS + kTLS, r = r0 + rr;
+            wl[kTLS] = (r < h) ? lut[absdiff(G[(rr + 1) * kTW + lane], G[rr * kTW + lane])] : 0.f;
+        }
+        const bool colok = x0 + lane < w;
+        const size_t ao = (size_t)(x0 + lane) * kAgg * ntile + tile;  // agg[x][k][t]
+        const size_t co = (size_t)(x0 + lane) * kCar * ntile + tile;  // car[x][k][t]
+        Aff m = sweep_fwd<kTLS>(v, wl, kTLS);
+        agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
+        __syncthreads();
+        if (!kApply) {
+            Aff pre{1.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < sg; q++) {
+                const Aff4 a = agg[q][lane];
+                pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+            }
+            if (sg == kTSeg - 1 && colok) {
+                const Aff f = compose(pre, m);
+                agg_out[ao + 0 * ntile] = f.A;
+                agg_out[ao + 1 * ntile] = f.B0;
+                agg_out[ao + 2 * ntile] = f.B1;
+                agg_out[ao + 3 * ntile] = f.B2;
+            }
+            carry_fwd<kTLS>(v, wl, kTLS, pre);  // v = J0
+            float pv[kTLS];
+            float lp = pre.A;
+#pragma unroll
+            for (int i = 0; i < kTLS; i++) {
+                lp *= wl[i];
+                pv[i] = lp;
+            }
+            __syncthreads();
+            float k0 = 0.f, k1 = 0.f, k2 = 0.f, k3 = 0.f, A = 1.f;
+#pragma unroll
+            for (int i = kTLS - 1; i >= 0; i--) {
+                const float wt = wl[i + 1];
+                k0 = fmaf(wt, k0 - v[0][i], v[0][i]);
+                k1 = fmaf(wt, k1 - v[1][i], v[1][i]);
+                k2 = fmaf(wt, k2 - v[2][i], v[2][i]);
+                k3 = fmaf(wt, k3 - pv[i], pv[i]);
+                A *= wt;
+            }
+            agg[sg][lane] = Aff4{A, k0, k1, k2, k3};
+            __syncthreads();
+            if (sg == 0 && colok) {
+                Aff4 suf{1.f, 0.f, 0.f, 0.f, 0.f};
+                for (int q = kTSeg - 1; q > 0; q--) suf = compose4(suf, agg[q][lane]);
+                const Aff4 t4 = compose4(suf, agg[0][lane]);
+                agg_out[ao + 4 * ntile] = t4.B0;
+                agg_out[ao + 5 * ntile] = t4.B1;
+                agg_out[ao + 6 * ntile] = t4.B2;
+                agg_out[ao + 7 * ntile] = t4.B3;
+                agg_out[ao + 8 * ntile] = t4.A;
+            }
+            __syncthreads();  // agg reused by the next item
+        } else {
+            Aff pre = colok ? Aff{0.f, car[co], car[co + ntile], car[co + 2 * ntile]}
+                            : Aff{0.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < sg; q++) {
+                const Aff4 a = agg[q][lane];
+                pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+            }
+            carry_fwd<kTLS>(v, wl, kTLS, pre);
+            __syncthreads();
+            m = sweep_bwd<kTLS>(v, wl, kTLS);
+            agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
+            __syncthreads();
+            Aff suf = colok ? Aff{0.f, car[co + 3 * ntile], car[co + 4 * ntile], car[co + 5 * ntile]}
+                            : Aff{0.f, 0.f, 0.f, 0.f};
+            for (int q = kTSeg - 1; q > sg; q--) {
+                const Aff4 a = agg[q][lane];
+                suf = compose(suf, Aff{a.A, a.B0, a.B1, a.B2});
+            }
+            carry_bwd<kTLS>(v, wl, kTLS, suf);
+#pragma unroll
+            for (int i = 0; i < kTLS; i++) {
+                const int rr = sg * kTLS + i;
+                if (final_pass) {
+                    const bool okn = v[2][i] >= flow_eps;
+                    P[(0 * kTR + rr) * kTW + lane] = okn ? v[0][i] / v[2][i] : 0.f;
+                    P[(1 * kTR + rr) * kTW + lane] = okn ? v[1][i] / v[2][i] : 0.f;
+                } else {
+                    P[(0 * kTR + rr) * kTW + lane] = v[0][i];
+                    P[(1 * kTR + rr) * kTW + lane] = v[1][i];
+                    P[(2 * kTR + rr) * kTW + lane] = v[2][i];
+                }
+            }
+            fence_async_smem();
+            __syncthreads();  // also: agg reads of this item are done
+            if (tid == 0) {
+                const int np = final_pass ? 2 : 3;
+                for (int q = 0; q < np; q++) tma_store_2d(&maps.out[q], x0, r0, P + q * kTR * kTW);
+                bulk_commit();
+            }
+        }
+    }
+    if (kApply && tid == 0) bulk_wait_read();
+}
+
+// One warp per column; lane = tile (32 tiles per round, carried across rounds):
+// forward carries by an exclusive shuffle scan of the maps (A_f, B_f), then the
+// backward carries by a reverse exclusive scan of (S, K0 + Q c).
+__global__ void __launch_bounds__(256) k_dt_cols_chain(const float* __restrict__ agg, int w,
+                                                      int ntile, float* __restrict__ car)
+{
+    const int x = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (x >= w) return;
+    const float* ag = agg + (size_t)x * kAgg * ntile;  // ag[k * ntile + t]
+    float* ca = car + (size_t)x * kCar * ntile;         // ca[k * ntile + t]
+    Aff run{1.f, 0.f, 0.f, 0.f};  // maps of the tiles before this round
+    for (int t0 = 0; t0 < ntile; t0 += 32) {
+        const int t = t0 + lane;
+        const Aff m = t < ntile ? Aff{ag[t], ag[ntile + t], ag[2 * ntile + t], ag[3 * ntile + t]}
+                                : Aff{1.f, 0.f, 0.f, 0.f};
+        Aff inc = m;
+        for (int d = 1; d < 32; d <<= 1) {
+            const Aff q = shfl_aff<true>(inc, d);
+            if (lane >= d) inc = compose(q, inc);
+        }
+        Aff exc = shfl_aff<true>(inc, 1);
+        if (lane == 0) exc = Aff{1.f, 0.f, 0.f, 0.f};
+        const Aff c = compose(run, exc);
+        if (t < ntile) {
+            ca[t] = c.B0;
+            ca[ntile + t] = c.B1;
+            ca[2 * ntile + t] = c.B2;
+        }
+        run = compose(run, Aff{__shfl_sync(0xffffffffu, inc.A, 31), __shfl_sync(0xffffffffu, inc.B0, 31),
+                               __shfl_sync(0xffffffffu, inc.B1, 31), __shfl_sync(0xffffffffu, inc.B2, 31)});
+    }
+    run = Aff{1.f, 0.f, 0.f, 0.f};  // maps of the tiles after this round, from the bottom
+    for (int rd = (ntile + 31) / 32 - 1; rd >= 0; rd--) {
+        const int t = rd * 32 + lane;
+        Aff m{1.f, 0.f, 0.f, 0.f};
+        if (t < ntile) {
+            const float Q = ag[7 * ntile + t];
+            m = Aff{ag[8 * ntile + t], fmaf(Q, ca[t], ag[4 * ntile + t]),
+                    fmaf(Q, ca[ntile + t], ag[5 * ntile + t]), fmaf(Q, ca[2 * ntile + t], ag[6 * ntile + t])};
+        }
+        Aff inc = m;
+        for (int d = 1; d < 32; d <<= 1) {
+            const Aff q = shfl_aff<false>(inc, d);
+            if (lane + d < 32) inc = compose(q, inc);
+        }
+        Aff exc = shfl_aff<false>(inc, 1);
+        if (lane == 31) exc = Aff{1.f, 0.f, 0.f, 0.f};
+        const Aff c = compose(run, exc);
+        if (t < ntile) {
+            ca[3 * ntile + t] = c.B0;
+            ca[4 * ntile + t] = c.B1;
+            ca[5 * ntile + t] = c.B2;
+        }
+        run = compose(run, Aff{__shfl_sync(0xffffffffu, inc.A, 0), __shfl_sync(0xffffffffu, inc.B0, 0),
+                               __shfl_sync(0xffffffffu, inc.B1, 0), __shfl_sync(0xffffffffu, inc.B2, 0)});
+    }
+}
+
+// ------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2D tensor map over a w x h plane with 32 x `rows` boxes (4-byte FP32 or 1-byte u8 elements)
+bool make_map(CUtensorMap* m, const void* base, int w, int h, int esize, int rows = kTR)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    const cuuint64_t strides[1] = {(cuuint64_t)w * esize};
+    const cuuint32_t box[2] = {(cuuint32_t)kTW, (cuuint32_t)rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType t =
+        esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    return fn(m, t, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+int odd_up(int v) { return (v & 1) ? v : v + 1; }
+
+
+// row segment length: the smem plane length kRowNT*L must keep 16-byte alignment
+int row_L(int w)
+{
+    int L = odd_up((w + kRowNT - 1) / kRowNT);
+    return L;
+}
+
+size_t row_fast_smem(int w)
+{
+    const size_t Wp = (size_t)kRowNT * row_L(w);
+    return Wp * 12 + align_up(Wp, 16);
+}
+
+constexpr size_t kFastBudget = 225 * 1024;
+
+int sm_count()
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int final_pass,
+                       float eps, float* agg, float* car, int* err, cudaStream_t s)
+{
+    const size_t smem = 2 * (size_t)kTileBuf;
+    ensure_smem((const void*)k_dt_tiles<false>, smem);
+    ensure_smem((const void*)k_dt_tiles<true>, smem);
+    const int ntx = (w + kTW - 1) / kTW, ntile = (h + kTR - 1) / kTR;
+    const int nitems = ntx * ntile;
+    const int grid = nitems < 3 * sm_count() ? nitems : 3 * sm_count();
+    note_launch();
+    k_dt_tiles<false><<<grid, kTNT, smem, s>>>(maps, w, h, ntx, ntile, lut, agg, car, 0, eps, err);
+    note_launch();
+    k_dt_cols_chain<<<(w + 7) / 8, 256, 0, s>>>(agg, w, ntile, car);
+    note_launch();
+    k_dt_tiles<true><<<grid, kTNT, smem, s>>>(maps, w, h, ntx, ntile, lut, agg, car, final_pass,
+                                             eps, err);
+}
+
+template <int LM>
+void launch_rows_pipe(int first, float* P0, float* P1, float* P2, const uint8_t* guide, int w,
+                      int h, const DtLut& lut, const FlowCorners& fc, int* err, cudaStream_t s)
+{
+    const size_t smem = 2 * ((size_t)3 * kRowNT * LM * 4 + (size_t)kRowNT * LM);
+    const int per_sm = (int)((225 * 1024) / (smem + 2048));
+    const int grid = h < per_sm * sm_count() ? h : per_sm * sm_count();
+    note_launch();
+    if (first) {
+        ensure_smem((const void*)k_dt_rows_pipe<LM, true>, smem);
+        k_dt_rows_pipe<LM, true><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, lut, fc, err);
+    } else {
+        ensure_smem((const void*)k_dt_rows_pipe<LM, false>, smem);
+        k_dt_rows_pipe<LM, false><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, lut, fc, err);
+    }
+}
+
+}  // namespace
+
+bool flow_fast_supported(int w, int h, const uint8_t* guide, const float* fu, const float* fv)
+{
+    // TMA: 16-byte aligned bases and row pitches (w % 16 for the u8 guide)
+    if (w % 16 != 0 || w < 32 || h < 2) return false;
+    if (((uintptr_t)guide % 16) != 0 || ((uintptr_t)fu % 16) != 0 || ((uintptr_t)fv % 16) != 0)
+        return false;
+    if (row_L(w) > 17 || 2 * row_fast_smem(w) > kFastBudget) return false;
+    return encode_fn() != nullptr;
+}
+
+// The six passes of the flow on the fast path; `ws` holds the three planes and,
+// after them, the error word.
+size_t flow_fast_extra_bytes(int w, int h)
+{
+    const size_t ntile = (size_t)((h + kTR - 1) / kTR);
+    const size_t wp = (size_t)((w + kTW - 1) / kTW) * kTW;
+    return align_up((size_t)kAgg * ntile * wp * 4, 256) + align_up((size_t)kCar * ntile * wp * 4, 256);
+}
+
+bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc, const DtLut* luts,
+                      int iters, double flow_eps, float* flow_u, float* flow_v, float* P0,
+                      float* P1, float* P2, int* err, void* extra, cudaStream_t s)
+{
+    const size_t ntile = (size_t)((h + kTR - 1) / kTR);
+    const size_t wp = (size_t)((w + kTW - 1) / kTW) * kTW;
+    float* agg = static_cast<float*>(extra);
+    float* car = reinterpret_cast<float*>(static_cast<uint8_t*>(extra) +
+                                          align_up((size_t)kAgg * ntile * wp * 4, 256));
+    ColMaps mid, fin;
+    if (!make_map(&mid.in[0], P0, w, h, 4) || !make_map(&mid.in[1], P1, w, h, 4) ||
+        !make_map(&mid.in[2], P2, w, h, 4) || !make_map(&mid.guide, guide, w, h, 1, kGRows))
+        return false;
+    mid.out[0] = mid.in[0];
+    mid.out[1] = mid.in[1];
+    mid.out[2] = mid.in[2];
+    fin = mid;
+    if (!make_map(&fin.out[0], flow_u, w, h, 4) || !make_map(&fin.out[1], flow_v, w, h, 4))
+        return false;
+    const int Lr = row_L(w);
+    for (int i = 0; i < iters; i++) {
+        const DtLut& lut = luts[i];
+        const int first = i == 0;
+        switch (Lr) {
+            case 1: launch_rows_pipe<1>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            case 3: launch_rows_pipe<3>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            case 5: launch_rows_pipe<5>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            case 7: launch_rows_pipe<7>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            case 9: launch_rows_pipe<9>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            case 11: launch_rows_pipe<11>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            case 13: launch_rows_pipe<13>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            case 15: launch_rows_pipe<15>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            default: launch_rows_pipe<17>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+        }
+        launch_cols_tiles((i == iters - 1) ? fin : mid, w, h, lut, i == iters - 1, (float)flow_eps,
+                          agg, car, err, s);
+    }
+    return true;
+}
+
+}  // namespace hdrreg

@@ -26,10 +26,7 @@ namespace hdrreg {
 namespace {
 
 constexpr int kNT = 256;
-
-struct DtLut {
-    float w[256];
-};
+constexpr int kMaxDtIters = 8;
 
 struct Aff {  // y -> A y + B, one A for the three planes
     float A, B0, B1, B2;
@@ -456,19 +453,6 @@ size_t row_smem(int w)
     return wp * 12 + align_up(wp, 16);
 }
 
-DtLut make_lut(double sigma_s, double sigma_r, int iters, int i)
-{
-    const double sig = sigma_s * sqrt(3.0) * pow(2.0, (double)(iters - 1 - i)) /
-                       sqrt(pow(4.0, (double)iters) - 1.0);
-    const double a = exp(-sqrt(2.0) / sig);
-    DtLut t;
-    for (int v = 0; v < 256; v++) {
-        const double d = 1.0 + (sigma_s / sigma_r) * (double)v / 255.0;
-        t.w[v] = (float)pow(a, d);
-    }
-    return t;
-}
-
 template <int SW>
 void launch_cols(float* P0, float* P1, float* P2, const uint8_t* guide, int w, int h,
                  const DtLut& lut, int final_pass, float eps, float* Fu, float* Fv,
@@ -491,12 +475,28 @@ void launch_cols(float* P0, float* P1, float* P2, const uint8_t* guide, int w, i
 
 }  // namespace
 
+DtLut make_dt_lut(double sigma_s, double sigma_r, int iters, int i)
+{
+    const double sig = sigma_s * sqrt(3.0) * pow(2.0, (double)(iters - 1 - i)) /
+                       sqrt(pow(4.0, (double)iters) - 1.0);
+    const double a = exp(-sqrt(2.0) / sig);
+    DtLut t;
+    for (int v = 0; v < 256; v++) {
+        const double d = 1.0 + (sigma_s / sigma_r) * (double)v / 255.0;
+        t.w[v] = (float)pow(a, d);
+    }
+    return t;
+}
+
 int flow_supported(int w, int h)
 {
     return w >= 1 && h >= 1 && row_smem(w) <= kSmemBudget && pick_sw(h) != 0;
 }
 
-size_t flow_ws_bytes(int w, int h) { return 3 * align_up((size_t)w * h * 4, 256); }
+size_t flow_ws_bytes(int w, int h)
+{
+    return 3 * align_up((size_t)w * h * 4, 256) + 256 + flow_fast_extra_bytes(w, h);
+}
 
 void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, double sigma_s,
                  double sigma_r, int iters, double flow_eps, float* flow_u, float* flow_v,
@@ -506,6 +506,14 @@ void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, doub
     float* P0 = static_cast<float*>(ws);
     float* P1 = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + plane);
     float* P2 = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + 2 * plane);
+    int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + 3 * plane);
+    if (iters <= kMaxDtIters && flow_fast_supported(w, h, guide, flow_u, flow_v)) {
+        DtLut luts[kMaxDtIters];
+        for (int i = 0; i < iters; i++) luts[i] = make_dt_lut(sigma_s, sigma_r, iters, i);
+        if (launch_flow_fast(guide, w, h, fc, luts, iters, flow_eps, flow_u, flow_v, P0, P1, P2,
+                             err, static_cast<uint8_t*>(ws) + 3 * plane + 256, s))
+            return;
+    }
     const int Lr = odd_up((w + kNT - 1) / kNT);
     const size_t rs = row_smem(w);
     ensure_smem((const void*)k_dt_rows<true>, rs);
@@ -514,7 +522,7 @@ void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, doub
     const int gmode = ((uintptr_t)guide % 16 == 0 && w % 16 == 0) ? 2
                       : (((uintptr_t)guide % 4 == 0 && w % 4 == 0) ? 1 : 0);
     for (int i = 0; i < iters; i++) {
-        const DtLut lut = make_lut(sigma_s, sigma_r, iters, i);
+        const DtLut lut = make_dt_lut(sigma_s, sigma_r, iters, i);
         note_launch();
         if (i == 0)
             k_dt_rows<true><<<h, kNT, rs, s>>>(P0, P1, P2, guide, w, h, Lr, gmode, lut, fc);

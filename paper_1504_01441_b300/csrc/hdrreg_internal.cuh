@@ -239,6 +239,15 @@ struct FlowCorners {  // sparse input of the first row pass
     int ntx, nty, tile;
     int full;  // propagate q - p instead of q - H(p)
 };
+struct DtLut {  // per-iteration link weights a_i^(1 + (sigma_s/sigma_r) d / 255), d = 0..255
+    float w[256];
+};
+DtLut make_dt_lut(double sigma_s, double sigma_r, int iters, int i);
+bool flow_fast_supported(int w, int h, const uint8_t* guide, const float* fu, const float* fv);
+size_t flow_fast_extra_bytes(int w, int h);
+bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc, const DtLut* luts,
+                      int iters, double flow_eps, float* flow_u, float* flow_v, float* P0,
+                      float* P1, float* P2, int* err, void* extra, cudaStream_t s);
 size_t flow_ws_bytes(int w, int h);
 void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, double sigma_s,
                  double sigma_r, int iters, double flow_eps, float* flow_u, float* flow_v,
