@@ -206,7 +206,7 @@ hdrreg_status hdrreg_weed(const int32_t* corner_xy, const int32_t* match_xy, con
  * real-time pipelines that allow no allocation after start-up, or plugins
  * whose host owns all device memory. Same inputs, output and result as
  * hdrreg_weed; it allocates nothing and calls no allocating routine.
- * Its scratch is a fixed array inside this library (about 416 KB on every GPU
+ * Its scratch is a fixed array inside this library (about 160 KB on every GPU
  * that loads the library, kept until the process exits), so n must not exceed
  * HDRREG_WEED_STATIC_MAX_TILES (larger n returns HDRREG_E_INVALID_ARG and
  * launches nothing). The first call on each device looks up the array's device
@@ -233,6 +233,26 @@ hdrreg_status hdrreg_fit_homography(const int32_t* corner_xy, const int32_t* mat
                                     const uint32_t* mask_bits, int n, int w, int h,
                                     const double* H_prev, double* H_out, int32_t* status,
                                     void* stream);
+
+/* ------------------------------------- a6 + a7 of one level in one launch
+ * The weeding of hdrreg_weed over iterations [iter_begin, iter_end) followed
+ * by the level fit of hdrreg_fit_homography over the weeded set, as one
+ * kernel: every CTA stages the level's matches in shared memory and the CTA
+ * that finishes last solves the fit. Results are bit-identical to
+ * hdrreg_weed + hdrreg_fit_homography. mask_bits (ceil(n/32) words, device)
+ * is zeroed by the call and receives the weeded set; H_out and *status
+ * (optional) as in hdrreg_fit_homography; H_prev and H_out may alias.
+ * `counter` is one device word that must be zero before the first call and
+ * that every call leaves zero; calls that may run concurrently need distinct
+ * counters. Needs hdrreg_weed_fit_supported(n) (the staged matches fit in
+ * shared memory, about 12,000 tiles), else HDRREG_E_UNSUPPORTED.
+ */
+int hdrreg_weed_fit_supported(int n);
+hdrreg_status hdrreg_weed_fit(const int32_t* corner_xy, const int32_t* match_xy,
+                              const uint8_t* valid, int n, int w, int h,
+                              const hdrreg_params* p, uint64_t seed, int iter_begin,
+                              int iter_end, uint32_t* mask_bits, const double* H_prev,
+                              double* H_out, int32_t* status, uint32_t* counter, void* stream);
 
 /* -------------------------------------------------- a8: sparse-to-dense flow
  * Dense flow from the weeded matches (Sec. 2.4, Eq. 5-6): the maps P_u, P_v

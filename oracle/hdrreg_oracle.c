@@ -299,8 +299,10 @@ int orc_weed_sample(uint64_t seed, long iter, int nv, int pick[4])
 /*
  * Solve the 8x8 system A x = b by Gaussian elimination with partial pivoting
  * (pivot = first row of largest |a_ik|): each pivot is inverted once, the
- * elimination factors are a_ik * (1 / a_kk), back substitution subtracts in
- * increasing column order and multiplies by the stored reciprocal. Every
+ * elimination factors are a_ik * (1 / a_kk). Back substitution runs by
+ * columns: x_k = b_k * (1 / a_kk) once every column to its right has been
+ * removed from b_k, then the term a_ik x_k is subtracted from every row i
+ * above it, so each b_i loses its terms in decreasing column order. Every
  * operation is rounded in the written order. Returns 0 on success, 1 if a pivot
  * magnitude is below tol.
  */
@@ -329,9 +331,8 @@ int orc_solve8(const double A_in[64], const double b_in[8], double x[8], double 
         }
     }
     for (int k = 7; k >= 0; k--) {
-        double s = b[k];
-        for (int j = k + 1; j < 8; j++) s = s - A[k][j] * x[j];
-        x[k] = s * inv[k];
+        x[k] = b[k] * inv[k];
+        for (int i = 0; i < k; i++) b[i] = b[i] - A[i][k] * x[k];
     }
     return 0;
 }

@@ -108,7 +108,7 @@ struct Layout {
 struct FusedLayout {
     int L = 1, n0 = 0, nsrc = 1;
     size_t ref_lv[kMaxLevels], src_lv[kMaxLevels];
-    size_t corner, match, cost, valid, mask, H, fit_st, weed, hist, luts, flow, fu, fv;
+    size_t corner, match, cost, valid, mask, H, fit_st, done, weed, hist, luts, flow, fu, fv;
     size_t wy[kMaxSources], wu[kMaxSources], wv[kMaxSources], refn[kMaxSources];
     size_t total;
     FusedLayout(int w, int h, int ns, const hdrreg_params* p)
@@ -130,6 +130,7 @@ struct FusedLayout {
         mask = lay.add((nn / 32 + 1) * 4);
         H = lay.add((size_t)(kMaxLevels + 2) * 9 * 8);
         fit_st = lay.add(kMaxLevels * 4);
+        done = lay.add(kMaxLevels * 4);
         weed = lay.add(weed_ws_bytes(n0));
         hist = lay.add(2 * 256 * 4);
         luts = lay.add((size_t)kMaxSources * 512);
@@ -391,6 +392,36 @@ hdrreg_status hdrreg_fit_homography(const int32_t* corner_xy, const int32_t* mat
     return launch_status("fit");
 }
 
+int hdrreg_weed_fit_supported(int n) { return n >= 0 && n <= (1 << 20) && weed_level_fits(n); }
+
+hdrreg_status hdrreg_weed_fit(const int32_t* corner_xy, const int32_t* match_xy,
+                              const uint8_t* valid, int n, int w, int h, const hdrreg_params* p,
+                              uint64_t seed, int iter_begin, int iter_end, uint32_t* mask_bits,
+                              const double* H_prev, double* H_out, int32_t* status,
+                              uint32_t* counter, void* stream)
+{
+    hdrreg_status st = hdrreg_validate_params(p);
+    if (st) return st;
+    if (n < 0 || n > (1 << 20)) return fail(HDRREG_E_INVALID_ARG, "weed_fit: n out of range");
+    if (!mask_bits || !H_prev || !H_out || !counter || (n > 0 && (!corner_xy || !match_xy || !valid)))
+        return fail(HDRREG_E_INVALID_ARG, "weed_fit: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "weed_fit: bad size");
+    if (iter_begin < 0 || iter_end < iter_begin)
+        return fail(HDRREG_E_INVALID_ARG, "weed_fit: bad iteration range [%d, %d)", iter_begin,
+                    iter_end);
+    if (!weed_level_fits(n))
+        return fail(HDRREG_E_UNSUPPORTED,
+                    "weed_fit: %d tiles do not fit the shared-memory plan (%zu bytes > %zu)", n,
+                    weed_level_smem_bytes(n), kWeedLevelSmemMax);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n > 0) cudaMemsetAsync(mask_bits, 0, (size_t)((n + 31) / 32) * 4, s);
+    WeedLevelArgs a{corner_xy, match_xy, valid, n, w, h, p->weed_eps, p->weed_delta_min,
+                    p->weed_delta_div, seed, iter_begin, iter_end, mask_bits, H_prev, H_out,
+                    status, counter};
+    launch_weed_level(a, s);
+    return launch_status("weed_fit");
+}
+
 // -------------------------------------------------------------------- a8
 size_t hdrreg_flow_workspace_size(int w, int h)
 {
@@ -533,6 +564,7 @@ hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int n
     uint32_t* mask = reinterpret_cast<uint32_t*>(at(lay.mask));
     double* Hs = reinterpret_cast<double*>(at(lay.H));
     int32_t* fit_st = reinterpret_cast<int32_t*>(at(lay.fit_st));
+    unsigned* done = reinterpret_cast<unsigned*>(at(lay.done));
     const WeedWs wws = weed_ws_carve(at(lay.weed), lay.n0);
     uint32_t* hist = reinterpret_cast<uint32_t*>(at(lay.hist));
     float* fu = reinterpret_cast<float*>(at(lay.fu));
@@ -581,19 +613,27 @@ hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int n
             launch_pyramid2(ins, w, h, L, luts, outs0, lvs, 2, s);
         }
         // ---- a3..a7 from the coarsest level to level 0
-        launch_set_identity(Hs + 9 * L, s);
+        launch_set_identity(Hs + 9 * L, s, done, kMaxLevels);
         for (int l = L - 1; l >= 0; l--) {
             const int lw = w >> l, lh = h >> l;
             const uint8_t* rl = l == 0 ? ref0 : at(lay.ref_lv[l]);
             const uint8_t* sl = l == 0 ? src0 : at(lay.src_lv[l]);
             const SearchGeom g = make_geom(lw, lh, p);
             const int n = g.ntx * g.nty;
-            launch_local_search(rl, sl, Hs + 9 * (l + 1), g, corner, match, cost, valid, s);
-            cudaMemsetAsync(mask, 0, (size_t)(n / 32 + 1) * 4, s);
-            launch_weed(corner, match, valid, n, lw, lh, p->weed_eps, p->weed_delta_min,
-                        p->weed_delta_div, p->weed_seed + (uint64_t)l, 0, p->weed_iters, mask,
-                        wws, s);
-            launch_fit(corner, match, mask, n, lw, lh, Hs + 9 * (l + 1), Hs + 9 * l, fit_st + l, s);
+            launch_local_search(rl, sl, Hs + 9 * (l + 1), g, corner, match, cost, valid, s,
+                                mask);  // also zeroes the level's mask words
+            if (weed_level_fits(n)) {
+                WeedLevelArgs a{corner, match, valid, n, lw, lh, p->weed_eps, p->weed_delta_min,
+                                p->weed_delta_div, p->weed_seed + (uint64_t)l, 0, p->weed_iters,
+                                mask, Hs + 9 * (l + 1), Hs + 9 * l, fit_st + l, done + l};
+                launch_weed_level(a, s);
+            } else {
+                launch_weed(corner, match, valid, n, lw, lh, p->weed_eps, p->weed_delta_min,
+                            p->weed_delta_div, p->weed_seed + (uint64_t)l, 0, p->weed_iters,
+                            mask, wws, s);
+                launch_fit(corner, match, mask, n, lw, lh, Hs + 9 * (l + 1), Hs + 9 * l,
+                           fit_st + l, s);
+            }
         }
         // ---- a8: dense flow guided by the normalized reference
         const double* Hw = Hs;

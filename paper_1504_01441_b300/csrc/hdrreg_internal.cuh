@@ -18,7 +18,7 @@ void ensure_smem(const void* kernel, size_t bytes);  // raise the dynamic smem l
 constexpr int kMaxLevels = 8;
 constexpr int kSsimRadius = 5;
 
-inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // ----------------------------------------------------- binary64, one rounding
 // Every FP64 step whose result decides an integer (search centre, inlier flag)
@@ -72,6 +72,67 @@ __device__ inline void search_center(const double* H, int x, int y, int w, int h
     cy = (int)ty;
 }
 
+// The search centre of search_center from an FP32 evaluation with a certified
+// interval: hf = (float)H, ha = |hf|. The FP32 values X, Y, D are within
+// 4.01u (|h0 xn| + |h1 yn| + |h2|) of the exact ones (rounding of H and of xn, two
+// FMAs; u = 2^-24), bounded here by 6u plus a tiny absolute term, which also covers
+// the binary64 evaluation's own (2^-29 times smaller) error. The ratio and the pixel
+// position are then bracketed with directed rounding and widened by 2^-20 of their
+// magnitude, far beyond the binary64 rounding of the remaining steps. If both ends
+// of the bracket round and clamp to the same pixel, that pixel is the binary64
+// result; the function returns false when the bracket straddles a rounding boundary
+// or a value is not finite, and the caller evaluates search_center in binary64.
+__device__ __forceinline__ bool center_bracket(float num, float e_num, float Dlo, float Dhi,
+                                               int extent, float W, int& out)
+{
+    const float nlo = __fadd_rd(num, -e_num), nhi = __fadd_ru(num, e_num);
+    const float rlo = nlo >= 0.f ? __fdiv_rd(nlo, Dhi) : __fdiv_rd(nlo, Dlo);
+    const float rhi = nhi >= 0.f ? __fdiv_ru(nhi, Dlo) : __fdiv_ru(nhi, Dhi);
+    const float em1 = (float)(extent - 1);
+    const float xlo = 0.5f * __fmaf_rd(rlo, W, em1), xhi = 0.5f * __fmaf_ru(rhi, W, em1);
+    if (!isfinite(xlo) || !isfinite(xhi)) return false;
+    const float m = 9.5367432e-7f * (fabsf(xlo) + fabsf(xhi) + W);  // 2^-20
+    float tlo = floorf(__fadd_rd(__fadd_rd(xlo, -m), 0.5f));
+    float thi = floorf(__fadd_ru(__fadd_ru(xhi, m), 0.5f));
+    tlo = fminf(fmaxf(tlo, 0.f), em1);
+    thi = fminf(fmaxf(thi, 0.f), em1);
+    if (tlo != thi) return false;
+    out = (int)tlo;
+    return true;
+}
+
+__device__ inline bool search_center_f32(const float* hf, const float* ha, int x, int y, int w,
+                                         int h, int& cx, int& cy)
+{
+    const float W = (float)w;
+    const float xn = __fdiv_rn((float)(2 * x - (w - 1)), W);
+    const float yn = __fdiv_rn((float)(2 * y - (h - 1)), W);
+    const float ax = fabsf(xn), ay = fabsf(yn);
+    const float X = fmaf(hf[0], xn, fmaf(hf[1], yn, hf[2]));
+    const float Y = fmaf(hf[3], xn, fmaf(hf[4], yn, hf[5]));
+    const float D = fmaf(hf[6], xn, fmaf(hf[7], yn, hf[8]));
+    const float g = 6.0f * 5.9604645e-8f, tiny = 1e-30f;
+    const float eX = fmaf(g, fmaf(ha[0], ax, fmaf(ha[1], ay, ha[2])), tiny);
+    const float eY = fmaf(g, fmaf(ha[3], ax, fmaf(ha[4], ay, ha[5])), tiny);
+    const float eD = fmaf(g, fmaf(ha[6], ax, fmaf(ha[7], ay, ha[8])), tiny);
+    if (!isfinite(X) || !isfinite(Y) || !isfinite(D) || !isfinite(eX) || !isfinite(eY) ||
+        !isfinite(eD))
+        return false;
+    if (__fadd_ru(D, eD) <= 0.f) {  // the binary64 denominator is not positive
+        cx = x;
+        cy = y;
+        return true;
+    }
+    const float Dlo = __fadd_rd(D, -eD), Dhi = __fadd_ru(D, eD);
+    if (!(Dlo > 0.f)) return false;
+    int tx, ty;
+    if (!center_bracket(X, eX, Dlo, Dhi, w, W, tx)) return false;
+    if (!center_bracket(Y, eY, Dlo, Dhi, h, W, ty)) return false;
+    cx = tx;
+    cy = ty;
+    return true;
+}
+
 // SplitMix64 (Steele, Lea, Flood 2014) as a counter-based stream.
 __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k)
 {
@@ -81,63 +142,164 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k)
     return z ^ (z >> 31);
 }
 
-// 4 distinct indices in [0, nv) for weeding iteration `it`: draws 16*it + t,
-// index = (hi32(draw) * nv) >> 32, duplicates rejected, at most 16 draws.
-__device__ inline bool weed_sample(uint64_t seed, long long it, int nv, int pick[4])
+constexpr unsigned kFull = 0xffffffffu;
+
+// 4 distinct indices in [0, nv) for weeding iteration `it`, drawn as in Sec. 2.3:
+// draws 16*it + t (t = 0..15), index = (hi32(draw) * nv) >> 32, a draw equal to an
+// earlier one rejected, the first four survivors kept. Warp-collective: lanes
+// 0..15 evaluate the 16 draws at once; a draw survives iff no earlier draw has its
+// value (an earlier equal draw is either kept or equal to a kept one). Returns
+// false (all lanes) if fewer than four distinct draws; otherwise lane k of every
+// quad (lane & 3 == k) receives pick k.
+__device__ inline bool weed_sample_warp(uint64_t seed, long long it, int nv, int& pick)
 {
-    int np = 0;
-    for (int t = 0; t < 16 && np < 4; t++) {
-        const uint64_t z = splitmix64_at(seed, (uint64_t)it * 16u + (uint64_t)t);
-        const int j = (int)(((z >> 32) * (uint64_t)nv) >> 32);
-        bool dup = false;
-        for (int k = 0; k < np; k++) dup |= (pick[k] == j);
-        if (!dup) pick[np++] = j;
+    const int lane = threadIdx.x & 31;
+    int j = -1;
+    if (lane < 16) {
+        const uint64_t z = splitmix64_at(seed, (uint64_t)it * 16u + (uint64_t)lane);
+        j = (int)(((z >> 32) * (uint64_t)nv) >> 32);
     }
-    return np == 4;
+    bool first = lane < 16;
+#pragma unroll
+    for (int s = 0; s < 15; s++) {
+        const int js = __shfl_sync(kFull, j, s);
+        if (s < lane && js == j) first = false;
+    }
+    const unsigned fb = __ballot_sync(kFull, first);
+    if (__popc(fb) < 4) return false;
+    pick = __shfl_sync(kFull, j, (int)__fns(fb, 0, (lane & 3) + 1));
+    return true;
 }
 
-// Gaussian elimination with partial pivoting on an 8x8 system (first row of
-// largest |a_ik| is the pivot); each pivot is inverted once, factors are
-// a_ik * (1/a_kk), back substitution subtracts in increasing column order and
-// multiplies by the stored reciprocal; each operation one binary64 rounding.
-// Returns 0, or 1 if a pivot magnitude is below tol.
-__device__ inline int solve8(double (&A)[8][8], double (&b)[8], double (&x)[8], double tol)
+// The binary64 value m * 2^-e, exact for |m| < 2^53 and a normal result, built
+// with integer operations only; a zero result is -0.0 when neg_zero is set.
+__device__ __forceinline__ double exact_scaled(long long m, int e, bool neg_zero = false)
 {
+    if (m == 0) return neg_zero ? -0.0 : 0.0;
+    const unsigned long long sgn = m < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned long long a = m < 0 ? 0ull - (unsigned long long)m : (unsigned long long)m;
+    const int lz = __clzll((long long)a);
+    const unsigned long long frac = ((a << lz) << 1) >> 12;  // drop the leading one
+    const unsigned long long ex = (unsigned long long)(1023 + 63 - lz - e);
+    return __longlong_as_double((long long)(sgn | (ex << 52) | frac));
+}
+
+// Gaussian elimination on four independent 8x8 systems in one warp, the same
+// arithmetic as the sequential algorithm: partial pivoting (first row of largest
+// |a_ik|; a NaN diagonal fails, other NaN rows never win), one reciprocal per
+// pivot, factors a_ik * (1/a_kk), updates a_ij - f a_kj, then back substitution by
+// columns (x_k = b_k * (1/a_kk), then b_i -= a_ik x_k for every row i above), every
+// operation one binary64 rounding. Lane layout: system g = lane >> 3, row r =
+// lane & 7; a[0..7] = A[r][0..7], a[8] = b[r]. Each step is one warp instruction for
+// all four systems, which matters on a part whose binary64 pipe costs a full warp
+// issue per instruction whatever the number of active lanes. Pivot magnitudes are
+// compared as integers (|v| as bits is monotone for non-NaN values). Returns, per
+// lane, 0 with x[] = its system's solution, or 1 if a pivot magnitude of its system
+// is below tol (tol > 0); systems never interact.
+__device__ inline int solve8_rows(double (&a)[9], double (&x)[8], double tol)
+{
+    constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL, kInf = 0x7FF0000000000000LL;
+    const int lane = threadIdx.x & 31, r = lane & 7, base = lane & ~7;
+    const long long tol_bits = __double_as_longlong(tol);
     double inv[8];
+    int bad = 0;
+#pragma unroll
     for (int k = 0; k < 8; k++) {
-        int piv = k;
-        double best = fabs(A[k][k]);
-        for (int i = k + 1; i < 8; i++) {
-            const double v = fabs(A[i][k]);
-            if (v > best) {
-                best = v;
-                piv = i;
+        long long key = __double_as_longlong(a[k]) & kAbs;
+        const int nan = key > kInf;
+        bad |= __shfl_sync(kFull, nan, base + k);
+        if (r < k || nan) key = -1;
+        int idx = r;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const long long k2 = __shfl_xor_sync(kFull, key, o);
+            const int i2 = __shfl_xor_sync(kFull, idx, o);
+            if (k2 > key || (k2 == key && i2 < idx)) {
+                key = k2;
+                idx = i2;
             }
         }
-        if (!(best >= tol)) return 1;
-        if (piv != k) {
-            for (int j = 0; j < 8; j++) {
-                const double t = A[k][j];
-                A[k][j] = A[piv][j];
-                A[piv][j] = t;
-            }
-            const double t = b[k];
-            b[k] = b[piv];
-            b[piv] = t;
-        }
-        inv[k] = ddiv(1.0, A[k][k]);
-        for (int i = k + 1; i < 8; i++) {
-            const double f = dmul(A[i][k], inv[k]);
-            for (int j = k + 1; j < 8; j++) A[i][j] = dsub(A[i][j], dmul(f, A[k][j]));
-            b[i] = dsub(b[i], dmul(f, b[k]));
+        bad |= key < tol_bits;
+        const int src = r == k ? base + idx : (r == idx ? base + k : lane);  // swap rows k, idx
+#pragma unroll
+        for (int j = k; j < 9; j++) a[j] = __shfl_sync(kFull, a[j], src);
+        inv[k] = __drcp_rn(__shfl_sync(kFull, a[k], base + k));
+        const double f = dmul(a[k], inv[k]);
+#pragma unroll
+        for (int j = k + 1; j < 9; j++) {
+            const double nv = dsub(a[j], dmul(f, __shfl_sync(kFull, a[j], base + k)));
+            if (r > k) a[j] = nv;
         }
     }
+#pragma unroll
     for (int k = 7; k >= 0; k--) {
-        double s = b[k];
-        for (int j = k + 1; j < 8; j++) s = dsub(s, dmul(A[k][j], x[j]));
-        x[k] = dmul(s, inv[k]);
+        x[k] = dmul(__shfl_sync(kFull, a[8], base + k), inv[k]);
+        const double nv = dsub(a[8], dmul(a[k], x[k]));
+        if (r < k) a[8] = nv;
     }
-    return 0;
+    return bad;
+}
+
+// One row of the 4-point DLT system of a weeding iteration (lane layout of
+// solve8_rows): rows 2k, 2k+1 of sample k are
+//   [x~, y~, 1, 0, 0, 0, -x~ u~, -y~ u~ | u~],  [0, 0, 0, x~, y~, 1, -x~ v~, -y~ v~ | v~]
+// with x~ = xc / S, u~ = qxc / S (centred integers, S = 2^lg). Every entry is an
+// exact binary64 value, so it is built from integers; the products' zero signs
+// follow binary64 multiplication and negation.
+__device__ __forceinline__ void dlt4_row(int r, int xc, int yc, int qxc, int qyc, int lg,
+                                         double (&a)[9])
+{
+    const bool odd = r & 1;
+    const int q = odd ? qyc : qxc;
+    const double xs = exact_scaled(xc, lg), ys = exact_scaled(yc, lg);
+    a[0] = odd ? 0.0 : xs;
+    a[1] = odd ? 0.0 : ys;
+    a[2] = odd ? 0.0 : 1.0;
+    a[3] = odd ? xs : 0.0;
+    a[4] = odd ? ys : 0.0;
+    a[5] = odd ? 1.0 : 0.0;
+    a[6] = exact_scaled(-(long long)xc * (long long)q, 2 * lg, !((xc < 0) ^ (q < 0)));
+    a[7] = exact_scaled(-(long long)yc * (long long)q, 2 * lg, !((yc < 0) ^ (q < 0)));
+    a[8] = exact_scaled(q, lg);
+}
+
+// Round-to-nearest-even binary64 value of the integer v, times 2^-e, with integer
+// operations. For |v| < 2^85 this equals (double)(v >> 32) * 2^32 + (double)(v mod
+// 2^32) (the first product is exact there, the sum the only rounding) scaled by the
+// exact power of two. Returns false (nothing written) for larger |v|.
+__device__ __forceinline__ bool i128_rn_scaled(__int128 v, int e, double& out)
+{
+    if (v == 0) {
+        out = 0.0;
+        return true;
+    }
+    const bool neg = v < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    if ((a >> 84) != 0) return false;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    unsigned long long mant;
+    int ex = msb;
+    if (msb <= 52) {
+        mant = lo << (52 - msb);
+    } else {
+        const int sh = msb - 52;
+        mant = (unsigned long long)(a >> sh);
+        const unsigned __int128 rem = a & ((((unsigned __int128)1) << sh) - 1);
+        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) {
+            mant++;
+            if (mant >> 53) {
+                mant >>= 1;
+                ex++;
+            }
+        }
+    }
+    const unsigned long long bits = (neg ? 0x8000000000000000ull : 0ull) |
+                                    ((unsigned long long)(ex + 1023 - e) << 52) |
+                                    (mant & 0x000FFFFFFFFFFFFFull);
+    out = __longlong_as_double((long long)bits);
+    return true;
 }
 
 // Smallest power of two >= w: the scale S of the coordinates x~ = (2x - (w-1)) / S
@@ -211,14 +373,15 @@ struct SearchGeom {
     int w, h, tile, radius, patch_half, grid_half, quad, step, ntx, nty;
     long long corner_thr;
 };
+// mask_zero (optional): the level's weeding mask, zeroed word by word on the way
 void launch_local_search(const uint8_t* ref, const uint8_t* src, const double* H,
                          const SearchGeom& g, int32_t* corner_xy, int32_t* match_xy,
-                         uint32_t* cost, uint8_t* valid, cudaStream_t s);
+                         uint32_t* cost, uint8_t* valid, cudaStream_t s,
+                         uint32_t* mask_zero = nullptr);
 
 struct WeedWs {  // workspace of the weeding step
     int32_t* list;      // n: valid tile indices in tile order
     int32_t* count;     // 1: number of valid tiles
-    double* coords;     // 4n: x~, y~, x_qc, y_qc per valid match (binary64, exact)
     float4* coords32;   // n: x~, y~, x_qc / S, y_qc / S (FP32, exact for w < 2^23)
 };
 size_t weed_ws_bytes(int n);
@@ -229,7 +392,29 @@ void launch_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_
 void launch_fit(const int32_t* corner_xy, const int32_t* match_xy, const uint32_t* mask, int n,
                 int w, int h, const double* H_prev, double* H_out, int32_t* status,
                 cudaStream_t s);
-void launch_set_identity(double* H, cudaStream_t s);
+
+// Weeding + level fit of one level in one launch (matches staged in shared memory).
+struct WeedLevelArgs {
+    const int32_t* corner_xy;
+    const int32_t* match_xy;
+    const uint8_t* valid;
+    int n, w, h;
+    double eps;
+    int delta_min, delta_div;
+    uint64_t seed;
+    int it0, it1;
+    uint32_t* mask;        // zero on entry; receives the union of accepted inlier sets
+    const double* H_prev;  // fit: coarser level's homography (kept if the fit fails)
+    double* H_out;
+    int32_t* status;       // 0 fitted, 1 fewer than 4 matches, 2 singular
+    unsigned* done;        // completion counter, zero on entry and left zero
+};
+constexpr size_t kWeedLevelSmemMax = 200 * 1024;
+size_t weed_level_smem_bytes(int n);
+bool weed_level_fits(int n);
+void launch_weed_level(const WeedLevelArgs& a, cudaStream_t s);
+void launch_set_identity(double* H, cudaStream_t s, unsigned* counters = nullptr,
+                         int ncounters = 0);
 
 struct FlowCorners {  // sparse input of the first row pass
     const int32_t* corner_xy;

@@ -2,13 +2,18 @@
 // coarser level's homography (Eq. 3) and the integer SSD patch search (Sec. 2.2).
 //
 // One CTA per tile. The reference region around the tile (candidate grid plus
-// quadrants / patch) is staged once in shared memory with an integral image
-// (Sec. 2.2 notes quadrant means come cheaply from integral images); the
-// source search window is staged as four byte-shifted word copies so every
-// thread reads aligned 32-bit words for any horizontal offset. The SSD of four
-// pixels is one __vabsdiffu4 + one unsigned __dp4a (exact: |a-b|^2 <= 65025,
-// a 21x21 patch sums to < 2^25). Costs and argmins are exact integers; the
-// argmin key (cost << 16 | row-major index of d) is reduced with warp shuffles.
+// quadrants / patch) and the source search window are staged in shared memory
+// with aligned 4-byte loads and funnel shifts (byte gathers with clamp-to-edge
+// only for blocks that touch the border). Quadrant sums come from an integral
+// image of the region (Sec. 2.2 notes they come cheaply from integral images),
+// built one row, then one column, per thread. The search centre is evaluated in
+// FP32 with a certified interval and in binary64 only when that interval
+// straddles a rounding boundary. The SSD of four pixels is one __vabsdiffu4 + one
+// unsigned __dp4a (exact: |a-b|^2 <= 65025, a 31x31 patch sums to < 2^26); the
+// window words of four neighbouring offsets are funnel shifts by 0, 8, 16, 24 bits
+// of the same two aligned words, so a thread takes four offsets per load. Costs
+// and argmins are exact integers; the argmin key (cost << 16 | row-major index of
+// d) is reduced with warp shuffles.
 #include "hdrreg_internal.cuh"
 
 namespace hdrreg {
@@ -16,13 +21,14 @@ namespace hdrreg {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v)
 {
     for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        const uint64_t u = __shfl_xor_sync(kFull, v, o);
         v = u > v ? u : v;
     }
     return v;
@@ -31,36 +37,71 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v)
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v)
 {
     for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        const uint64_t u = __shfl_xor_sync(kFull, v, o);
         v = u < v ? u : v;
     }
     return v;
+}
+
+// Stage the rows x cols block with top-left pixel (x0, y0) of a w x h plane into
+// shared-memory rows of pw <= 32 words (4 pw >= cols; the bytes past cols are
+// don't-care). Pixels outside the plane clamp to the edge. A warp covers
+// floor(32 / pw) rows per step. Blocks inside the plane of a 4-byte aligned buffer
+// read two aligned words per output word (the last read stays inside the buffer by
+// the explicit bound below).
+__device__ __forceinline__ void stage_block(const uint8_t* __restrict__ img, int w, int h, int x0,
+                                            int y0, int cols, int rows, uint32_t* dst, int pw)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rpw = 32 / pw, sub = lane / pw, j = lane - sub * pw;
+    if (sub >= rpw) return;
+    const bool fast = ((uintptr_t)img & 3u) == 0 && x0 >= 0 && y0 >= 0 && x0 + cols <= w &&
+                      y0 + rows <= h &&
+                      (size_t)(y0 + rows - 1) * w + x0 + 4 * (size_t)pw + 4 <= (size_t)w * h;
+    for (int r = warp * rpw + sub; r < rows; r += kWarps * rpw) {
+        uint32_t word;
+        if (fast) {
+            const size_t off = (size_t)(y0 + r) * w + x0 + 4 * j;
+            const uint32_t* q = reinterpret_cast<const uint32_t*>(img + (off & ~(size_t)3));
+            word = __funnelshift_r(__ldg(q), __ldg(q + 1), 8u * (unsigned)(off & 3));
+        } else {
+            const uint8_t* row = img + (size_t)clampi(y0 + r, 0, h - 1) * w;
+            word = 0;
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+                word |= (uint32_t)__ldg(row + clampi(x0 + 4 * j + b, 0, w - 1)) << (8 * b);
+        }
+        dst[r * pw + j] = word;
+    }
 }
 
 }  // namespace
 
 // shared-memory layout sizes (host and device agree through this helper)
 struct SearchSmem {
-    int E, RS, WS, WW, P, PW;
-    size_t off_region, off_ii, off_win, off_patch, total;
+    int E, RS, RPW, IS, WS, WW, P, PWc;
+    size_t off_region, off_ii, off_win, off_patch, off_ssd, total;
     __host__ __device__ SearchSmem(const SearchGeom& g)
     {
         E = g.grid_half * g.step + (g.quad > g.patch_half ? g.quad : g.patch_half);
-        RS = 2 * E + 1;                       // reference region side
-        WS = 2 * (g.radius + g.patch_half) + 1;  // search window side
-        WW = (WS + 3) / 4 + 1;                 // words per window row (per shifted copy)
-        P = 2 * g.patch_half + 1;
-        PW = P / 4;                            // full words per patch row
+        RS = 2 * E + 1;                        // reference region side
+        RPW = (RS + 3) / 4;                    // words per region row
+        IS = RS + 1;                           // integral image side
+        P = 2 * g.patch_half + 1;              // patch side
+        PWc = (P + 3) / 4;                     // words per patch row (last one partial)
+        WS = 2 * g.radius + P;                 // search window side
+        WW = (2 * g.radius) / 4 + PWc + 1;     // words per window row (funnel reads one past)
         size_t o = 0;
         off_region = o;
-        o += (size_t)RS * RS;
-        o = (o + 15) & ~(size_t)15;
+        o += (size_t)RS * RPW * 4;
         off_ii = o;
-        o += (size_t)(RS + 1) * (RS + 1) * 4;
+        o += (size_t)IS * IS * 4;
         off_win = o;
-        o += (size_t)4 * WS * WW * 4;
+        o += (size_t)WS * WW * 4;
         off_patch = o;
-        o += (size_t)P * (PW > 0 ? PW : 1) * 4;
+        o += (size_t)P * PWc * 4;
+        off_ssd = o;
+        o += (size_t)(2 * g.radius + 1) * (2 * g.radius + 1) * 4;
         total = o;
     }
 };
@@ -68,45 +109,66 @@ struct SearchSmem {
 __global__ void __launch_bounds__(kThreads) k_local_search(
     const uint8_t* __restrict__ ref, const uint8_t* __restrict__ src, const double* __restrict__ H,
     SearchGeom g, int32_t* __restrict__ corner_xy, int32_t* __restrict__ match_xy,
-    uint32_t* __restrict__ cost_out, uint8_t* __restrict__ valid_out)
+    uint32_t* __restrict__ cost_out, uint8_t* __restrict__ valid_out,
+    uint32_t* __restrict__ mask_zero)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ uint64_t red[kThreads / 32];
+    __shared__ uint64_t red[kWarps];
+    __shared__ float hs[18];  // (float)H, |(float)H|
     __shared__ int s_corner[2], s_center[2];
 
     const SearchSmem L(g);
-    uint8_t* region = smem + L.off_region;
+    uint32_t* region = reinterpret_cast<uint32_t*>(smem + L.off_region);
+    const uint8_t* rb = smem + L.off_region;
     int32_t* ii = reinterpret_cast<int32_t*>(smem + L.off_ii);
     uint32_t* win = reinterpret_cast<uint32_t*>(smem + L.off_win);
     uint32_t* patch = reinterpret_cast<uint32_t*>(smem + L.off_patch);
+    uint32_t* ssd = reinterpret_cast<uint32_t*>(smem + L.off_ssd);
 
     const int t = blockIdx.x;
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int cx = tx * g.tile + g.tile / 2, cy = ty * g.tile + g.tile / 2;
     const int ox = cx - L.E, oy = cy - L.E;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int RSP = 4 * L.RPW, IS = L.IS;
 
-    // ---- stage the reference region (clamp-to-edge) and its integral image
-    for (int i = tid; i < L.RS * L.RS; i += kThreads) {
-        const int yy = i / L.RS, xx = i % L.RS;
-        region[i] = ref[(size_t)clampi(oy + yy, 0, g.h - 1) * g.w + clampi(ox + xx, 0, g.w - 1)];
+    if (mask_zero && tid == 0 && (t & 31) == 0) mask_zero[t >> 5] = 0u;
+    if (tid < 9) {
+        const float f = (float)H[tid];
+        hs[tid] = f;
+        hs[9 + tid] = fabsf(f);
     }
+    // ---- stage the reference region (clamp-to-edge) and its integral image
+    stage_block(ref, g.w, g.h, ox, oy, L.RS, L.RS, region, L.RPW);
     __syncthreads();
-    const int IS = L.RS + 1;
-    for (int r = tid; r <= L.RS; r += kThreads) {   // row prefix sums (row 0 = zeros)
+    if (tid < IS) {  // row prefix sums, one row per thread (row 0 and column 0 zero)
+        const int r = tid;
+        int32_t* out = ii + r * IS;
+        out[0] = 0;
         int run = 0;
-        ii[r * IS] = 0;
-        for (int x = 1; x <= L.RS; x++) {
-            if (r > 0) run += region[(r - 1) * L.RS + (x - 1)];
-            ii[r * IS + x] = run;
+        if (r == 0) {
+            for (int x = 1; x < IS; x++) out[x] = 0;
+        } else {
+            const uint32_t* row = region + (r - 1) * L.RPW;
+            for (int j = 0; j < L.RPW; j++) {
+                const uint32_t wv = row[j];
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const int x = 4 * j + b + 1;
+                    if (x < IS) {
+                        run += (int)((wv >> (8 * b)) & 255u);
+                        out[x] = run;
+                    }
+                }
+            }
         }
     }
     __syncthreads();
-    for (int c = tid; c <= L.RS; c += kThreads) {   // column prefix sums
+    if (tid < IS) {  // column prefix sums, one column per thread
         int run = 0;
-        for (int r = 0; r <= L.RS; r++) {
-            run += ii[r * IS + c];
-            ii[r * IS + c] = run;
+        for (int r = 1; r < IS; r++) {
+            run += ii[r * IS + tid];
+            ii[r * IS + tid] = run;
         }
     }
     __syncthreads();
@@ -135,17 +197,19 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
     if (lane == 0) red[warp] = best;
     __syncthreads();
     if (warp == 0) {
-        uint64_t v = lane < kThreads / 32 ? red[lane] : 0;
+        uint64_t v = lane < kWarps ? red[lane] : 0;
         v = warp_max_u64(v);
         if (lane == 0) {
             if (v == 0) {
                 s_corner[0] = -1;
             } else {
                 const int c = 0xFFFFF - (int)(v & 0xFFFFF);
-                s_corner[0] = cx + g.step * (c % side - K);
-                s_corner[1] = cy + g.step * (c / side - K);
+                const int px = cx + g.step * (c % side - K), py = cy + g.step * (c / side - K);
+                s_corner[0] = px;
+                s_corner[1] = py;
                 int sx, sy;
-                search_center(H, s_corner[0], s_corner[1], g.w, g.h, sx, sy);
+                if (!search_center_f32(hs, hs + 9, px, py, g.w, g.h, sx, sy))
+                    search_center(H, px, py, g.w, g.h, sx, sy);
                 s_center[0] = sx;
                 s_center[1] = sy;
             }
@@ -165,66 +229,83 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
     }
     const int px = s_corner[0], py = s_corner[1];
     const int sx = s_center[0], sy = s_center[1];
-    const int R = g.radius, hp = g.patch_half;
+    const int R = g.radius, hp = g.patch_half, P = L.P, PWc = L.PWc;
 
-    // ---- stage the source window as 4 byte-shifted word copies, and the patch words
-    const int wx0 = sx - R - hp, wy0 = sy - R - hp;
-    for (int i = tid; i < 4 * L.WS * L.WW; i += kThreads) {
-        const int k = i / (L.WS * L.WW), rem = i % (L.WS * L.WW);
-        const int r = rem / L.WW, j = rem % L.WW;
-        const int gy = clampi(wy0 + r, 0, g.h - 1);
-        const uint8_t* row = src + (size_t)gy * g.w;
-        uint32_t word = 0;
-        for (int b = 0; b < 4; b++) {
-            const int col = 4 * j + k + b;
-            const uint32_t v = col < L.WS ? row[clampi(wx0 + col, 0, g.w - 1)] : 0u;
-            word |= v << (8 * b);
-        }
-        win[i] = word;
-    }
+    // ---- stage the source window (byte 0 of a row = column sx - R - hp) and the patch
+    stage_block(src, g.w, g.h, sx - R - hp, sy - R - hp, L.WS, L.WS, win, L.WW);
     const int prx = px - ox - hp, pry = py - oy - hp;  // patch origin inside the region
-    for (int i = tid; i < L.P * L.PW; i += kThreads) {
-        const int v = i / L.PW, j = i % L.PW;
-        const uint8_t* rr = region + (pry + v) * L.RS + prx + 4 * j;
-        patch[i] = (uint32_t)rr[0] | ((uint32_t)rr[1] << 8) | ((uint32_t)rr[2] << 16) |
-                   ((uint32_t)rr[3] << 24);
+    {
+        const int rpw = 32 / PWc, sub = lane / PWc, j = lane - sub * PWc;
+        if (sub < rpw) {
+            for (int v = warp * rpw + sub; v < P; v += kWarps * rpw) {
+                const uint8_t* rr = rb + (pry + v) * RSP + prx + 4 * j;
+                uint32_t word = 0;
+#pragma unroll
+                for (int b = 0; b < 4; b++)
+                    if (4 * j + b < P) word |= (uint32_t)rr[b] << (8 * b);
+                patch[v * PWc + j] = word;
+            }
+        }
     }
+    const int side_d = 2 * R + 1, nd = side_d * side_d, nq = (side_d + 3) >> 2;
+    for (int i = tid; i < nd; i += kThreads) ssd[i] = 0u;
     __syncthreads();
 
-    // ---- SSD over d in [-R, R]^2, exact unsigned integers
-    const int nd = (2 * R + 1) * (2 * R + 1);
+    // ---- SSD over d in [-R, R]^2, exact unsigned integers. A thread takes four
+    //      horizontal offsets 4q..4q+3 of one row dy of offsets (the same two window
+    //      words, shifted by 0, 8, 16, 24 bits) over a quarter of the patch rows; the
+    //      partial sums meet in shared memory.
+    const uint32_t tail = (P & 3) ? ((1u << (8 * (P & 3))) - 1u) : 0xFFFFFFFFu;
+    {
+        constexpr int kSplit = 4;
+        const int rows_per = (P + kSplit - 1) / kSplit;
+        for (int item = tid; item < side_d * nq * kSplit; item += kThreads) {
+            const int part = item % kSplit, rest = item / kSplit;
+            const int dq = rest % nq, dy = rest / nq;
+            const int v0 = part * rows_per, v1 = min(P, v0 + rows_per);
+            uint32_t acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+            for (int v = v0; v < v1; v++) {
+                const uint32_t* pr = patch + v * PWc;
+                const uint32_t* wr = win + (dy + v) * L.WW + dq;
+                uint32_t cur = wr[0];
+#pragma unroll 8
+                for (int j = 0; j < PWc; j++) {
+                    const uint32_t nxt = wr[j + 1], pv = pr[j];
+                    const uint32_t m = j == PWc - 1 ? tail : 0xFFFFFFFFu;
+                    uint32_t d;
+                    d = __vabsdiffu4(pv, cur & m);
+                    acc0 = __dp4a(d, d, acc0);
+                    d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 8) & m);
+                    acc1 = __dp4a(d, d, acc1);
+                    d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 16) & m);
+                    acc2 = __dp4a(d, d, acc2);
+                    d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 24) & m);
+                    acc3 = __dp4a(d, d, acc3);
+                    cur = nxt;
+                }
+            }
+            const int dx0 = 4 * dq, base = dy * side_d + dx0;
+            atomicAdd(&ssd[base], acc0);
+            if (dx0 + 1 < side_d) atomicAdd(&ssd[base + 1], acc1);
+            if (dx0 + 2 < side_d) atomicAdd(&ssd[base + 2], acc2);
+            if (dx0 + 3 < side_d) atomicAdd(&ssd[base + 3], acc3);
+        }
+    }
+    __syncthreads();
     uint64_t bestk = ~0ull;
     for (int di = tid; di < nd; di += kThreads) {
-        const int dy = di / (2 * R + 1), dx = di % (2 * R + 1);  // offsets from window origin
-        uint32_t acc = 0;
-        for (int v = 0; v < L.P; v++) {
-            const uint32_t* prow = patch + v * L.PW;
-            int o = dx;  // byte offset of this row's segment inside the window row
-            const uint32_t* wrow = win + ((o & 3) * L.WS + (dy + v)) * L.WW + (o >> 2);
-            for (int j = 0; j < L.PW; j++) {
-                const uint32_t d = __vabsdiffu4(prow[j], wrow[j]);
-                acc = __dp4a(d, d, acc);
-            }
-            const uint8_t* prb = region + (pry + v) * L.RS + prx;
-            for (int u = 4 * L.PW; u < L.P; u++) {
-                const int col = dx + u;
-                const uint32_t wv = (win[((col & 3) * L.WS + (dy + v)) * L.WW + (col >> 2)]) & 255u;
-                const int e = (int)prb[u] - (int)wv;
-                acc += (uint32_t)(e * e);
-            }
-        }
-        const uint64_t key = ((uint64_t)acc << 16) | (uint64_t)di;
+        const uint64_t key = ((uint64_t)ssd[di] << 16) | (uint64_t)di;
         bestk = key < bestk ? key : bestk;
     }
     bestk = warp_min_u64(bestk);
     if (lane == 0) red[warp] = bestk;
     __syncthreads();
     if (warp == 0) {
-        uint64_t v = lane < kThreads / 32 ? red[lane] : ~0ull;
+        uint64_t v = lane < kWarps ? red[lane] : ~0ull;
         v = warp_min_u64(v);
         if (lane == 0) {
             const int di = (int)(v & 0xFFFF);
-            const int dy = di / (2 * R + 1) - R, dx = di % (2 * R + 1) - R;
+            const int dy = di / side_d - R, dx = di % side_d - R;
             corner_xy[2 * t] = px;
             corner_xy[2 * t + 1] = py;
             match_xy[2 * t] = sx + dx;
@@ -237,15 +318,15 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
 
 void launch_local_search(const uint8_t* ref, const uint8_t* src, const double* H,
                          const SearchGeom& g, int32_t* corner_xy, int32_t* match_xy,
-                         uint32_t* cost, uint8_t* valid, cudaStream_t s)
+                         uint32_t* cost, uint8_t* valid, cudaStream_t s, uint32_t* mask_zero)
 {
     const int n = g.ntx * g.nty;
     if (n <= 0) return;
     const SearchSmem L(g);
-    if (L.total > 48 * 1024)
-        ensure_smem((const void*)k_local_search, L.total);
+    if (L.total > 48 * 1024) ensure_smem((const void*)k_local_search, L.total);
     note_launch();
-    k_local_search<<<n, kThreads, L.total, s>>>(ref, src, H, g, corner_xy, match_xy, cost, valid);
+    k_local_search<<<n, kThreads, L.total, s>>>(ref, src, H, g, corner_xy, match_xy, cost, valid,
+                                                mask_zero);
 }
 
 }  // namespace hdrreg

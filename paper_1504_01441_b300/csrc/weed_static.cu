@@ -3,7 +3,7 @@
 // instead of a caller-provided workspace.
 //
 // The scratch is a file-scope __device__ array, so every GPU that loads the
-// library holds it (about 416 KB) until the process exits. In host code the
+// library holds it (about 160 KB) until the process exits. In host code the
 // array's name is only a host-side stand-in, never a device address: the
 // device address is obtained once per device with cudaGetSymbolAddress (with
 // that device current) and cached; that set-up runs inside the first call made
@@ -21,10 +21,9 @@ namespace {
 
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Same carve-up as weed_ws_bytes(): tile list, count, binary64 and FP32 coordinates.
+// Same carve-up as weed_ws_bytes(): tile list, count, FP32 coordinates.
 constexpr size_t kStaticTiles = HDRREG_WEED_STATIC_MAX_TILES;
-constexpr size_t kStaticBytes =
-    align256(kStaticTiles * 4) + 256 + align256(kStaticTiles * 32) + align256(kStaticTiles * 16);
+constexpr size_t kStaticBytes = align256(kStaticTiles * 4) + 256 + align256(kStaticTiles * 16);
 
 __device__ __align__(256) unsigned char g_weed_scratch[kStaticBytes];
 

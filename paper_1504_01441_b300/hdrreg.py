@@ -26,7 +26,7 @@ EXPORTS = [
     "hdrreg_validate_params", "hdrreg_num_tiles", "hdrreg_normalize_workspace_size",
     "hdrreg_normalize_exposure", "hdrreg_pyramid_bytes", "hdrreg_build_pyramid",
     "hdrreg_local_search", "hdrreg_weed_workspace_size", "hdrreg_weed", "hdrreg_weed_static",
-    "hdrreg_fit_homography",
+    "hdrreg_fit_homography", "hdrreg_weed_fit_supported", "hdrreg_weed_fit",
     "hdrreg_flow_workspace_size", "hdrreg_flow_upsample", "hdrreg_warp", "hdrreg_merge",
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
 ]
@@ -108,6 +108,9 @@ def lib():
         L.hdrreg_weed_static.argtypes = [vp, vp, vp, i, i, i, C.POINTER(Params), C.c_uint64, i,
                                          i, vp, vp]
         L.hdrreg_fit_homography.argtypes = [vp, vp, vp, i, i, i, vp, vp, vp, vp]
+        L.hdrreg_weed_fit_supported.argtypes = [i]
+        L.hdrreg_weed_fit.argtypes = [vp, vp, vp, i, i, i, C.POINTER(Params), C.c_uint64, i, i,
+                                      vp, vp, vp, vp, vp, vp]
         L.hdrreg_flow_workspace_size.restype = sz
         L.hdrreg_flow_workspace_size.argtypes = [i, i]
         L.hdrreg_flow_upsample.argtypes = [vp, i, i, vp, vp, vp, i, vp, C.POINTER(Params), vp,
@@ -260,6 +263,26 @@ def fit_homography(corner_xy, match_xy, mask, w: int, h: int, H_prev, stream=Non
     _check(lib().hdrreg_fit_homography(_ptr(corner_xy), _ptr(match_xy), _ptr(mask), n, w, h,
                                        _ptr(H_prev), _ptr(H), _ptr(st), _stream(stream)))
     return H, st
+
+
+# ---------------------------------------------------------- a6 + a7
+def weed_fit(corner_xy, match_xy, valid, w: int, h: int, p: Params, seed: int, H_prev,
+             iter_begin=0, iter_end=None, counter=None, stream=None):
+    """Weeding and level fit of one level in one launch -> (mask, H, status)"""
+    import torch
+    n = valid.numel()
+    if iter_end is None:
+        iter_end = p.weed_iters
+    mask = torch.empty((n // 32 + 1,), dtype=torch.int32, device=valid.device)
+    H = _empty((9,), torch.float64, H_prev)
+    st = _empty((1,), torch.int32, H_prev)
+    if counter is None:
+        counter = torch.zeros((1,), dtype=torch.int32, device=valid.device)
+    _check(lib().hdrreg_weed_fit(_ptr(corner_xy), _ptr(match_xy), _ptr(valid), n, w, h,
+                                 C.byref(p), C.c_uint64(seed), iter_begin, iter_end, _ptr(mask),
+                                 _ptr(H_prev), _ptr(H), _ptr(st), _ptr(counter),
+                                 _stream(stream)))
+    return mask, H, st
 
 
 # ---------------------------------------------------------------- a8

@@ -163,6 +163,22 @@ def test_local_search_flat_and_identity(hd, orc):
     _search_case(hd, orc, img, img, np.eye(3), cfg(16, 4))
 
 
+def test_local_search_centres_on_rounding_boundaries(hd, orc):
+    # A translation of exactly half a pixel (1/W in normalized coordinates) puts every
+    # projected corner on a rounding boundary, where only the binary64 evaluation
+    # decides; strong perspective makes D <= 0 on part of the frame (centre = corner);
+    # huge entries overflow FP32 (the binary64 path decides finiteness).
+    rng = np.random.default_rng(8)
+    h, w = 192, 256
+    ref = random_img(rng, h, w)
+    src = np.roll(ref, (2, 1), axis=(0, 1))
+    half = np.array([[1.0, 0.0, 1.0 / w], [0.0, 1.0, 1.0 / w], [0.0, 0.0, 1.0]])
+    persp = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [2.0, 0.0, 1.0]])
+    huge = np.array([[1e300, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    for H in (half, persp, huge):
+        assert _search_case(hd, orc, ref, src, H, cfg(16, 4)) > 0
+
+
 # --------------------------------------------------------------------- a6-a7
 def _level_matches(orc, vga, c):
     rn, sn = orc.normalize_ratio(vga.ref.y, vga.srcs[0].y, 4, 1)
@@ -219,6 +235,68 @@ def test_fit_bit_exact(hd, orc, vga):
     H, st = hd.fit_homography(dev(cxy), dev(mxy), dev(few.view(np.int32)), w, h,
                               dev(Hprev.reshape(9)))
     assert host(st)[0] == 1 and np.array_equal(host(H), Hprev.reshape(9))
+
+
+def _weed_fit_case(hd, orc, shape_cxy_mxy_valid, c, seed, it0=0, it1=None, counter=None):
+    (h, w), cxy, mxy, valid = shape_cxy_mxy_valid
+    it1 = c["weed_iters"] if it1 is None else it1
+    p = hd.params_from_dict(c)
+    Hprev = np.array([[1.0, 0.01, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    mask, H, st = hd.weed_fit(dev(cxy), dev(mxy), dev(valid), w, h, p, seed,
+                              dev(Hprev.reshape(9)), it0, it1, counter=counter)
+    obits, _ = orc.weed(cxy, mxy, valid, w, h, c, seed, it0, it1)
+    oH, ost = orc.fit_homography(cxy, mxy, obits, w, h, Hprev)
+    got = host(mask).view(np.uint32)[: len(obits)]
+    assert np.array_equal(got, obits)
+    assert host(st)[0] == ost
+    assert np.array_equal(host(H).view(np.uint64), oH.reshape(9).view(np.uint64))
+    return obits, ost
+
+
+@pytest.mark.parametrize("seed", [1, 99])
+def test_weed_fit_one_launch_bit_exact(hd, orc, vga, seed):
+    c = cfg()
+    m = _level_matches(orc, vga, c)
+    counter = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):  # the counter is left zero, so calls repeat
+        obits, ost = _weed_fit_case(hd, orc, m, c, seed, counter=counter)
+        assert ost == 0 and int(host(counter)[0]) == 0
+
+
+def test_weed_fit_ranges_and_no_iterations(hd, orc, vga):
+    c = cfg()
+    m = _level_matches(orc, vga, c)
+    _weed_fit_case(hd, orc, m, c, 5, 37, 170)   # iterations split over partial CTAs
+    _, ost = _weed_fit_case(hd, orc, m, c, 5, 10, 10)  # no iteration: empty mask, H_prev kept
+    assert ost == 1
+
+
+def test_weed_fit_odd_level_sizes(hd, orc):
+    # odd extents put centred coordinates (and DLT products) at exactly zero
+    rng = np.random.default_rng(12)
+    for (h, w) in [(241, 321), (121, 163)]:
+        img = random_img(rng, h, w)
+        c = cfg(16, 4)
+        rn = img
+        sn = np.roll(img, (1, -2), axis=(0, 1))
+        cxy, valid, _ = orc.pick_corners(rn, c)
+        _, mxy, _ = orc.search(rn, sn, np.eye(3), c, cxy, valid)
+        _weed_fit_case(hd, orc, ((h, w), cxy, mxy, valid), c, 3)
+
+
+def test_weed_fit_two_plane_toy_scene(hd, orc):
+    import test_oracle_pins as pins
+    rng = np.random.default_rng(6)
+    p_xy, q_xy, lab = pins._two_plane_scene(rng)
+    c = cfg(weed_delta_div=3)
+    valid = np.ones(len(p_xy), np.uint8)
+    _weed_fit_case(hd, orc, ((480, 640), p_xy, q_xy, valid), c, 99)
+
+
+def test_weed_fit_capacity(hd):
+    lib = hd.lib()
+    assert lib.hdrreg_weed_fit_supported(4860) == 1
+    assert lib.hdrreg_weed_fit_supported(12288) == 0
 
 
 # --------------------------------------------------------------------- a8
@@ -360,6 +438,16 @@ def test_fused_three_frame_yuv(hd, orc):
 def test_fused_five_mp(hd, orc, five_mp):
     _, diags = _fused_case(hd, orc, five_mp, cfg(32, 6))
     assert diags[0].levels == 5 and diags[0].tiles == 81 * 60
+
+
+def test_fused_level_beyond_shared_memory_plan(hd, orc):
+    # 1024 x 768 at 8-pixel tiles: 12288 level-0 tiles take the workspace weeding path
+    from paper_1504_01441_b300 import synth
+    spec = synth.StackSpec(1024, 768, ratios=((1, 4),), noise_sigma=1.0, field_amp=2.0,
+                           movers=1, chroma=False)
+    assert hd.lib().hdrreg_weed_fit_supported(12288) == 0
+    _, diags = _fused_case(hd, orc, synth.make_stack(spec, 55), cfg(8, 3, grid_half=3))
+    assert diags[0].tiles == 12288
 
 
 def test_fused_histeq_mode(hd, orc, small_yuv_stack):
