@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=16, help="stacks per step (inputs > L2)")
     ap.add_argument("--distinct", type=int, default=2, help="distinct generated stacks")
+    ap.add_argument("--lanes", type=int, default=4, help="concurrent lanes of the batched call")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short run for a profiler")
@@ -148,21 +149,13 @@ def run_ours(args):
         ref = tuple(torch.from_numpy(a).to(dev) for a in (s.ref.y, s.ref.u, s.ref.v))
         src = tuple(torch.from_numpy(a).to(dev) for a in (s.srcs[0].y, s.srcs[0].u, s.srcs[0].v))
         frames.append((ref, [src], s.ratios))
-    runner = hdrreg.RegisterMerge(W, H, 1, p, True, device=dev)
-    outs = [(torch.empty((H, W), dtype=torch.float32, device=dev),
-             torch.empty((H // 2, W // 2), dtype=torch.float32, device=dev),
-             torch.empty((H // 2, W // 2), dtype=torch.float32, device=dev)) for _ in range(P)]
+    runner = hdrreg.RegisterMergeBatch(W, H, 1, p, True, slots=P, lanes=args.lanes, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
     def step():
-        for i, (ref, srcs, ratios) in enumerate(frames):
-            ey, eu, ev = runner(ref, srcs, ratios)
-            outs[i][0].copy_(ey, non_blocking=True)
-            outs[i][1].copy_(eu, non_blocking=True)
-            outs[i][2].copy_(ev, non_blocking=True)
+        runner(frames, stream=stream)
 
-    with torch.cuda.stream(stream):
-        step()  # warm the library (smem attributes) before capture
+    step()  # warm the library (smem attributes, lane streams) before capture
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     n0 = hdrreg.launch_count()
@@ -216,7 +209,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "width": W, "height": H, "format": "YUV420",
                        "frames": 2, "exposure_ratio": 4, "pairs_per_step": P,
                        "distinct_stacks": len(stacks), "tile": 32, "radius": 6,
-                       "path": "plain (a1-a11)", "graph": True,
+                       "path": "plain (a1-a11)", "graph": True, "lanes": args.lanes,
                        "l2": f"inputs larger than L2: {P} resident pairs x 15.1 MB per step",
                        "parallelism": f"replicas x{ws}"},
             "gpu_launches": launches_per_step * K,
@@ -270,23 +263,24 @@ def measure_stages(torch, hdrreg, p, stack, dev, args):
     Hid = torch.tensor([1, 0, 0, 0, 1, 0, 0, 0, 1], dtype=torch.float64, device=dev)
     res = {}
 
+    counter = torch.zeros(1, dtype=torch.int32, device=dev)
+
     def matcher():
         Hc = Hid
         for l in range(L - 1, -1, -1):
             lh, lw = pr[l].shape
             cxy, mxy, cost, valid = hdrreg.local_search(pr[l], ps[l], Hc, p)
-            mask = hdrreg.weed(cxy, mxy, valid, lw, lh, p, p.weed_seed + l)
-            Hc, _ = hdrreg.fit_homography(cxy, mxy, mask, lw, lh, Hc)
+            mask, Hc, _ = hdrreg.weed_fit(cxy, mxy, valid, lw, lh, p, p.weed_seed + l, Hc,
+                                          counter=counter)
         res.update(cxy=cxy, mxy=mxy, mask=mask, H=Hc)
 
     matcher()
     out["matcher"] = _graph_time_us(torch, matcher, reps)
     cxy, mxy, cost, valid = hdrreg.local_search(rn, sn, res["H"], p)
     out["search_level0"] = _graph_time_us(torch, lambda: hdrreg.local_search(rn, sn, res["H"], p), reps)
-    out["weed_level0"] = _graph_time_us(
-        torch, lambda: hdrreg.weed(cxy, mxy, valid, W, H, p, p.weed_seed), reps)
-    out["fit_level0"] = _graph_time_us(
-        torch, lambda: hdrreg.fit_homography(res["cxy"], res["mxy"], res["mask"], W, H, Hid), reps)
+    out["weed_fit_level0"] = _graph_time_us(
+        torch, lambda: hdrreg.weed_fit(cxy, mxy, valid, W, H, p, p.weed_seed, Hid,
+                                       counter=counter), reps)
     fu, fv = hdrreg.flow_upsample(rn, res["cxy"], res["mxy"], res["mask"], res["H"], p)
     out["flow"] = _graph_time_us(
         torch, lambda: hdrreg.flow_upsample(rn, res["cxy"], res["mxy"], res["mask"], res["H"], p), reps)
@@ -310,28 +304,30 @@ def measure_flow_roofline(stages, p):
 
 
 def measure_e2e(torch, hdrreg, runner, stacks, dev, P, args):
-    """Host (pinned) inputs -> device -> fused call -> device -> host outputs, per step."""
+    """Host (pinned) inputs -> device -> batched fused call -> device -> host outputs, per
+    step of P stacks."""
     hin = []
     for i in range(P):
         s = stacks[i % len(stacks)]
         planes = [s.ref.y, s.ref.u, s.ref.v, s.srcs[0].y, s.srcs[0].u, s.srcs[0].v]
         hin.append([torch.from_numpy(a).pin_memory() for a in planes])
-    din = [[torch.empty(t.shape, dtype=t.dtype, device=dev) for t in h] for h in hin[:1]]
+    din = [[torch.empty(t.shape, dtype=t.dtype, device=dev) for t in h] for h in hin]
     hout = [[torch.empty((H, W), dtype=torch.float32).pin_memory(),
              torch.empty((H // 2, W // 2), dtype=torch.float32).pin_memory(),
              torch.empty((H // 2, W // 2), dtype=torch.float32).pin_memory()] for _ in range(P)]
-    s = torch.cuda.current_stream(dev)
+    s = torch.cuda.Stream(device=dev)
     ratios = stacks[0].ratios
+    batch = [((d[0], d[1], d[2]), [(d[3], d[4], d[5])], ratios) for d in din]
 
     def step():
-        for i in range(P):
-            d = din[0]
-            for k in range(6):
-                d[k].copy_(hin[i][k], non_blocking=True)
-            ey, eu, ev = runner((d[0], d[1], d[2]), [(d[3], d[4], d[5])], ratios)
-            hout[i][0].copy_(ey, non_blocking=True)
-            hout[i][1].copy_(eu, non_blocking=True)
-            hout[i][2].copy_(ev, non_blocking=True)
+        with torch.cuda.stream(s):
+            for i in range(P):
+                for k in range(6):
+                    din[i][k].copy_(hin[i][k], non_blocking=True)
+            outs = runner(batch, stream=s)
+            for i in range(P):
+                for k in range(3):
+                    hout[i][k].copy_(outs[i][k], non_blocking=True)
 
     for _ in range(2):
         step()

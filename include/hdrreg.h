@@ -312,6 +312,35 @@ hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int n
                                     const hdrreg_planes_f32* out, hdrreg_diag* diag,
                                     void* stream);
 
+/* ------------------------------------- a1-a11 fused, a batch of stacks
+ * The paper has no counterpart (it registers one burst at a time): many stacks of
+ * one shape run through the fused path of hdrreg_register_merge, stack i on lane
+ * i % lanes. Lanes are streams owned by this library, forked from `stream` and
+ * joined back into it, so that the latency-bound matching of one stack overlaps
+ * the bandwidth-bound flow and merge of others; everything completes before later
+ * work on `stream`, and the call can be captured into a CUDA graph. Results are
+ * identical to one hdrreg_register_merge per stack. The first batched call on a
+ * device (with lanes > 1 and count > 1) creates its lane streams: make it before
+ * any stream capture. Calls from several host threads are serialized inside.
+ * stacks (host array of `count`) and the arrays it points to are read during the
+ * call only. Workspace: hdrreg_register_merge_batch_workspace_size(w, h, nsrc,
+ * lanes, p) (one fused workspace per lane).
+ */
+#define HDRREG_MAX_LANES 16
+typedef struct hdrreg_stack {
+    const hdrreg_frame* ref;  /* reference frame */
+    const hdrreg_frame* srcs; /* nsrc source frames */
+    const int* ratio_num;     /* nsrc exposure ratios t_src / t_ref = num / den */
+    const int* ratio_den;
+    hdrreg_planes_f32 out;    /* merged planes (FP32, device) */
+    hdrreg_diag* diag;        /* optional, device, nsrc entries */
+} hdrreg_stack;
+size_t hdrreg_register_merge_batch_workspace_size(int w, int h, int nsrc, int lanes,
+                                                  const hdrreg_params* p);
+hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count, int w, int h,
+                                          int nsrc, int lanes, const hdrreg_params* p,
+                                          void* workspace, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -524,12 +524,15 @@ size_t hdrreg_register_merge_workspace_size(int w, int h, int nsrc, const hdrreg
     return FusedLayout(w, h, nsrc, p).total;
 }
 
-hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int nsrc,
-                                    const hdrreg_frame* srcs, const int* ratio_num,
-                                    const int* ratio_den, const hdrreg_params* p,
-                                    void* workspace, size_t ws_bytes,
-                                    const hdrreg_planes_f32* out, hdrreg_diag* diag,
-                                    void* stream)
+}  // extern "C"
+
+namespace hdrreg {
+
+// Argument checks of one fused call (everything but the workspace).
+static hdrreg_status rm_validate(const hdrreg_frame* ref, int w, int h, int nsrc,
+                                 const hdrreg_frame* srcs, const int* ratio_num,
+                                 const int* ratio_den, const hdrreg_params* p,
+                                 const hdrreg_planes_f32* out)
 {
     hdrreg_status st = hdrreg_validate_params(p);
     if (st) return st;
@@ -550,11 +553,19 @@ hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int n
     if (!flow_supported(w, h))
         return fail(HDRREG_E_UNSUPPORTED, "register_merge: %dx%d exceeds the flow strip capacity",
                     w, h);
-    const FusedLayout lay(w, h, nsrc, p);
-    if (!workspace || ws_bytes < lay.total)
-        return fail(HDRREG_E_WORKSPACE, "register_merge: workspace of %zu bytes required",
-                    lay.total);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return HDRREG_OK;
+}
+
+// Enqueue the whole path for one validated stack on stream s, using the workspace
+// laid out by `lay`.
+static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
+                                const hdrreg_frame* srcs, const int* ratio_num,
+                                const int* ratio_den, const hdrreg_params* p,
+                                const FusedLayout& lay, void* workspace,
+                                const hdrreg_planes_f32* out, hdrreg_diag* diag, cudaStream_t s)
+{
+    hdrreg_status st = HDRREG_OK;
+    const bool chroma = ref->u && ref->v && out->u && out->v;
     uint8_t* base = static_cast<uint8_t*>(workspace);
     auto at = [&](size_t off) { return base + off; };
     int32_t* corner = reinterpret_cast<int32_t*>(at(lay.corner));
@@ -670,6 +681,126 @@ hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int n
                  p->ssim_sigma, p->we_sigma, out->y, chroma ? out->u : nullptr,
                  chroma ? out->v : nullptr, nullptr, s);
     return launch_status("register_merge(merge)");
+}
+
+// Streams and events of the batched call, created once per device on its first
+// batched call and kept for the process lifetime.
+struct LaneSet {
+    cudaStream_t stream[HDRREG_MAX_LANES];
+    cudaEvent_t fork, join[HDRREG_MAX_LANES];
+    bool ready = false;
+};
+
+static hdrreg_status lane_set(LaneSet** out)
+{
+    static std::mutex mu;
+    static std::map<int, LaneSet> sets;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(HDRREG_E_CUDA, "batch: cudaGetDevice: %s", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(mu);
+    LaneSet& ls = sets[dev];
+    if (!ls.ready) {
+        e = cudaEventCreateWithFlags(&ls.fork, cudaEventDisableTiming);
+        for (int i = 0; i < HDRREG_MAX_LANES && e == cudaSuccess; i++) {
+            e = cudaStreamCreateWithFlags(&ls.stream[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ls.join[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess)
+            return fail(HDRREG_E_CUDA, "batch: creating lane streams: %s", cudaGetErrorString(e));
+        ls.ready = true;
+    }
+    *out = &ls;
+    return HDRREG_OK;
+}
+
+}  // namespace hdrreg
+
+extern "C" {
+
+hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int nsrc,
+                                    const hdrreg_frame* srcs, const int* ratio_num,
+                                    const int* ratio_den, const hdrreg_params* p,
+                                    void* workspace, size_t ws_bytes,
+                                    const hdrreg_planes_f32* out, hdrreg_diag* diag,
+                                    void* stream)
+{
+    hdrreg_status st = rm_validate(ref, w, h, nsrc, srcs, ratio_num, ratio_den, p, out);
+    if (st) return st;
+    const FusedLayout lay(w, h, nsrc, p);
+    if (!workspace || ws_bytes < lay.total)
+        return fail(HDRREG_E_WORKSPACE, "register_merge: workspace of %zu bytes required",
+                    lay.total);
+    return rm_enqueue(ref, w, h, nsrc, srcs, ratio_num, ratio_den, p, lay, workspace, out, diag,
+                      static_cast<cudaStream_t>(stream));
+}
+
+size_t hdrreg_register_merge_batch_workspace_size(int w, int h, int nsrc, int lanes,
+                                                  const hdrreg_params* p)
+{
+    if (!p || bad_dims(w, h) || nsrc < 1 || nsrc > kMaxSources || lanes < 1 ||
+        lanes > HDRREG_MAX_LANES)
+        return 0;
+    return (size_t)lanes * align_up(FusedLayout(w, h, nsrc, p).total, 256);
+}
+
+hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count, int w, int h,
+                                          int nsrc, int lanes, const hdrreg_params* p,
+                                          void* workspace, size_t ws_bytes, void* stream)
+{
+    if (count < 0 || (count > 0 && !stacks))
+        return fail(HDRREG_E_INVALID_ARG, "register_merge_batch: bad stack array");
+    if (lanes < 1 || lanes > HDRREG_MAX_LANES)
+        return fail(HDRREG_E_INVALID_ARG, "register_merge_batch: lanes must be in [1, %d]",
+                    HDRREG_MAX_LANES);
+    for (int i = 0; i < count; i++) {
+        const hdrreg_stack& k = stacks[i];
+        hdrreg_status st =
+            rm_validate(k.ref, w, h, nsrc, k.srcs, k.ratio_num, k.ratio_den, p, &k.out);
+        if (st) return fail(st, "register_merge_batch: stack %d: %s", i, hdrreg_last_error());
+    }
+    const size_t per = align_up(FusedLayout(w, h, nsrc, p).total, 256);
+    if (!workspace || ws_bytes < per * lanes)
+        return fail(HDRREG_E_WORKSPACE, "register_merge_batch: workspace of %zu bytes required",
+                    per * lanes);
+    if (count == 0) return HDRREG_OK;
+    const FusedLayout lay(w, h, nsrc, p);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int used = count < lanes ? count : lanes;
+    if (used == 1) {
+        for (int i = 0; i < count; i++) {
+            const hdrreg_stack& k = stacks[i];
+            hdrreg_status st = rm_enqueue(k.ref, w, h, nsrc, k.srcs, k.ratio_num, k.ratio_den, p,
+                                          lay, workspace, &k.out, k.diag, s);
+            if (st) return st;
+        }
+        return HDRREG_OK;
+    }
+    LaneSet* ls = nullptr;
+    hdrreg_status st = lane_set(&ls);
+    if (st) return st;
+    static std::mutex enqueue_mu;  // one batched enqueue at a time per process
+    std::lock_guard<std::mutex> lock(enqueue_mu);
+    cudaError_t e = cudaEventRecord(ls->fork, s);
+    for (int j = 0; j < used && e == cudaSuccess; j++) e = cudaStreamWaitEvent(ls->stream[j], ls->fork, 0);
+    if (e != cudaSuccess)
+        return fail(HDRREG_E_CUDA, "register_merge_batch: fork: %s", cudaGetErrorString(e));
+    for (int i = 0; i < count; i++) {
+        const int j = i % used;
+        const hdrreg_stack& k = stacks[i];
+        st = rm_enqueue(k.ref, w, h, nsrc, k.srcs, k.ratio_num, k.ratio_den, p, lay,
+                        static_cast<uint8_t*>(workspace) + per * j, &k.out, k.diag,
+                        ls->stream[j]);
+        if (st) break;
+    }
+    for (int j = 0; j < used; j++) {  // join every lane, also after an error
+        cudaError_t e1 = cudaEventRecord(ls->join[j], ls->stream[j]);
+        cudaError_t e2 = cudaStreamWaitEvent(s, ls->join[j], 0);
+        if (!st && (e1 != cudaSuccess || e2 != cudaSuccess))
+            st = fail(HDRREG_E_CUDA, "register_merge_batch: join: %s",
+                      cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    }
+    return st;
 }
 
 }  // extern "C"

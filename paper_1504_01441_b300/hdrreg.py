@@ -29,7 +29,10 @@ EXPORTS = [
     "hdrreg_fit_homography", "hdrreg_weed_fit_supported", "hdrreg_weed_fit",
     "hdrreg_flow_workspace_size", "hdrreg_flow_upsample", "hdrreg_warp", "hdrreg_merge",
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
+    "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
 ]
+
+MAX_LANES = 16
 
 
 class HdrregError(RuntimeError):
@@ -66,6 +69,12 @@ class PlanesF32(C.Structure):
 class MergeSrc(C.Structure):
     _fields_ = [("y", C.c_void_p), ("u", C.c_void_p), ("v", C.c_void_p), ("ref_n", C.c_void_p),
                 ("src_lut", C.c_void_p), ("ratio_num", C.c_int), ("ratio_den", C.c_int)]
+
+
+class Stack(C.Structure):
+    _fields_ = [("ref", C.POINTER(Frame)), ("srcs", C.POINTER(Frame)),
+                ("ratio_num", C.POINTER(C.c_int)), ("ratio_den", C.POINTER(C.c_int)),
+                ("out", PlanesF32), ("diag", C.c_void_p)]
 
 
 class Diag(C.Structure):
@@ -124,6 +133,10 @@ def lib():
                                             C.POINTER(C.c_int), C.POINTER(C.c_int),
                                             C.POINTER(Params), vp, sz, C.POINTER(PlanesF32),
                                             vp, vp]
+        L.hdrreg_register_merge_batch_workspace_size.restype = sz
+        L.hdrreg_register_merge_batch_workspace_size.argtypes = [i, i, i, i, C.POINTER(Params)]
+        L.hdrreg_register_merge_batch.argtypes = [C.POINTER(Stack), i, i, i, i, i,
+                                                  C.POINTER(Params), vp, sz, vp]
         for name in EXPORTS:
             if not hasattr(L, name):
                 raise ImportError(f"libhdrreg.so does not export {name}")
@@ -376,6 +389,63 @@ class RegisterMerge:
 
     def diagnostics(self) -> List[Diag]:
         raw = self.diag.cpu().numpy().tobytes()
+        n = C.sizeof(Diag)
+        return [Diag.from_buffer_copy(raw[i * n:(i + 1) * n]) for i in range(self.nsrc)]
+
+
+class RegisterMergeBatch:
+    """Batched fused call for stacks of one shape on `lanes` concurrent lanes: owns the
+    lane workspaces and one set of output planes per stack slot."""
+
+    def __init__(self, w: int, h: int, nsrc: int, p: Params, chroma: bool, slots: int,
+                 lanes: int = 4, device="cuda"):
+        import torch
+        self.w, self.h, self.nsrc, self.p, self.chroma = w, h, nsrc, p, chroma
+        self.lanes = lanes
+        n = lib().hdrreg_register_merge_batch_workspace_size(w, h, nsrc, lanes, C.byref(p))
+        if n == 0:
+            raise HdrregError(1, "bad shape, lanes or parameters for register_merge_batch")
+        self.ws = torch.empty((n,), dtype=torch.uint8, device=device)
+
+        def plane(hh, ww):
+            return torch.empty((hh, ww), dtype=torch.float32, device=device)
+        self.outs = [(plane(h, w), plane(h // 2, w // 2) if chroma else None,
+                      plane(h // 2, w // 2) if chroma else None) for _ in range(slots)]
+        self.diag = torch.zeros((slots, nsrc, C.sizeof(Diag)), dtype=torch.uint8, device=device)
+        self._keep = None
+
+    def __call__(self, stacks, stream=None):
+        """stacks: list of (ref, srcs, ratios) as for RegisterMerge; -> list of planes."""
+        k = len(stacks)
+        if k > len(self.outs):
+            raise ValueError("more stacks than output slots")
+        arr = (Stack * max(k, 1))()
+        keep = []
+        for i, (ref, srcs, ratios) in enumerate(stacks):
+            if len(srcs) != self.nsrc:
+                raise ValueError("number of sources differs from the one this call was built for")
+            fr = Frame(_ptr(ref[0]), _ptr(ref[1]) if self.chroma else None,
+                       _ptr(ref[2]) if self.chroma else None)
+            fs = (Frame * self.nsrc)(*[Frame(_ptr(s[0]), _ptr(s[1]) if self.chroma else None,
+                                             _ptr(s[2]) if self.chroma else None) for s in srcs])
+            num = (C.c_int * self.nsrc)(*[r[0] for r in ratios])
+            den = (C.c_int * self.nsrc)(*[r[1] for r in ratios])
+            o = self.outs[i]
+            arr[i].ref = C.pointer(fr)
+            arr[i].srcs = C.cast(fs, C.POINTER(Frame))
+            arr[i].ratio_num = C.cast(num, C.POINTER(C.c_int))
+            arr[i].ratio_den = C.cast(den, C.POINTER(C.c_int))
+            arr[i].out = PlanesF32(_ptr(o[0]), _ptr(o[1]), _ptr(o[2]))
+            arr[i].diag = _ptr(self.diag[i])
+            keep.append((fr, fs, num, den))
+        _check(lib().hdrreg_register_merge_batch(arr, k, self.w, self.h, self.nsrc, self.lanes,
+                                                 C.byref(self.p), _ptr(self.ws),
+                                                 self.ws.numel(), _stream(stream)))
+        self._keep = keep
+        return self.outs[:k]
+
+    def diagnostics(self, slot: int) -> List[Diag]:
+        raw = self.diag[slot].cpu().numpy().tobytes()
         n = C.sizeof(Diag)
         return [Diag.from_buffer_copy(raw[i * n:(i + 1) * n]) for i in range(self.nsrc)]
 

@@ -102,6 +102,28 @@ def test_null_and_size_errors_return_before_any_launch(hd):
     assert b"NULL" in lib.hdrreg_last_error() or b"range" in lib.hdrreg_last_error()
 
 
+def test_batch_sizes_and_argument_errors(hd):
+    lib = hd.lib()
+    p = hd.params(tile=32, radius=6)
+    one = hd.register_merge_workspace_size(2592, 1944, 1, p)
+    four = lib.hdrreg_register_merge_batch_workspace_size(2592, 1944, 1, 4, C.byref(p))
+    assert four >= 4 * one and four < 4 * (one + 256)
+    assert lib.hdrreg_register_merge_batch_workspace_size(2592, 1944, 1, 0, C.byref(p)) == 0
+    assert lib.hdrreg_register_merge_batch_workspace_size(2592, 1944, 1, hd.MAX_LANES + 1,
+                                                          C.byref(p)) == 0
+    # rejected on the host: bad lane count, negative count, missing stack array, NULL planes
+    assert lib.hdrreg_register_merge_batch(None, 0, 64, 64, 1, 0, C.byref(p), None, 0, None) == 1
+    assert lib.hdrreg_register_merge_batch(None, -1, 64, 64, 1, 2, C.byref(p), None, 0, None) == 1
+    assert lib.hdrreg_register_merge_batch(None, 3, 64, 64, 1, 2, C.byref(p), None, 0, None) == 1
+    f = hd.Frame(None, None, None)
+    st = (hd.Stack * 1)()
+    st[0].ref = C.pointer(f)
+    assert lib.hdrreg_register_merge_batch(st, 1, 64, 64, 1, 2, C.byref(p), None, 0, None) == 1
+    assert b"stack 0" in lib.hdrreg_last_error()
+    # an empty batch with a workspace check only
+    assert lib.hdrreg_register_merge_batch(None, 0, 64, 64, 1, 2, C.byref(p), None, 0, None) == 6
+
+
 def test_python_binding_refuses_cpu_tensors(hd):
     import torch
     with pytest.raises(ValueError):
