@@ -103,6 +103,18 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+def max_over_ranks(torch, dist, ms, device):
+    """Slowest rank's step time: every rank contributes its own, all receive the max."""
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size, mpix_per_rank_step, ms_step):
+    """Whole-job throughput: the pixels all replicas processed per step over the step time."""
+    return world_size * mpix_per_rank_step / (ms_step / 1e3)
+
+
 def make_inputs(n_distinct):
     from paper_1504_01441_b300 import synth
     stacks = [synth.make_stack(synth.FIVE_MP, synth.stack_seed(2, i)) for i in range(n_distinct)]
@@ -180,13 +192,11 @@ def run_ours(args):
         torch.cuda.synchronize()
     ms = start.elapsed_time(end)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(torch, dist, ms, dev)
         dist.barrier()
     ms_step = ms / K
     mpix_step = P * W * H / 1e6
-    value = ws * mpix_step / (ms_step / 1e3)
+    value = job_value(ws, mpix_step, ms_step)
 
     # -- dominant stage: the flow (6 domain-transform passes), timed alone on its stream
     roof, stages = None, None
