@@ -312,6 +312,19 @@ hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int n
                                     const hdrreg_planes_f32* out, hdrreg_diag* diag,
                                     void* stream);
 
+/* --------------------------------------- a-L: tensor-core bf16 product
+ * The paper has no counterpart (it has no learned component): the dense
+ * contraction under every convolution of the learned displacement predictor.
+ * C[M x N] (FP32, row stride ldc) = A[M x K] * B[N x K]^T, A and B bfloat16 with K
+ * contiguous (row strides lda, ldb elements), accumulated in FP32 on the tensor
+ * cores. A and B must be 16-byte aligned with lda, ldb multiples of 8; M, N, K >= 1.
+ * status (device int32, zero on entry) is set to 1 if the kernel gave up waiting
+ * for its own copies (nothing then is written to C). HDRREG_E_UNSUPPORTED if the
+ * alignment rules are not met or the driver has no tensor-map support.
+ */
+hdrreg_status hdrreg_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N,
+                               int K, float* C, int ldc, int32_t* status, void* stream);
+
 /* ------------------------------------- a1-a11 fused, a batch of stacks
  * The paper has no counterpart (it registers one burst at a time): many stacks of
  * one shape run through the fused path of hdrreg_register_merge, stack i on lane

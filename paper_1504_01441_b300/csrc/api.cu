@@ -735,6 +735,22 @@ hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int n
                       static_cast<cudaStream_t>(stream));
 }
 
+hdrreg_status hdrreg_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N,
+                               int K, float* C, int ldc, int32_t* status, void* stream)
+{
+    if (!A || !B || !C || !status) return fail(HDRREG_E_INVALID_ARG, "gemm: NULL pointer");
+    if (M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N)
+        return fail(HDRREG_E_INVALID_ARG, "gemm: bad sizes M=%d N=%d K=%d lda=%d ldb=%d ldc=%d", M,
+                    N, K, lda, ldb, ldc);
+    if (!gemm_supported(A, lda, B, ldb))
+        return fail(HDRREG_E_UNSUPPORTED,
+                    "gemm: operands must be 16-byte aligned with lda, ldb multiples of 8");
+    GemmEpi e{kEpiF32, C, nullptr, nullptr, ldc, 0};
+    if (!launch_gemm_bf16(A, lda, B, ldb, M, N, K, 1, e, status, static_cast<cudaStream_t>(stream)))
+        return fail(HDRREG_E_UNSUPPORTED, "gemm: tensor map creation failed");
+    return launch_status("gemm_bf16");
+}
+
 size_t hdrreg_register_merge_batch_workspace_size(int w, int h, int nsrc, int lanes,
                                                   const hdrreg_params* p)
 {

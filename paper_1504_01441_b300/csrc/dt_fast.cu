@@ -728,6 +728,8 @@ void launch_rows_pipe(int first, float* P0, float* P1, float* P2, const uint8_t*
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 bool flow_fast_supported(int w, int h, const uint8_t* guide, const float* fu, const float* fv)
 {
     // TMA: 16-byte aligned bases and row pitches (w % 16 for the u8 guide)

@@ -1,6 +1,9 @@
 // Internal declarations of the hdrreg CUDA library (sm_103a).
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -350,6 +353,9 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// cuTensorMapEncodeTiled from the driver (resolved once; nullptr if unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
 // ----------------------------------------------------------------- launchers
 struct LutSpec {         // a per-frame 8-bit map: device table, or round(v*gn/gd) clipped
     const uint8_t* dev;  // 256 entries, or nullptr
@@ -457,5 +463,24 @@ constexpr int kMaxSources = 4;
 void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v, int w, int h,
                   int nsrc, const MergeSrcDev* srcs, double ssim_sigma, double we_sigma,
                   float* oy, float* ou, float* ov, float* q_out, cudaStream_t s);
+
+// ------------------------------------------ tensor-core GEMM (row a-L)
+// C[M x N] = A[M x K] * B[N x K]^T, bf16 K-major operands (16-byte aligned, ld % 8 == 0),
+// FP32 accumulation; the epilogue writes FP32 (per K split at out + split * split_stride),
+// FP32 + bias, or bf16 max(0, acc + bias).
+enum { kEpiF32 = 0, kEpiBiasF32 = 1, kEpiBiasReluBf16 = 2 };
+struct GemmEpi {
+    int mode;
+    float* out;
+    __nv_bfloat16* out_bf16;
+    const float* bias;
+    int ldc;
+    size_t split_stride;
+};
+int gemm_bn_for(int N);
+bool gemm_supported(const void* A, int lda, const void* B, int ldb);
+int gemm_splits_used(int K, int splits);
+bool launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                      int splits, const GemmEpi& epi, int* err, cudaStream_t s);
 
 }  // namespace hdrreg

@@ -30,6 +30,7 @@ EXPORTS = [
     "hdrreg_flow_workspace_size", "hdrreg_flow_upsample", "hdrreg_warp", "hdrreg_merge",
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
+    "hdrreg_gemm_bf16",
 ]
 
 MAX_LANES = 16
@@ -137,6 +138,7 @@ def lib():
         L.hdrreg_register_merge_batch_workspace_size.argtypes = [i, i, i, i, C.POINTER(Params)]
         L.hdrreg_register_merge_batch.argtypes = [C.POINTER(Stack), i, i, i, i, i,
                                                   C.POINTER(Params), vp, sz, vp]
+        L.hdrreg_gemm_bf16.argtypes = [vp, i, vp, i, i, i, i, vp, i, vp, vp]
         for name in EXPORTS:
             if not hasattr(L, name):
                 raise ImportError(f"libhdrreg.so does not export {name}")
@@ -391,6 +393,18 @@ class RegisterMerge:
         raw = self.diag.cpu().numpy().tobytes()
         n = C.sizeof(Diag)
         return [Diag.from_buffer_copy(raw[i * n:(i + 1) * n]) for i in range(self.nsrc)]
+
+
+def gemm_bf16(A, B, stream=None):
+    """C = A @ B.T for bf16 CUDA matrices A [M, K], B [N, K] (row-major) -> FP32 [M, N]."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    st = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().hdrreg_gemm_bf16(_ptr(A), A.stride(0), _ptr(B), B.stride(0), M, N, K, _ptr(C),
+                                  N, _ptr(st), _stream(stream)))
+    return C, st
 
 
 class RegisterMergeBatch:
