@@ -325,6 +325,37 @@ hdrreg_status hdrreg_register_merge(const hdrreg_frame* ref, int w, int h, int n
 hdrreg_status hdrreg_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N,
                                int K, float* C, int ldc, int32_t* status, void* stream);
 
+/* ----------------------------------- a-L: the learned displacement predictor
+ * The paper has no counterpart (its level-0 displacements come from the SSD search
+ * of Sec. 2.2). A convolutional network reads the normalized reference and the
+ * source pre-warped by the level-1 homography at quarter resolution, x [n][h][w][2]
+ * (bfloat16 bits, NHWC), and outputs one displacement per 32x32 full-resolution
+ * tile, out [n][ho][wo][2] FP32 (ho, wo from hdrreg_cnn_out_dims: three stride-2
+ * steps, ceil). Layers: 3x3 convolutions 2-16, 16-16, 16-32 (stride 2), 32-32,
+ * 32-48 (stride 2), 48-48, 48-64 (stride 2), 64-64, each with bias and ReLU, then a
+ * 1x1 head 64-2. theta: HDRREG_CNN_PARAMS FP32 values, per layer W[cout][ky][kx][cin]
+ * then b[cout]. Activations are stored in bfloat16, products accumulate in FP32 on
+ * the tensor cores. hdrreg_cnn_backward uses the activations the preceding
+ * hdrreg_cnn_forward left in the same workspace (same n, h, w, x, theta): loss (a
+ * device float) = sum over valid cells |out - label|^2 / max(n_valid, 1), grad
+ * (HDRREG_CNN_PARAMS floats) = its gradient. hdrreg_cnn_adam applies one Adam step
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias correction at step >= 1) in place.
+ * status: device int32, zero on entry, set to 1 if a tensor-core kernel gave up
+ * waiting for its copies. Workspace: hdrreg_cnn_workspace_size(n, h, w).
+ */
+#define HDRREG_CNN_PARAMS 115938
+size_t hdrreg_cnn_workspace_size(int n, int h, int w);
+int hdrreg_cnn_out_dims(int h, int w, int* ho, int* wo);
+hdrreg_status hdrreg_cnn_forward(const float* theta, const uint16_t* x, int n, int h, int w,
+                                 float* out, void* workspace, size_t ws_bytes, int32_t* status,
+                                 void* stream);
+hdrreg_status hdrreg_cnn_backward(const float* theta, const uint16_t* x, int n, int h, int w,
+                                  const float* out, const float* label, const uint8_t* valid,
+                                  float* grad, float* loss, void* workspace, size_t ws_bytes,
+                                  int32_t* status, void* stream);
+hdrreg_status hdrreg_cnn_adam(float* theta, float* m, float* v, const float* grad, int step,
+                              float lr, void* stream);
+
 /* ------------------------------------- a1-a11 fused, a batch of stacks
  * The paper has no counterpart (it registers one burst at a time): many stacks of
  * one shape run through the fused path of hdrreg_register_merge, stack i on lane

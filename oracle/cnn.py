@@ -148,8 +148,11 @@ def loss_and_grad_out(out, label, valid):
     return float((d * d).sum() / nv), 2.0 * d / nv
 
 
-def backward(cache, dout, layers=LAYERS):
-    """Flat gradient of the loss w.r.t. theta (float64), given dL/dout."""
+def backward(cache, dout, bf16=False, layers=LAYERS):
+    """Flat gradient of the loss w.r.t. theta (float64), given dL/dout. bf16=True rounds
+    each layer's output gradient (after the ReLU mask) to bfloat16, where the CUDA path
+    stores it; the cache of a bf16 forward already holds bfloat16 weights and
+    activations."""
     params, acts = cache
     grads = [None] * len(layers)
     g = dout
@@ -158,6 +161,8 @@ def backward(cache, dout, layers=LAYERS):
         W, b = params[i]
         if r:
             g = g * (acts[i + 1] > 0)
+        if bf16:
+            g = bf16_round(g)
         dx, dW, db = conv_backward(acts[i], W, g, s)
         grads[i] = (dW, db)
         g = dx

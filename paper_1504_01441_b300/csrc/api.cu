@@ -751,6 +751,66 @@ hdrreg_status hdrreg_gemm_bf16(const void* A, int lda, const void* B, int ldb, i
     return launch_status("gemm_bf16");
 }
 
+static bool cnn_bad_dims(int n, int h, int w)
+{
+    return n < 1 || h < 8 || w < 8 || h > 4096 || w > 4096 || (long long)n * h * w > (1LL << 24);
+}
+
+size_t hdrreg_cnn_workspace_size(int n, int h, int w)
+{
+    return cnn_bad_dims(n, h, w) ? 0 : cnn_ws_bytes(n, h, w);
+}
+
+int hdrreg_cnn_out_dims(int h, int w, int* ho, int* wo)
+{
+    if (!ho || !wo || cnn_bad_dims(1, h, w)) return 1;
+    cnn_out_dims(h, w, ho, wo);
+    return 0;
+}
+
+hdrreg_status hdrreg_cnn_forward(const float* theta, const uint16_t* x, int n, int h, int w,
+                                 float* out, void* workspace, size_t ws_bytes, int32_t* status,
+                                 void* stream)
+{
+    if (!theta || !x || !out || !status) return fail(HDRREG_E_INVALID_ARG, "cnn_forward: NULL pointer");
+    if (cnn_bad_dims(n, h, w))
+        return fail(HDRREG_E_INVALID_ARG, "cnn_forward: bad batch %d x %d x %d", n, h, w);
+    if (!workspace || ws_bytes < cnn_ws_bytes(n, h, w))
+        return fail(HDRREG_E_WORKSPACE, "cnn_forward: workspace of %zu bytes required",
+                    cnn_ws_bytes(n, h, w));
+    if (!cnn_forward(theta, reinterpret_cast<const __nv_bfloat16*>(x), n, h, w, out, workspace,
+                     status, static_cast<cudaStream_t>(stream)))
+        return fail(HDRREG_E_UNSUPPORTED, "cnn_forward: tensor-core product not available");
+    return launch_status("cnn_forward");
+}
+
+hdrreg_status hdrreg_cnn_backward(const float* theta, const uint16_t* x, int n, int h, int w,
+                                  const float* out, const float* label, const uint8_t* valid,
+                                  float* grad, float* loss, void* workspace, size_t ws_bytes,
+                                  int32_t* status, void* stream)
+{
+    if (!theta || !x || !out || !label || !valid || !grad || !loss || !status)
+        return fail(HDRREG_E_INVALID_ARG, "cnn_backward: NULL pointer");
+    if (cnn_bad_dims(n, h, w))
+        return fail(HDRREG_E_INVALID_ARG, "cnn_backward: bad batch %d x %d x %d", n, h, w);
+    if (!workspace || ws_bytes < cnn_ws_bytes(n, h, w))
+        return fail(HDRREG_E_WORKSPACE, "cnn_backward: workspace of %zu bytes required",
+                    cnn_ws_bytes(n, h, w));
+    if (!cnn_backward(theta, reinterpret_cast<const __nv_bfloat16*>(x), n, h, w, out, label, valid,
+                      grad, loss, workspace, status, static_cast<cudaStream_t>(stream)))
+        return fail(HDRREG_E_UNSUPPORTED, "cnn_backward: tensor-core product not available");
+    return launch_status("cnn_backward");
+}
+
+hdrreg_status hdrreg_cnn_adam(float* theta, float* m, float* v, const float* grad, int step,
+                              float lr, void* stream)
+{
+    if (!theta || !m || !v || !grad) return fail(HDRREG_E_INVALID_ARG, "cnn_adam: NULL pointer");
+    if (step < 1 || !(lr > 0)) return fail(HDRREG_E_INVALID_ARG, "cnn_adam: step >= 1, lr > 0");
+    cnn_adam(theta, m, v, grad, step, lr, static_cast<cudaStream_t>(stream));
+    return launch_status("cnn_adam");
+}
+
 size_t hdrreg_register_merge_batch_workspace_size(int w, int h, int nsrc, int lanes,
                                                   const hdrreg_params* p)
 {

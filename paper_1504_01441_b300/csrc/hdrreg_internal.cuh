@@ -483,4 +483,16 @@ int gemm_splits_used(int K, int splits);
 bool launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
                       int splits, const GemmEpi& epi, int* err, cudaStream_t s);
 
+// ------------------------------------------- learned predictor (row a-L)
+size_t cnn_params();
+size_t cnn_ws_bytes(int n, int h, int w);
+void cnn_out_dims(int h, int w, int* ho, int* wo);
+bool cnn_forward(const float* theta, const __nv_bfloat16* x, int n, int h, int w, float* out,
+                 void* ws, int* err, cudaStream_t s);
+bool cnn_backward(const float* theta, const __nv_bfloat16* x, int n, int h, int w, const float* out,
+                  const float* label, const uint8_t* valid, float* grad, float* loss, void* ws,
+                  int* err, cudaStream_t s);
+void cnn_adam(float* theta, float* m, float* v, const float* grad, int step, float lr,
+              cudaStream_t s);
+
 }  // namespace hdrreg

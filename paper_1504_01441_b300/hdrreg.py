@@ -30,8 +30,11 @@ EXPORTS = [
     "hdrreg_flow_workspace_size", "hdrreg_flow_upsample", "hdrreg_warp", "hdrreg_merge",
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
-    "hdrreg_gemm_bf16",
+    "hdrreg_gemm_bf16", "hdrreg_cnn_workspace_size", "hdrreg_cnn_out_dims", "hdrreg_cnn_forward",
+    "hdrreg_cnn_backward", "hdrreg_cnn_adam",
 ]
+
+CNN_PARAMS = 115938
 
 MAX_LANES = 16
 
@@ -139,6 +142,12 @@ def lib():
         L.hdrreg_register_merge_batch.argtypes = [C.POINTER(Stack), i, i, i, i, i,
                                                   C.POINTER(Params), vp, sz, vp]
         L.hdrreg_gemm_bf16.argtypes = [vp, i, vp, i, i, i, i, vp, i, vp, vp]
+        L.hdrreg_cnn_workspace_size.restype = sz
+        L.hdrreg_cnn_workspace_size.argtypes = [i, i, i]
+        L.hdrreg_cnn_out_dims.argtypes = [i, i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.hdrreg_cnn_forward.argtypes = [vp, vp, i, i, i, vp, vp, sz, vp, vp]
+        L.hdrreg_cnn_backward.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp, vp, sz, vp, vp]
+        L.hdrreg_cnn_adam.argtypes = [vp, vp, vp, vp, i, C.c_float, vp]
         for name in EXPORTS:
             if not hasattr(L, name):
                 raise ImportError(f"libhdrreg.so does not export {name}")
@@ -405,6 +414,51 @@ def gemm_bf16(A, B, stream=None):
     _check(lib().hdrreg_gemm_bf16(_ptr(A), A.stride(0), _ptr(B), B.stride(0), M, N, K, _ptr(C),
                                   N, _ptr(st), _stream(stream)))
     return C, st
+
+
+class Predictor:
+    """The learned tile-displacement network on the GPU: FP32 parameters, Adam state and a
+    workspace for one batch shape (n, h, w) of quarter-resolution inputs."""
+
+    def __init__(self, n: int, h: int, w: int, theta=None, device="cuda"):
+        import torch
+        self.n, self.h, self.w = n, h, w
+        ho, wo = C.c_int(), C.c_int()
+        if lib().hdrreg_cnn_out_dims(h, w, C.byref(ho), C.byref(wo)):
+            raise HdrregError(1, "bad predictor input size")
+        self.ho, self.wo = ho.value, wo.value
+        nb = lib().hdrreg_cnn_workspace_size(n, h, w)
+        if nb == 0:
+            raise HdrregError(1, "bad predictor batch")
+        self.ws = torch.empty((nb,), dtype=torch.uint8, device=device)
+        self.theta = (torch.zeros(CNN_PARAMS, dtype=torch.float32, device=device) if theta is None
+                      else torch.as_tensor(theta, dtype=torch.float32).to(device).contiguous())
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.grad = torch.zeros_like(self.theta)
+        self.out = torch.zeros((n, self.ho, self.wo, 2), dtype=torch.float32, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.t = 0
+
+    def forward(self, x, stream=None):
+        """x: bfloat16 [n, h, w, 2] CUDA tensor -> out FP32 [n, ho, wo, 2]."""
+        _check(lib().hdrreg_cnn_forward(_ptr(self.theta), _ptr(x), self.n, self.h, self.w,
+                                        _ptr(self.out), _ptr(self.ws), self.ws.numel(),
+                                        _ptr(self.status), _stream(stream)))
+        return self.out
+
+    def backward(self, x, label, valid, stream=None):
+        _check(lib().hdrreg_cnn_backward(_ptr(self.theta), _ptr(x), self.n, self.h, self.w,
+                                         _ptr(self.out), _ptr(label), _ptr(valid), _ptr(self.grad),
+                                         _ptr(self.loss), _ptr(self.ws), self.ws.numel(),
+                                         _ptr(self.status), _stream(stream)))
+        return self.loss, self.grad
+
+    def adam(self, lr=1e-3, stream=None):
+        self.t += 1
+        _check(lib().hdrreg_cnn_adam(_ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.grad),
+                                     self.t, C.c_float(lr), _stream(stream)))
 
 
 class RegisterMergeBatch:

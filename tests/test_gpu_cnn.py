@@ -1,0 +1,99 @@
+"""Learned displacement predictor (row a-L) on the GPU against the float64 oracle
+(oracle/cnn.py with the same bfloat16 rounding points): forward output, loss, the
+gradient of every layer's weights and biases, the Adam step, and a loss that falls
+under training. Tolerance: max-norm relative 2e-2 for bf16 tensor-core paths
+(the oracle rounds the same stored values to bfloat16; the rest is FP32 vs FP64
+accumulation order), 1e-5 for the FP32 Adam update."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_01441_b300 import build, hdrreg
+    build.build()
+    return hdrreg
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+def layer_slices():
+    from oracle import cnn
+    out, o = [], 0
+    for ci, co, k, s, r in cnn.LAYERS:
+        nw = co * k * k * ci
+        out.append((slice(o, o + nw), slice(o + nw, o + nw + co)))
+        o += nw + co
+    return out
+
+
+@pytest.mark.parametrize("n,h,w", [(2, 24, 40), (1, 61, 33)])
+def test_forward_and_gradients_match_oracle(hd, n, h, w):
+    from oracle import cnn
+    rng = np.random.default_rng(n * 100 + h)
+    theta = cnn.init_params(7)
+    theta[cnn.n_params() - 2:] = [0.3, -0.2]  # nonzero head bias
+    xb = torch.tensor(rng.uniform(-1, 1, (n, h, w, 2)), dtype=torch.bfloat16)
+    P = hd.Predictor(n, h, w, theta)
+    out = P.forward(xb.cuda()).cpu().numpy()
+    o_or, cache = cnn.forward(theta, xb.double().numpy(), bf16=True)
+    assert out.shape == o_or.shape
+    assert rel(out, o_or) <= 2e-2
+    label = rng.normal(size=out.shape).astype(np.float32)
+    valid = (rng.random(out.shape[:3]) > 0.25).astype(np.uint8)
+    loss, grad = P.backward(xb.cuda(), torch.tensor(label).cuda(), torch.tensor(valid).cuda())
+    torch.cuda.synchronize()
+    assert int(P.status.item()) == 0
+    L, dout = cnn.loss_and_grad_out(o_or, label, valid.astype(bool))
+    g_or = cnn.backward(cache, dout, bf16=True)
+    assert float(loss.item()) == pytest.approx(L, rel=2e-2)
+    g = grad.cpu().numpy()
+    for i, (sw, sb) in enumerate(layer_slices()):
+        assert rel(g[sw], g_or[sw]) <= 2e-2, f"layer {i} weights"
+        assert rel(g[sb], g_or[sb]) <= 2e-2, f"layer {i} biases"
+
+
+def test_adam_matches_oracle(hd):
+    from oracle import cnn
+    rng = np.random.default_rng(4)
+    P = hd.Predictor(1, 16, 16, cnn.init_params(1))
+    th = P.theta.cpu().numpy().astype(np.float64)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    for t in (1, 2, 3):
+        g = rng.normal(size=th.size).astype(np.float32)
+        P.grad.copy_(torch.tensor(g))
+        P.adam(lr=1e-3)
+        th, m, v = cnn.adam_step(th, m, v, g.astype(np.float64), t, lr=1e-3)
+        torch.cuda.synchronize()
+        d = P.theta.cpu().numpy() - th
+        assert np.abs(d).max() <= 1e-5 * np.abs(th).max() + 1e-7
+
+
+def test_training_reduces_the_loss(hd):
+    from oracle import cnn
+    rng = np.random.default_rng(11)
+    n, h, w = 8, 32, 32
+    x = rng.uniform(-1, 1, (n, h, w, 2))
+    xb = torch.tensor(x, dtype=torch.bfloat16).cuda()
+    P = hd.Predictor(n, h, w, cnn.init_params(2))
+    # a learnable target: the mean of channel 1 minus channel 0 over each output cell's 8x8 block
+    blk = (x[..., 1] - x[..., 0]).reshape(n, 4, 8, 4, 8).mean(axis=(2, 4))
+    label = np.stack([blk, -blk], -1).astype(np.float32) * 4
+    lab, val = torch.tensor(label).cuda(), torch.ones((n, 4, 4), dtype=torch.uint8).cuda()
+    losses = []
+    for _ in range(60):
+        P.forward(xb)
+        loss, _ = P.backward(xb, lab, val)
+        losses.append(float(loss.item()))
+        P.adam(lr=3e-3)
+    assert int(P.status.item()) == 0
+    assert losses[-1] < 0.3 * losses[0], losses[::10]
