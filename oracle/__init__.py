@@ -167,6 +167,39 @@ def search(ref_n, src_n, H, cfg, corner_xy, valid):
     return ctr[:n], mxy[:n], cost[:n]
 
 
+# ---------------------------------------------------------------- a-L
+def predictor_input(ref_q, src_q, H):
+    ref_q, src_q = _u8(ref_q), _u8(src_q)
+    h, w = ref_q.shape
+    out = np.zeros((h, w, 2))
+    lib().orc_predictor_input(_p(ref_q), _p(src_q), w, h, _p(_f64(H).reshape(9)), _p(out))
+    return out
+
+
+def tile_labels(corner_xy, match_xy, valid, w, h, H):
+    cxy, mxy, valid = _i32(corner_xy).reshape(-1, 2), _i32(match_xy).reshape(-1, 2), _u8(valid)
+    n = valid.size
+    lab = np.zeros((max(n, 1), 2), np.float32)
+    lib().orc_tile_labels(_p(cxy), _p(mxy), _p(valid), n, w, h, _p(_f64(H).reshape(9)), _p(lab))
+    return lab[:n]
+
+
+def search_predicted(ref_n, src_n, H, cfg, corner_xy, valid, pred, fallback_cost):
+    ref_n, src_n = _u8(ref_n), _u8(src_n)
+    h, w = ref_n.shape
+    cxy, valid = _i32(corner_xy).reshape(-1, 2), _u8(valid)
+    pred = np.ascontiguousarray(pred, np.float32).reshape(-1, 2)
+    n = valid.size
+    mxy = np.zeros((max(n, 1), 2), np.int32)
+    cost = np.zeros(max(n, 1), np.uint32)
+    fb = np.zeros(max(n, 1), np.uint8)
+    prm = make_params(cfg)
+    lib().orc_search_predicted(_p(ref_n), _p(src_n), w, h, _p(_f64(H).reshape(9)), C.byref(prm), n,
+                               _p(cxy), _p(valid), _p(pred), C.c_uint32(int(fallback_cost)),
+                               _p(mxy), _p(cost), _p(fb))
+    return mxy[:n], cost[:n], fb[:n]
+
+
 # ---------------------------------------------------------------- a6
 def splitmix64_at(seed, k):
     f = lib().orc_splitmix64_at

@@ -264,6 +264,91 @@ void orc_search(const uint8_t* ref_n, const uint8_t* src_n, int w, int h, const 
     }
 }
 
+/* ==================================================================== a-L */
+/*
+ * Learned-path pieces (the paper has none; they replace the level-0 search of
+ * Sec. 2.2 by a prediction). Network input at quarter resolution (level q of
+ * the pyramid, w x h): channel 0 = (ref - 127.5) / 127.5, channel 1 = the source
+ * level sampled bilinearly at H(p) (the coarser homography, Eq. 3, reference ->
+ * source), or at p itself when the projection is unusable, scaled the same way.
+ */
+void orc_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,
+                         const double H[9], double* x_out)
+{
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            long i = (long)y * w + x;
+            double xs, ys;
+            int ok = orc_project(H, x, y, w, h, &xs, &ys);
+            if (!ok || !isfinite(xs) || !isfinite(ys)) { xs = x; ys = y; }
+            x_out[2 * i] = ((double)ref_q[i] - 127.5) / 127.5;
+            x_out[2 * i + 1] = (orc_bilinear(src_q, w, h, xs, ys) - 127.5) / 127.5;
+        }
+}
+
+/*
+ * Training label of a tile: its level-0 match minus its search centre (Eq. 3 with
+ * the level-1 homography), i.e. the displacement the plain search found; (0, 0)
+ * for tiles without a corner.
+ */
+void orc_tile_labels(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* valid,
+                     int n, int w, int h, const double H[9], float* label)
+{
+    for (int t = 0; t < n; t++) {
+        label[2 * t] = label[2 * t + 1] = 0.f;
+        if (!valid[t]) continue;
+        int32_t cx, cy;
+        orc_search_center(H, corner_xy[2 * t], corner_xy[2 * t + 1], w, h, &cx, &cy);
+        label[2 * t] = (float)(match_xy[2 * t] - cx);
+        label[2 * t + 1] = (float)(match_xy[2 * t + 1] - cy);
+    }
+}
+
+/*
+ * Search with a prediction: for a tile with a corner p and search centre c, the
+ * predicted displacement d (FP32) is rounded to floor(d + 0.5) (in FP32) and the
+ * SSD of the patches at p and c + round(d) is computed; if it is at most
+ * `fallback_cost` that is the match, otherwise the tile falls back to the full
+ * search of orc_search (fell_back = 1). Tiles without a corner are as in orc_search.
+ */
+void orc_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w, int h,
+                          const double H[9], const orc_params* p, int ntiles,
+                          const int32_t* corner_xy, const uint8_t* valid, const float* pred,
+                          uint32_t fallback_cost, int32_t* match_xy, uint32_t* cost,
+                          uint8_t* fell_back)
+{
+    int hp = p->patch_half;
+    for (int t = 0; t < ntiles; t++) {
+        int32_t ctr[2];
+        fell_back[t] = 0;
+        if (!valid[t]) {
+            orc_search(ref_n, src_n, w, h, H, p, 1, corner_xy + 2 * t, valid + t, ctr,
+                       match_xy + 2 * t, cost + t);
+            continue;
+        }
+        int px = corner_xy[2 * t], py = corner_xy[2 * t + 1];
+        int32_t cx, cy;
+        orc_search_center(H, px, py, w, h, &cx, &cy);
+        float fx = pred[2 * t] + 0.5f, fy = pred[2 * t + 1] + 0.5f;
+        int qx = cx + (int)floorf(fx), qy = cy + (int)floorf(fy);
+        uint64_t c = 0;
+        for (int v = -hp; v <= hp; v++)
+            for (int u = -hp; u <= hp; u++) {
+                long e = (long)pix(ref_n, w, h, px + u, py + v) - (long)pix(src_n, w, h, qx + u, qy + v);
+                c += (uint64_t)(e * e);
+            }
+        if (c <= fallback_cost) {
+            match_xy[2 * t] = qx;
+            match_xy[2 * t + 1] = qy;
+            cost[t] = (uint32_t)c;
+        } else {
+            fell_back[t] = 1;
+            orc_search(ref_n, src_n, w, h, H, p, 1, corner_xy + 2 * t, valid + t, ctr,
+                       match_xy + 2 * t, cost + t);
+        }
+    }
+}
+
 /* ===================================================================== a6 */
 /*
  * SplitMix64 (Steele, Lea and Flood, 2014) used as a counter-based generator:

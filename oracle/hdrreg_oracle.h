@@ -81,6 +81,15 @@ void orc_search(const uint8_t* ref_n, const uint8_t* src_n, int w, int h, const 
 /* ---- a6: weeding (Eq. 4) ------------------------------------------------- */
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k);
 int  orc_weed_sample(uint64_t seed, long iter, int nv, int pick[4]);
+void orc_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,
+                         const double H[9], double* x_out);
+void orc_tile_labels(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* valid,
+                     int n, int w, int h, const double H[9], float* label);
+void orc_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w, int h,
+                          const double H[9], const orc_params* p, int ntiles,
+                          const int32_t* corner_xy, const uint8_t* valid, const float* pred,
+                          uint32_t fallback_cost, int32_t* match_xy, uint32_t* cost,
+                          uint8_t* fell_back);
 int  orc_solve8(const double A[64], const double b[8], double x[8], double tol);
 int  orc_pow2_scale(int w);
 int  orc_is_inlier(const double Ht[9], int px, int py, int qx, int qy, int w, int h, double eps);

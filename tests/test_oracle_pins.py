@@ -671,3 +671,60 @@ def test_merge_source_weight_closed_form(orc, z, taper):
     else:
         w1 = w0 * (z0 - e) / (e - z / r)
         assert abs(w1 - want) < 1e-9 * max(want, 1e-3)
+
+
+# --------------------------------------------------------------------- a-L (learned path)
+def test_predictor_input_identity_and_integer_shift(orc):
+    rng = np.random.default_rng(30)
+    ref = rng.integers(0, 256, (24, 40), dtype=np.uint8)
+    src = rng.integers(0, 256, (24, 40), dtype=np.uint8)
+    x = orc.predictor_input(ref, src, np.eye(3))
+    assert np.array_equal(x[..., 0], (ref - 127.5) / 127.5)
+    assert np.array_equal(x[..., 1], (src - 127.5) / 127.5)
+    # a translation of +3 px in x (normalized 2*3/w) samples src[y, x + 3] exactly
+    H = np.eye(3)
+    H[0, 2] = 2 * 3 / 40
+    x = orc.predictor_input(ref, src, H)
+    assert np.allclose(x[:, :37, 1], (src[:, 3:] - 127.5) / 127.5, atol=1e-12)
+
+
+def test_tile_labels_recover_an_integer_shift(orc):
+    rng = np.random.default_rng(31)
+    c = cfg_for(16, 4)
+    img = np.clip(np.kron(rng.integers(0, 256, (34, 42)), np.ones((4, 4))) +
+                  rng.normal(0, 3, (136, 168)), 0, 255).astype(np.uint8)[:128, :160]
+    src = np.roll(img, (2, -3), axis=(0, 1))  # src(p + (-3, 2)) = ref(p)
+    cxy, valid, _ = orc.pick_corners(img, c)
+    _, mxy, _ = orc.search(img, src, np.eye(3), c, cxy, valid)
+    lab = orc.tile_labels(cxy, mxy, valid, 160, 128, np.eye(3))
+    inner = valid.astype(bool) & (cxy[:, 0] > 12) & (cxy[:, 0] < 147) & (cxy[:, 1] > 12) & \
+        (cxy[:, 1] < 115)
+    assert inner.sum() > 20
+    assert np.all(lab[inner] == [-3.0, 2.0])
+    assert np.all(lab[~valid.astype(bool)] == 0)
+
+
+def test_search_predicted_accepts_good_and_rejects_bad_predictions(orc):
+    rng = np.random.default_rng(32)
+    c = cfg_for(16, 4)
+    img = np.clip(np.kron(rng.integers(0, 256, (34, 42)), np.ones((4, 4))) +
+                  rng.normal(0, 3, (136, 168)), 0, 255).astype(np.uint8)[:128, :160]
+    src = np.roll(img, (1, 2), axis=(0, 1))
+    H = np.eye(3)
+    cxy, valid, _ = orc.pick_corners(img, c)
+    ctr, mxy, cost = orc.search(img, src, H, c, cxy, valid)
+    lab = orc.tile_labels(cxy, mxy, valid, 160, 128, H)
+    # exact predictions with an unbounded threshold give the plain matches and costs
+    m, co, fb = orc.search_predicted(img, src, H, c, cxy, valid, lab + 0.3, 2 ** 32 - 1)
+    assert np.array_equal(m, mxy) and np.array_equal(co, cost) and not fb.any()
+    # predictions far off with a finite threshold fall back to the full search
+    far = lab + np.float32(7.0)
+    m, co, fb = orc.search_predicted(img, src, H, c, cxy, valid, far, 1000)
+    assert np.array_equal(m, mxy) and np.array_equal(co, cost)
+    assert fb.sum() >= (valid.astype(bool) & (cost <= 1000)).sum() * 0.9
+    # rounding is floor(d + 0.5): -0.5 rounds to 0, 0.5 rounds to 1
+    one = valid.astype(bool).nonzero()[0][:1]
+    p0 = np.zeros_like(lab)
+    p0[one] = [-0.5, 0.5]
+    m, _, _ = orc.search_predicted(img, src, H, c, cxy, valid, p0, 2 ** 32 - 1)
+    assert np.array_equal(m[one], ctr[one] + [[0, 1]])
