@@ -90,6 +90,11 @@ typedef struct hdrreg_params {
     double we_sigma;      /* well-exposedness sigma                                     */
     double flow_eps;      /* F = 0 where the filtered normalization map is below this   */
     uint64_t weed_seed;   /* stream of the counter-based sampler (level l uses seed+l)  */
+    const float* predictor; /* learned level-0 search (row a-L): device parameters of the
+                               displacement network, or NULL for the plain SSD search   */
+    uint32_t fallback_cost; /* learned search: a tile whose SSD at the predicted match
+                               exceeds this falls back to the full search              */
+    uint32_t reserved1;
 } hdrreg_params;
 
 /* A YUV420 (or luma-only: u = v = NULL) 8-bit frame, device pointers. */
@@ -125,7 +130,9 @@ typedef struct hdrreg_diag {
     int32_t valid;           /* level-0 tiles with a corner                                 */
     int32_t kept;            /* level-0 matches kept by the weeding                         */
     int32_t fit_status;      /* bit l set: level l kept the coarser homography              */
-    int32_t reserved[3];
+    int32_t fallbacks;       /* learned search: level-0 tiles that fell back to the full
+                                search; -1 on the plain path                                */
+    int32_t reserved[2];
 } hdrreg_diag;
 
 /* ---------------------------------------------------------------- misc */
@@ -355,6 +362,42 @@ hdrreg_status hdrreg_cnn_backward(const float* theta, const uint16_t* x, int n, 
                                   int32_t* status, void* stream);
 hdrreg_status hdrreg_cnn_adam(float* theta, float* m, float* v, const float* grad, int step,
                               float lr, void* stream);
+
+/* ------------------------------------------- a-L: the learned level-0 search
+ * The paper has no counterpart. hdrreg_predictor_input: the network input at
+ * quarter resolution (pyramid level 2, w x h): x[y][x] = ((ref - 127.5) / 127.5,
+ * (s - 127.5) / 127.5) as bfloat16 pairs, s the source level sampled bilinearly
+ * (clamp to edge) at H(p) (H = the level-1 homography, Eq. 3), or at p where the
+ * projection's denominator is not positive. hdrreg_tile_labels: per tile the
+ * displacement match - centre (FP32 integers; 0 without a corner), the centre
+ * being the rounded projection of the corner by H (Eq. 3): the training label.
+ * hdrreg_predictor_crops: gathers n training crops of crop_tiles x crop_tiles
+ * tiles (8 x 8 quarter-resolution pixels each) at the tile origins origins[2i],
+ * origins[2i+1] (device int32, inside the tile grid) from the full input, labels
+ * and validity (a valid label needs a corner). hdrreg_local_search_predicted:
+ * hdrreg_local_search where the match of a tile with a corner is its centre plus
+ * floor(pred + 0.5) (pred: FP32 pairs, pred_rows x pred_ld cells covering the tile grid,
+ * cell (ty, tx)) if the patch SSD there is at most fallback_cost, else the full
+ * search's (fell_back[t] = 1). All pointers are device pointers. The fused calls use
+ * the learned search when params.predictor is set, the tile is 32 and the pyramid has
+ * at least three levels (the network reads level 2); otherwise the plain search.
+ */
+hdrreg_status hdrreg_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,
+                                     const double* H, uint16_t* x_out, void* stream);
+hdrreg_status hdrreg_tile_labels(const int32_t* corner_xy, const int32_t* match_xy,
+                                 const uint8_t* valid, int n, int w, int h, const double* H,
+                                 float* label, void* stream);
+hdrreg_status hdrreg_predictor_crops(const uint16_t* x_full, int wq, int hq, const float* label_full,
+                                     const uint8_t* valid_full, int ntx, int nty,
+                                     const int32_t* origins, int n, int crop_tiles,
+                                     uint16_t* x_out, float* label_out, uint8_t* valid_out,
+                                     void* stream);
+hdrreg_status hdrreg_local_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w,
+                                            int h, const double* H, const hdrreg_params* p,
+                                            const float* pred, int pred_rows, int pred_ld,
+                                            uint32_t fallback_cost, int32_t* corner_xy,
+                                            int32_t* match_xy, uint32_t* cost, uint8_t* valid,
+                                            uint8_t* fell_back, void* stream);
 
 /* ------------------------------------- a1-a11 fused, a batch of stacks
  * The paper has no counterpart (it registers one burst at a time): many stacks of

@@ -109,6 +109,9 @@ struct FusedLayout {
     int L = 1, n0 = 0, nsrc = 1;
     size_t ref_lv[kMaxLevels], src_lv[kMaxLevels];
     size_t corner, match, cost, valid, mask, H, fit_st, done, weed, hist, luts, flow, fu, fv;
+    bool learned = false;  // level-0 search by the predictor (row a-L)
+    int wq = 0, hq = 0, pho = 0, pwo = 0;
+    size_t xq = 0, pred = 0, cnn = 0, fellback = 0;
     size_t wy[kMaxSources], wu[kMaxSources], wv[kMaxSources], refn[kMaxSources];
     size_t total;
     FusedLayout(int w, int h, int ns, const hdrreg_params* p)
@@ -130,13 +133,28 @@ struct FusedLayout {
         mask = lay.add((nn / 32 + 1) * 4);
         H = lay.add((size_t)(kMaxLevels + 2) * 9 * 8);
         fit_st = lay.add(kMaxLevels * 4);
-        done = lay.add(kMaxLevels * 4);
+        done = lay.add((kMaxLevels + 1) * 4);  // completion counters + predictor status word
         weed = lay.add(weed_ws_bytes(n0));
         hist = lay.add(2 * 256 * 4);
         luts = lay.add((size_t)kMaxSources * 512);
         flow = lay.add(flow_ws_bytes(w, h));
         fu = lay.add((size_t)w * h * 4);
         fv = lay.add((size_t)w * h * 4);
+        // one network output cell per 32 x 32 tile (8 x 8 quarter-resolution pixels)
+        learned = p->predictor != nullptr && L >= 3 && p->tile == 32 && (w >> 2) >= 8 &&
+                  (h >> 2) >= 8;
+        if (learned) {
+            wq = w >> 2;
+            hq = h >> 2;
+            cnn_out_dims(hq, wq, &pho, &pwo);
+            learned = pho >= h / 32 && pwo >= w / 32;
+        }
+        if (learned) {
+            xq = lay.add((size_t)wq * hq * 4);
+            pred = lay.add((size_t)pho * pwo * 8);
+            cnn = lay.add(cnn_ws_bytes(1, hq, wq));
+            fellback = lay.add(nn);
+        }
         for (int k = 0; k < ns; k++) {
             wy[k] = lay.add((size_t)w * h * 4);
             wu[k] = lay.add((size_t)(w / 2) * (h / 2) * 4);
@@ -148,21 +166,25 @@ struct FusedLayout {
 };
 
 __global__ void k_diag(const double* H0, const uint8_t* valid, const uint32_t* mask, int n,
-                       const int32_t* fit_st, int levels, hdrreg_diag* d)
+                       const int32_t* fit_st, int levels, const uint8_t* fell_back,
+                       hdrreg_diag* d)
 {
-    __shared__ int sv, sk;
+    __shared__ int sv, sk, sf;
     if (threadIdx.x == 0) {
         sv = 0;
         sk = 0;
+        sf = 0;
     }
     __syncthreads();
-    int v = 0, k = 0;
+    int v = 0, k = 0, f = 0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         v += valid[t];
         k += (mask[t >> 5] >> (t & 31)) & 1u;
+        if (fell_back) f += fell_back[t];
     }
     atomicAdd(&sv, v);
     atomicAdd(&sk, k);
+    atomicAdd(&sf, f);
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 0; i < 9; i++) d->H0[i] = H0[i];
@@ -173,7 +195,8 @@ __global__ void k_diag(const double* H0, const uint8_t* valid, const uint32_t* m
         int bits = 0;
         for (int l = 0; l < levels; l++) bits |= (fit_st[l] != 0) << l;
         d->fit_status = bits;
-        d->reserved[0] = d->reserved[1] = d->reserved[2] = 0;
+        d->fallbacks = fell_back ? sf : -1;
+        d->reserved[0] = d->reserved[1] = 0;
     }
 }
 
@@ -215,6 +238,8 @@ void hdrreg_params_default(hdrreg_params* p)
     p->we_sigma = 0.2;
     p->flow_eps = 1e-20;
     p->weed_seed = 0x1504014410ull;
+    p->predictor = nullptr;
+    p->fallback_cost = 0u;
 }
 
 hdrreg_status hdrreg_validate_params(const hdrreg_params* p)
@@ -624,15 +649,29 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
             launch_pyramid2(ins, w, h, L, luts, outs0, lvs, 2, s);
         }
         // ---- a3..a7 from the coarsest level to level 0
-        launch_set_identity(Hs + 9 * L, s, done, kMaxLevels);
+        launch_set_identity(Hs + 9 * L, s, done, kMaxLevels + 1);
         for (int l = L - 1; l >= 0; l--) {
             const int lw = w >> l, lh = h >> l;
             const uint8_t* rl = l == 0 ? ref0 : at(lay.ref_lv[l]);
             const uint8_t* sl = l == 0 ? src0 : at(lay.src_lv[l]);
             const SearchGeom g = make_geom(lw, lh, p);
             const int n = g.ntx * g.nty;
-            launch_local_search(rl, sl, Hs + 9 * (l + 1), g, corner, match, cost, valid, s,
-                                mask);  // also zeroes the level's mask words
+            if (l == 0 && lay.learned) {
+                // learned level-0 search: network input at quarter resolution (level 2),
+                // prediction per tile, SSD check with fallback to the full search
+                launch_predictor_input(at(lay.ref_lv[2]), at(lay.src_lv[2]), lay.wq, lay.hq,
+                                       Hs + 9, at(lay.xq), s);
+                if (!cnn_forward(p->predictor, reinterpret_cast<const __nv_bfloat16*>(at(lay.xq)), 1,
+                                 lay.hq, lay.wq, reinterpret_cast<float*>(at(lay.pred)),
+                                 at(lay.cnn), reinterpret_cast<int*>(done + kMaxLevels), s))
+                    return fail(HDRREG_E_UNSUPPORTED, "register_merge: tensor-core product not available");
+                const PredSearch ps{reinterpret_cast<const float*>(at(lay.pred)), lay.pwo,
+                                    p->fallback_cost, at(lay.fellback)};
+                launch_local_search(rl, sl, Hs + 9, g, corner, match, cost, valid, s, mask, &ps);
+            } else {
+                launch_local_search(rl, sl, Hs + 9 * (l + 1), g, corner, match, cost, valid, s,
+                                    mask);  // also zeroes the level's mask words
+            }
             if (weed_level_fits(n)) {
                 WeedLevelArgs a{corner, match, valid, n, lw, lh, p->weed_eps, p->weed_delta_min,
                                 p->weed_delta_div, p->weed_seed + (uint64_t)l, 0, p->weed_iters,
@@ -664,7 +703,8 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
                     Hw, fu, fv, wy, chroma ? wu : nullptr, chroma ? wv : nullptr, s);
         if (diag) {
             note_launch();
-            k_diag<<<1, 256, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L, diag + k);
+            k_diag<<<1, 256, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L,
+                                     lay.learned ? at(lay.fellback) : nullptr, diag + k);
         }
         md[k].y = wy;
         md[k].u = chroma ? wu : nullptr;
@@ -749,6 +789,69 @@ hdrreg_status hdrreg_gemm_bf16(const void* A, int lda, const void* B, int ldb, i
     if (!launch_gemm_bf16(A, lda, B, ldb, M, N, K, 1, e, status, static_cast<cudaStream_t>(stream)))
         return fail(HDRREG_E_UNSUPPORTED, "gemm: tensor map creation failed");
     return launch_status("gemm_bf16");
+}
+
+hdrreg_status hdrreg_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,
+                                     const double* H, uint16_t* x_out, void* stream)
+{
+    if (!ref_q || !src_q || !H || !x_out)
+        return fail(HDRREG_E_INVALID_ARG, "predictor_input: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "predictor_input: bad size %dx%d", w, h);
+    launch_predictor_input(ref_q, src_q, w, h, H, x_out, static_cast<cudaStream_t>(stream));
+    return launch_status("predictor_input");
+}
+
+hdrreg_status hdrreg_tile_labels(const int32_t* corner_xy, const int32_t* match_xy,
+                                 const uint8_t* valid, int n, int w, int h, const double* H,
+                                 float* label, void* stream)
+{
+    if (n < 0 || n > (1 << 20)) return fail(HDRREG_E_INVALID_ARG, "tile_labels: n out of range");
+    if (n > 0 && (!corner_xy || !match_xy || !valid || !H || !label))
+        return fail(HDRREG_E_INVALID_ARG, "tile_labels: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "tile_labels: bad size");
+    launch_tile_labels(corner_xy, match_xy, valid, n, w, h, H, label,
+                       static_cast<cudaStream_t>(stream));
+    return launch_status("tile_labels");
+}
+
+hdrreg_status hdrreg_predictor_crops(const uint16_t* x_full, int wq, int hq, const float* label_full,
+                                     const uint8_t* valid_full, int ntx, int nty,
+                                     const int32_t* origins, int n, int crop_tiles,
+                                     uint16_t* x_out, float* label_out, uint8_t* valid_out,
+                                     void* stream)
+{
+    if (!x_full || !label_full || !valid_full || !origins || !x_out || !label_out || !valid_out)
+        return fail(HDRREG_E_INVALID_ARG, "predictor_crops: NULL pointer");
+    if (n < 1 || n > 65535 || crop_tiles < 1 || crop_tiles > 64 || bad_dims(wq, hq) || ntx < 1 ||
+        nty < 1)
+        return fail(HDRREG_E_INVALID_ARG, "predictor_crops: bad sizes");
+    launch_predictor_crops(x_full, wq, hq, label_full, valid_full, ntx, nty, origins, n,
+                           crop_tiles, x_out, label_out, valid_out,
+                           static_cast<cudaStream_t>(stream));
+    return launch_status("predictor_crops");
+}
+
+hdrreg_status hdrreg_local_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w,
+                                            int h, const double* H, const hdrreg_params* p,
+                                            const float* pred, int pred_rows, int pred_ld,
+                                            uint32_t fallback_cost, int32_t* corner_xy,
+                                            int32_t* match_xy, uint32_t* cost, uint8_t* valid,
+                                            uint8_t* fell_back, void* stream)
+{
+    hdrreg_status st = hdrreg_validate_params(p);
+    if (st) return st;
+    if (!ref_n || !src_n || !H || !pred || !corner_xy || !match_xy || !cost || !valid)
+        return fail(HDRREG_E_INVALID_ARG, "local_search_predicted: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "local_search_predicted: bad size");
+    const SearchGeom g = make_geom(w, h, p);
+    if (pred_ld < g.ntx || pred_rows < g.nty)
+        return fail(HDRREG_E_INVALID_ARG,
+                    "local_search_predicted: prediction grid %d x %d smaller than the %d x %d tiles",
+                    pred_rows, pred_ld, g.nty, g.ntx);
+    const PredSearch ps{pred, pred_ld, fallback_cost, fell_back};
+    launch_local_search(ref_n, src_n, H, g, corner_xy, match_xy, cost, valid,
+                        static_cast<cudaStream_t>(stream), nullptr, &ps);
+    return launch_status("local_search_predicted");
 }
 
 static bool cnn_bad_dims(int n, int h, int w)

@@ -379,11 +379,26 @@ struct SearchGeom {
     int w, h, tile, radius, patch_half, grid_half, quad, step, ntx, nty;
     long long corner_thr;
 };
+// Learned level-0 search (row a-L): predicted displacement per tile and the fallback rule.
+struct PredSearch {
+    const float* pred;  // FP32 pairs, cell (ty, tx) at 2 * (ty * pred_ld + tx); nullptr: plain
+    int pred_ld;
+    uint32_t fallback_cost;
+    uint8_t* fell_back;  // optional: 1 where the tile fell back to the full search
+};
 // mask_zero (optional): the level's weeding mask, zeroed word by word on the way
 void launch_local_search(const uint8_t* ref, const uint8_t* src, const double* H,
                          const SearchGeom& g, int32_t* corner_xy, int32_t* match_xy,
                          uint32_t* cost, uint8_t* valid, cudaStream_t s,
-                         uint32_t* mask_zero = nullptr);
+                         uint32_t* mask_zero = nullptr, const PredSearch* pred = nullptr);
+void launch_tile_labels(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* valid,
+                        int n, int w, int h, const double* H, float* label, cudaStream_t s);
+void launch_predictor_crops(const void* x_full, int wq, int hq, const float* label_full,
+                            const uint8_t* valid_full, int ntx, int nty, const int32_t* origins,
+                            int n, int ct, void* x_out, float* label_out, uint8_t* valid_out,
+                            cudaStream_t s);
+void launch_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,
+                            const double* H, void* out, cudaStream_t s);
 
 struct WeedWs {  // workspace of the weeding step
     int32_t* list;      // n: valid tile indices in tile order

@@ -110,12 +110,13 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
     const uint8_t* __restrict__ ref, const uint8_t* __restrict__ src, const double* __restrict__ H,
     SearchGeom g, int32_t* __restrict__ corner_xy, int32_t* __restrict__ match_xy,
     uint32_t* __restrict__ cost_out, uint8_t* __restrict__ valid_out,
-    uint32_t* __restrict__ mask_zero)
+    uint32_t* __restrict__ mask_zero, PredSearch ps)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t red[kWarps];
     __shared__ float hs[18];  // (float)H, |(float)H|
     __shared__ int s_corner[2], s_center[2];
+    __shared__ uint32_t s_pcost;
 
     const SearchSmem L(g);
     uint32_t* region = reinterpret_cast<uint32_t*>(smem + L.off_region);
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
             match_xy[2 * t + 1] = cy;
             cost_out[t] = 0xFFFFFFFFu;
             valid_out[t] = 0;
+            if (ps.fell_back) ps.fell_back[t] = 0;
         }
         return;
     }
@@ -231,8 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
     const int sx = s_center[0], sy = s_center[1];
     const int R = g.radius, hp = g.patch_half, P = L.P, PWc = L.PWc;
 
-    // ---- stage the source window (byte 0 of a row = column sx - R - hp) and the patch
-    stage_block(src, g.w, g.h, sx - R - hp, sy - R - hp, L.WS, L.WS, win, L.WW);
+    // ---- the reference patch as words (byte 0 = column px - hp)
     const int prx = px - ox - hp, pry = py - oy - hp;  // patch origin inside the region
     {
         const int rpw = 32 / PWc, sub = lane / PWc, j = lane - sub * PWc;
@@ -247,6 +248,43 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
             }
         }
     }
+    const uint32_t tail = (P & 3) ? ((1u << (8 * (P & 3))) - 1u) : 0xFFFFFFFFu;
+    if (ps.pred) {
+        // ---- learned search: the SSD at the rounded prediction; keep it if cheap enough
+        const float* pp = ps.pred + 2 * ((size_t)ty * ps.pred_ld + tx);
+        const int qx = sx + (int)floorf(pp[0] + 0.5f), qy = sy + (int)floorf(pp[1] + 0.5f);
+        stage_block(src, g.w, g.h, qx - hp, qy - hp, P, P, win, PWc + 1);
+        if (tid == 0) s_pcost = 0u;
+        __syncthreads();
+        if (tid < P) {
+            const uint32_t* pr = patch + tid * PWc;
+            const uint32_t* wr = win + tid * (PWc + 1);
+            uint32_t acc = 0;
+            for (int j = 0; j < PWc; j++) {
+                const uint32_t d = __vabsdiffu4(pr[j], wr[j] & (j == PWc - 1 ? tail : 0xFFFFFFFFu));
+                acc = __dp4a(d, d, acc);
+            }
+            atomicAdd(&s_pcost, acc);
+        }
+        __syncthreads();
+        const uint32_t pc = s_pcost;
+        if (pc <= ps.fallback_cost) {
+            if (tid == 0) {
+                corner_xy[2 * t] = px;
+                corner_xy[2 * t + 1] = py;
+                match_xy[2 * t] = qx;
+                match_xy[2 * t + 1] = qy;
+                cost_out[t] = pc;
+                valid_out[t] = 1;
+                if (ps.fell_back) ps.fell_back[t] = 0;
+            }
+            return;
+        }
+        if (tid == 0 && ps.fell_back) ps.fell_back[t] = 1;
+    }
+
+    // ---- stage the source window (byte 0 of a row = column sx - R - hp)
+    stage_block(src, g.w, g.h, sx - R - hp, sy - R - hp, L.WS, L.WS, win, L.WW);
     const int side_d = 2 * R + 1, nd = side_d * side_d, nq = (side_d + 3) >> 2;
     for (int i = tid; i < nd; i += kThreads) ssd[i] = 0u;
     __syncthreads();
@@ -255,7 +293,6 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
     //      horizontal offsets 4q..4q+3 of one row dy of offsets (the same two window
     //      words, shifted by 0, 8, 16, 24 bits) over a quarter of the patch rows; the
     //      partial sums meet in shared memory.
-    const uint32_t tail = (P & 3) ? ((1u << (8 * (P & 3))) - 1u) : 0xFFFFFFFFu;
     {
         constexpr int kSplit = 4;
         const int rows_per = (P + kSplit - 1) / kSplit;
@@ -318,15 +355,94 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
 
 void launch_local_search(const uint8_t* ref, const uint8_t* src, const double* H,
                          const SearchGeom& g, int32_t* corner_xy, int32_t* match_xy,
-                         uint32_t* cost, uint8_t* valid, cudaStream_t s, uint32_t* mask_zero)
+                         uint32_t* cost, uint8_t* valid, cudaStream_t s, uint32_t* mask_zero,
+                         const PredSearch* pred)
 {
     const int n = g.ntx * g.nty;
     if (n <= 0) return;
     const SearchSmem L(g);
     if (L.total > 48 * 1024) ensure_smem((const void*)k_local_search, L.total);
+    const PredSearch ps = pred ? *pred : PredSearch{nullptr, 0, 0u, nullptr};
     note_launch();
     k_local_search<<<n, kThreads, L.total, s>>>(ref, src, H, g, corner_xy, match_xy, cost, valid,
-                                                mask_zero);
+                                                mask_zero, ps);
+}
+
+// Training label of every tile: match - search centre (Eq. 3), 0 without a corner.
+__global__ void k_tile_labels(const int32_t* __restrict__ corner_xy,
+                              const int32_t* __restrict__ match_xy,
+                              const uint8_t* __restrict__ valid, int n, int w, int h,
+                              const double* __restrict__ H, float* __restrict__ label)
+{
+    __shared__ float hs[18];
+    if (threadIdx.x < 9) {
+        const float f = (float)H[threadIdx.x];
+        hs[threadIdx.x] = f;
+        hs[9 + threadIdx.x] = fabsf(f);
+    }
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        float lx = 0.f, ly = 0.f;
+        if (valid[t]) {
+            const int px = corner_xy[2 * t], py = corner_xy[2 * t + 1];
+            int cx, cy;
+            if (!search_center_f32(hs, hs + 9, px, py, w, h, cx, cy)) search_center(H, px, py, w, h, cx, cy);
+            lx = (float)(match_xy[2 * t] - cx);
+            ly = (float)(match_xy[2 * t + 1] - cy);
+        }
+        label[2 * t] = lx;
+        label[2 * t + 1] = ly;
+    }
+}
+
+void launch_tile_labels(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* valid,
+                        int n, int w, int h, const double* H, float* label, cudaStream_t s)
+{
+    if (n <= 0) return;
+    note_launch();
+    k_tile_labels<<<(n + 255) / 256, 256, 0, s>>>(corner_xy, match_xy, valid, n, w, h, H, label);
+}
+
+// Training crops: crop b covers tiles (tx0 .. tx0 + ct - 1, ty0 .. ty0 + ct - 1), i.e. the
+// quarter-resolution pixels [8 tx0, 8 (tx0 + ct)) x [8 ty0, 8 (ty0 + ct)).
+__global__ void k_predictor_crops(const uint32_t* __restrict__ x_full, int wq, int hq,
+                                  const float* __restrict__ label_full,
+                                  const uint8_t* __restrict__ valid_full, int ntx, int nty,
+                                  const int32_t* __restrict__ origins, int ct,
+                                  uint32_t* __restrict__ x_out, float* __restrict__ label_out,
+                                  uint8_t* __restrict__ valid_out)
+{
+    const int b = blockIdx.y;
+    const int tx0 = origins[2 * b], ty0 = origins[2 * b + 1];
+    const int side = 8 * ct;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < side * side; i += gridDim.x * blockDim.x) {
+        const int y = i / side, x = i % side;
+        const int gy = min(max(8 * ty0 + y, 0), hq - 1), gx = min(max(8 * tx0 + x, 0), wq - 1);
+        x_out[(size_t)b * side * side + i] = x_full[(size_t)gy * wq + gx];
+    }
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < ct * ct; i += blockDim.x) {
+            const int ty = ty0 + i / ct, tx = tx0 + i % ct;
+            const bool in = tx >= 0 && tx < ntx && ty >= 0 && ty < nty;
+            const size_t t = in ? (size_t)ty * ntx + tx : 0;
+            label_out[((size_t)b * ct * ct + i) * 2] = in ? label_full[2 * t] : 0.f;
+            label_out[((size_t)b * ct * ct + i) * 2 + 1] = in ? label_full[2 * t + 1] : 0.f;
+            valid_out[(size_t)b * ct * ct + i] = in ? valid_full[t] : 0;
+        }
+    }
+}
+
+void launch_predictor_crops(const void* x_full, int wq, int hq, const float* label_full,
+                            const uint8_t* valid_full, int ntx, int nty, const int32_t* origins,
+                            int n, int ct, void* x_out, float* label_out, uint8_t* valid_out,
+                            cudaStream_t s)
+{
+    if (n <= 0) return;
+    note_launch();
+    k_predictor_crops<<<dim3(16, n), 256, 0, s>>>(static_cast<const uint32_t*>(x_full), wq, hq,
+                                                   label_full, valid_full, ntx, nty, origins, ct,
+                                                   static_cast<uint32_t*>(x_out), label_out,
+                                                   valid_out);
 }
 
 }  // namespace hdrreg

@@ -112,6 +112,30 @@ __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
     }
 }
 
+// Network input of the learned search (row a-L) at quarter resolution: the reference
+// and the source sampled at H(p) (the displacement form above), both mapped to
+// (v - 127.5) / 127.5 and stored as a bfloat16 pair per pixel.
+__global__ void __launch_bounds__(256) k_predictor_input(const uint8_t* __restrict__ ref_q,
+                                                         const uint8_t* __restrict__ src_q, int w,
+                                                         int h, const double* __restrict__ H,
+                                                         __nv_bfloat162* __restrict__ out)
+{
+    __shared__ WarpCoef cs;
+    if (threadIdx.x == 0) prep_coef(H, w, cs);
+    __syncthreads();
+    const WarpCoef c = cs;
+    const long long n = (long long)w * h;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % w), y = (int)(i / w);
+        float dx, dy;
+        h_disp(c, x, y, w, h, dx, dy);
+        const float v = bilerp(src_q, w, h, x, y, dx, dy);
+        const float r = (float)ref_q[i];
+        out[i] = __floats2bfloat162_rn((r - 127.5f) / 127.5f, (v - 127.5f) / 127.5f);
+    }
+}
+
 // ----------------------------------------------------------------- merge
 constexpr int kTile = 32;
 constexpr int kHalo = kSsimRadius;
@@ -306,6 +330,17 @@ void launch_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_
     const int grid = (int)((nb + 255) / 256);
     note_launch();
     k_warp<<<grid, 256, 0, s>>>(src_y, src_u, src_v, w, h, H, fu, fv, oy, ou, ov);
+}
+
+void launch_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,
+                            const double* H, void* out, cudaStream_t s)
+{
+    const long long n = (long long)w * h;
+    long long g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    note_launch();
+    k_predictor_input<<<(int)g, 256, 0, s>>>(ref_q, src_q, w, h, H,
+                                             static_cast<__nv_bfloat162*>(out));
 }
 
 void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v, int w, int h,

@@ -31,7 +31,8 @@ EXPORTS = [
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
     "hdrreg_gemm_bf16", "hdrreg_cnn_workspace_size", "hdrreg_cnn_out_dims", "hdrreg_cnn_forward",
-    "hdrreg_cnn_backward", "hdrreg_cnn_adam",
+    "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_predictor_input", "hdrreg_tile_labels",
+    "hdrreg_predictor_crops", "hdrreg_local_search_predicted",
 ]
 
 CNN_PARAMS = 115938
@@ -55,11 +56,13 @@ class Params(C.Structure):
         ("reserved0", C.c_int),
         ("weed_eps", C.c_double), ("sigma_s", C.c_double), ("sigma_r", C.c_double),
         ("ssim_sigma", C.c_double), ("we_sigma", C.c_double), ("flow_eps", C.c_double),
-        ("weed_seed", C.c_uint64),
+        ("weed_seed", C.c_uint64), ("predictor", C.c_void_p), ("fallback_cost", C.c_uint32),
+        ("reserved1", C.c_uint32),
     ]
 
     def as_dict(self) -> Dict:
-        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved0"}
+        return {n: getattr(self, n) for n, _ in self._fields_
+                if n not in ("reserved0", "reserved1", "predictor", "fallback_cost")}
 
 
 class Frame(C.Structure):
@@ -84,7 +87,7 @@ class Stack(C.Structure):
 class Diag(C.Structure):
     _fields_ = [("H0", C.c_double * 9), ("levels", C.c_int32), ("tiles", C.c_int32),
                 ("valid", C.c_int32), ("kept", C.c_int32), ("fit_status", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("fallbacks", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 _lib = None
@@ -148,6 +151,11 @@ def lib():
         L.hdrreg_cnn_forward.argtypes = [vp, vp, i, i, i, vp, vp, sz, vp, vp]
         L.hdrreg_cnn_backward.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp, vp, sz, vp, vp]
         L.hdrreg_cnn_adam.argtypes = [vp, vp, vp, vp, i, C.c_float, vp]
+        L.hdrreg_predictor_input.argtypes = [vp, vp, i, i, vp, vp, vp]
+        L.hdrreg_tile_labels.argtypes = [vp, vp, vp, i, i, i, vp, vp, vp]
+        L.hdrreg_predictor_crops.argtypes = [vp, i, i, vp, vp, i, i, vp, i, i, vp, vp, vp, vp]
+        L.hdrreg_local_search_predicted.argtypes = [vp, vp, i, i, vp, C.POINTER(Params), vp, i, i,
+                                                    C.c_uint32, vp, vp, vp, vp, vp, vp]
         for name in EXPORTS:
             if not hasattr(L, name):
                 raise ImportError(f"libhdrreg.so does not export {name}")
@@ -459,6 +467,61 @@ class Predictor:
         self.t += 1
         _check(lib().hdrreg_cnn_adam(_ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.grad),
                                      self.t, C.c_float(lr), _stream(stream)))
+
+
+def predictor_input(ref_q, src_q, H, stream=None):
+    """Network input (bfloat16 [h, w, 2]) from quarter-resolution reference and source levels."""
+    import torch
+    h, w = ref_q.shape
+    x = torch.empty((h, w, 2), dtype=torch.bfloat16, device=ref_q.device)
+    _check(lib().hdrreg_predictor_input(_ptr(ref_q), _ptr(src_q), w, h, _ptr(H), _ptr(x),
+                                        _stream(stream)))
+    return x
+
+
+def tile_labels(corner_xy, match_xy, valid, w: int, h: int, H, stream=None):
+    import torch
+    n = valid.numel()
+    lab = torch.empty((n, 2), dtype=torch.float32, device=valid.device)
+    _check(lib().hdrreg_tile_labels(_ptr(corner_xy), _ptr(match_xy), _ptr(valid), n, w, h, _ptr(H),
+                                    _ptr(lab), _stream(stream)))
+    return lab
+
+
+def predictor_crops(x_full, label_full, valid_full, ntx: int, nty: int, origins, crop_tiles=8,
+                    stream=None):
+    """Gather training crops at tile origins (int32 [n, 2] CUDA tensor) -> (x, label, valid)."""
+    import torch
+    hq, wq = x_full.shape[0], x_full.shape[1]
+    n = origins.shape[0]
+    side = 8 * crop_tiles
+    x = torch.empty((n, side, side, 2), dtype=torch.bfloat16, device=x_full.device)
+    lab = torch.empty((n, crop_tiles, crop_tiles, 2), dtype=torch.float32, device=x_full.device)
+    val = torch.empty((n, crop_tiles, crop_tiles), dtype=torch.uint8, device=x_full.device)
+    _check(lib().hdrreg_predictor_crops(_ptr(x_full), wq, hq, _ptr(label_full), _ptr(valid_full),
+                                        ntx, nty, _ptr(origins), n, crop_tiles, _ptr(x), _ptr(lab),
+                                        _ptr(val), _stream(stream)))
+    return x, lab, val
+
+
+def local_search_predicted(ref_n, src_n, H, p: Params, pred, fallback_cost: int, stream=None):
+    """pred: FP32 [rows, cols, 2] with cols >= tiles across -> (corner, match, cost, valid,
+    fell_back)."""
+    import torch
+    h, w = ref_n.shape
+    n = num_tiles(w, h, p.tile)
+    dev = ref_n.device
+    corner = torch.empty((max(n, 1), 2), dtype=torch.int32, device=dev)
+    match = torch.empty((max(n, 1), 2), dtype=torch.int32, device=dev)
+    cost = torch.empty((max(n, 1),), dtype=torch.int32, device=dev)
+    valid = torch.empty((max(n, 1),), dtype=torch.uint8, device=dev)
+    fb = torch.empty((max(n, 1),), dtype=torch.uint8, device=dev)
+    _check(lib().hdrreg_local_search_predicted(_ptr(ref_n), _ptr(src_n), w, h, _ptr(H), C.byref(p),
+                                               _ptr(pred), pred.shape[0], pred.shape[1],
+                                               C.c_uint32(fallback_cost),
+                                               _ptr(corner), _ptr(match), _ptr(cost), _ptr(valid),
+                                               _ptr(fb), _stream(stream)))
+    return corner[:n], match[:n], cost[:n], valid[:n], fb[:n]
 
 
 class RegisterMergeBatch:

@@ -1,0 +1,122 @@
+"""Learned level-0 search (row a-L) pieces on the GPU against the oracle: the
+quarter-resolution network input, tile labels, training crops, the search with a
+predicted displacement and its fallback, and the fused path wired with a
+predictor. Integer outputs (labels, matches, costs, fallback flags) are bit-exact;
+the bfloat16 network input is within one bfloat16 step (1/64) of the float64 value."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_01441_b300 import build, hdrreg
+    build.build()
+    return hdrreg
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def cfg(tile=16, radius=4, **kw):
+    from paper_1504_01441_b300 import synth
+    return synth.method_params(tile, radius, **kw)
+
+
+@pytest.fixture(scope="module")
+def level_pair(orc):
+    from paper_1504_01441_b300 import synth
+    st = synth.make_stack(synth.VGA_LUMA, synth.stack_seed(1))
+    rn, sn = orc.normalize_ratio(st.ref.y, st.srcs[0].y, 4, 1)
+    return rn, sn
+
+
+def test_predictor_input_matches_oracle(hd, orc, level_pair):
+    rn, sn = level_pair
+    rq, sq = orc.pyramid(rn, 3)[2], orc.pyramid(sn, 3)[2]
+    H = np.array([[1.01, 0.02, 0.03], [-0.015, 0.99, -0.02], [0.01, -0.008, 1.0]])
+    x = hd.predictor_input(dev(rq), dev(sq), dev(H.reshape(9))).float().cpu().numpy()
+    want = orc.predictor_input(rq, sq, H)
+    assert x.shape == want.shape
+    assert np.abs(x - want).max() <= 1.0 / 64
+
+
+def test_tile_labels_bit_exact(hd, orc, level_pair):
+    rn, sn = level_pair
+    c = cfg()
+    H = np.array([[1.0, 0.004, 0.01], [0.0, 1.0, -0.012], [0.0, 0.0, 1.0]])
+    cxy, valid, _ = orc.pick_corners(rn, c)
+    _, mxy, _ = orc.search(rn, sn, H, c, cxy, valid)
+    lab = hd.tile_labels(dev(cxy), dev(mxy), dev(valid), 640, 480, dev(H.reshape(9)))
+    assert np.array_equal(lab.cpu().numpy(), orc.tile_labels(cxy, mxy, valid, 640, 480, H))
+
+
+def test_search_predicted_bit_exact(hd, orc, level_pair):
+    rn, sn = level_pair
+    c = cfg()
+    p = hd.params_from_dict(c)
+    H = np.array([[1.0, 0.004, 0.01], [0.0, 1.0, -0.012], [0.0, 0.0, 1.0]])
+    cxy, valid, _ = orc.pick_corners(rn, c)
+    _, mxy, cost = orc.search(rn, sn, H, c, cxy, valid)
+    lab = orc.tile_labels(cxy, mxy, valid, 640, 480, H)
+    rng = np.random.default_rng(3)
+    pred = (lab + rng.normal(0, 0.8, lab.shape) + (rng.random(lab.shape) < 0.15) * 6).astype(np.float32)
+    thr = int(np.median(cost[valid.astype(bool)]) * 1.5)
+    ntx = 640 // 16
+    grid = np.zeros((480 // 16 + 1, ntx + 3, 2), np.float32)  # wider than the tile grid
+    grid[:30, :ntx] = pred.reshape(30, ntx, 2)
+    gc, gm, gcost, gv, gfb = hd.local_search_predicted(dev(rn), dev(sn), dev(H.reshape(9)), p,
+                                                       dev(grid), thr)
+    om, oc, ofb = orc.search_predicted(rn, sn, H, c, cxy, valid, pred, thr)
+    assert np.array_equal(gc.cpu().numpy(), cxy) and np.array_equal(gv.cpu().numpy(), valid)
+    assert np.array_equal(gm.cpu().numpy(), om)
+    assert np.array_equal(gcost.cpu().numpy().view(np.uint32), oc)
+    assert np.array_equal(gfb.cpu().numpy(), ofb)
+    assert 0 < int(ofb.sum()) < int(valid.sum())  # both branches exercised
+
+
+def test_crops_are_the_covered_tiles(hd):
+    rng = np.random.default_rng(5)
+    hq, wq, ntx, nty = 40, 56, 7, 5
+    x = torch.tensor(rng.normal(size=(hq, wq, 2)), dtype=torch.bfloat16)
+    lab = rng.normal(size=(nty * ntx, 2)).astype(np.float32)
+    val = (rng.random(nty * ntx) > 0.3).astype(np.uint8)
+    org = np.array([[0, 0], [3, 1], [4, 2]], np.int32)
+    xc, lc, vc = hd.predictor_crops(x.cuda(), dev(lab), dev(val), ntx, nty, dev(org), crop_tiles=3)
+    xc, lc, vc = xc.cpu(), lc.cpu().numpy(), vc.cpu().numpy()
+    for b, (tx, ty) in enumerate(org):
+        assert torch.equal(xc[b], x[8 * ty:8 * ty + 24, 8 * tx:8 * tx + 24])
+        L = lab.reshape(nty, ntx, 2)
+        V = val.reshape(nty, ntx)
+        assert np.array_equal(lc[b], L[ty:ty + 3, tx:tx + 3])
+        assert np.array_equal(vc[b], V[ty:ty + 3, tx:tx + 3])
+
+
+def test_fused_learned_path_with_zero_fallback_cost_equals_plain(hd):
+    from oracle import cnn
+    from paper_1504_01441_b300 import synth
+    st = synth.make_stack(synth.VGA_LUMA, synth.stack_seed(1))
+    c = cfg(32, 6)  # the network predicts one displacement per 32 x 32 tile
+    p = hd.params_from_dict(c)
+    ref = (dev(st.ref.y), None, None)
+    srcs = [(dev(st.srcs[0].y), None, None)]
+    (y0, _, _), rm0 = hd.register_merge(ref, srcs, st.ratios, p)
+    y0 = y0.clone()
+    d0 = rm0.diagnostics()[0]
+    theta = torch.tensor(cnn.init_params(9)).cuda()
+    p.predictor = theta.data_ptr()
+    p.fallback_cost = 0  # every prediction with a nonzero SSD falls back: the plain result
+    (y1, _, _), rm1 = hd.register_merge(ref, srcs, st.ratios, p)
+    d1 = rm1.diagnostics()[0]
+    assert d0.fallbacks == -1 and d1.fallbacks == d1.valid
+    assert list(d1.H0) == list(d0.H0)
+    assert torch.equal(y1, y0)
+    p.fallback_cost = 2 ** 32 - 1  # every prediction accepted
+    (y2, _, _), rm2 = hd.register_merge(ref, srcs, st.ratios, p)
+    d2 = rm2.diagnostics()[0]
+    assert d2.fallbacks == 0 and np.isfinite(y2.cpu().numpy()).all()
