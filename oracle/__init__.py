@@ -184,7 +184,7 @@ def tile_labels(corner_xy, match_xy, valid, w, h, H):
     return lab[:n]
 
 
-def search_predicted(ref_n, src_n, H, cfg, corner_xy, valid, pred, fallback_cost):
+def search_predicted(ref_n, src_n, H, cfg, corner_xy, valid, pred, fallback_cost, refine=0):
     ref_n, src_n = _u8(ref_n), _u8(src_n)
     h, w = ref_n.shape
     cxy, valid = _i32(corner_xy).reshape(-1, 2), _u8(valid)
@@ -195,7 +195,8 @@ def search_predicted(ref_n, src_n, H, cfg, corner_xy, valid, pred, fallback_cost
     fb = np.zeros(max(n, 1), np.uint8)
     prm = make_params(cfg)
     lib().orc_search_predicted(_p(ref_n), _p(src_n), w, h, _p(_f64(H).reshape(9)), C.byref(prm), n,
-                               _p(cxy), _p(valid), _p(pred), C.c_uint32(int(fallback_cost)),
+                               _p(cxy), _p(valid), _p(pred), int(refine),
+                               C.c_uint32(int(fallback_cost)),
                                _p(mxy), _p(cost), _p(fb))
     return mxy[:n], cost[:n], fb[:n]
 

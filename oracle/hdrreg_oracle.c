@@ -306,15 +306,17 @@ void orc_tile_labels(const int32_t* corner_xy, const int32_t* match_xy, const ui
 
 /*
  * Search with a prediction: for a tile with a corner p and search centre c, the
- * predicted displacement d (FP32) is rounded to floor(d + 0.5) (in FP32) and the
- * SSD of the patches at p and c + round(d) is computed; if it is at most
- * `fallback_cost` that is the match, otherwise the tile falls back to the full
- * search of orc_search (fell_back = 1). Tiles without a corner are as in orc_search.
+ * predicted displacement d (FP32) is rounded to floor(d + 0.5) (in FP32), giving
+ * q = c + round(d); the SSD is evaluated at q + e for every e in [-r, r]^2
+ * (r = refine; r = 0 is the single SSD at q) and the least key (cost, row-major
+ * index of e) is taken as in orc_search. If that cost is at most `fallback_cost`
+ * it is the match, otherwise the tile falls back to the full search of
+ * orc_search (fell_back = 1). Tiles without a corner are as in orc_search.
  */
 void orc_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w, int h,
                           const double H[9], const orc_params* p, int ntiles,
                           const int32_t* corner_xy, const uint8_t* valid, const float* pred,
-                          uint32_t fallback_cost, int32_t* match_xy, uint32_t* cost,
+                          int refine, uint32_t fallback_cost, int32_t* match_xy, uint32_t* cost,
                           uint8_t* fell_back)
 {
     int hp = p->patch_half;
@@ -331,16 +333,25 @@ void orc_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w, int
         orc_search_center(H, px, py, w, h, &cx, &cy);
         float fx = pred[2 * t] + 0.5f, fy = pred[2 * t + 1] + 0.5f;
         int qx = cx + (int)floorf(fx), qy = cy + (int)floorf(fy);
-        uint64_t c = 0;
-        for (int v = -hp; v <= hp; v++)
-            for (int u = -hp; u <= hp; u++) {
-                long e = (long)pix(ref_n, w, h, px + u, py + v) - (long)pix(src_n, w, h, qx + u, qy + v);
-                c += (uint64_t)(e * e);
+        uint64_t best = UINT64_MAX;
+        int bex = 0, bey = 0;
+        for (int ey = -refine; ey <= refine; ey++)
+            for (int ex = -refine; ex <= refine; ex++) {
+                uint64_t c = 0;
+                for (int v = -hp; v <= hp; v++)
+                    for (int u = -hp; u <= hp; u++) {
+                        long e = (long)pix(ref_n, w, h, px + u, py + v) -
+                                 (long)pix(src_n, w, h, qx + ex + u, qy + ey + v);
+                        c += (uint64_t)(e * e);
+                    }
+                uint64_t idx = (uint64_t)((ey + refine) * (2 * refine + 1) + (ex + refine));
+                uint64_t key = (c << 16) | idx;
+                if (key < best) { best = key; bex = ex; bey = ey; }
             }
-        if (c <= fallback_cost) {
-            match_xy[2 * t] = qx;
-            match_xy[2 * t + 1] = qy;
-            cost[t] = (uint32_t)c;
+        if ((best >> 16) <= fallback_cost) {
+            match_xy[2 * t] = qx + bex;
+            match_xy[2 * t + 1] = qy + bey;
+            cost[t] = (uint32_t)(best >> 16);
         } else {
             fell_back[t] = 1;
             orc_search(ref_n, src_n, w, h, H, p, 1, corner_xy + 2 * t, valid + t, ctr,

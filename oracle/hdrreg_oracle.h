@@ -88,7 +88,7 @@ void orc_tile_labels(const int32_t* corner_xy, const int32_t* match_xy, const ui
 void orc_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w, int h,
                           const double H[9], const orc_params* p, int ntiles,
                           const int32_t* corner_xy, const uint8_t* valid, const float* pred,
-                          uint32_t fallback_cost, int32_t* match_xy, uint32_t* cost,
+                          int refine, uint32_t fallback_cost, int32_t* match_xy, uint32_t* cost,
                           uint8_t* fell_back);
 int  orc_solve8(const double A[64], const double b[8], double x[8], double tol);
 int  orc_pow2_scale(int w);

@@ -728,3 +728,24 @@ def test_search_predicted_accepts_good_and_rejects_bad_predictions(orc):
     p0[one] = [-0.5, 0.5]
     m, _, _ = orc.search_predicted(img, src, H, c, cxy, valid, p0, 2 ** 32 - 1)
     assert np.array_equal(m[one], ctr[one] + [[0, 1]])
+
+
+def test_search_predicted_refinement_recovers_one_pixel_errors(orc):
+    rng = np.random.default_rng(33)
+    c = cfg_for(16, 4)
+    img = np.clip(np.kron(rng.integers(0, 256, (34, 42)), np.ones((4, 4))) +
+                  rng.normal(0, 3, (136, 168)), 0, 255).astype(np.uint8)[:128, :160]
+    src = np.roll(img, (1, 2), axis=(0, 1))
+    H = np.eye(3)
+    cxy, valid, _ = orc.pick_corners(img, c)
+    ctr, mxy, cost = orc.search(img, src, H, c, cxy, valid)
+    lab = orc.tile_labels(cxy, mxy, valid, 160, 128, H)
+    off = rng.integers(-1, 2, lab.shape).astype(np.float32)  # predictions off by up to 1 px
+    # refine = 1 searches the 3 x 3 offsets around the rounded prediction: the plain optimum
+    # (inside that window) is found again with its cost, without falling back
+    m, co, fb = orc.search_predicted(img, src, H, c, cxy, valid, lab + off, 2 ** 32 - 1, refine=1)
+    assert np.array_equal(m, mxy) and np.array_equal(co, cost) and not fb.any()
+    # refine = 0 keeps the off-by-one matches where the threshold lets them through
+    m0, _, _ = orc.search_predicted(img, src, H, c, cxy, valid, lab + off, 2 ** 32 - 1, refine=0)
+    moved = valid.astype(bool) & (np.abs(off).sum(1) > 0)
+    assert np.array_equal(m0[moved] - mxy[moved], off[moved].astype(np.int32))
