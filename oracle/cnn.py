@@ -11,8 +11,13 @@ homography at quarter resolution and outputs one residual displacement per
 is the reference those kernels are checked against: a direct, unoptimized
 statement of the network, its loss, its gradients and its optimizer step.
 
-Network (layer list, in order): 3x3 convolutions with zero padding 1,
-  c0: 2 -> 16 stride 1, c1: 16 -> 16 stride 1,
+Network: a fixed feature stage, then learned layers. Features of a quarter-resolution
+pixel p with inputs a = x[..., 0] (reference) and b = x[..., 1] (pre-warped source):
+  a(p), b(p), and -(a(p) - b(p + o))^2 for the 25 offsets o = (u, v) in [-2, 2]^2
+  (row-major in v then u; b = 0 outside the image)
+-- a local SSD cost volume over +-8 full-resolution pixels, 27 channels. Learned
+layers (in order), 3x3 convolutions with zero padding 1,
+  c0: 27 -> 16 stride 1, c1: 16 -> 16 stride 1,
   c2: 16 -> 32 stride 2, c3: 32 -> 32 stride 1,
   c4: 32 -> 48 stride 2, c5: 48 -> 48 stride 1,
   c6: 48 -> 64 stride 2, c7: 64 -> 64 stride 1,
@@ -22,7 +27,7 @@ Tensors are NHWC. Parameters are one flat float32 vector: for every layer in
 order, W[cout][ky][kx][cin] then b[cout] (the head as W[2][1][1][64], b[2]).
 
 bf16=True rounds the values the CUDA path stores in bfloat16 (the input, the
-weights, every post-ReLU activation) to the nearest bfloat16, ties to even,
+features, the weights, every post-ReLU activation) to the nearest bfloat16, ties to even,
 and keeps everything else in float64; bf16=False is the exact network (used for
 the gradient pins).
 """
@@ -31,7 +36,7 @@ from __future__ import annotations
 import numpy as np
 
 LAYERS = [  # (cin, cout, kernel, stride, relu)
-    (2, 16, 3, 1, True), (16, 16, 3, 1, True),
+    (27, 16, 3, 1, True), (16, 16, 3, 1, True),
     (16, 32, 3, 2, True), (32, 32, 3, 1, True),
     (32, 48, 3, 2, True), (48, 48, 3, 1, True),
     (48, 64, 3, 2, True), (64, 64, 3, 1, True),
@@ -122,13 +127,36 @@ def conv_backward(x, W, dy, stride):
     return dxp[:, p:p + h, p:p + w, :], dW, db
 
 
-def forward(theta, x, bf16=False, layers=LAYERS):
-    """x [n, h, w, 2] -> (out [n, h/8, w/8, 2] (ceil at each stride), cache for backward)."""
+CORR = 2  # offsets of the cost volume: [-CORR, CORR]^2
+
+
+def features(x):
+    """x [n, h, w, 2] -> [n, h, w, 2 + (2 CORR + 1)^2]: a, b, -(a(p) - b(p + o))^2."""
+    n, h, w, _ = x.shape
+    a, b = x[..., 0], x[..., 1]
+    bp = np.zeros((n, h + 2 * CORR, w + 2 * CORR))
+    bp[:, CORR:CORR + h, CORR:CORR + w] = b
+    out = [a, b]
+    for v in range(-CORR, CORR + 1):
+        for u in range(-CORR, CORR + 1):
+            d = a - bp[:, CORR + v:CORR + v + h, CORR + u:CORR + u + w]
+            out.append(-(d * d))
+    return np.stack(out, -1)
+
+
+def forward(theta, x, bf16=False, layers=LAYERS, feature_stage=True):
+    """x [n, h, w, 2] -> (out [n, h/8, w/8, 2] (ceil at each stride), cache for backward).
+    feature_stage=False feeds x straight to the first layer (used by the gradient pins)."""
     params = unpack(theta, layers)
     if bf16:
         params = [(bf16_round(W), np.asarray(b, np.float32).astype(np.float64)) for W, b in params]
         x = bf16_round(x)
-    acts = [np.asarray(x, np.float64)]
+    x = np.asarray(x, np.float64)
+    if feature_stage:
+        x = features(x)
+        if bf16:
+            x = bf16_round(x)
+    acts = [x]
     for (W, b), (ci, co, k, s, r) in zip(params, layers):
         z = conv_forward(acts[-1], W, b, s)
         if r:

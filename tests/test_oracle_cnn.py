@@ -75,15 +75,15 @@ def test_network_gradient_finite_differences():
     rng = np.random.default_rng(3)
     theta = rng.normal(0, 0.5, cnn.n_params(TINY))
     x = rng.normal(size=(2, 6, 5, 2))
-    out, _ = cnn.forward(theta, x, layers=TINY)
+    out, _ = cnn.forward(theta, x, layers=TINY, feature_stage=False)
     label = rng.normal(size=out.shape)
     valid = rng.random(out.shape[:3]) > 0.3
 
     def loss(t):
-        o, _ = cnn.forward(t, x, layers=TINY)
+        o, _ = cnn.forward(t, x, layers=TINY, feature_stage=False)
         return cnn.loss_and_grad_out(o, label, valid)[0]
 
-    out, cache = cnn.forward(theta, x, layers=TINY)
+    out, cache = cnn.forward(theta, x, layers=TINY, feature_stage=False)
     L, dout = cnn.loss_and_grad_out(out, label, valid)
     g = cnn.backward(cache, dout, layers=TINY)
     e = 1e-6
@@ -95,7 +95,7 @@ def test_network_gradient_finite_differences():
 
 
 def test_zero_weights_give_head_bias_and_param_count():
-    assert cnn.n_params() == 115938
+    assert cnn.n_params() == 119538
     theta = np.zeros(cnn.n_params())
     theta[-2:] = [1.5, -0.25]
     out, _ = cnn.forward(theta, np.random.default_rng(4).normal(size=(1, 16, 24, 2)))
@@ -141,3 +141,23 @@ def test_loss_is_mean_over_valid_cells():
     L, d = cnn.loss_and_grad_out(out, label, np.array([[[True, True, False]]]))
     assert L == pytest.approx((1.0 + 4.0) / 2)
     assert np.allclose(d[0, 0, 2], 0.0) and np.allclose(d[0, 0, 1], [0.0, -2.0])
+
+
+def test_features_are_a_local_ssd_cost_volume():
+    rng = np.random.default_rng(6)
+    x = rng.uniform(-1, 1, (2, 5, 7, 2))
+    f = cnn.features(x)
+    assert f.shape == (2, 5, 7, 27)
+    assert np.array_equal(f[..., 0], x[..., 0]) and np.array_equal(f[..., 1], x[..., 1])
+    for _ in range(40):
+        nb, y, xx = rng.integers(0, 2), rng.integers(0, 5), rng.integers(0, 7)
+        v, u = rng.integers(-2, 3), rng.integers(-2, 3)
+        bv = x[nb, y + v, xx + u, 1] if (0 <= y + v < 5 and 0 <= xx + u < 7) else 0.0
+        k = 2 + (v + 2) * 5 + (u + 2)
+        assert f[nb, y, xx, k] == -(x[nb, y, xx, 0] - bv) ** 2
+    # a source equal to the reference shifted by (u, v) = (1, -1) zeroes that channel inside
+    a = rng.uniform(-1, 1, (1, 9, 9))
+    b = np.zeros_like(a)
+    b[:, :8, 1:] = a[:, 1:, :8]  # b(p + (1, -1)) = a(p)
+    f = cnn.features(np.stack([a, b], -1))
+    assert np.all(f[0, 1:, :8, 2 + (-1 + 2) * 5 + (1 + 2)] == 0)
