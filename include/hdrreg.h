@@ -92,9 +92,10 @@ typedef struct hdrreg_params {
     uint64_t weed_seed;   /* stream of the counter-based sampler (level l uses seed+l)  */
     const float* predictor; /* learned level-0 search (row a-L): device parameters of the
                                displacement network, or NULL for the plain SSD search   */
-    uint32_t fallback_cost; /* learned search: a tile whose SSD at the predicted match
-                               exceeds this falls back to the full search              */
-    uint32_t reserved1;
+    uint32_t fallback_cost; /* learned search: a tile whose least SSD around the
+                               predicted match exceeds this falls back to the full search */
+    int32_t predictor_refine; /* learned search: offsets [-r, r]^2 around the rounded
+                               prediction are tried before the fallback test, 0..radius */
 } hdrreg_params;
 
 /* A YUV420 (or luma-only: u = v = NULL) 8-bit frame, device pointers. */
@@ -338,9 +339,10 @@ hdrreg_status hdrreg_gemm_bf16(const void* A, int lda, const void* B, int ldb, i
  * source pre-warped by the level-1 homography at quarter resolution, x [n][h][w][2]
  * (bfloat16 bits, NHWC), and outputs one displacement per 32x32 full-resolution
  * tile, out [n][ho][wo][2] FP32 (ho, wo from hdrreg_cnn_out_dims: three stride-2
- * steps, ceil). Layers: 3x3 convolutions 2-16, 16-16, 16-32 (stride 2), 32-32,
- * 32-48 (stride 2), 48-48, 48-64 (stride 2), 64-64, each with bias and ReLU, then a
- * 1x1 head 64-2. theta: HDRREG_CNN_PARAMS FP32 values, per layer W[cout][ky][kx][cin]
+ * steps, ceil). A fixed feature stage gives per pixel a, b and -(a(p) - b(p + o))^2
+ * for o in [-2, 2]^2 (a local SSD cost volume, 27 channels); then 3x3 convolutions
+ * 27-16, 16-16, 16-32 (stride 2), 32-32, 32-48 (stride 2), 48-48, 48-64 (stride 2),
+ * 64-64, each with bias and ReLU, then a 1x1 head 64-2. theta: HDRREG_CNN_PARAMS FP32 values, per layer W[cout][ky][kx][cin]
  * then b[cout]. Activations are stored in bfloat16, products accumulate in FP32 on
  * the tensor cores. hdrreg_cnn_backward uses the activations the preceding
  * hdrreg_cnn_forward left in the same workspace (same n, h, w, x, theta): loss (a
@@ -350,7 +352,7 @@ hdrreg_status hdrreg_gemm_bf16(const void* A, int lda, const void* B, int ldb, i
  * status: device int32, zero on entry, set to 1 if a tensor-core kernel gave up
  * waiting for its copies. Workspace: hdrreg_cnn_workspace_size(n, h, w).
  */
-#define HDRREG_CNN_PARAMS 115938
+#define HDRREG_CNN_PARAMS 119538
 size_t hdrreg_cnn_workspace_size(int n, int h, int w);
 int hdrreg_cnn_out_dims(int h, int w, int* ho, int* wo);
 hdrreg_status hdrreg_cnn_forward(const float* theta, const uint16_t* x, int n, int h, int w,
@@ -362,6 +364,13 @@ hdrreg_status hdrreg_cnn_backward(const float* theta, const uint16_t* x, int n, 
                                   int32_t* status, void* stream);
 hdrreg_status hdrreg_cnn_adam(float* theta, float* m, float* v, const float* grad, int step,
                               float lr, void* stream);
+/* Where a workspace of batch (n, h, w) keeps what the last hdrreg_cnn_forward stored:
+ * layer -1 = the feature stage (bfloat16 [n*h*w][27]), layers 0..7 = the post-ReLU
+ * outputs (bfloat16 [rows][cols]). Writes the device address (inside the workspace,
+ * valid until the next call that uses it) and the shape; the head (layer 8) stores no
+ * bfloat16 output (its FP32 result is `out`): HDRREG_E_INVALID_ARG. */
+hdrreg_status hdrreg_cnn_activation(const void* workspace, int n, int h, int w, int layer,
+                                    const uint16_t** ptr, int* rows, int* cols);
 
 /* ------------------------------------------- a-L: the learned level-0 search
  * The paper has no counterpart. hdrreg_predictor_input: the network input at
@@ -372,13 +381,18 @@ hdrreg_status hdrreg_cnn_adam(float* theta, float* m, float* v, const float* gra
  * displacement match - centre (FP32 integers; 0 without a corner), the centre
  * being the rounded projection of the corner by H (Eq. 3): the training label.
  * hdrreg_predictor_crops: gathers n training crops of crop_tiles x crop_tiles
- * tiles (8 x 8 quarter-resolution pixels each) at the tile origins origins[2i],
- * origins[2i+1] (device int32, inside the tile grid) from the full input, labels
- * and validity (a valid label needs a corner). hdrreg_local_search_predicted:
- * hdrreg_local_search where the match of a tile with a corner is its centre plus
- * floor(pred + 0.5) (pred: FP32 pairs, pred_rows x pred_ld cells covering the tile grid,
- * cell (ty, tx)) if the patch SSD there is at most fallback_cost, else the full
- * search's (fell_back[t] = 1). All pointers are device pointers. The fused calls use
+ * tiles (8 x 8 quarter-resolution pixels each) from the full input, labels and
+ * validity; origins (device int32, 4 per crop) = tile origin x, y inside the tile
+ * grid, a symmetry (bit 0 mirror x, bit 1 mirror y, bit 2 transpose; pixels, tiles
+ * and label components follow it) and an unused word. A label is valid where the
+ * tile has a corner and both components are below label_bound in magnitude (use
+ * the search radius: a displacement on the border of the search is not a
+ * measurement). hdrreg_local_search_predicted:
+ * hdrreg_local_search where a tile with a corner first searches the offsets
+ * [-refine, refine]^2 around its centre plus floor(pred + 0.5) (pred: FP32 pairs,
+ * pred_rows x pred_ld cells covering the tile grid, cell (ty, tx)); if the least SSD
+ * there is at most fallback_cost that is the match, else the tile runs the full
+ * search (fell_back[t] = 1). refine = 0 checks the single predicted match. All pointers are device pointers. The fused calls use
  * the learned search when params.predictor is set, the tile is 32 and the pyramid has
  * at least three levels (the network reads level 2); otherwise the plain search.
  */
@@ -390,14 +404,15 @@ hdrreg_status hdrreg_tile_labels(const int32_t* corner_xy, const int32_t* match_
 hdrreg_status hdrreg_predictor_crops(const uint16_t* x_full, int wq, int hq, const float* label_full,
                                      const uint8_t* valid_full, int ntx, int nty,
                                      const int32_t* origins, int n, int crop_tiles,
-                                     uint16_t* x_out, float* label_out, uint8_t* valid_out,
-                                     void* stream);
+                                     float label_bound, uint16_t* x_out, float* label_out,
+                                     uint8_t* valid_out, void* stream);
 hdrreg_status hdrreg_local_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w,
                                             int h, const double* H, const hdrreg_params* p,
                                             const float* pred, int pred_rows, int pred_ld,
-                                            uint32_t fallback_cost, int32_t* corner_xy,
-                                            int32_t* match_xy, uint32_t* cost, uint8_t* valid,
-                                            uint8_t* fell_back, void* stream);
+                                            int refine, uint32_t fallback_cost,
+                                            int32_t* corner_xy, int32_t* match_xy,
+                                            uint32_t* cost, uint8_t* valid, uint8_t* fell_back,
+                                            void* stream);
 
 /* ------------------------------------- a1-a11 fused, a batch of stacks
  * The paper has no counterpart (it registers one burst at a time): many stacks of

@@ -152,7 +152,7 @@ struct FusedLayout {
         if (learned) {
             xq = lay.add((size_t)wq * hq * 4);
             pred = lay.add((size_t)pho * pwo * 8);
-            cnn = lay.add(cnn_ws_bytes(1, hq, wq));
+            cnn = lay.add(cnn_ws_bytes(1, hq, wq, false));
             fellback = lay.add(nn);
         }
         for (int k = 0; k < ns; k++) {
@@ -271,6 +271,8 @@ hdrreg_status hdrreg_validate_params(const hdrreg_params* p)
         return fail(HDRREG_E_INVALID_ARG, "dt_iters must be in [1, 8]");
     if (p->ssim_radius != kSsimRadius)
         return fail(HDRREG_E_INVALID_ARG, "ssim_radius must be %d", kSsimRadius);
+    if (p->predictor && (p->predictor_refine < 0 || p->predictor_refine > p->radius))
+        return fail(HDRREG_E_INVALID_ARG, "predictor_refine must be in [0, radius]");
     if (p->propagate_full != 0 && p->propagate_full != 1)
         return fail(HDRREG_E_INVALID_ARG, "propagate_full must be 0 or 1");
     if (!(p->weed_eps > 0) || !(p->sigma_s > 0) || !(p->sigma_r > 0) || !(p->ssim_sigma > 0) ||
@@ -666,7 +668,7 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
                                  at(lay.cnn), reinterpret_cast<int*>(done + kMaxLevels), s))
                     return fail(HDRREG_E_UNSUPPORTED, "register_merge: tensor-core product not available");
                 const PredSearch ps{reinterpret_cast<const float*>(at(lay.pred)), lay.pwo,
-                                    p->fallback_cost, at(lay.fellback)};
+                                    p->predictor_refine, p->fallback_cost, at(lay.fellback)};
                 launch_local_search(rl, sl, Hs + 9, g, corner, match, cost, valid, s, mask, &ps);
             } else {
                 launch_local_search(rl, sl, Hs + 9 * (l + 1), g, corner, match, cost, valid, s,
@@ -817,8 +819,8 @@ hdrreg_status hdrreg_tile_labels(const int32_t* corner_xy, const int32_t* match_
 hdrreg_status hdrreg_predictor_crops(const uint16_t* x_full, int wq, int hq, const float* label_full,
                                      const uint8_t* valid_full, int ntx, int nty,
                                      const int32_t* origins, int n, int crop_tiles,
-                                     uint16_t* x_out, float* label_out, uint8_t* valid_out,
-                                     void* stream)
+                                     float label_bound, uint16_t* x_out, float* label_out,
+                                     uint8_t* valid_out, void* stream)
 {
     if (!x_full || !label_full || !valid_full || !origins || !x_out || !label_out || !valid_out)
         return fail(HDRREG_E_INVALID_ARG, "predictor_crops: NULL pointer");
@@ -826,7 +828,7 @@ hdrreg_status hdrreg_predictor_crops(const uint16_t* x_full, int wq, int hq, con
         nty < 1)
         return fail(HDRREG_E_INVALID_ARG, "predictor_crops: bad sizes");
     launch_predictor_crops(x_full, wq, hq, label_full, valid_full, ntx, nty, origins, n,
-                           crop_tiles, x_out, label_out, valid_out,
+                           crop_tiles, label_bound, x_out, label_out, valid_out,
                            static_cast<cudaStream_t>(stream));
     return launch_status("predictor_crops");
 }
@@ -834,9 +836,10 @@ hdrreg_status hdrreg_predictor_crops(const uint16_t* x_full, int wq, int hq, con
 hdrreg_status hdrreg_local_search_predicted(const uint8_t* ref_n, const uint8_t* src_n, int w,
                                             int h, const double* H, const hdrreg_params* p,
                                             const float* pred, int pred_rows, int pred_ld,
-                                            uint32_t fallback_cost, int32_t* corner_xy,
-                                            int32_t* match_xy, uint32_t* cost, uint8_t* valid,
-                                            uint8_t* fell_back, void* stream)
+                                            int refine, uint32_t fallback_cost,
+                                            int32_t* corner_xy, int32_t* match_xy,
+                                            uint32_t* cost, uint8_t* valid, uint8_t* fell_back,
+                                            void* stream)
 {
     hdrreg_status st = hdrreg_validate_params(p);
     if (st) return st;
@@ -848,7 +851,9 @@ hdrreg_status hdrreg_local_search_predicted(const uint8_t* ref_n, const uint8_t*
         return fail(HDRREG_E_INVALID_ARG,
                     "local_search_predicted: prediction grid %d x %d smaller than the %d x %d tiles",
                     pred_rows, pred_ld, g.nty, g.ntx);
-    const PredSearch ps{pred, pred_ld, fallback_cost, fell_back};
+    if (refine < 0 || refine > p->radius)
+        return fail(HDRREG_E_INVALID_ARG, "local_search_predicted: refine must be in [0, radius]");
+    const PredSearch ps{pred, pred_ld, refine, fallback_cost, fell_back};
     launch_local_search(ref_n, src_n, H, g, corner_xy, match_xy, cost, valid,
                         static_cast<cudaStream_t>(stream), nullptr, &ps);
     return launch_status("local_search_predicted");
@@ -903,6 +908,19 @@ hdrreg_status hdrreg_cnn_backward(const float* theta, const uint16_t* x, int n, 
                       grad, loss, workspace, status, static_cast<cudaStream_t>(stream)))
         return fail(HDRREG_E_UNSUPPORTED, "cnn_backward: tensor-core product not available");
     return launch_status("cnn_backward");
+}
+
+hdrreg_status hdrreg_cnn_activation(const void* workspace, int n, int h, int w, int layer,
+                                    const uint16_t** ptr, int* rows, int* cols)
+{
+    if (!workspace || !ptr || !rows || !cols)
+        return fail(HDRREG_E_INVALID_ARG, "cnn_activation: NULL pointer");
+    if (cnn_bad_dims(n, h, w))
+        return fail(HDRREG_E_INVALID_ARG, "cnn_activation: bad batch %d x %d x %d", n, h, w);
+    const void* p = cnn_activation(workspace, n, h, w, layer, rows, cols);
+    if (!p) return fail(HDRREG_E_INVALID_ARG, "cnn_activation: layer %d stores no activation", layer);
+    *ptr = static_cast<const uint16_t*>(p);
+    return HDRREG_OK;
 }
 
 hdrreg_status hdrreg_cnn_adam(float* theta, float* m, float* v, const float* grad, int step,

@@ -1,10 +1,11 @@
 // Row a-L: the learned tile-displacement predictor -- forward pass, backward pass,
 // masked mean-squared loss and Adam, with every convolution on the tensor cores.
 //
-// Network (NHWC, bf16 storage, FP32 accumulation): eight 3x3 convolutions with zero
-// padding 1 -- 2->16, 16->16, 16->32 (stride 2), 32->32, 32->48 (stride 2), 48->48,
-// 48->64 (stride 2), 64->64 -- each with bias and ReLU, then a 1x1 head 64->2 (bias,
-// no activation). Parameters: one FP32 vector, per layer W[cout][ky][kx][cin] then
+// Network (NHWC, bf16 storage, FP32 accumulation): a fixed feature stage (the two
+// inputs a, b and a local SSD cost volume -(a(p) - b(p + o))^2, o in [-2, 2]^2: 27
+// channels), then eight 3x3 convolutions with zero padding 1 -- 27->16, 16->16, 16->32
+// (stride 2), 32->32, 32->48 (stride 2), 48->48, 48->64 (stride 2), 64->64 -- each with
+// bias and ReLU, then a 1x1 head 64->2 (bias, no activation). Parameters: one FP32 vector, per layer W[cout][ky][kx][cin] then
 // b[cout]. A convolution is the product im2col(x) [M x 9 cin] * W^T (gemm_tc.cu); the
 // data gradient is dY * W gathered back by col2im; the weight gradient is
 // im2col(x)^T * dY over all M output pixels (K split across CTAs, partial sums added
@@ -25,7 +26,9 @@ struct LayerSpec {
     int cin, cout, k, stride, relu;
 };
 constexpr int kNL = 9;
-constexpr LayerSpec kNet[kNL] = {{2, 16, 3, 1, 1},  {16, 16, 3, 1, 1}, {16, 32, 3, 2, 1},
+constexpr int kCorr = 2;                                   // cost-volume offsets [-2, 2]^2
+constexpr int kFeat = 2 + (2 * kCorr + 1) * (2 * kCorr + 1);  // 27 feature channels
+constexpr LayerSpec kNet[kNL] = {{kFeat, 16, 3, 1, 1}, {16, 16, 3, 1, 1}, {16, 32, 3, 2, 1},
                                  {32, 32, 3, 1, 1}, {32, 48, 3, 2, 1}, {48, 48, 3, 1, 1},
                                  {48, 64, 3, 2, 1}, {64, 64, 3, 1, 1}, {64, 2, 1, 1, 0}};
 
@@ -36,6 +39,35 @@ int cpad(const LayerSpec& L) { return round_up(L.cout, 16); }
 int osz(int n, const LayerSpec& L) { return (n + 2 * (L.k / 2) - L.k) / L.stride + 1; }
 
 // ------------------------------------------------------------------ kernels
+// Fixed feature stage: per pixel a, b and -(a(p) - b(p + o))^2 for o = (u, v) in
+// [-2, 2]^2 (row-major in v, then u; b = 0 outside). With bfloat16 inputs in [-1, 1] the
+// difference and its square are exact in FP32, so only the final rounding to bfloat16
+// remains.
+__global__ void k_features(const __nv_bfloat162* __restrict__ x, int n, int h, int w,
+                           __nv_bfloat16* __restrict__ f)
+{
+    const long long total = (long long)n * h * w;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int xx = (int)(p % w), yy = (int)((p / w) % h);
+        const long long base = p - ((long long)yy * w + xx);  // first pixel of this image
+        const float2 ab = __bfloat1622float2(x[p]);
+        __nv_bfloat16* o = f + p * kFeat;
+        o[0] = __float2bfloat16_rn(ab.x);
+        o[1] = __float2bfloat16_rn(ab.y);
+        int c = 2;
+        for (int v = -kCorr; v <= kCorr; v++)
+            for (int u = -kCorr; u <= kCorr; u++, c++) {
+                const int ys = yy + v, xs = xx + u;
+                const float b = (ys >= 0 && ys < h && xs >= 0 && xs < w)
+                                    ? __high2float(x[base + (long long)ys * w + xs])
+                                    : 0.f;
+                const float d = ab.x - b;
+                o[c] = __float2bfloat16_rn(-(d * d));
+            }
+    }
+}
+
 // col[m][k] for output pixel m = (b, i, j) and k = (ky * K + kx) * cin + ci: the input
 // value at (s i + ky - p, s j + kx - p, ci), 0 outside the image and for k >= K*K*cin.
 __global__ void k_im2col(const __nv_bfloat16* __restrict__ x, int n, int h, int w, int cin,
@@ -238,9 +270,10 @@ struct CnnLayout {
     int H[kNL + 1], Wd[kNL + 1];  // spatial size at the input of layer i (i = kNL: output)
     long long M[kNL];             // output pixels of layer i
     size_t wb[kNL], wt[kNL], col[kNL], act[kNL];
-    size_t colT, dyT, dxcol, dy0, dy1, part, gW, total;
+    size_t feat, colT, dyT, dxcol, dy0, dy1, part, gW, total;
     int splits_max = 64;
-    CnnLayout(int n_, int h_, int w_)
+    // train = false: the forward pass only (no backward scratch)
+    CnnLayout(int n_, int h_, int w_, bool train = true)
     {
         n = n_;
         h = h_;
@@ -271,20 +304,46 @@ struct CnnLayout {
             dyTmax = std::max<long long>(dyTmax, (long long)cpad(L) * round_up((int)M[i], 8));
             partmax = std::max<long long>(partmax, (long long)splits_max * kpad(L) * cpad(L));
         }
-        colT = add((size_t)colTmax * 2);
-        dyT = add((size_t)dyTmax * 2);
-        dxcol = add((size_t)MKmax * 4);
-        dy0 = add((size_t)Mmax * 64 * 2);
-        dy1 = add((size_t)Mmax * 64 * 2);
-        part = add((size_t)partmax * 4);
-        gW = add((size_t)64 * 576 * 4);
+        feat = add((size_t)n * h * w * kFeat * 2);
+        colT = dyT = dxcol = dy0 = dy1 = part = gW = 0;
+        if (train) {
+            colT = add((size_t)colTmax * 2);
+            dyT = add((size_t)dyTmax * 2);
+            dxcol = add((size_t)MKmax * 4);
+            dy0 = add((size_t)Mmax * 64 * 2);
+            dy1 = add((size_t)Mmax * 64 * 2);
+            part = add((size_t)partmax * 4);
+            gW = add((size_t)64 * 576 * 4);
+        }
         total = o;
     }
 };
 
-size_t cnn_params() { return 115938; }
+size_t cnn_params()
+{
+    size_t t = 0;
+    for (int i = 0; i < kNL; i++) t += (size_t)kdim(kNet[i]) * kNet[i].cout + kNet[i].cout;
+    return t;
+}
 
-size_t cnn_ws_bytes(int n, int h, int w) { return CnnLayout(n, h, w).total; }
+size_t cnn_ws_bytes(int n, int h, int w, bool train) { return CnnLayout(n, h, w, train).total; }
+
+// Device address of layer `layer`'s stored output (bf16 [M][cout]; layer kNL - 1 = the 1x1
+// head has none) or of the feature stage (layer -1, bf16 [n][h][w][27]) inside a workspace.
+const void* cnn_activation(const void* ws, int n, int h, int w, int layer, int* rows, int* cols)
+{
+    const CnnLayout lay(n, h, w);
+    const uint8_t* base = static_cast<const uint8_t*>(ws);
+    if (layer == -1) {
+        *rows = n * h * w;
+        *cols = kFeat;
+        return base + lay.feat;
+    }
+    if (layer < 0 || layer >= kNL || !kNet[layer].relu) return nullptr;
+    *rows = (int)lay.M[layer];
+    *cols = kNet[layer].cout;
+    return base + lay.act[layer];
+}
 
 void cnn_out_dims(int h, int w, int* ho, int* wo)
 {
@@ -307,7 +366,11 @@ bool cnn_forward(const float* theta, const __nv_bfloat16* x, int n, int h, int w
 {
     const CnnLayout lay(n, h, w);
     uint8_t* base = static_cast<uint8_t*>(ws);
-    const __nv_bfloat16* in = x;
+    __nv_bfloat16* feat = reinterpret_cast<__nv_bfloat16*>(base + lay.feat);
+    note_launch();
+    k_features<<<grid_for((long long)n * h * w), 256, 0, s>>>(
+        reinterpret_cast<const __nv_bfloat162*>(x), n, h, w, feat);
+    const __nv_bfloat16* in = feat;
     for (int i = 0; i < kNL; i++) {
         const LayerSpec& L = kNet[i];
         const int K = kdim(L), kp = kpad(L), cp = cpad(L);
@@ -368,7 +431,8 @@ bool cnn_backward(const float* theta, const __nv_bfloat16* x, int n, int h, int 
         note_launch();
         k_bias_grad<<<L.cout, 1024, 0, s>>>(dy, M, dy_ld, gb);
         // weight gradient: dW^T [K x cout] = col^T [kp x M] * dY^T [cp x M]^T
-        const __nv_bfloat16* colsrc = L.k == 1 ? (i > 0 ? bf(lay.act[i - 1]) : x) : bf(lay.col[i]);
+        const __nv_bfloat16* colsrc = L.k == 1 ? (i > 0 ? bf(lay.act[i - 1]) : bf(lay.feat))
+                                               : bf(lay.col[i]);
         const int col_ld = L.k == 1 ? L.cin : kp;
         const int rowsA = L.k == 1 ? L.cin : kp;
         dim3 tb(32, 8);

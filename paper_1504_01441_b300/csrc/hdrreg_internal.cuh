@@ -383,6 +383,7 @@ struct SearchGeom {
 struct PredSearch {
     const float* pred;  // FP32 pairs, cell (ty, tx) at 2 * (ty * pred_ld + tx); nullptr: plain
     int pred_ld;
+    int refine;         // offsets [-refine, refine]^2 around the rounded prediction
     uint32_t fallback_cost;
     uint8_t* fell_back;  // optional: 1 where the tile fell back to the full search
 };
@@ -395,8 +396,8 @@ void launch_tile_labels(const int32_t* corner_xy, const int32_t* match_xy, const
                         int n, int w, int h, const double* H, float* label, cudaStream_t s);
 void launch_predictor_crops(const void* x_full, int wq, int hq, const float* label_full,
                             const uint8_t* valid_full, int ntx, int nty, const int32_t* origins,
-                            int n, int ct, void* x_out, float* label_out, uint8_t* valid_out,
-                            cudaStream_t s);
+                            int n, int ct, float bound, void* x_out, float* label_out,
+                            uint8_t* valid_out, cudaStream_t s);
 void launch_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,
                             const double* H, void* out, cudaStream_t s);
 
@@ -500,7 +501,8 @@ bool launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int
 
 // ------------------------------------------- learned predictor (row a-L)
 size_t cnn_params();
-size_t cnn_ws_bytes(int n, int h, int w);
+size_t cnn_ws_bytes(int n, int h, int w, bool train = true);  // train = false: forward only
+const void* cnn_activation(const void* ws, int n, int h, int w, int layer, int* rows, int* cols);
 void cnn_out_dims(int h, int w, int* ho, int* wo);
 bool cnn_forward(const float* theta, const __nv_bfloat16* x, int n, int h, int w, float* out,
                  void* ws, int* err, cudaStream_t s);

@@ -116,7 +116,6 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
     __shared__ uint64_t red[kWarps];
     __shared__ float hs[18];  // (float)H, |(float)H|
     __shared__ int s_corner[2], s_center[2];
-    __shared__ uint32_t s_pcost;
 
     const SearchSmem L(g);
     uint32_t* region = reinterpret_cast<uint32_t*>(smem + L.off_region);
@@ -249,107 +248,94 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
         }
     }
     const uint32_t tail = (P & 3) ? ((1u << (8 * (P & 3))) - 1u) : 0xFFFFFFFFu;
-    if (ps.pred) {
-        // ---- learned search: the SSD at the rounded prediction; keep it if cheap enough
+    // Pass 1 of the learned search: offsets [-r, r]^2 around the rounded prediction; the
+    // plain search (and the fallback) is one pass over [-R, R]^2 around the centre.
+    bool learned = ps.pred != nullptr;
+    int ccx = sx, ccy = sy, RR = R;
+    if (learned) {
         const float* pp = ps.pred + 2 * ((size_t)ty * ps.pred_ld + tx);
-        const int qx = sx + (int)floorf(pp[0] + 0.5f), qy = sy + (int)floorf(pp[1] + 0.5f);
-        stage_block(src, g.w, g.h, qx - hp, qy - hp, P, P, win, PWc + 1);
-        if (tid == 0) s_pcost = 0u;
+        ccx = sx + (int)floorf(pp[0] + 0.5f);
+        ccy = sy + (int)floorf(pp[1] + 0.5f);
+        RR = ps.refine;
+    }
+    for (;;) {
+        // ---- stage the source window (byte 0 of a row = column ccx - RR - hp)
+        const int side_d = 2 * RR + 1, nd = side_d * side_d, nq = (side_d + 3) >> 2;
+        stage_block(src, g.w, g.h, ccx - RR - hp, ccy - RR - hp, 2 * RR + P, 2 * RR + P, win, L.WW);
+        for (int i = tid; i < nd; i += kThreads) ssd[i] = 0u;
         __syncthreads();
-        if (tid < P) {
-            const uint32_t* pr = patch + tid * PWc;
-            const uint32_t* wr = win + tid * (PWc + 1);
-            uint32_t acc = 0;
-            for (int j = 0; j < PWc; j++) {
-                const uint32_t d = __vabsdiffu4(pr[j], wr[j] & (j == PWc - 1 ? tail : 0xFFFFFFFFu));
-                acc = __dp4a(d, d, acc);
+
+        // ---- SSD over d in [-RR, RR]^2, exact unsigned integers. A thread takes four
+        //      horizontal offsets 4q..4q+3 of one row dy of offsets (the same two window
+        //      words, shifted by 0, 8, 16, 24 bits) over a quarter of the patch rows; the
+        //      partial sums meet in shared memory.
+        {
+            constexpr int kSplit = 4;
+            const int rows_per = (P + kSplit - 1) / kSplit;
+            for (int item = tid; item < side_d * nq * kSplit; item += kThreads) {
+                const int part = item % kSplit, rest = item / kSplit;
+                const int dq = rest % nq, dy = rest / nq;
+                const int v0 = part * rows_per, v1 = min(P, v0 + rows_per);
+                uint32_t acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+                for (int v = v0; v < v1; v++) {
+                    const uint32_t* pr = patch + v * PWc;
+                    const uint32_t* wr = win + (dy + v) * L.WW + dq;
+                    uint32_t cur = wr[0];
+#pragma unroll 8
+                    for (int j = 0; j < PWc; j++) {
+                        const uint32_t nxt = wr[j + 1], pv = pr[j];
+                        const uint32_t m = j == PWc - 1 ? tail : 0xFFFFFFFFu;
+                        uint32_t d;
+                        d = __vabsdiffu4(pv, cur & m);
+                        acc0 = __dp4a(d, d, acc0);
+                        d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 8) & m);
+                        acc1 = __dp4a(d, d, acc1);
+                        d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 16) & m);
+                        acc2 = __dp4a(d, d, acc2);
+                        d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 24) & m);
+                        acc3 = __dp4a(d, d, acc3);
+                        cur = nxt;
+                    }
+                }
+                const int dx0 = 4 * dq, base = dy * side_d + dx0;
+                atomicAdd(&ssd[base], acc0);
+                if (dx0 + 1 < side_d) atomicAdd(&ssd[base + 1], acc1);
+                if (dx0 + 2 < side_d) atomicAdd(&ssd[base + 2], acc2);
+                if (dx0 + 3 < side_d) atomicAdd(&ssd[base + 3], acc3);
             }
-            atomicAdd(&s_pcost, acc);
         }
         __syncthreads();
-        const uint32_t pc = s_pcost;
-        if (pc <= ps.fallback_cost) {
+        uint64_t bestk = ~0ull;
+        for (int di = tid; di < nd; di += kThreads) {
+            const uint64_t key = ((uint64_t)ssd[di] << 16) | (uint64_t)di;
+            bestk = key < bestk ? key : bestk;
+        }
+        bestk = warp_min_u64(bestk);
+        if (lane == 0) red[warp] = bestk;
+        __syncthreads();
+        uint64_t v = lane < kWarps ? red[lane] : ~0ull;
+        v = warp_min_u64(v);  // every warp holds the CTA minimum
+        const uint32_t best_cost = (uint32_t)(v >> 16);
+        if (!learned || best_cost <= ps.fallback_cost) {
             if (tid == 0) {
+                const int di = (int)(v & 0xFFFF);
+                const int dy = di / side_d - RR, dx = di % side_d - RR;
                 corner_xy[2 * t] = px;
                 corner_xy[2 * t + 1] = py;
-                match_xy[2 * t] = qx;
-                match_xy[2 * t + 1] = qy;
-                cost_out[t] = pc;
+                match_xy[2 * t] = ccx + dx;
+                match_xy[2 * t + 1] = ccy + dy;
+                cost_out[t] = best_cost;
                 valid_out[t] = 1;
-                if (ps.fell_back) ps.fell_back[t] = 0;
+                if (ps.fell_back) ps.fell_back[t] = learned ? 0 : (ps.pred ? 1 : 0);
             }
             return;
         }
-        if (tid == 0 && ps.fell_back) ps.fell_back[t] = 1;
-    }
-
-    // ---- stage the source window (byte 0 of a row = column sx - R - hp)
-    stage_block(src, g.w, g.h, sx - R - hp, sy - R - hp, L.WS, L.WS, win, L.WW);
-    const int side_d = 2 * R + 1, nd = side_d * side_d, nq = (side_d + 3) >> 2;
-    for (int i = tid; i < nd; i += kThreads) ssd[i] = 0u;
-    __syncthreads();
-
-    // ---- SSD over d in [-R, R]^2, exact unsigned integers. A thread takes four
-    //      horizontal offsets 4q..4q+3 of one row dy of offsets (the same two window
-    //      words, shifted by 0, 8, 16, 24 bits) over a quarter of the patch rows; the
-    //      partial sums meet in shared memory.
-    {
-        constexpr int kSplit = 4;
-        const int rows_per = (P + kSplit - 1) / kSplit;
-        for (int item = tid; item < side_d * nq * kSplit; item += kThreads) {
-            const int part = item % kSplit, rest = item / kSplit;
-            const int dq = rest % nq, dy = rest / nq;
-            const int v0 = part * rows_per, v1 = min(P, v0 + rows_per);
-            uint32_t acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
-            for (int v = v0; v < v1; v++) {
-                const uint32_t* pr = patch + v * PWc;
-                const uint32_t* wr = win + (dy + v) * L.WW + dq;
-                uint32_t cur = wr[0];
-#pragma unroll 8
-                for (int j = 0; j < PWc; j++) {
-                    const uint32_t nxt = wr[j + 1], pv = pr[j];
-                    const uint32_t m = j == PWc - 1 ? tail : 0xFFFFFFFFu;
-                    uint32_t d;
-                    d = __vabsdiffu4(pv, cur & m);
-                    acc0 = __dp4a(d, d, acc0);
-                    d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 8) & m);
-                    acc1 = __dp4a(d, d, acc1);
-                    d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 16) & m);
-                    acc2 = __dp4a(d, d, acc2);
-                    d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 24) & m);
-                    acc3 = __dp4a(d, d, acc3);
-                    cur = nxt;
-                }
-            }
-            const int dx0 = 4 * dq, base = dy * side_d + dx0;
-            atomicAdd(&ssd[base], acc0);
-            if (dx0 + 1 < side_d) atomicAdd(&ssd[base + 1], acc1);
-            if (dx0 + 2 < side_d) atomicAdd(&ssd[base + 2], acc2);
-            if (dx0 + 3 < side_d) atomicAdd(&ssd[base + 3], acc3);
-        }
-    }
-    __syncthreads();
-    uint64_t bestk = ~0ull;
-    for (int di = tid; di < nd; di += kThreads) {
-        const uint64_t key = ((uint64_t)ssd[di] << 16) | (uint64_t)di;
-        bestk = key < bestk ? key : bestk;
-    }
-    bestk = warp_min_u64(bestk);
-    if (lane == 0) red[warp] = bestk;
-    __syncthreads();
-    if (warp == 0) {
-        uint64_t v = lane < kWarps ? red[lane] : ~0ull;
-        v = warp_min_u64(v);
-        if (lane == 0) {
-            const int di = (int)(v & 0xFFFF);
-            const int dy = di / side_d - R, dx = di % side_d - R;
-            corner_xy[2 * t] = px;
-            corner_xy[2 * t + 1] = py;
-            match_xy[2 * t] = sx + dx;
-            match_xy[2 * t + 1] = sy + dy;
-            cost_out[t] = (uint32_t)(v >> 16);
-            valid_out[t] = 1;
-        }
+        // the prediction was not good enough: the full search around the centre
+        learned = false;
+        ccx = sx;
+        ccy = sy;
+        RR = R;
+        __syncthreads();  // every thread is done with win, ssd and red
     }
 }
 
@@ -362,7 +348,7 @@ void launch_local_search(const uint8_t* ref, const uint8_t* src, const double* H
     if (n <= 0) return;
     const SearchSmem L(g);
     if (L.total > 48 * 1024) ensure_smem((const void*)k_local_search, L.total);
-    const PredSearch ps = pred ? *pred : PredSearch{nullptr, 0, 0u, nullptr};
+    const PredSearch ps = pred ? *pred : PredSearch{nullptr, 0, 0, 0u, nullptr};
     note_launch();
     k_local_search<<<n, kThreads, L.total, s>>>(ref, src, H, g, corner_xy, match_xy, cost, valid,
                                                 mask_zero, ps);
@@ -404,44 +390,78 @@ void launch_tile_labels(const int32_t* corner_xy, const int32_t* match_xy, const
 }
 
 // Training crops: crop b covers tiles (tx0 .. tx0 + ct - 1, ty0 .. ty0 + ct - 1), i.e. the
-// quarter-resolution pixels [8 tx0, 8 (tx0 + ct)) x [8 ty0, 8 (ty0 + ct)).
+// quarter-resolution pixels [8 tx0, 8 (tx0 + ct)) x [8 ty0, 8 (ty0 + ct)), seen through the
+// symmetry origins[4b + 2] (bit 0: mirror x, bit 1: mirror y, bit 2: transpose, applied to
+// the crop in that order): pixels and tiles move accordingly and each displacement label
+// (dx, dy) becomes (+-dx, +-dy), swapped by the transpose. A label whose component reaches
+// the search radius (|d| >= bound) marks its tile invalid (the plain search hit its border).
+__device__ __forceinline__ void crop_src(int i, int j, int n, int sym, int& si, int& sj)
+{
+    // output (i, j) -> source (si, sj) inside an n x n crop
+    int a = i, b = j;
+    if (sym & 4) {
+        const int t = a;
+        a = b;
+        b = t;
+    }
+    if (sym & 2) a = n - 1 - a;
+    if (sym & 1) b = n - 1 - b;
+    si = a;
+    sj = b;
+}
+
 __global__ void k_predictor_crops(const uint32_t* __restrict__ x_full, int wq, int hq,
                                   const float* __restrict__ label_full,
                                   const uint8_t* __restrict__ valid_full, int ntx, int nty,
-                                  const int32_t* __restrict__ origins, int ct,
+                                  const int32_t* __restrict__ origins, int ct, float bound,
                                   uint32_t* __restrict__ x_out, float* __restrict__ label_out,
                                   uint8_t* __restrict__ valid_out)
 {
     const int b = blockIdx.y;
-    const int tx0 = origins[2 * b], ty0 = origins[2 * b + 1];
+    const int tx0 = origins[4 * b], ty0 = origins[4 * b + 1], sym = origins[4 * b + 2] & 7;
     const int side = 8 * ct;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < side * side; i += gridDim.x * blockDim.x) {
-        const int y = i / side, x = i % side;
-        const int gy = min(max(8 * ty0 + y, 0), hq - 1), gx = min(max(8 * tx0 + x, 0), wq - 1);
+        int sy, sx;
+        crop_src(i / side, i % side, side, sym, sy, sx);
+        const int gy = min(max(8 * ty0 + sy, 0), hq - 1), gx = min(max(8 * tx0 + sx, 0), wq - 1);
         x_out[(size_t)b * side * side + i] = x_full[(size_t)gy * wq + gx];
     }
     if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < ct * ct; i += blockDim.x) {
-            const int ty = ty0 + i / ct, tx = tx0 + i % ct;
+            int si, sj;
+            crop_src(i / ct, i % ct, ct, sym, si, sj);
+            const int ty = ty0 + si, tx = tx0 + sj;
             const bool in = tx >= 0 && tx < ntx && ty >= 0 && ty < nty;
             const size_t t = in ? (size_t)ty * ntx + tx : 0;
-            label_out[((size_t)b * ct * ct + i) * 2] = in ? label_full[2 * t] : 0.f;
-            label_out[((size_t)b * ct * ct + i) * 2 + 1] = in ? label_full[2 * t + 1] : 0.f;
-            valid_out[(size_t)b * ct * ct + i] = in ? valid_full[t] : 0;
+            float dx = in ? label_full[2 * t] : 0.f, dy = in ? label_full[2 * t + 1] : 0.f;
+            bool ok = in && valid_full[t] && fabsf(dx) < bound && fabsf(dy) < bound;
+            if (sym & 4) {  // undo in reverse order: the displacement of the output frame
+                const float tmp = dx;
+                dx = dy;
+                dy = tmp;
+            }
+            // mirror of the source axes, expressed in output axes after the transpose
+            const bool mx = (sym & 4) ? (sym & 2) : (sym & 1);
+            const bool my = (sym & 4) ? (sym & 1) : (sym & 2);
+            if (mx) dx = -dx;
+            if (my) dy = -dy;
+            label_out[((size_t)b * ct * ct + i) * 2] = ok ? dx : 0.f;
+            label_out[((size_t)b * ct * ct + i) * 2 + 1] = ok ? dy : 0.f;
+            valid_out[(size_t)b * ct * ct + i] = ok ? 1 : 0;
         }
     }
 }
 
 void launch_predictor_crops(const void* x_full, int wq, int hq, const float* label_full,
                             const uint8_t* valid_full, int ntx, int nty, const int32_t* origins,
-                            int n, int ct, void* x_out, float* label_out, uint8_t* valid_out,
-                            cudaStream_t s)
+                            int n, int ct, float bound, void* x_out, float* label_out,
+                            uint8_t* valid_out, cudaStream_t s)
 {
     if (n <= 0) return;
     note_launch();
     k_predictor_crops<<<dim3(16, n), 256, 0, s>>>(static_cast<const uint32_t*>(x_full), wq, hq,
                                                    label_full, valid_full, ntx, nty, origins, ct,
-                                                   static_cast<uint32_t*>(x_out), label_out,
+                                                   bound, static_cast<uint32_t*>(x_out), label_out,
                                                    valid_out);
 }
 

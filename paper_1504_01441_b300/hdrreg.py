@@ -31,11 +31,12 @@ EXPORTS = [
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
     "hdrreg_gemm_bf16", "hdrreg_cnn_workspace_size", "hdrreg_cnn_out_dims", "hdrreg_cnn_forward",
-    "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_predictor_input", "hdrreg_tile_labels",
+    "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_cnn_activation", "hdrreg_predictor_input",
+    "hdrreg_tile_labels",
     "hdrreg_predictor_crops", "hdrreg_local_search_predicted",
 ]
 
-CNN_PARAMS = 115938
+CNN_PARAMS = 119538
 
 MAX_LANES = 16
 
@@ -57,12 +58,12 @@ class Params(C.Structure):
         ("weed_eps", C.c_double), ("sigma_s", C.c_double), ("sigma_r", C.c_double),
         ("ssim_sigma", C.c_double), ("we_sigma", C.c_double), ("flow_eps", C.c_double),
         ("weed_seed", C.c_uint64), ("predictor", C.c_void_p), ("fallback_cost", C.c_uint32),
-        ("reserved1", C.c_uint32),
+        ("predictor_refine", C.c_int32),
     ]
 
     def as_dict(self) -> Dict:
         return {n: getattr(self, n) for n, _ in self._fields_
-                if n not in ("reserved0", "reserved1", "predictor", "fallback_cost")}
+                if n not in ("reserved0", "predictor", "fallback_cost", "predictor_refine")}
 
 
 class Frame(C.Structure):
@@ -151,11 +152,14 @@ def lib():
         L.hdrreg_cnn_forward.argtypes = [vp, vp, i, i, i, vp, vp, sz, vp, vp]
         L.hdrreg_cnn_backward.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp, vp, sz, vp, vp]
         L.hdrreg_cnn_adam.argtypes = [vp, vp, vp, vp, i, C.c_float, vp]
+        L.hdrreg_cnn_activation.argtypes = [vp, i, i, i, i, C.POINTER(C.c_void_p),
+                                             C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.hdrreg_predictor_input.argtypes = [vp, vp, i, i, vp, vp, vp]
         L.hdrreg_tile_labels.argtypes = [vp, vp, vp, i, i, i, vp, vp, vp]
-        L.hdrreg_predictor_crops.argtypes = [vp, i, i, vp, vp, i, i, vp, i, i, vp, vp, vp, vp]
+        L.hdrreg_predictor_crops.argtypes = [vp, i, i, vp, vp, i, i, vp, i, i, C.c_float, vp, vp,
+                                             vp, vp]
         L.hdrreg_local_search_predicted.argtypes = [vp, vp, i, i, vp, C.POINTER(Params), vp, i, i,
-                                                    C.c_uint32, vp, vp, vp, vp, vp, vp]
+                                                    i, C.c_uint32, vp, vp, vp, vp, vp, vp]
         for name in EXPORTS:
             if not hasattr(L, name):
                 raise ImportError(f"libhdrreg.so does not export {name}")
@@ -463,6 +467,16 @@ class Predictor:
                                          _ptr(self.status), _stream(stream)))
         return self.loss, self.grad
 
+    def activation(self, layer: int):
+        """Copy of what the last forward stored for `layer` (-1 = features) as FP32 [rows, cols]."""
+        import torch
+        ptr, rows, cols = C.c_void_p(), C.c_int(), C.c_int()
+        _check(lib().hdrreg_cnn_activation(_ptr(self.ws), self.n, self.h, self.w, layer,
+                                           C.byref(ptr), C.byref(rows), C.byref(cols)))
+        off = ptr.value - self.ws.data_ptr()
+        nb = rows.value * cols.value * 2
+        return self.ws[off:off + nb].view(torch.bfloat16).float().reshape(rows.value, cols.value)
+
     def adam(self, lr=1e-3, stream=None):
         self.t += 1
         _check(lib().hdrreg_cnn_adam(_ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.grad),
@@ -489,8 +503,9 @@ def tile_labels(corner_xy, match_xy, valid, w: int, h: int, H, stream=None):
 
 
 def predictor_crops(x_full, label_full, valid_full, ntx: int, nty: int, origins, crop_tiles=8,
-                    stream=None):
-    """Gather training crops at tile origins (int32 [n, 2] CUDA tensor) -> (x, label, valid)."""
+                    label_bound=1e30, stream=None):
+    """Gather training crops (origins: int32 [n, 4] CUDA tensor of tile x, tile y, symmetry,
+    unused) -> (x, label, valid)."""
     import torch
     hq, wq = x_full.shape[0], x_full.shape[1]
     n = origins.shape[0]
@@ -499,12 +514,14 @@ def predictor_crops(x_full, label_full, valid_full, ntx: int, nty: int, origins,
     lab = torch.empty((n, crop_tiles, crop_tiles, 2), dtype=torch.float32, device=x_full.device)
     val = torch.empty((n, crop_tiles, crop_tiles), dtype=torch.uint8, device=x_full.device)
     _check(lib().hdrreg_predictor_crops(_ptr(x_full), wq, hq, _ptr(label_full), _ptr(valid_full),
-                                        ntx, nty, _ptr(origins), n, crop_tiles, _ptr(x), _ptr(lab),
-                                        _ptr(val), _stream(stream)))
+                                        ntx, nty, _ptr(origins), n, crop_tiles,
+                                        C.c_float(label_bound), _ptr(x), _ptr(lab), _ptr(val),
+                                        _stream(stream)))
     return x, lab, val
 
 
-def local_search_predicted(ref_n, src_n, H, p: Params, pred, fallback_cost: int, stream=None):
+def local_search_predicted(ref_n, src_n, H, p: Params, pred, fallback_cost: int, refine=0,
+                           stream=None):
     """pred: FP32 [rows, cols, 2] with cols >= tiles across -> (corner, match, cost, valid,
     fell_back)."""
     import torch
@@ -517,7 +534,7 @@ def local_search_predicted(ref_n, src_n, H, p: Params, pred, fallback_cost: int,
     valid = torch.empty((max(n, 1),), dtype=torch.uint8, device=dev)
     fb = torch.empty((max(n, 1),), dtype=torch.uint8, device=dev)
     _check(lib().hdrreg_local_search_predicted(_ptr(ref_n), _ptr(src_n), w, h, _ptr(H), C.byref(p),
-                                               _ptr(pred), pred.shape[0], pred.shape[1],
+                                               _ptr(pred), pred.shape[0], pred.shape[1], refine,
                                                C.c_uint32(fallback_cost),
                                                _ptr(corner), _ptr(match), _ptr(cost), _ptr(valid),
                                                _ptr(fb), _stream(stream)))

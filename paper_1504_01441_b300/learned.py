@@ -1,0 +1,233 @@
+"""Training and evaluation of the learned level-0 search (row a-L).
+
+The network (csrc/cnn.cu) predicts, per 32x32 tile, the displacement the plain
+SSD search of Sec. 2.2 finds at level 0, from the normalized reference and the
+source pre-warped by the level-1 homography at quarter resolution. Everything
+numeric runs in the library's kernels; this module only sequences the calls:
+
+  prepare(stack)  plain matcher down to level 1 (H1), the network input, and the
+                  plain level-0 search whose displacements are the labels;
+  train(...)      Adam on random crops of 8 x 8 tiles (64 x 64 input pixels);
+  evaluate(...)   end-point error of the learned search against the plain one
+                  (mean |match_learned - match_plain| over tiles with a corner) and
+                  its fallback rate, with the fallback cost calibrated as 1.5 x the
+                  median plain level-0 SSD cost.
+
+Training inputs are seeded synthetic stacks of synth.py shaped like the headline 5 MP pairs
+(+-4 px fields); evaluation also reports stacks with +-8 px fields, where the field exceeds the
+plain search's radius and the plain labels stop being measurements.
+`python -m paper_1504_01441_b300.learned --out FILE` trains from scratch and writes
+the parameters (float32, HDRREG_CNN_PARAMS values); the committed
+paper_1504_01441_b300/predictor_theta.npy was written this way.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import os
+import time
+from typing import List
+
+import numpy as np
+
+from . import hdrreg, synth
+
+CROP_TILES = 8
+# the headline workload's distribution (5 MP, r = 4, sigma 1.5, +-4 px fields, 3 movers),
+# luma only; STRESS_SPEC doubles the field, beyond the plain search's radius of 6 px
+TRAIN_SPEC = synth.StackSpec(2592, 1944, ratios=((4, 1),), noise_sigma=1.5, field_amp=4.0,
+                             movers=3, chroma=False)
+STRESS_SPEC = synth.StackSpec(2592, 1944, ratios=((4, 1),), noise_sigma=1.5, field_amp=8.0,
+                              movers=3, chroma=False)
+THETA_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "predictor_theta.npy")
+
+
+@dataclasses.dataclass
+class Prepared:
+    x: object          # bfloat16 [hq, wq, 2] network input
+    label: object      # FP32 [nty * ntx, 2] plain displacement from the search centre
+    valid: object      # uint8 [nty * ntx]
+    match: object      # int32 [nty * ntx, 2] plain level-0 matches
+    cost: object       # int32 [nty * ntx] plain level-0 SSD costs
+    H1: object         # float64 [9] level-1 homography
+    ref_n: object
+    src_n: object
+    ntx: int
+    nty: int
+    gt: object = None  # optional FP32 [2, H, W]: generator ground truth (source position)
+
+
+def prepare(stack, p: hdrreg.Params, device="cuda", keep_gt: bool = False) -> Prepared:
+    import torch
+    dev = torch.device(device)
+    ref = torch.from_numpy(stack.ref.y).to(dev)
+    src = torch.from_numpy(stack.srcs[0].y).to(dev)
+    rn, sn, _ = hdrreg.normalize_exposure(ref, src, hdrreg.NORM_RATIO, stack.ratios[0])
+    h, w = rn.shape
+    L = hdrreg.num_levels(w, h, p)
+    if L < 3 or p.tile != 32:
+        raise ValueError("the learned search needs tile 32 and three pyramid levels")
+    pr, ps = hdrreg.build_pyramid(rn, L), hdrreg.build_pyramid(sn, L)
+    Hc = torch.tensor([1, 0, 0, 0, 1, 0, 0, 0, 1], dtype=torch.float64, device=dev)
+    counter = torch.zeros(1, dtype=torch.int32, device=dev)
+    for lv in range(L - 1, 0, -1):
+        lh, lw = pr[lv].shape
+        cxy, mxy, cost, valid = hdrreg.local_search(pr[lv], ps[lv], Hc, p)
+        _, Hc, _ = hdrreg.weed_fit(cxy, mxy, valid, lw, lh, p, p.weed_seed + lv, Hc, counter=counter)
+    H1 = Hc.clone()
+    x = hdrreg.predictor_input(pr[2], ps[2], H1)
+    cxy, mxy, cost, valid = hdrreg.local_search(rn, sn, H1, p)
+    lab = hdrreg.tile_labels(cxy, mxy, valid, w, h, H1)
+    gt = None
+    if keep_gt and stack.gt and stack.gt[0] is not None:
+        gt = torch.from_numpy(np.stack(stack.gt[0])).to(dev)
+    return Prepared(x, lab, valid, mxy, cost, H1, rn, sn, w // p.tile, h // p.tile, gt)
+
+
+def make_stacks(n: int, first_index: int, spec=TRAIN_SPEC):
+    return [synth.make_stack(spec, synth.stack_seed(4, first_index + i)) for i in range(n)]
+
+
+def train(prepared: List[Prepared], steps: int, batch: int = 64, lr: float = 2e-3, seed: int = 0,
+          theta=None, log_every: int = 50, augment: bool = True, label_bound: float = 6.0):
+    """Adam on random crops (each under one of the 8 mirror/transpose symmetries when
+    augment); crops of one batch come from all prepared stacks in turn; labels on the
+    border of the plain search (|d| >= label_bound, the search radius) are left out."""
+    import torch
+    from . import hdrreg as hd
+    dev = prepared[0].x.device
+    side = 8 * CROP_TILES
+    pred = hd.Predictor(batch, side, side, theta, device=dev)
+    if theta is None:
+        pred.theta.copy_(torch.tensor(init_theta(seed)))
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    xb = torch.empty((batch, side, side, 2), dtype=torch.bfloat16, device=dev)
+    lb = torch.empty((batch, CROP_TILES, CROP_TILES, 2), dtype=torch.float32, device=dev)
+    vb = torch.empty((batch, CROP_TILES, CROP_TILES), dtype=torch.uint8, device=dev)
+    per = [batch // len(prepared) + (1 if i < batch % len(prepared) else 0)
+           for i in range(len(prepared))]
+    history = []
+    t0 = time.perf_counter()
+    for step in range(steps):
+        o = 0
+        for P, k in zip(prepared, per):
+            if k == 0:
+                continue
+            org = torch.stack([torch.randint(0, P.ntx - CROP_TILES + 1, (k,), generator=g),
+                               torch.randint(0, P.nty - CROP_TILES + 1, (k,), generator=g),
+                               torch.randint(0, 8 if augment else 1, (k,), generator=g),
+                               torch.zeros(k, dtype=torch.int64)], 1)
+            org = org.to(torch.int32).to(dev)
+            xc, lc, vc = hd.predictor_crops(P.x, P.label, P.valid, P.ntx, P.nty, org, CROP_TILES,
+                                            label_bound)
+            xb[o:o + k].copy_(xc)
+            lb[o:o + k].copy_(lc)
+            vb[o:o + k].copy_(vc)
+            o += k
+        pred.forward(xb)
+        loss, _ = pred.backward(xb, lb, vb)
+        pred.adam(lr=lr * (1.0 - 0.9 * step / max(steps - 1, 1)))  # linear decay to 10%
+        if step % log_every == 0 or step == steps - 1:
+            history.append((step, float(loss.item())))
+    torch.cuda.synchronize()
+    if int(pred.status.item()) != 0:
+        raise hd.HdrregError(2, "a tensor-core kernel timed out during training")
+    return pred.theta.detach().clone(), history, time.perf_counter() - t0
+
+
+def init_theta(seed: int):
+    """He-normal weights (std sqrt(2 / fan_in)), zero biases, head scaled by 0.1 -- the
+    network's starting point for training."""
+    rng = np.random.default_rng(seed)
+    layers = [(27, 16, 3, True), (16, 16, 3, True), (16, 32, 3, True), (32, 32, 3, True),
+              (32, 48, 3, True), (48, 48, 3, True), (48, 64, 3, True), (64, 64, 3, True),
+              (64, 2, 1, False)]
+    parts = []
+    for ci, co, k, relu in layers:
+        std = np.sqrt(2.0 / (ci * k * k)) * (1.0 if relu else 0.1)
+        parts.append(rng.normal(0.0, std, co * k * k * ci))
+        parts.append(np.zeros(co))
+    th = np.concatenate(parts).astype(np.float32)
+    assert th.size == hdrreg.CNN_PARAMS
+    return th
+
+
+def evaluate(prepared: List[Prepared], theta, p: hdrreg.Params, fallback_ratio: float = 1.5,
+             refine: int = 1):
+    """Learned vs plain level-0 search on prepared stacks -> metrics dict."""
+    import torch
+    errs, fb_tot, val_tot, raw = [], 0, 0, []
+    P0 = prepared[0]
+    hq, wq = P0.x.shape[0], P0.x.shape[1]
+    net = hdrreg.Predictor(1, hq, wq, theta, device=P0.x.device)
+    costs = torch.cat([P.cost[P.valid.bool()] for P in prepared]).double()
+    thr = int(fallback_ratio * float(costs.median().item()))
+    gt_plain, gt_learned = [], []
+    for P in prepared:
+        out = net.forward(P.x.unsqueeze(0))[0]
+        c, m, co, v, fb = hdrreg.local_search_predicted(P.ref_n, P.src_n, P.H1, p, out, thr, refine)
+        ok = (v.bool() & P.valid.bool())
+        d = (m[ok] - P.match[ok]).double()
+        errs.append(torch.sqrt((d * d).sum(1)))
+        if P.gt is not None:
+            cc = c[ok].long()
+            g = torch.stack([P.gt[0][cc[:, 1], cc[:, 0]], P.gt[1][cc[:, 1], cc[:, 0]]], 1).double()
+            gt_plain.append(torch.sqrt(((P.match[ok].double() - g) ** 2).sum(1)))
+            gt_learned.append(torch.sqrt(((m[ok].double() - g) ** 2).sum(1)))
+        pr = out[:P.nty, :P.ntx].reshape(-1, 2)[ok]
+        dr = (pr.double() - P.label[ok].double())
+        raw.append(torch.sqrt((dr * dr).sum(1)))
+        fb_tot += int(fb[ok].sum().item())
+        val_tot += int(ok.sum().item())
+    e = torch.cat(errs)
+    r = torch.cat(raw)
+    extra = {}
+    if gt_plain:
+        gp, gl = torch.cat(gt_plain), torch.cat(gt_learned)
+        extra = {"plain_vs_truth_px": float(gp.mean().item()),
+                 "learned_vs_truth_px": float(gl.mean().item()),
+                 "plain_vs_truth_median_px": float(gp.median().item()),
+                 "learned_vs_truth_median_px": float(gl.median().item())}
+    return {**extra, "epe_px": float(e.mean().item()), "epe_median_px": float(e.median().item()),
+            "within_half_px": float((e <= 0.5).double().mean().item()),
+            "epe_network_px": float(r.mean().item()),
+            "fallback_rate": fb_tot / max(val_tot, 1), "tiles": val_tot, "fallback_cost": thr,
+            "refine": refine}
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=THETA_FILE)
+    ap.add_argument("--train-stacks", type=int, default=16)
+    ap.add_argument("--eval-stacks", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--log", default=None)
+    args = ap.parse_args()
+    p = hdrreg.params_from_dict(synth.method_params(32, 6))
+    t0 = time.perf_counter()
+    train_set = [prepare(s, p) for s in make_stacks(args.train_stacks, 0)]
+    eval_set = [prepare(s, p, keep_gt=True) for s in make_stacks(args.eval_stacks, 1000)]
+    t_data = time.perf_counter() - t0
+    theta, hist, t_train = train(train_set, args.steps, args.batch, args.lr, args.seed)
+    m_train = evaluate(train_set[:2], theta, p)
+    m_eval = {f"refine{r}_ratio{fr}": evaluate(eval_set, theta, p, fallback_ratio=fr, refine=r)
+              for r in (0, 1) for fr in (1.0, 1.5)}
+    stress = [prepare(s, p, keep_gt=True) for s in make_stacks(1, 2000, STRESS_SPEC)]
+    m_eval["stress_refine1_ratio1.5"] = evaluate(stress, theta, p, fallback_ratio=1.5, refine=1)
+    np.save(args.out, theta.cpu().numpy())
+    rep = {"steps": args.steps, "batch": args.batch, "lr": args.lr, "seed": args.seed,
+           "train_stacks": args.train_stacks, "data_s": round(t_data, 1),
+           "train_s": round(t_train, 2), "ms_per_step": round(1e3 * t_train / args.steps, 3),
+           "loss": hist[::10] + hist[-1:], "train_metrics": m_train, "eval_metrics": m_eval}
+    print(json.dumps(rep))
+    if args.log:
+        json.dump(rep, open(args.log, "w"))
+
+
+if __name__ == "__main__":
+    main()

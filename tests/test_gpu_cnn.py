@@ -1,9 +1,20 @@
 """Learned displacement predictor (row a-L) on the GPU against the float64 oracle
-(oracle/cnn.py with the same bfloat16 rounding points): forward output, loss, the
-gradient of every layer's weights and biases, the Adam step, and a loss that falls
-under training. Tolerance: max-norm relative 2e-2 for bf16 tensor-core paths
-(the oracle rounds the same stored values to bfloat16; the rest is FP32 vs FP64
-accumulation order), 1e-5 for the FP32 Adam update."""
+(oracle/cnn.py with the same bfloat16 rounding points): forward output and every stored
+activation, loss, the gradient of every layer's weights and biases, the Adam step, and a
+loss that falls under training.
+
+Forward. The oracle rounds the same stored values to bfloat16, so the two differ only
+where FP32 and FP64 accumulation land on opposite sides of a bfloat16 rounding boundary
+(one step = 2^-8 relative), compounding over nine layers: max-norm relative 2e-2 on the
+output. Such a difference can also flip a ReLU whose pre-activation is within rounding of
+zero (observed: one or two per layer in a thousand), which changes that element's gradient
+entirely. Backward is therefore checked on the GPU's own forward: the oracle's backward
+runs on the activations the GPU stored (read back through hdrreg_cnn_activation), so the
+ReLU masks agree and the remaining difference is accumulation order plus bfloat16
+rounding of the output gradients at nine layers: relative L2 error 1e-2 per layer's
+weights and biases, max-norm relative 3e-2. The Adam step is FP32 arithmetic on identical
+inputs: 1e-5.
+"""
 import numpy as np
 import pytest
 
@@ -25,6 +36,11 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
 def layer_slices():
     from oracle import cnn
     out, o = [], 0
@@ -35,30 +51,38 @@ def layer_slices():
     return out
 
 
-@pytest.mark.parametrize("n,h,w", [(2, 24, 40), (1, 61, 33)])
+@pytest.mark.parametrize("n,h,w", [(2, 24, 40), (1, 61, 33), (1, 64, 64), (2, 40, 32)])
 def test_forward_and_gradients_match_oracle(hd, n, h, w):
     from oracle import cnn
-    rng = np.random.default_rng(n * 100 + h)
+    rng = np.random.default_rng(n * 100 + h + w)
     theta = cnn.init_params(7)
     theta[cnn.n_params() - 2:] = [0.3, -0.2]  # nonzero head bias
     xb = torch.tensor(rng.uniform(-1, 1, (n, h, w, 2)), dtype=torch.bfloat16)
     P = hd.Predictor(n, h, w, theta)
     out = P.forward(xb.cuda()).cpu().numpy()
-    o_or, cache = cnn.forward(theta, xb.double().numpy(), bf16=True)
+    o_or, (params, acts) = cnn.forward(theta, xb.double().numpy(), bf16=True)
     assert out.shape == o_or.shape
     assert rel(out, o_or) <= 2e-2
+    # every stored activation within bfloat16 rounding of the oracle's, bar rare flips
+    gacts = [P.activation(-1).cpu().numpy().reshape(acts[0].shape)]
+    assert np.array_equal(gacts[0], acts[0])  # the feature stage is exact
+    for i in range(len(cnn.LAYERS) - 1):
+        a = P.activation(i).cpu().numpy().reshape(acts[i + 1].shape)
+        assert rel_l2(a, acts[i + 1]) <= 1e-2, f"activation {i}"
+        gacts.append(a)
     label = rng.normal(size=out.shape).astype(np.float32)
     valid = (rng.random(out.shape[:3]) > 0.25).astype(np.uint8)
     loss, grad = P.backward(xb.cuda(), torch.tensor(label).cuda(), torch.tensor(valid).cuda())
     torch.cuda.synchronize()
     assert int(P.status.item()) == 0
-    L, dout = cnn.loss_and_grad_out(o_or, label, valid.astype(bool))
-    g_or = cnn.backward(cache, dout, bf16=True)
-    assert float(loss.item()) == pytest.approx(L, rel=2e-2)
+    L, dout = cnn.loss_and_grad_out(out.astype(np.float64), label, valid.astype(bool))
+    assert float(loss.item()) == pytest.approx(L, rel=1e-5)
+    g_or = cnn.backward((params, gacts + [out.astype(np.float64)]), dout, bf16=True)
     g = grad.cpu().numpy()
     for i, (sw, sb) in enumerate(layer_slices()):
-        assert rel(g[sw], g_or[sw]) <= 2e-2, f"layer {i} weights"
-        assert rel(g[sb], g_or[sb]) <= 2e-2, f"layer {i} biases"
+        for part, sl in (("weights", sw), ("biases", sb)):
+            assert rel_l2(g[sl], g_or[sl]) <= 1e-2, f"layer {i} {part}"
+            assert rel(g[sl], g_or[sl]) <= 3e-2, f"layer {i} {part}"
 
 
 def test_adam_matches_oracle(hd):

@@ -70,14 +70,15 @@ def test_search_predicted_bit_exact(hd, orc, level_pair):
     ntx = 640 // 16
     grid = np.zeros((480 // 16 + 1, ntx + 3, 2), np.float32)  # wider than the tile grid
     grid[:30, :ntx] = pred.reshape(30, ntx, 2)
-    gc, gm, gcost, gv, gfb = hd.local_search_predicted(dev(rn), dev(sn), dev(H.reshape(9)), p,
-                                                       dev(grid), thr)
-    om, oc, ofb = orc.search_predicted(rn, sn, H, c, cxy, valid, pred, thr)
-    assert np.array_equal(gc.cpu().numpy(), cxy) and np.array_equal(gv.cpu().numpy(), valid)
-    assert np.array_equal(gm.cpu().numpy(), om)
-    assert np.array_equal(gcost.cpu().numpy().view(np.uint32), oc)
-    assert np.array_equal(gfb.cpu().numpy(), ofb)
-    assert 0 < int(ofb.sum()) < int(valid.sum())  # both branches exercised
+    for refine in (0, 1, 2):
+        gc, gm, gcost, gv, gfb = hd.local_search_predicted(dev(rn), dev(sn), dev(H.reshape(9)), p,
+                                                           dev(grid), thr, refine)
+        om, oc, ofb = orc.search_predicted(rn, sn, H, c, cxy, valid, pred, thr, refine)
+        assert np.array_equal(gc.cpu().numpy(), cxy) and np.array_equal(gv.cpu().numpy(), valid)
+        assert np.array_equal(gm.cpu().numpy(), om), refine
+        assert np.array_equal(gcost.cpu().numpy().view(np.uint32), oc), refine
+        assert np.array_equal(gfb.cpu().numpy(), ofb), refine
+        assert 0 < int(ofb.sum()) < int(valid.sum())  # both branches exercised
 
 
 def test_crops_are_the_covered_tiles(hd):
@@ -86,15 +87,49 @@ def test_crops_are_the_covered_tiles(hd):
     x = torch.tensor(rng.normal(size=(hq, wq, 2)), dtype=torch.bfloat16)
     lab = rng.normal(size=(nty * ntx, 2)).astype(np.float32)
     val = (rng.random(nty * ntx) > 0.3).astype(np.uint8)
-    org = np.array([[0, 0], [3, 1], [4, 2]], np.int32)
-    xc, lc, vc = hd.predictor_crops(x.cuda(), dev(lab), dev(val), ntx, nty, dev(org), crop_tiles=3)
+    org = np.array([[0, 0, s, 0] for s in range(8)] + [[3, 1, 0, 0], [4, 2, 5, 0]], np.int32)
+    bound = 1.5
+    xc, lc, vc = hd.predictor_crops(x.cuda(), dev(lab), dev(val), ntx, nty, dev(org), crop_tiles=3,
+                                    label_bound=bound)
     xc, lc, vc = xc.cpu(), lc.cpu().numpy(), vc.cpu().numpy()
-    for b, (tx, ty) in enumerate(org):
-        assert torch.equal(xc[b], x[8 * ty:8 * ty + 24, 8 * tx:8 * tx + 24])
-        L = lab.reshape(nty, ntx, 2)
-        V = val.reshape(nty, ntx)
-        assert np.array_equal(lc[b], L[ty:ty + 3, tx:tx + 3])
-        assert np.array_equal(vc[b], V[ty:ty + 3, tx:tx + 3])
+    L = lab.reshape(nty, ntx, 2)
+    V = val.reshape(nty, ntx).astype(bool) & (np.abs(L) < bound).all(-1)
+    for b, (tx, ty, sym, _) in enumerate(org):
+        xs = x[8 * ty:8 * ty + 24, 8 * tx:8 * tx + 24]
+        ls, vs = L[ty:ty + 3, tx:tx + 3].copy(), V[ty:ty + 3, tx:tx + 3]
+        # the symmetry as numpy operations on the crop: transpose, then mirror rows, then columns
+        def apply(a, is_vec):
+            if sym & 4:
+                a = a.transpose(1, 0, 2) if a.ndim == 3 else a.T
+            if sym & 2:
+                a = a[::-1]
+            if sym & 1:
+                a = a[:, ::-1]
+            return a
+        # output (i, j) reads source crop_src(i, j): the inverse maps, applied to the source
+        def inv(a):
+            if sym & 1:
+                a = a[:, ::-1]
+            if sym & 2:
+                a = a[::-1]
+            if sym & 4:
+                a = a.transpose(1, 0, 2) if a.ndim == 3 else a.T
+            return a
+        assert torch.equal(xc[b], torch.from_numpy(np.ascontiguousarray(inv(xs.float().numpy()))).bfloat16())
+        lw = inv(ls)
+        d = lw.copy()
+        if sym & 4:
+            d = d[..., ::-1]
+        mx = (sym & 2) if (sym & 4) else (sym & 1)
+        my = (sym & 1) if (sym & 4) else (sym & 2)
+        if mx:
+            d[..., 0] = -d[..., 0]
+        if my:
+            d[..., 1] = -d[..., 1]
+        vw = inv(vs)
+        assert np.array_equal(vc[b].astype(bool), vw), sym
+        assert np.array_equal(lc[b][vw], d[vw]), sym
+        assert np.all(lc[b][~vw] == 0)
 
 
 def test_fused_learned_path_with_zero_fallback_cost_equals_plain(hd):
