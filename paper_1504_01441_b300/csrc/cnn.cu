@@ -42,53 +42,61 @@ int osz(int n, const LayerSpec& L) { return (n + 2 * (L.k / 2) - L.k) / L.stride
 // Fixed feature stage: per pixel a, b and -(a(p) - b(p + o))^2 for o = (u, v) in
 // [-2, 2]^2 (row-major in v, then u; b = 0 outside). With bfloat16 inputs in [-1, 1] the
 // difference and its square are exact in FP32, so only the final rounding to bfloat16
-// remains.
-__global__ void k_features(const __nv_bfloat162* __restrict__ x, int n, int h, int w,
+// remains. Grid: x over columns, y over rows, z over images.
+__global__ void k_features(const __nv_bfloat162* __restrict__ x, int h, int w,
                            __nv_bfloat16* __restrict__ f)
 {
-    const long long total = (long long)n * h * w;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int xx = (int)(p % w), yy = (int)((p / w) % h);
-        const long long base = p - ((long long)yy * w + xx);  // first pixel of this image
-        const float2 ab = __bfloat1622float2(x[p]);
-        __nv_bfloat16* o = f + p * kFeat;
-        o[0] = __float2bfloat16_rn(ab.x);
-        o[1] = __float2bfloat16_rn(ab.y);
-        int c = 2;
-        for (int v = -kCorr; v <= kCorr; v++)
-            for (int u = -kCorr; u <= kCorr; u++, c++) {
-                const int ys = yy + v, xs = xx + u;
-                const float b = (ys >= 0 && ys < h && xs >= 0 && xs < w)
-                                    ? __high2float(x[base + (long long)ys * w + xs])
-                                    : 0.f;
-                const float d = ab.x - b;
-                o[c] = __float2bfloat16_rn(-(d * d));
-            }
+    const int xx = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y, b = blockIdx.z;
+    if (xx >= w) return;
+    const __nv_bfloat162* img = x + (size_t)b * h * w;
+    const float2 ab = __bfloat1622float2(img[(size_t)yy * w + xx]);
+    __nv_bfloat16* o = f + ((size_t)b * h * w + (size_t)yy * w + xx) * kFeat;
+    o[0] = __float2bfloat16_rn(ab.x);
+    o[1] = __float2bfloat16_rn(ab.y);
+    int c = 2;
+#pragma unroll
+    for (int v = -kCorr; v <= kCorr; v++) {
+        const int ys = yy + v;
+        const bool rin = ys >= 0 && ys < h;
+#pragma unroll
+        for (int u = -kCorr; u <= kCorr; u++, c++) {
+            const int xs = xx + u;
+            const float bb = (rin && xs >= 0 && xs < w) ? __high2float(img[(size_t)ys * w + xs]) : 0.f;
+            const float d = ab.x - bb;
+            o[c] = __float2bfloat16_rn(-(d * d));
+        }
     }
 }
 
 // col[m][k] for output pixel m = (b, i, j) and k = (ky * K + kx) * cin + ci: the input
 // value at (s i + ky - p, s j + kx - p, ci), 0 outside the image and for k >= K*K*cin.
-__global__ void k_im2col(const __nv_bfloat16* __restrict__ x, int n, int h, int w, int cin,
-                         int ksz, int stride, int ho, int wo, int kp, __nv_bfloat16* __restrict__ col)
+// One thread per (output pixel, tap) copies the tap's cin contiguous channels (16-byte
+// vectors when cin is a multiple of 8); the thread of the last tap also zeroes the K tail.
+// Block (16, 16): x = tap (<= 16 taps), y = one of 16 output pixels.
+__global__ void k_im2col(const __nv_bfloat16* __restrict__ x, int h, int w, int cin, int ksz,
+                         int stride, int ho, int wo, int kp, int Mtot,
+                         __nv_bfloat16* __restrict__ col)
 {
-    const long long total = (long long)n * ho * wo * kp;
-    const int pad = ksz / 2;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % kp);
-        const long long m = e / kp;
-        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-        if (k < ksz * ksz * cin) {
-            const int ci = k % cin, tap = k / cin, kx = tap % ksz, ky = tap / ksz;
-            const int j = (int)(m % wo), i = (int)((m / wo) % ho), b = (int)(m / ((long long)wo * ho));
-            const int yy = stride * i + ky - pad, xx = stride * j + kx - pad;
-            if (yy >= 0 && yy < h && xx >= 0 && xx < w)
-                v = x[(((long long)b * h + yy) * w + xx) * cin + ci];
-        }
-        col[e] = v;
+    const int taps = ksz * ksz, pad = ksz / 2;
+    const int m = blockIdx.x * blockDim.y + threadIdx.y;
+    const int tap = threadIdx.x;
+    if (m >= Mtot || tap >= taps) return;
+    const int j = m % wo, t = m / wo, i = t % ho, b = t / ho;
+    const int ky = tap / ksz, kx = tap - ky * ksz;
+    const int yy = stride * i + ky - pad, xx = stride * j + kx - pad;
+    __nv_bfloat16* dst = col + (size_t)m * kp + tap * cin;
+    const bool in = yy >= 0 && yy < h && xx >= 0 && xx < w;
+    const __nv_bfloat16* src = x + (((size_t)b * h + (in ? yy : 0)) * w + (in ? xx : 0)) * cin;
+    if ((cin & 7) == 0 && (kp & 7) == 0) {
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        for (int c = 0; c < cin; c += 8)
+            *reinterpret_cast<uint4*>(dst + c) = in ? *reinterpret_cast<const uint4*>(src + c) : z;
+    } else {
+        const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+        for (int c = 0; c < cin; c++) dst[c] = in ? src[c] : z;
     }
+    if (tap == taps - 1)
+        for (int k = taps * cin; k < kp; k++) col[(size_t)m * kp + k] = __float2bfloat16_rn(0.f);
 }
 
 // out[c][r] = in[r][c] for an R x C bf16 matrix (row strides ld_in, ld_out); 32 x 32 tiles.
@@ -368,8 +376,8 @@ bool cnn_forward(const float* theta, const __nv_bfloat16* x, int n, int h, int w
     uint8_t* base = static_cast<uint8_t*>(ws);
     __nv_bfloat16* feat = reinterpret_cast<__nv_bfloat16*>(base + lay.feat);
     note_launch();
-    k_features<<<grid_for((long long)n * h * w), 256, 0, s>>>(
-        reinterpret_cast<const __nv_bfloat162*>(x), n, h, w, feat);
+    k_features<<<dim3((w + 127) / 128, h, n), 128, 0, s>>>(
+        reinterpret_cast<const __nv_bfloat162*>(x), h, w, feat);
     const __nv_bfloat16* in = feat;
     for (int i = 0; i < kNL; i++) {
         const LayerSpec& L = kNet[i];
@@ -385,9 +393,9 @@ bool cnn_forward(const float* theta, const __nv_bfloat16* x, int n, int h, int w
         if (L.k != 1) {
             __nv_bfloat16* col = reinterpret_cast<__nv_bfloat16*>(base + lay.col[i]);
             note_launch();
-            k_im2col<<<grid_for(lay.M[i] * kp), 256, 0, s>>>(in, n, lay.H[i], lay.Wd[i], L.cin, L.k,
-                                                             L.stride, lay.H[i + 1], lay.Wd[i + 1],
-                                                             kp, col);
+            k_im2col<<<(unsigned)((lay.M[i] + 15) / 16), dim3(16, 16), 0, s>>>(
+                in, lay.H[i], lay.Wd[i], L.cin, L.k, L.stride, lay.H[i + 1], lay.Wd[i + 1], kp,
+                (int)lay.M[i], col);
             A = col;
             lda = kp;
         }
