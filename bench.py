@@ -7,6 +7,7 @@ over a batch of 2592x1944 YUV420 two-frame stacks resident in HBM, replayed as
 one CUDA graph. Prints one JSON line (see the keys below).
 
   python bench.py --gpus N --steps K --warmup W [--impl reference]
+  python bench.py --workload mixed64    # 64 stacks of 1-12 MP, 2-3 frames, tuned (T, R)
 
 Under torchrun each rank (one GPU) registers its own batch of stacks: stacks
 are independent, so the ranks are replicas with no data-path collective; the
@@ -29,6 +30,9 @@ sys.path.insert(0, ROOT)
 METRIC = "registered+merged Mpix/s per B300 (5 MP pairs), learned vs plain at ≤0.5 px EPE"
 WORKLOAD = "5mp_yuv420_pair"
 W, H = 2592, 1944
+MIXED = "mixed64"                       # command-line name of the mixed batch
+MIXED_NAME = "mixed64_1to12mp_yuv420"
+MIXED_METRIC = "registered+merged output Mpix/s per B300 (64 stacks of 1-12 MP, 2-3 frames)"
 
 
 def parse():
@@ -44,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short run for a profiler")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED],
+                    help="the 5 MP pair batch (default) or the mixed 1-12 MP batch")
+    ap.add_argument("--stacks", type=int, default=64, help="stacks of the mixed batch")
     return ap.parse_args()
 
 
@@ -424,6 +431,169 @@ def measure_cpu_baseline(synth, stack, runs=3):
             "sample": f"{runs} runs of the oracle's whole path (a1-a11) on one 2592x1944 YUV420 pair"}
 
 
+# ------------------------------------------------------------ mixed batch (a-B)
+def mixed_inputs(n):
+    """The mixed workload's stacks (generated in a spawn pool, before CUDA starts)."""
+    from paper_1504_01441_b300 import synth
+    return synth.make_stacks_parallel([(i, 3, False) for i in range(n)])
+
+
+def run_mixed(args):
+    """Stacks of 1-12 MP with 2-3 frames, each with its size bucket's tuned (T, R), as one
+    multi-shape batched call on `lanes` lanes, replayed as one CUDA graph."""
+    ws, rank, local = dist_env()
+    t_gen = time.perf_counter()
+    stacks = mixed_inputs(args.stacks)
+    t_gen = time.perf_counter() - t_gen
+    import torch
+    import torch.distributed as dist
+    from paper_1504_01441_b300 import autotune, hdrreg, synth
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    if os.path.exists(autotune.TABLE_FILE):
+        table, picks_src = autotune.load_table(), "tune_table.json"
+    else:
+        table = {"buckets_mp": list(autotune.BUCKETS_MP), "picks": [autotune.DEFAULT] * 4}
+        picks_src = "default (no tuning table)"
+    params = [autotune.params_for(s.width, s.height, table) for s in stacks]
+
+    def up(a):
+        return torch.from_numpy(a).to(dev)
+    frames = [((up(s.ref.y), up(s.ref.u), up(s.ref.v)),
+               [(up(f.y), up(f.u), up(f.v)) for f in s.srcs], list(s.ratios)) for s in stacks]
+    shapes = [(s.width, s.height, len(s.srcs), p, True) for s, p in zip(stacks, params)]
+    runner = hdrreg.RegisterMergeMulti(shapes, lanes=args.lanes, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    runner(frames, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    n0 = hdrreg.launch_count()
+    with torch.cuda.graph(graph, stream=stream):
+        runner(frames, stream=stream)
+    launches_per_step = hdrreg.launch_count() - n0
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 0)):
+            graph.replay()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    K = args.steps
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk, torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(K):
+            graph.replay()
+        end.record(stream)
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    if ws > 1:
+        ms = max_over_ranks(torch, dist, ms, dev)
+        dist.barrier()
+    ms_step = ms / K
+    out_mpix = sum(s.width * s.height for s in stacks) / 1e6
+    reg_mpix = sum(s.width * s.height * len(s.srcs) for s in stacks) / 1e6
+    value = job_value(ws, out_mpix, ms_step)
+    in_bytes = sum(s.width * s.height * 3 // 2 * (1 + len(s.srcs)) for s in stacks)
+    e2e = cpu = roof = None
+    if rank == 0:
+        peak, src = peaks()
+        model = reg_mpix * 1e6 * 165      # the per-registration byte model, whole step
+        ach = model / (ms_step / 1e3) / 1e9
+        roof = {"kernel": "whole step (all kernels of all stacks): per-pixel byte model",
+                "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "peak_source": src,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                "algorithmic_bytes_per_launch": int(model),
+                "model": "165 B per registered luma pixel (a1-a11), see the design notes"}
+    if rank == 0 and not args.no_e2e:
+        e2e = measure_mixed_e2e(torch, runner, stacks, frames, dev, args)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.profile:
+        cpu = measure_mixed_cpu_baseline(synth, stacks, table)
+    if rank == 0:
+        buckets = {}
+        for s, p in zip(stacks, params):
+            b = autotune.bucket_of(s.width, s.height, table["buckets_mp"])
+            buckets.setdefault(b, [p.tile, p.radius, 0])[2] += 1
+        line = {
+            "metric": MIXED_METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/i32 match, f64 fit, f32 flow/warp/merge", "data": "synthetic",
+            "config": {"workload": MIXED_NAME, "stacks": len(stacks), "format": "YUV420",
+                       "output_mpix_per_step": round(out_mpix, 3),
+                       "registered_mpix_per_step": round(reg_mpix, 3),
+                       "input_bytes_per_step": in_bytes,
+                       "buckets_mp": table["buckets_mp"],
+                       "picks_T_R_count": {str(table["buckets_mp"][b]): v
+                                           for b, v in sorted(buckets.items())},
+                       "picks_source": picks_src, "graph": True, "lanes": args.lanes,
+                       "l2": f"inputs larger than L2: {in_bytes / 1e9:.2f} GB resident per step",
+                       "generation_s": round(t_gen, 1), "parallelism": f"replicas x{ws}"},
+            "gpu_launches": launches_per_step * K, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def measure_mixed_e2e(torch, runner, stacks, frames, dev, args):
+    """Pinned host planes -> device -> multi-shape batched call -> host, per step."""
+    hin = [[torch.from_numpy(a).pin_memory() for a in
+            [s.ref.y, s.ref.u, s.ref.v] + [x for f in s.srcs for x in (f.y, f.u, f.v)]]
+           for s in stacks]
+    din = [[t for t in (fr[0][0], fr[0][1], fr[0][2])] + [x for f in fr[1] for x in f]
+           for fr in frames]
+    hout = [[torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in o] for o in runner.outs]
+    s = torch.cuda.Stream(device=dev)
+
+    def step():
+        with torch.cuda.stream(s):
+            for h, d in zip(hin, din):
+                for a, b in zip(h, d):
+                    b.copy_(a, non_blocking=True)
+            outs = runner(frames, stream=s)
+            for h, o in zip(hout, outs):
+                for a, b in zip(h, o):
+                    a.copy_(b, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    K = 2 if args.profile else 3
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(K):
+        step()
+    b.record(s)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    h2d = sum(t.numel() * t.element_size() for h in hin for t in h)
+    d2h = sum(t.numel() * t.element_size() for h in hout for t in h)
+    out_mpix = sum(st.width * st.height for st in stacks) / 1e6
+    return {"value": round(out_mpix / (ms / 1e3), 2), "unit": "Mpix/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3)}
+
+
+def measure_mixed_cpu_baseline(synth, stacks, table, n=4):
+    """The oracle on the n smallest stacks of the batch, each with its bucket's (T, R)."""
+    import oracle
+    from paper_1504_01441_b300 import autotune
+    oracle.build()
+    sub = sorted(stacks, key=lambda s: s.width * s.height)[:n]
+    t0 = time.perf_counter()
+    for s in sub:
+        t, r = table["picks"][autotune.bucket_of(s.width, s.height, table["buckets_mp"])]
+        oracle.register_merge(s.ref, s.srcs, s.ratios, synth.method_params(t, r))
+    sec = time.perf_counter() - t0
+    mpix = sum(s.width * s.height for s in sub) / 1e6
+    return {"value": round(mpix / sec, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": f"the oracle's whole path on the {n} smallest stacks of the batch "
+                      f"({mpix:.2f} output Mpix, {sec:.1f} s)"}
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     ws, rank, local = dist_env()
@@ -432,6 +602,8 @@ def run_reference(args):
     from paper_1504_01441_b300 import synth
     import oracle
     oracle.build()
+    if args.workload == MIXED:
+        return run_reference_mixed(args, ws)
     stack = make_inputs(1)[0]
     cfg = synth.method_params(32, 6)
     for _ in range(max(args.warmup, 0)):
@@ -458,10 +630,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_mixed(args, ws):
+    """The oracle on the mixed workload: each step is one of the four smallest stacks of
+    the batch (cycled), with its bucket's (T, R); value = output Mpix / oracle time."""
+    import oracle
+    from paper_1504_01441_b300 import autotune, synth
+    order = sorted(range(args.stacks),
+                   key=lambda i: synth.mixed_spec(i).width * synth.mixed_spec(i).height)[:4]
+    stacks = [synth.make_mixed_stack(i) for i in order]
+    table = (autotune.load_table() if os.path.exists(autotune.TABLE_FILE) else
+             {"buckets_mp": list(autotune.BUCKETS_MP), "picks": [autotune.DEFAULT] * 4})
+
+    def run(s):
+        t, r = table["picks"][autotune.bucket_of(s.width, s.height, table["buckets_mp"])]
+        oracle.register_merge(s.ref, s.srcs, s.ratios, synth.method_params(t, r))
+
+    for i in range(max(args.warmup, 0)):
+        run(stacks[i % 4])
+    t0 = time.perf_counter()
+    mpix = 0.0
+    for i in range(args.steps):
+        run(stacks[i % 4])
+        mpix += stacks[i % 4].width * stacks[i % 4].height / 1e6
+    sec = time.perf_counter() - t0
+    value = mpix / sec
+    line = {
+        "impl": "reference", "metric": MIXED_METRIC, "value": round(value, 3), "unit": "Mpix/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sec * 1e3 / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64/int64 (CPU oracle)",
+        "data": "synthetic", "config": {"workload": MIXED_NAME, "stacks": args.stacks},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step one of the 4 smallest stacks of the mixed batch"},
+        "e2e": {"value": round(value, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == MIXED:
+        run_mixed(args)
     else:
         run_ours(args)
 

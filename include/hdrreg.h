@@ -443,6 +443,26 @@ hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count,
                                           int nsrc, int lanes, const hdrreg_params* p,
                                           void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------- a1-a11 fused, a batch of stacks of different shapes
+ * The paper has no counterpart. Like hdrreg_register_merge_batch, but every stack
+ * carries its own size, source count and parameters (e.g. the tile and radius an
+ * autotuner picked for its size). Stacks are placed on `lanes` lanes longest first
+ * (by w * h * nsrc), each on the lane with the least work so far; a lane runs its
+ * stacks one after another in a workspace sized for its largest. Everything forks
+ * from and joins back into `stream` (graph-capturable; the first call per device
+ * creates the lane streams). Results are identical to one hdrreg_register_merge per
+ * stack. Workspace: hdrreg_register_merge_multi_workspace_size(stacks, count, lanes).
+ */
+typedef struct hdrreg_stack_ex {
+    hdrreg_stack s;            /* frames, ratios, output planes, optional diagnostics */
+    int w, h, nsrc;            /* luma size and number of sources of this stack       */
+    const hdrreg_params* p;    /* parameters of this stack (host)                    */
+} hdrreg_stack_ex;
+size_t hdrreg_register_merge_multi_workspace_size(const hdrreg_stack_ex* stacks, int count,
+                                                  int lanes);
+hdrreg_status hdrreg_register_merge_multi(const hdrreg_stack_ex* stacks, int count, int lanes,
+                                          void* workspace, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

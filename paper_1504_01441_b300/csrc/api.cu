@@ -5,10 +5,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "hdrreg_internal.cuh"
 
@@ -733,6 +735,10 @@ struct LaneSet {
     bool ready = false;
 };
 
+// The lane streams and events are shared by every batched call of a device: one
+// batched enqueue at a time per process.
+static std::mutex lane_enqueue_mu;
+
 static hdrreg_status lane_set(LaneSet** out)
 {
     static std::mutex mu;
@@ -976,8 +982,7 @@ hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count,
     LaneSet* ls = nullptr;
     hdrreg_status st = lane_set(&ls);
     if (st) return st;
-    static std::mutex enqueue_mu;  // one batched enqueue at a time per process
-    std::lock_guard<std::mutex> lock(enqueue_mu);
+    std::lock_guard<std::mutex> lock(lane_enqueue_mu);
     cudaError_t e = cudaEventRecord(ls->fork, s);
     for (int j = 0; j < used && e == cudaSuccess; j++) e = cudaStreamWaitEvent(ls->stream[j], ls->fork, 0);
     if (e != cudaSuccess)
@@ -995,6 +1000,109 @@ hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count,
         cudaError_t e2 = cudaStreamWaitEvent(s, ls->join[j], 0);
         if (!st && (e1 != cudaSuccess || e2 != cudaSuccess))
             st = fail(HDRREG_E_CUDA, "register_merge_batch: join: %s",
+                      cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    }
+    return st;
+}
+
+// Lane plan of a multi-shape batch: longest first onto the least-loaded lane; per lane
+// the workspace of its largest stack (offsets into one buffer).
+struct MultiPlan {
+    std::vector<int> lane_of;
+    std::vector<size_t> lane_off;
+    size_t total = 0;
+    int used = 0;
+};
+
+static MultiPlan plan_multi(const hdrreg_stack_ex* st, int count, int lanes)
+{
+    MultiPlan mp;
+    mp.lane_of.assign(count, 0);
+    std::vector<int> order(count);
+    for (int i = 0; i < count; i++) order[i] = i;
+    auto work = [&](int i) { return (double)st[i].w * st[i].h * st[i].nsrc; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    const int L = count < lanes ? count : lanes;
+    std::vector<double> load(L, 0.0);
+    std::vector<size_t> need(L, 0);
+    for (int i : order) {
+        int best = 0;
+        for (int j = 1; j < L; j++)
+            if (load[j] < load[best]) best = j;
+        mp.lane_of[i] = best;
+        load[best] += work(i);
+        const size_t b = align_up(FusedLayout(st[i].w, st[i].h, st[i].nsrc, st[i].p).total, 256);
+        need[best] = need[best] > b ? need[best] : b;
+    }
+    mp.lane_off.assign(L, 0);
+    for (int j = 0; j < L; j++) {
+        mp.lane_off[j] = mp.total;
+        mp.total += need[j];
+    }
+    mp.used = L;
+    return mp;
+}
+
+size_t hdrreg_register_merge_multi_workspace_size(const hdrreg_stack_ex* stacks, int count,
+                                                  int lanes)
+{
+    if (!stacks || count < 1 || lanes < 1 || lanes > HDRREG_MAX_LANES) return 0;
+    for (int i = 0; i < count; i++)
+        if (!stacks[i].p || bad_dims(stacks[i].w, stacks[i].h) || stacks[i].nsrc < 1 ||
+            stacks[i].nsrc > kMaxSources)
+            return 0;
+    return plan_multi(stacks, count, lanes).total;
+}
+
+hdrreg_status hdrreg_register_merge_multi(const hdrreg_stack_ex* stacks, int count, int lanes,
+                                          void* workspace, size_t ws_bytes, void* stream)
+{
+    if (count < 0 || (count > 0 && !stacks))
+        return fail(HDRREG_E_INVALID_ARG, "register_merge_multi: bad stack array");
+    if (lanes < 1 || lanes > HDRREG_MAX_LANES)
+        return fail(HDRREG_E_INVALID_ARG, "register_merge_multi: lanes must be in [1, %d]",
+                    HDRREG_MAX_LANES);
+    for (int i = 0; i < count; i++) {
+        const hdrreg_stack_ex& k = stacks[i];
+        hdrreg_status st = rm_validate(k.s.ref, k.w, k.h, k.nsrc, k.s.srcs, k.s.ratio_num,
+                                       k.s.ratio_den, k.p, &k.s.out);
+        if (st) return fail(st, "register_merge_multi: stack %d: %s", i, hdrreg_last_error());
+    }
+    if (count == 0) return HDRREG_OK;
+    const MultiPlan mp = plan_multi(stacks, count, lanes);
+    if (!workspace || ws_bytes < mp.total)
+        return fail(HDRREG_E_WORKSPACE, "register_merge_multi: workspace of %zu bytes required",
+                    mp.total);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* base = static_cast<uint8_t*>(workspace);
+    auto run = [&](int i, cudaStream_t q) {
+        const hdrreg_stack_ex& k = stacks[i];
+        const FusedLayout lay(k.w, k.h, k.nsrc, k.p);
+        return rm_enqueue(k.s.ref, k.w, k.h, k.nsrc, k.s.srcs, k.s.ratio_num, k.s.ratio_den, k.p,
+                          lay, base + mp.lane_off[mp.lane_of[i]], &k.s.out, k.s.diag, q);
+    };
+    if (mp.used == 1) {
+        for (int i = 0; i < count; i++) {
+            hdrreg_status st = run(i, s);
+            if (st) return st;
+        }
+        return HDRREG_OK;
+    }
+    LaneSet* ls = nullptr;
+    hdrreg_status st = lane_set(&ls);
+    if (st) return st;
+    std::lock_guard<std::mutex> lock(lane_enqueue_mu);
+    cudaError_t e = cudaEventRecord(ls->fork, s);
+    for (int j = 0; j < mp.used && e == cudaSuccess; j++)
+        e = cudaStreamWaitEvent(ls->stream[j], ls->fork, 0);
+    if (e != cudaSuccess)
+        return fail(HDRREG_E_CUDA, "register_merge_multi: fork: %s", cudaGetErrorString(e));
+    for (int i = 0; i < count && !st; i++) st = run(i, ls->stream[mp.lane_of[i]]);
+    for (int j = 0; j < mp.used; j++) {
+        cudaError_t e1 = cudaEventRecord(ls->join[j], ls->stream[j]);
+        cudaError_t e2 = cudaStreamWaitEvent(s, ls->join[j], 0);
+        if (!st && (e1 != cudaSuccess || e2 != cudaSuccess))
+            st = fail(HDRREG_E_CUDA, "register_merge_multi: join: %s",
                       cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
     }
     return st;

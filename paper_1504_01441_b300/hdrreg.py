@@ -30,6 +30,7 @@ EXPORTS = [
     "hdrreg_flow_workspace_size", "hdrreg_flow_upsample", "hdrreg_warp", "hdrreg_merge",
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
+    "hdrreg_register_merge_multi_workspace_size", "hdrreg_register_merge_multi",
     "hdrreg_gemm_bf16", "hdrreg_cnn_workspace_size", "hdrreg_cnn_out_dims", "hdrreg_cnn_forward",
     "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_cnn_activation", "hdrreg_predictor_input",
     "hdrreg_tile_labels",
@@ -83,6 +84,11 @@ class Stack(C.Structure):
     _fields_ = [("ref", C.POINTER(Frame)), ("srcs", C.POINTER(Frame)),
                 ("ratio_num", C.POINTER(C.c_int)), ("ratio_den", C.POINTER(C.c_int)),
                 ("out", PlanesF32), ("diag", C.c_void_p)]
+
+
+class StackEx(C.Structure):
+    _fields_ = [("s", Stack), ("w", C.c_int), ("h", C.c_int), ("nsrc", C.c_int),
+                ("p", C.POINTER(Params))]
 
 
 class Diag(C.Structure):
@@ -145,6 +151,9 @@ def lib():
         L.hdrreg_register_merge_batch_workspace_size.argtypes = [i, i, i, i, C.POINTER(Params)]
         L.hdrreg_register_merge_batch.argtypes = [C.POINTER(Stack), i, i, i, i, i,
                                                   C.POINTER(Params), vp, sz, vp]
+        L.hdrreg_register_merge_multi_workspace_size.restype = sz
+        L.hdrreg_register_merge_multi_workspace_size.argtypes = [C.POINTER(StackEx), i, i]
+        L.hdrreg_register_merge_multi.argtypes = [C.POINTER(StackEx), i, i, vp, sz, vp]
         L.hdrreg_gemm_bf16.argtypes = [vp, i, vp, i, i, i, i, vp, i, vp, vp]
         L.hdrreg_cnn_workspace_size.restype = sz
         L.hdrreg_cnn_workspace_size.argtypes = [i, i, i]
@@ -596,6 +605,76 @@ class RegisterMergeBatch:
         raw = self.diag[slot].cpu().numpy().tobytes()
         n = C.sizeof(Diag)
         return [Diag.from_buffer_copy(raw[i * n:(i + 1) * n]) for i in range(self.nsrc)]
+
+
+class RegisterMergeMulti:
+    """Batched fused call for stacks of different sizes, source counts and parameters on
+    `lanes` concurrent lanes. `shapes` lists (w, h, nsrc, params, chroma) per stack slot;
+    the object owns the workspace and each slot's output planes and diagnostics."""
+
+    def __init__(self, shapes, lanes: int = 4, device="cuda"):
+        import torch
+        self.shapes = [(int(w), int(h), int(n), p, bool(c)) for w, h, n, p, c in shapes]
+        self.lanes = lanes
+        self._params = [C.pointer(p) for _, _, _, p, _ in self.shapes]
+        arr = self._array(len(self.shapes))
+        n = lib().hdrreg_register_merge_multi_workspace_size(arr, len(self.shapes), lanes)
+        if n == 0:
+            raise HdrregError(1, "bad shape, lanes or parameters for register_merge_multi")
+        self.ws = torch.empty((n,), dtype=torch.uint8, device=device)
+
+        def plane(hh, ww):
+            return torch.empty((hh, ww), dtype=torch.float32, device=device)
+        self.outs = [(plane(h, w), plane(h // 2, w // 2) if c else None,
+                      plane(h // 2, w // 2) if c else None) for w, h, _, _, c in self.shapes]
+        self.diag = [torch.zeros((n, C.sizeof(Diag)), dtype=torch.uint8, device=device)
+                     for _, _, n, _, _ in self.shapes]
+        self._keep = None
+
+    def _array(self, k):
+        arr = (StackEx * max(k, 1))()
+        for i in range(k):
+            w, h, n, _, _ = self.shapes[i]
+            arr[i].w, arr[i].h, arr[i].nsrc = w, h, n
+            arr[i].p = self._params[i]
+        return arr
+
+    def __call__(self, stacks, stream=None):
+        """stacks: one (ref, srcs, ratios) per slot, shaped as that slot was declared;
+        -> the list of output planes."""
+        k = len(stacks)
+        if k != len(self.shapes):
+            raise ValueError("one stack per declared slot is required")
+        arr = self._array(k)
+        keep = []
+        for i, (ref, srcs, ratios) in enumerate(stacks):
+            w, h, n, _, chroma = self.shapes[i]
+            if len(srcs) != n or tuple(ref[0].shape) != (h, w):
+                raise ValueError(f"stack {i} differs from its declared shape")
+            fr = Frame(_ptr(ref[0]), _ptr(ref[1]) if chroma else None,
+                       _ptr(ref[2]) if chroma else None)
+            fs = (Frame * n)(*[Frame(_ptr(s[0]), _ptr(s[1]) if chroma else None,
+                                     _ptr(s[2]) if chroma else None) for s in srcs])
+            num = (C.c_int * n)(*[r[0] for r in ratios])
+            den = (C.c_int * n)(*[r[1] for r in ratios])
+            o = self.outs[i]
+            arr[i].s.ref = C.pointer(fr)
+            arr[i].s.srcs = C.cast(fs, C.POINTER(Frame))
+            arr[i].s.ratio_num = C.cast(num, C.POINTER(C.c_int))
+            arr[i].s.ratio_den = C.cast(den, C.POINTER(C.c_int))
+            arr[i].s.out = PlanesF32(_ptr(o[0]), _ptr(o[1]), _ptr(o[2]))
+            arr[i].s.diag = _ptr(self.diag[i])
+            keep.append((fr, fs, num, den))
+        _check(lib().hdrreg_register_merge_multi(arr, k, self.lanes, _ptr(self.ws),
+                                                 self.ws.numel(), _stream(stream)))
+        self._keep = keep
+        return self.outs
+
+    def diagnostics(self, slot: int) -> List[Diag]:
+        raw = self.diag[slot].cpu().numpy().tobytes()
+        n = C.sizeof(Diag)
+        return [Diag.from_buffer_copy(raw[i * n:(i + 1) * n])
+                for i in range(self.shapes[slot][2])]
 
 
 def register_merge(ref, srcs, ratios, p: Params, stream=None):

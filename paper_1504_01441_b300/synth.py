@@ -355,6 +355,41 @@ def method_params(tile: int = 32, radius: int = 6, **over) -> dict:
     return p
 
 
+def mixed_spec(stack_index: int, config_index: int = 3, with_gt: bool = False) -> StackSpec:
+    """One stack of the mixed batch workload: luma area U(1, 12) MP, aspect 4:3 or 16:9
+    (even sides), 2 or 3 frames, YUV420, noise 1.5 DN, +-4 px local field, 3 movers. The
+    reference is the darkest frame; every other frame draws its ratio from {2, 4, 8}.
+    The draws come from their own PCG64 stream seeded by the stack's seed, so a stack's
+    shape does not depend on which other stacks are made."""
+    rng = np.random.Generator(np.random.PCG64(stack_seed(config_index, stack_index) ^ 0x5EED))
+    area = rng.uniform(1.0, 12.0) * 1e6
+    aspect = (4.0 / 3.0) if rng.uniform() < 0.5 else (16.0 / 9.0)
+    nsrc = 1 if rng.uniform() < 0.5 else 2
+    ratios = tuple((int(rng.choice((2, 4, 8))), 1) for _ in range(nsrc))
+    w = 2 * int(round(math.sqrt(area * aspect) / 2.0))
+    h = 2 * int(round(w / aspect / 2.0))
+    return StackSpec(w, h, ratios=ratios, noise_sigma=1.5, field_amp=4.0, movers=3,
+                     chroma=True, with_gt=with_gt)
+
+
+def make_mixed_stack(stack_index: int, config_index: int = 3, with_gt: bool = False) -> Stack:
+    return make_stack(mixed_spec(stack_index, config_index, with_gt),
+                      stack_seed(config_index, stack_index))
+
+
+def make_stacks_parallel(jobs, processes=None):
+    """make_mixed_stack over (stack_index, config_index, with_gt) jobs in a spawn-started
+    process pool (safe after CUDA is initialized); returns the stacks in job order."""
+    import multiprocessing as mp
+    import os
+    jobs = list(jobs)
+    n = processes or min(len(jobs), os.cpu_count() or 1)
+    if n <= 1:
+        return [make_mixed_stack(*j) for j in jobs]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.starmap(make_mixed_stack, jobs)
+
+
 WORKLOADS = {
     "vga_luma_pair": (VGA_LUMA, dict(tile=16, radius=4)),
     "5mp_yuv420_pair": (FIVE_MP, dict(tile=32, radius=6)),
