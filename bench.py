@@ -506,7 +506,7 @@ def run_mixed(args):
         roof = {"kernel": "whole step (all kernels of all stacks): per-pixel byte model",
                 "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "peak_source": src,
                 "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
-                "algorithmic_bytes_per_launch": int(model),
+                "algorithmic_bytes_per_step": int(model),
                 "model": "165 B per registered luma pixel (a1-a11), see the design notes"}
     if rank == 0 and not args.no_e2e:
         e2e = measure_mixed_e2e(torch, runner, stacks, frames, dev, args)

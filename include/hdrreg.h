@@ -364,6 +364,19 @@ hdrreg_status hdrreg_cnn_backward(const float* theta, const uint16_t* x, int n, 
                                   int32_t* status, void* stream);
 hdrreg_status hdrreg_cnn_adam(float* theta, float* m, float* v, const float* grad, int step,
                               float lr, void* stream);
+/* Inference form of hdrreg_cnn_forward: the same network on the same inputs, computed
+ * without the stored intermediates a backward pass needs. The 3x3 convolutions are
+ * implicit GEMMs on the tensor cores (inputs gathered per tap into shared memory, no
+ * im2col matrix in memory) with the parameters rounded to bfloat16 as they are staged;
+ * the 1x1 head sums in FP32. Results equal hdrreg_cnn_forward's up to the order of the
+ * FP32 sums. x must be 4-byte aligned and the workspace 256-byte aligned; the library
+ * allocates nothing. Workspace: hdrreg_cnn_infer_workspace_size(n, h, w) (0 for a bad
+ * batch). The fused call runs this form for its learned level-0 search.
+ */
+size_t hdrreg_cnn_infer_workspace_size(int n, int h, int w);
+hdrreg_status hdrreg_cnn_infer(const float* theta, const uint16_t* x, int n, int h, int w,
+                               float* out, void* workspace, size_t ws_bytes, int32_t* status,
+                               void* stream);
 /* Where a workspace of batch (n, h, w) keeps what the last hdrreg_cnn_forward stored:
  * layer -1 = the feature stage (bfloat16 [n*h*w][27]), layers 0..7 = the post-ReLU
  * outputs (bfloat16 [rows][cols]). Writes the device address (inside the workspace,

@@ -6,8 +6,9 @@ have fewer tiles to amortize a wide search, large ones more. For every size buck
 this module measures each candidate (T, R) on seeded generator stacks of that
 bucket:
 
-  * time: device time of the fused register+merge call (CUDA-graph replay, CUDA
-    events, L2 flushed before every replay);
+  * time: device time per stack of the batched fused call with one copy of the stack
+    on each of four lanes, as stacks of a bucket run in a batch (CUDA-graph replay,
+    CUDA events, L2 flushed before every replay);
   * error: the end-point error of the registration H^0 + F (Eq. 3 homography plus
     the dense residual flow of Sec. 2.4) against the generator's ground-truth map,
     averaged over the reference pixels whose true source position lies inside the
@@ -95,8 +96,12 @@ def registration_epe(stack, p, device="cuda") -> float:
         for lv in range(L - 1, -1, -1):
             lh, lw = pr[lv].shape
             cxy, mxy, _, valid = hdrreg.local_search(pr[lv], ps[lv], Hc, p)
-            mask, Hc, _ = hdrreg.weed_fit(cxy, mxy, valid, lw, lh, p, p.weed_seed + lv, Hc,
-                                          counter=counter)
+            if hdrreg.lib().hdrreg_weed_fit_supported(valid.numel()):
+                mask, Hc, _ = hdrreg.weed_fit(cxy, mxy, valid, lw, lh, p, p.weed_seed + lv, Hc,
+                                              counter=counter)
+            else:   # beyond the one-launch plan: the workspace weeding, then the fit
+                mask = hdrreg.weed(cxy, mxy, valid, lw, lh, p, p.weed_seed + lv)
+                Hc, _ = hdrreg.fit_homography(cxy, mxy, mask, lw, lh, Hc)
         fu, fv = hdrreg.flow_upsample(rn, cxy, mxy, mask, Hc, p)
         H = Hc.view(3, 3)
         den = H[2, 0] * xn + H[2, 1] * yn + H[2, 2]
@@ -119,21 +124,24 @@ def _device_stack(stack, device):
     return ref, srcs, list(stack.ratios)
 
 
-def fused_time_us(stack, p, reps: int = 5, device="cuda", flush=None) -> float:
-    """Median device time (us) of one fused register+merge call on `stack`, replayed
-    from a CUDA graph with L2 flushed (a write larger than L2) before each replay."""
+def fused_time_us(stack, p, reps: int = 5, device="cuda", flush=None, lanes: int = 4) -> float:
+    """Device time (us) per stack of the batched fused call on `lanes` copies of `stack`
+    (one per lane, as stacks of one bucket run in a batch), replayed from a CUDA graph
+    with L2 flushed (a write larger than L2) before each replay; the median replay over
+    `lanes`."""
     import torch
     from . import hdrreg
-    ref, srcs, ratios = _device_stack(stack, device)
-    h, w = ref[0].shape
-    rm = hdrreg.RegisterMerge(w, h, len(srcs), p, ref[1] is not None, device=device)
+    copies = [_device_stack(stack, device) for _ in range(lanes)]
+    h, w = copies[0][0][0].shape
+    rm = hdrreg.RegisterMergeBatch(w, h, len(stack.srcs), p, copies[0][0][1] is not None,
+                                   slots=lanes, lanes=lanes, device=device)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        rm(ref, srcs, ratios, stream=s)          # first call raises kernel smem limits
+        rm(copies, stream=s)                     # first call raises kernel smem limits
     s.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        rm(ref, srcs, ratios, stream=s)
+        rm(copies, stream=s)
     if flush is None:
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     times = []
@@ -146,7 +154,7 @@ def fused_time_us(stack, p, reps: int = 5, device="cuda", flush=None) -> float:
             b.record(s)
             b.synchronize()
             if i:
-                times.append(a.elapsed_time(b) * 1e3)
+                times.append(a.elapsed_time(b) * 1e3 / lanes)
     times.sort()
     return times[len(times) // 2]
 
@@ -199,7 +207,7 @@ def tune(stacks, cands: Optional[Sequence[Tuple[int, int]]] = None, reps: int = 
     return {"buckets_mp": list(buckets), "picks": [list(x) for x in picks],
             "default": list(DEFAULT), "measurements": meas,
             "stacks": [[st.width, st.height, len(st.srcs), st.seed] for st in stacks],
-            "device": torch.cuda.get_device_name(device), "reps": reps}
+            "device": torch.cuda.get_device_name(device), "reps": reps, "lanes": 4}
 
 
 def main():

@@ -154,7 +154,7 @@ struct FusedLayout {
         if (learned) {
             xq = lay.add((size_t)wq * hq * 4);
             pred = lay.add((size_t)pho * pwo * 8);
-            cnn = lay.add(cnn_ws_bytes(1, hq, wq, false));
+            cnn = lay.add(cnn_infer_ws_bytes(1, hq, wq));
             fellback = lay.add(nn);
         }
         for (int k = 0; k < ns; k++) {
@@ -665,9 +665,9 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
                 // prediction per tile, SSD check with fallback to the full search
                 launch_predictor_input(at(lay.ref_lv[2]), at(lay.src_lv[2]), lay.wq, lay.hq,
                                        Hs + 9, at(lay.xq), s);
-                if (!cnn_forward(p->predictor, reinterpret_cast<const __nv_bfloat16*>(at(lay.xq)), 1,
-                                 lay.hq, lay.wq, reinterpret_cast<float*>(at(lay.pred)),
-                                 at(lay.cnn), reinterpret_cast<int*>(done + kMaxLevels), s))
+                if (!cnn_infer(p->predictor, reinterpret_cast<const __nv_bfloat16*>(at(lay.xq)), 1,
+                               lay.hq, lay.wq, reinterpret_cast<float*>(at(lay.pred)),
+                               at(lay.cnn), reinterpret_cast<int*>(done + kMaxLevels), s))
                     return fail(HDRREG_E_UNSUPPORTED, "register_merge: tensor-core product not available");
                 const PredSearch ps{reinterpret_cast<const float*>(at(lay.pred)), lay.pwo,
                                     p->predictor_refine, p->fallback_cost, at(lay.fellback)};
@@ -896,6 +896,29 @@ hdrreg_status hdrreg_cnn_forward(const float* theta, const uint16_t* x, int n, i
                      status, static_cast<cudaStream_t>(stream)))
         return fail(HDRREG_E_UNSUPPORTED, "cnn_forward: tensor-core product not available");
     return launch_status("cnn_forward");
+}
+
+size_t hdrreg_cnn_infer_workspace_size(int n, int h, int w)
+{
+    return cnn_bad_dims(n, h, w) ? 0 : cnn_infer_ws_bytes(n, h, w);
+}
+
+hdrreg_status hdrreg_cnn_infer(const float* theta, const uint16_t* x, int n, int h, int w,
+                               float* out, void* workspace, size_t ws_bytes, int32_t* status,
+                               void* stream)
+{
+    if (!theta || !x || !out || !status) return fail(HDRREG_E_INVALID_ARG, "cnn_infer: NULL pointer");
+    if (cnn_bad_dims(n, h, w))
+        return fail(HDRREG_E_INVALID_ARG, "cnn_infer: bad batch %d x %d x %d", n, h, w);
+    if (!workspace || ws_bytes < cnn_infer_ws_bytes(n, h, w))
+        return fail(HDRREG_E_WORKSPACE, "cnn_infer: workspace of %zu bytes required",
+                    cnn_infer_ws_bytes(n, h, w));
+    if (((uintptr_t)x & 3u) || ((uintptr_t)workspace & 255u))
+        return fail(HDRREG_E_INVALID_ARG, "cnn_infer: x must be 4-byte, workspace 256-byte aligned");
+    if (!cnn_infer(theta, reinterpret_cast<const __nv_bfloat16*>(x), n, h, w, out, workspace,
+                   status, static_cast<cudaStream_t>(stream)))
+        return fail(HDRREG_E_UNSUPPORTED, "cnn_infer: no convolution kernel for a layer");
+    return launch_status("cnn_infer");
 }
 
 hdrreg_status hdrreg_cnn_backward(const float* theta, const uint16_t* x, int n, int h, int w,

@@ -68,6 +68,78 @@ __global__ void k_features(const __nv_bfloat162* __restrict__ x, int h, int w,
     }
 }
 
+// The same features with the channels padded to 32 (27..31 zero): one 64-byte pixel,
+// written as four 16-byte vectors (the layout the implicit-GEMM convolution gathers).
+constexpr int kFeatPad = 32;
+__global__ void k_features32(const __nv_bfloat162* __restrict__ x, int h, int w,
+                             __nv_bfloat16* __restrict__ f)
+{
+    const int xx = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y, b = blockIdx.z;
+    if (xx >= w) return;
+    const __nv_bfloat162* img = x + (size_t)b * h * w;
+    const float2 ab = __bfloat1622float2(img[(size_t)yy * w + xx]);
+    float v[kFeatPad];
+    v[0] = ab.x;
+    v[1] = ab.y;
+    int c = 2;
+#pragma unroll
+    for (int dv = -kCorr; dv <= kCorr; dv++) {
+        const int ys = yy + dv;
+        const bool rin = ys >= 0 && ys < h;
+#pragma unroll
+        for (int u = -kCorr; u <= kCorr; u++, c++) {
+            const int xs = xx + u;
+            const float bb = (rin && xs >= 0 && xs < w) ? __high2float(img[(size_t)ys * w + xs]) : 0.f;
+            const float d = ab.x - bb;
+            v[c] = -(d * d);
+        }
+    }
+#pragma unroll
+    for (int k = kFeat; k < kFeatPad; k++) v[k] = 0.f;
+    uint4* o = reinterpret_cast<uint4*>(f + ((size_t)b * h * w + (size_t)yy * w + xx) * kFeatPad);
+#pragma unroll
+    for (int q = 0; q < kFeatPad / 8; q++) {
+        uint32_t p[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const __nv_bfloat162 t = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
+            p[e] = *reinterpret_cast<const uint32_t*>(&t);
+        }
+        o[q] = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+}
+
+// The 1x1 head: out[m][o] = b[o] + sum_c bf16(W[o][c]) act[m][c], o = 0, 1 (FP32 sums).
+__global__ void k_head(const __nv_bfloat16* __restrict__ act, long long M, const float* __restrict__ W,
+                       const float* __restrict__ bias, float* __restrict__ out)
+{
+    constexpr int C = 64;
+    __shared__ float ws[2 * C];
+    if (threadIdx.x < 2 * C) ws[threadIdx.x] = __bfloat162float(__float2bfloat16_rn(W[threadIdx.x]));
+    __syncthreads();
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M;
+         m += (long long)gridDim.x * blockDim.x) {
+        const uint4* a = reinterpret_cast<const uint4*>(act + m * C);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int q = 0; q < C / 8; q++) {
+            const uint4 u = a[q];
+            const uint32_t wds[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wds[e]));
+                const int c = 8 * q + 2 * e;
+                s0 = fmaf(f.x, ws[c], s0);
+                s0 = fmaf(f.y, ws[c + 1], s0);
+                s1 = fmaf(f.x, ws[C + c], s1);
+                s1 = fmaf(f.y, ws[C + c + 1], s1);
+            }
+        }
+        out[2 * m] = s0 + bias[0];
+        out[2 * m + 1] = s1 + bias[1];
+    }
+}
+
 // col[m][k] for output pixel m = (b, i, j) and k = (ky * K + kx) * cin + ci: the input
 // value at (s i + ky - p, s j + kx - p, ci), 0 outside the image and for k >= K*K*cin.
 // One thread per (output pixel, tap) copies the tap's cin contiguous channels (16-byte
@@ -409,6 +481,67 @@ bool cnn_forward(const float* theta, const __nv_bfloat16* x, int n, int h, int w
             e = GemmEpi{kEpiBiasF32, out, nullptr, bias, L.cout, 0};
         }
         if (!launch_gemm_bf16(A, lda, Wb, kp, (int)lay.M[i], L.cout, kp, 1, e, err, s)) return false;
+    }
+    return true;
+}
+
+// Inference workspace: the padded features and one activation buffer per ReLU layer.
+struct InferLayout {
+    size_t feat, act[kNL], total;
+    int H[kNL + 1], Wd[kNL + 1];
+    long long M[kNL];
+    InferLayout(int n, int h, int w)
+    {
+        H[0] = h;
+        Wd[0] = w;
+        size_t o = 0;
+        auto add = [&](size_t bytes) {
+            const size_t r = o;
+            o += align_up(bytes > 0 ? bytes : 1, 256);
+            return r;
+        };
+        feat = add((size_t)n * h * w * kFeatPad * 2);
+        for (int i = 0; i < kNL; i++) {
+            H[i + 1] = osz(H[i], kNet[i]);
+            Wd[i + 1] = osz(Wd[i], kNet[i]);
+            M[i] = (long long)n * H[i + 1] * Wd[i + 1];
+            act[i] = kNet[i].relu ? add((size_t)M[i] * kNet[i].cout * 2) : 0;
+        }
+        total = o;
+    }
+};
+
+size_t cnn_infer_ws_bytes(int n, int h, int w) { return InferLayout(n, h, w).total; }
+
+// Forward pass for inference: features (32 padded channels), eight implicit-GEMM 3x3
+// convolutions, the 1x1 head. No im2col matrix, no packed weights (the convolution
+// kernels round the FP32 parameters to bfloat16 as they stage them).
+bool cnn_infer(const float* theta, const __nv_bfloat16* x, int n, int h, int w, float* out,
+               void* ws, int* err, cudaStream_t s)
+{
+    const InferLayout lay(n, h, w);
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    __nv_bfloat16* feat = reinterpret_cast<__nv_bfloat16*>(base + lay.feat);
+    note_launch();
+    k_features32<<<dim3((w + 127) / 128, h, n), 128, 0, s>>>(
+        reinterpret_cast<const __nv_bfloat162*>(x), h, w, feat);
+    const __nv_bfloat16* in = feat;
+    int cin_pad = kFeatPad;
+    for (int i = 0; i < kNL; i++) {
+        const LayerSpec& L = kNet[i];
+        const size_t po = param_offset(i);
+        const float* bias = theta + po + (size_t)kdim(L) * L.cout;
+        if (L.k == 3) {
+            __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(base + lay.act[i]);
+            const ConvArgs a{in, lay.H[i], lay.Wd[i], lay.H[i + 1], lay.Wd[i + 1], (int)lay.M[i],
+                             theta + po, L.cin, cin_pad, L.stride, L.cout, bias, act, err};
+            if (!launch_conv3x3(a, s)) return false;
+            in = act;
+            cin_pad = L.cout;
+        } else {
+            note_launch();
+            k_head<<<grid_for(lay.M[i]), 256, 0, s>>>(in, lay.M[i], theta + po, bias, out);
+        }
     }
     return true;
 }

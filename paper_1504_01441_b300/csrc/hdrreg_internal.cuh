@@ -500,7 +500,24 @@ bool launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int
                       int splits, const GemmEpi& epi, int* err, cudaStream_t s);
 
 // ------------------------------------------- learned predictor (row a-L)
+// Implicit-GEMM 3x3 convolution (conv_tc.cu): x bf16 [n][h][w][cin] (cin = padded channel
+// count, a multiple of 8), W FP32 [cout][3][3][cin_src] (cin_src <= cin; channels past
+// cin_src weigh 0), bias FP32 [cout], out bf16 [M][cout] = relu(conv + bias), M = n*ho*wo.
+struct ConvArgs {
+    const __nv_bfloat16* x;
+    int h, w, ho, wo, M;
+    const float* W;
+    int cin_src, cin, stride, cout;
+    const float* bias;
+    __nv_bfloat16* out;
+    int* err;
+};
+bool launch_conv3x3(const ConvArgs& a, cudaStream_t s);  // false: no kernel for this shape
+
 size_t cnn_params();
+size_t cnn_infer_ws_bytes(int n, int h, int w);
+bool cnn_infer(const float* theta, const __nv_bfloat16* x, int n, int h, int w, float* out,
+               void* ws, int* err, cudaStream_t s);
 size_t cnn_ws_bytes(int n, int h, int w, bool train = true);  // train = false: forward only
 const void* cnn_activation(const void* ws, int n, int h, int w, int layer, int* rows, int* cols);
 void cnn_out_dims(int h, int w, int* ho, int* wo);

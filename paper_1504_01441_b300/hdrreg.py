@@ -32,7 +32,8 @@ EXPORTS = [
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
     "hdrreg_register_merge_multi_workspace_size", "hdrreg_register_merge_multi",
     "hdrreg_gemm_bf16", "hdrreg_cnn_workspace_size", "hdrreg_cnn_out_dims", "hdrreg_cnn_forward",
-    "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_cnn_activation", "hdrreg_predictor_input",
+    "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_cnn_activation",
+    "hdrreg_cnn_infer_workspace_size", "hdrreg_cnn_infer", "hdrreg_predictor_input",
     "hdrreg_tile_labels",
     "hdrreg_predictor_crops", "hdrreg_local_search_predicted",
 ]
@@ -160,6 +161,9 @@ def lib():
         L.hdrreg_cnn_out_dims.argtypes = [i, i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.hdrreg_cnn_forward.argtypes = [vp, vp, i, i, i, vp, vp, sz, vp, vp]
         L.hdrreg_cnn_backward.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp, vp, sz, vp, vp]
+        L.hdrreg_cnn_infer_workspace_size.restype = sz
+        L.hdrreg_cnn_infer_workspace_size.argtypes = [i, i, i]
+        L.hdrreg_cnn_infer.argtypes = [vp, vp, i, i, i, vp, vp, sz, vp, vp]
         L.hdrreg_cnn_adam.argtypes = [vp, vp, vp, vp, i, C.c_float, vp]
         L.hdrreg_cnn_activation.argtypes = [vp, i, i, i, i, C.POINTER(C.c_void_p),
                                              C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -461,6 +465,7 @@ class Predictor:
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.t = 0
+        self._infer_ws = None
 
     def forward(self, x, stream=None):
         """x: bfloat16 [n, h, w, 2] CUDA tensor -> out FP32 [n, ho, wo, 2]."""
@@ -468,6 +473,19 @@ class Predictor:
                                         _ptr(self.out), _ptr(self.ws), self.ws.numel(),
                                         _ptr(self.status), _stream(stream)))
         return self.out
+
+    def infer(self, x, stream=None):
+        """Inference form (implicit-GEMM convolutions, no stored intermediates): x bfloat16
+        [n, h, w, 2] -> a new FP32 [n, ho, wo, 2]."""
+        import torch
+        if self._infer_ws is None:
+            nb = lib().hdrreg_cnn_infer_workspace_size(self.n, self.h, self.w)
+            self._infer_ws = torch.empty((nb,), dtype=torch.uint8, device=self.theta.device)
+        out = torch.zeros_like(self.out)
+        _check(lib().hdrreg_cnn_infer(_ptr(self.theta), _ptr(x), self.n, self.h, self.w,
+                                      _ptr(out), _ptr(self._infer_ws), self._infer_ws.numel(),
+                                      _ptr(self.status), _stream(stream)))
+        return out
 
     def backward(self, x, label, valid, stream=None):
         _check(lib().hdrreg_cnn_backward(_ptr(self.theta), _ptr(x), self.n, self.h, self.w,

@@ -121,3 +121,39 @@ def test_training_reduces_the_loss(hd):
         P.adam(lr=3e-3)
     assert int(P.status.item()) == 0
     assert losses[-1] < 0.3 * losses[0], losses[::10]
+
+
+@pytest.mark.parametrize("n,h,w", [(2, 24, 40), (1, 61, 33), (1, 130, 70), (3, 47, 29)])
+def test_inference_form_matches_oracle_and_training_forward(hd, n, h, w):
+    # implicit-GEMM convolutions (inputs gathered per tap, several M tiles, a ragged
+    # last tile): same network, FP32 sums in another order than the im2col GEMMs
+    from oracle import cnn
+    rng = np.random.default_rng(n * 1000 + h + w)
+    theta = cnn.init_params(11)
+    theta[cnn.n_params() - 2:] = [-0.1, 0.25]
+    xb = torch.tensor(rng.uniform(-1, 1, (n, h, w, 2)), dtype=torch.bfloat16)
+    P = hd.Predictor(n, h, w, theta)
+    got = P.infer(xb.cuda())
+    fwd = P.forward(xb.cuda())
+    torch.cuda.synchronize()
+    assert int(P.status.item()) == 0
+    got, fwd = got.cpu().numpy(), fwd.cpu().numpy()
+    o_or, _ = cnn.forward(theta, xb.double().numpy(), bf16=True)
+    assert got.shape == o_or.shape
+    assert rel(got, o_or) <= 2e-2
+    assert rel(got, fwd) <= 2e-2
+    assert rel_l2(got, fwd) <= 5e-3
+
+
+def test_inference_form_at_the_predictor_size(hd):
+    # the quarter-resolution input of a 2592 x 1944 frame (648 x 486, 2461 M tiles at the
+    # first layer) with the trained parameters: equals the training forward up to order
+    from paper_1504_01441_b300 import learned
+    theta = np.load(learned.THETA_FILE)
+    rng = np.random.default_rng(5)
+    xb = torch.tensor(rng.uniform(-1, 1, (1, 486, 648, 2)), dtype=torch.bfloat16).cuda()
+    P = hd.Predictor(1, 486, 648, theta)
+    got = P.infer(xb).cpu().numpy()
+    fwd = P.forward(xb).cpu().numpy()
+    assert int(P.status.item()) == 0
+    assert rel(got, fwd) <= 2e-2 and rel_l2(got, fwd) <= 5e-3

@@ -155,3 +155,40 @@ def test_fused_learned_path_with_zero_fallback_cost_equals_plain(hd):
     (y2, _, _), rm2 = hd.register_merge(ref, srcs, st.ratios, p)
     d2 = rm2.diagnostics()[0]
     assert d2.fallbacks == 0 and np.isfinite(y2.cpu().numpy()).all()
+
+
+def test_fused_learned_path_equals_its_step_calls(hd):
+    # the fused call's learned level 0 = predictor input -> inference network -> search
+    # with the prediction (threshold near the median cost, so both branches occur),
+    # then the level fit: the same H0 bits and the same number of fallbacks
+    from paper_1504_01441_b300 import learned, synth
+    st = synth.make_stack(synth.VGA_LUMA, synth.stack_seed(1))
+    p = hd.params_from_dict(cfg(32, 6))
+    theta = torch.tensor(np.load(learned.THETA_FILE)).cuda()
+    ref, src = dev(st.ref.y), dev(st.srcs[0].y)
+    rn, sn, _ = hd.normalize_exposure(ref, src, hd.NORM_RATIO, st.ratios[0])
+    h, w = rn.shape
+    L = hd.num_levels(w, h, p)
+    pr, ps = hd.build_pyramid(rn, L), hd.build_pyramid(sn, L)
+    Hc = torch.tensor([1, 0, 0, 0, 1, 0, 0, 0, 1], dtype=torch.float64).cuda()
+    counter = torch.zeros(1, dtype=torch.int32).cuda()
+    for lv in range(L - 1, 0, -1):
+        lh, lw = pr[lv].shape
+        cxy, mxy, cost, valid = hd.local_search(pr[lv], ps[lv], Hc, p)
+        _, Hc, _ = hd.weed_fit(cxy, mxy, valid, lw, lh, p, p.weed_seed + lv, Hc, counter=counter)
+    _, _, c_plain, v_plain = hd.local_search(rn, sn, Hc, p)
+    thr = int(c_plain[v_plain.bool()].double().median().item())
+    x = hd.predictor_input(pr[2], ps[2], Hc)
+    net = hd.Predictor(1, x.shape[0], x.shape[1], theta)
+    pred = net.infer(x.unsqueeze(0))[0]
+    cxy, mxy, cost, valid, fb = hd.local_search_predicted(rn, sn, Hc, p, pred, thr, refine=1)
+    _, H0, _ = hd.weed_fit(cxy, mxy, valid, w, h, p, p.weed_seed, Hc, counter=counter)
+    nfb = int(fb[valid.bool()].sum().item())
+    assert 0 < nfb < int(valid.sum().item())
+    p.predictor = theta.data_ptr()
+    p.fallback_cost = thr
+    p.predictor_refine = 1
+    _, rm = hd.register_merge((ref, None, None), [(src, None, None)], st.ratios, p)
+    d = rm.diagnostics()[0]
+    assert np.array_equal(np.array(d.H0[:]).view(np.uint64), H0.cpu().numpy().view(np.uint64))
+    assert d.fallbacks == nfb
