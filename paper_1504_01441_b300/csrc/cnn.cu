@@ -487,7 +487,7 @@ bool cnn_forward(const float* theta, const __nv_bfloat16* x, int n, int h, int w
 
 // Inference workspace: the padded features and one activation buffer per ReLU layer.
 struct InferLayout {
-    size_t feat, act[kNL], total;
+    size_t feat, act[kNL], wimg[kNL], total;
     int H[kNL + 1], Wd[kNL + 1];
     long long M[kNL];
     InferLayout(int n, int h, int w)
@@ -506,6 +506,9 @@ struct InferLayout {
             Wd[i + 1] = osz(Wd[i], kNet[i]);
             M[i] = (long long)n * H[i + 1] * Wd[i + 1];
             act[i] = kNet[i].relu ? add((size_t)M[i] * kNet[i].cout * 2) : 0;
+            wimg[i] = kNet[i].k == 3 ? add(conv_wimg_size(i == 0 ? kFeatPad : kNet[i].cin,
+                                                          kNet[i].cout))
+                                     : 0;
         }
         total = o;
     }
@@ -525,6 +528,17 @@ bool cnn_infer(const float* theta, const __nv_bfloat16* x, int n, int h, int w, 
     note_launch();
     k_features32<<<dim3((w + 127) / 128, h, n), 128, 0, s>>>(
         reinterpret_cast<const __nv_bfloat162*>(x), h, w, feat);
+    ConvPack pk{};
+    for (int i = 0; i < kNL; i++) {
+        if (kNet[i].k != 3) continue;
+        const int l = pk.layers++;
+        pk.W[l] = theta + param_offset(i);
+        pk.img[l] = base + lay.wimg[i];
+        pk.cin[l] = i == 0 ? kFeatPad : kNet[i].cin;
+        pk.cin_src[l] = kNet[i].cin;
+        pk.cout[l] = kNet[i].cout;
+    }
+    launch_pack_conv(pk, s);
     const __nv_bfloat16* in = feat;
     int cin_pad = kFeatPad;
     for (int i = 0; i < kNL; i++) {
@@ -534,7 +548,8 @@ bool cnn_infer(const float* theta, const __nv_bfloat16* x, int n, int h, int w, 
         if (L.k == 3) {
             __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(base + lay.act[i]);
             const ConvArgs a{in, lay.H[i], lay.Wd[i], lay.H[i + 1], lay.Wd[i + 1], (int)lay.M[i],
-                             theta + po, L.cin, cin_pad, L.stride, L.cout, bias, act, err};
+                             theta + po, L.cin, cin_pad, L.stride, L.cout, bias, act, err,
+                             base + lay.wimg[i]};
             if (!launch_conv3x3(a, s)) return false;
             in = act;
             cin_pad = L.cout;

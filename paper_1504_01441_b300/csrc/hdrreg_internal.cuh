@@ -503,6 +503,7 @@ bool launch_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int
 // Implicit-GEMM 3x3 convolution (conv_tc.cu): x bf16 [n][h][w][cin] (cin = padded channel
 // count, a multiple of 8), W FP32 [cout][3][3][cin_src] (cin_src <= cin; channels past
 // cin_src weigh 0), bias FP32 [cout], out bf16 [M][cout] = relu(conv + bias), M = n*ho*wo.
+// wimg must hold the packed weights (launch_pack_conv) when the convolution runs.
 struct ConvArgs {
     const __nv_bfloat16* x;
     int h, w, ho, wo, M;
@@ -511,8 +512,18 @@ struct ConvArgs {
     const float* bias;
     __nv_bfloat16* out;
     int* err;
+    void* wimg;  // conv_wimg_size(cin, cout) bytes, 16-byte aligned: the packed weights
 };
 bool launch_conv3x3(const ConvArgs& a, cudaStream_t s);  // false: no kernel for this shape
+size_t conv_wimg_size(int cin, int cout);
+// The weight images (wimg) of up to 8 layers in one launch, before the convolutions.
+struct ConvPack {
+    const float* W[8];
+    void* img[8];
+    int cin[8], cin_src[8], cout[8];
+    int layers;
+};
+void launch_pack_conv(const ConvPack& p, cudaStream_t s);
 
 size_t cnn_params();
 size_t cnn_infer_ws_bytes(int n, int h, int w);
