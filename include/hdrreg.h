@@ -456,6 +456,24 @@ hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count,
                                           int nsrc, int lanes, const hdrreg_params* p,
                                           void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------- a1-a11 fused, a batch of stacks in host memory
+ * The paper has no counterpart. hdrreg_register_merge_batch for stacks whose planes
+ * (ref/srcs frames), merged outputs (out) and optional diagnostics (diag) are HOST
+ * pointers. On every lane the library copies one stack's input planes into that lane's
+ * part of the workspace, runs the fused path and copies the FP32 planes (and the
+ * diagnostics) back, all on the lane's stream, so copies of one lane overlap the
+ * kernels of the others. The call returns once everything is enqueued: the host
+ * buffers must stay valid and untouched until `stream` has passed the call (synchronize
+ * it). Page-locked host buffers are needed for the copies to run asynchronously.
+ * Workspace (device): hdrreg_register_merge_host_workspace_size(w, h, nsrc, lanes, p),
+ * 0 for bad arguments. Results equal hdrreg_register_merge's bit for bit.
+ */
+size_t hdrreg_register_merge_host_workspace_size(int w, int h, int nsrc, int lanes,
+                                                 const hdrreg_params* p);
+hdrreg_status hdrreg_register_merge_host(const hdrreg_stack* stacks, int count, int w, int h,
+                                         int nsrc, int lanes, const hdrreg_params* p,
+                                         void* workspace, size_t ws_bytes, void* stream);
+
 /* ------------------------- a1-a11 fused, a batch of stacks of different shapes
  * The paper has no counterpart. Like hdrreg_register_merge_batch, but every stack
  * carries its own size, source count and parameters (e.g. the tile and radius an

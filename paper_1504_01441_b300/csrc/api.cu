@@ -1028,6 +1028,121 @@ hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count,
     return st;
 }
 
+// Per-lane layout of the host-staged batch: the fused workspace, then device copies of
+// one stack's input planes, its FP32 output planes and its diagnostics.
+struct HostStage {
+    size_t fused, in_y[kMaxSources + 1], in_u[kMaxSources + 1], in_v[kMaxSources + 1];
+    size_t out_y, out_u, out_v, diag, total;
+    HostStage(int w, int h, int nsrc, const hdrreg_params* p)
+    {
+        Layout L;
+        fused = L.add(FusedLayout(w, h, nsrc, p).total);
+        const size_t luma = (size_t)w * h, chr = (size_t)(w / 2) * (h / 2);
+        for (int k = 0; k <= nsrc; k++) {
+            in_y[k] = L.add(luma);
+            in_u[k] = L.add(chr);
+            in_v[k] = L.add(chr);
+        }
+        out_y = L.add(luma * 4);
+        out_u = L.add(chr * 4);
+        out_v = L.add(chr * 4);
+        diag = L.add(sizeof(hdrreg_diag) * nsrc);
+        total = align_up(L.total, 256);
+    }
+};
+
+size_t hdrreg_register_merge_host_workspace_size(int w, int h, int nsrc, int lanes,
+                                                 const hdrreg_params* p)
+{
+    if (!p || hdrreg_validate_params(p) || bad_dims(w, h) || nsrc < 1 || nsrc > kMaxSources ||
+        lanes < 1 || lanes > HDRREG_MAX_LANES)
+        return 0;
+    return HostStage(w, h, nsrc, p).total * lanes;
+}
+
+hdrreg_status hdrreg_register_merge_host(const hdrreg_stack* stacks, int count, int w, int h,
+                                         int nsrc, int lanes, const hdrreg_params* p,
+                                         void* workspace, size_t ws_bytes, void* stream)
+{
+    if (count < 0 || (count > 0 && !stacks))
+        return fail(HDRREG_E_INVALID_ARG, "register_merge_host: bad stack array");
+    if (lanes < 1 || lanes > HDRREG_MAX_LANES)
+        return fail(HDRREG_E_INVALID_ARG, "register_merge_host: lanes must be in [1, %d]",
+                    HDRREG_MAX_LANES);
+    for (int i = 0; i < count; i++) {
+        const hdrreg_stack& k = stacks[i];
+        hdrreg_status st =
+            rm_validate(k.ref, w, h, nsrc, k.srcs, k.ratio_num, k.ratio_den, p, &k.out);
+        if (st) return fail(st, "register_merge_host: stack %d: %s", i, hdrreg_last_error());
+    }
+    const HostStage hs(w, h, nsrc, p);
+    if (!workspace || ws_bytes < hs.total * lanes)
+        return fail(HDRREG_E_WORKSPACE, "register_merge_host: workspace of %zu bytes required",
+                    hs.total * lanes);
+    if (count == 0) return HDRREG_OK;
+    const FusedLayout lay(w, h, nsrc, p);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int used = count < lanes ? count : lanes;
+    LaneSet* ls = nullptr;
+    hdrreg_status st = lane_set(&ls);
+    if (st) return st;
+    const size_t luma = (size_t)w * h, chr = (size_t)(w / 2) * (h / 2);
+    std::lock_guard<std::mutex> lock(lane_enqueue_mu);
+    cudaError_t e = cudaEventRecord(ls->fork, s);
+    for (int j = 0; j < used && e == cudaSuccess; j++) e = cudaStreamWaitEvent(ls->stream[j], ls->fork, 0);
+    if (e != cudaSuccess)
+        return fail(HDRREG_E_CUDA, "register_merge_host: fork: %s", cudaGetErrorString(e));
+    for (int i = 0; i < count && !st; i++) {
+        const int j = i % used;
+        const hdrreg_stack& k = stacks[i];
+        cudaStream_t q = ls->stream[j];
+        uint8_t* lb = static_cast<uint8_t*>(workspace) + hs.total * j;
+        const bool chroma = k.ref->u && k.ref->v && k.out.u && k.out.v;
+        hdrreg_frame dref, dsrc[kMaxSources];
+        auto put = [&](size_t off, const uint8_t* host, size_t n) -> const uint8_t* {
+            if (!host) return nullptr;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(lb + off, host, n, cudaMemcpyHostToDevice, q);
+            return lb + off;
+        };
+        dref.y = put(hs.in_y[0], k.ref->y, luma);
+        dref.u = chroma ? put(hs.in_u[0], k.ref->u, chr) : nullptr;
+        dref.v = chroma ? put(hs.in_v[0], k.ref->v, chr) : nullptr;
+        for (int m = 0; m < nsrc; m++) {
+            dsrc[m].y = put(hs.in_y[m + 1], k.srcs[m].y, luma);
+            dsrc[m].u = chroma ? put(hs.in_u[m + 1], k.srcs[m].u, chr) : nullptr;
+            dsrc[m].v = chroma ? put(hs.in_v[m + 1], k.srcs[m].v, chr) : nullptr;
+        }
+        if (e != cudaSuccess) {
+            st = fail(HDRREG_E_CUDA, "register_merge_host: copy in: %s", cudaGetErrorString(e));
+            break;
+        }
+        const hdrreg_planes_f32 dout{reinterpret_cast<float*>(lb + hs.out_y),
+                                     chroma ? reinterpret_cast<float*>(lb + hs.out_u) : nullptr,
+                                     chroma ? reinterpret_cast<float*>(lb + hs.out_v) : nullptr};
+        hdrreg_diag* ddiag = reinterpret_cast<hdrreg_diag*>(lb + hs.diag);
+        st = rm_enqueue(&dref, w, h, nsrc, dsrc, k.ratio_num, k.ratio_den, p, lay, lb + hs.fused,
+                        &dout, ddiag, q);
+        if (st) break;
+        e = cudaMemcpyAsync(k.out.y, dout.y, luma * 4, cudaMemcpyDeviceToHost, q);
+        if (chroma && e == cudaSuccess)
+            e = cudaMemcpyAsync(k.out.u, dout.u, chr * 4, cudaMemcpyDeviceToHost, q);
+        if (chroma && e == cudaSuccess)
+            e = cudaMemcpyAsync(k.out.v, dout.v, chr * 4, cudaMemcpyDeviceToHost, q);
+        if (k.diag && e == cudaSuccess)
+            e = cudaMemcpyAsync(k.diag, ddiag, sizeof(hdrreg_diag) * nsrc, cudaMemcpyDeviceToHost, q);
+        if (e != cudaSuccess)
+            st = fail(HDRREG_E_CUDA, "register_merge_host: copy out: %s", cudaGetErrorString(e));
+    }
+    for (int j = 0; j < used; j++) {  // join every lane, also after an error
+        cudaError_t e1 = cudaEventRecord(ls->join[j], ls->stream[j]);
+        cudaError_t e2 = cudaStreamWaitEvent(s, ls->join[j], 0);
+        if (!st && (e1 != cudaSuccess || e2 != cudaSuccess))
+            st = fail(HDRREG_E_CUDA, "register_merge_host: join: %s",
+                      cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    }
+    return st;
+}
+
 // Lane plan of a multi-shape batch: longest first onto the least-loaded lane; per lane
 // the workspace of its largest stack (offsets into one buffer).
 struct MultiPlan {

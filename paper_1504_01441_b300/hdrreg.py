@@ -31,6 +31,7 @@ EXPORTS = [
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
     "hdrreg_register_merge_multi_workspace_size", "hdrreg_register_merge_multi",
+    "hdrreg_register_merge_host_workspace_size", "hdrreg_register_merge_host",
     "hdrreg_gemm_bf16", "hdrreg_cnn_workspace_size", "hdrreg_cnn_out_dims", "hdrreg_cnn_forward",
     "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_cnn_activation",
     "hdrreg_cnn_infer_workspace_size", "hdrreg_cnn_infer", "hdrreg_predictor_input",
@@ -152,6 +153,10 @@ def lib():
         L.hdrreg_register_merge_batch_workspace_size.argtypes = [i, i, i, i, C.POINTER(Params)]
         L.hdrreg_register_merge_batch.argtypes = [C.POINTER(Stack), i, i, i, i, i,
                                                   C.POINTER(Params), vp, sz, vp]
+        L.hdrreg_register_merge_host_workspace_size.restype = sz
+        L.hdrreg_register_merge_host_workspace_size.argtypes = [i, i, i, i, C.POINTER(Params)]
+        L.hdrreg_register_merge_host.argtypes = [C.POINTER(Stack), i, i, i, i, i,
+                                                 C.POINTER(Params), vp, sz, vp]
         L.hdrreg_register_merge_multi_workspace_size.restype = sz
         L.hdrreg_register_merge_multi_workspace_size.argtypes = [C.POINTER(StackEx), i, i]
         L.hdrreg_register_merge_multi.argtypes = [C.POINTER(StackEx), i, i, vp, sz, vp]
@@ -623,6 +628,55 @@ class RegisterMergeBatch:
         raw = self.diag[slot].cpu().numpy().tobytes()
         n = C.sizeof(Diag)
         return [Diag.from_buffer_copy(raw[i * n:(i + 1) * n]) for i in range(self.nsrc)]
+
+
+class RegisterMergeHost:
+    """Batched fused call for stacks of one shape held in (page-locked) host memory: the
+    library stages each stack through its lane's device buffers. The caller passes host
+    uint8 planes and receives the merged FP32 planes in host arrays it provides."""
+
+    def __init__(self, w: int, h: int, nsrc: int, p: Params, lanes: int = 4, device="cuda"):
+        import torch
+        self.w, self.h, self.nsrc, self.p, self.lanes = w, h, nsrc, p, lanes
+        n = lib().hdrreg_register_merge_host_workspace_size(w, h, nsrc, lanes, C.byref(p))
+        if n == 0:
+            raise HdrregError(1, "bad shape, lanes or parameters for register_merge_host")
+        self.ws = torch.empty((n,), dtype=torch.uint8, device=device)
+        self._keep = None
+
+    def __call__(self, stacks, outs, stream=None):
+        """stacks: (ref, srcs, ratios) with CPU uint8 tensors (y, u, v) (u = v = None for
+        luma); outs: one (y, u, v) of CPU FP32 tensors per stack. Enqueues only: the outputs
+        are valid after the stream is synchronized."""
+        k = len(stacks)
+        arr = (Stack * max(k, 1))()
+        keep = []
+
+        def hp(t):
+            if t is None:
+                return None
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("host planes must be contiguous CPU tensors")
+            return t.data_ptr()
+        for i, (ref, srcs, ratios) in enumerate(stacks):
+            if len(srcs) != self.nsrc:
+                raise ValueError("number of sources differs from the one this call was built for")
+            fr = Frame(hp(ref[0]), hp(ref[1]), hp(ref[2]))
+            fs = (Frame * self.nsrc)(*[Frame(hp(s[0]), hp(s[1]), hp(s[2])) for s in srcs])
+            num = (C.c_int * self.nsrc)(*[r[0] for r in ratios])
+            den = (C.c_int * self.nsrc)(*[r[1] for r in ratios])
+            arr[i].ref = C.pointer(fr)
+            arr[i].srcs = C.cast(fs, C.POINTER(Frame))
+            arr[i].ratio_num = C.cast(num, C.POINTER(C.c_int))
+            arr[i].ratio_den = C.cast(den, C.POINTER(C.c_int))
+            o = outs[i]
+            arr[i].out = PlanesF32(hp(o[0]), hp(o[1]), hp(o[2]))
+            arr[i].diag = None
+            keep.append((fr, fs, num, den))
+        _check(lib().hdrreg_register_merge_host(arr, k, self.w, self.h, self.nsrc, self.lanes,
+                                                C.byref(self.p), _ptr(self.ws), self.ws.numel(),
+                                                _stream(stream)))
+        self._keep = keep
 
 
 class RegisterMergeMulti:

@@ -128,3 +128,22 @@ def test_python_binding_refuses_cpu_tensors(hd):
     import torch
     with pytest.raises(ValueError):
         hd._ptr(torch.zeros(4))
+
+
+def test_host_staged_batch_sizes_and_errors(hd):
+    lib = hd.lib()
+    p = hd.params(tile=32, radius=6)
+    one = hd.register_merge_workspace_size(2592, 1944, 1, p)
+    n4 = lib.hdrreg_register_merge_host_workspace_size(2592, 1944, 1, 4, C.byref(p))
+    staging = 2592 * 1944 * (1.5 * 2 + 6)
+    assert n4 >= 4 * (one + staging) and n4 < 4 * (one + staging + 16 * 256 + 4096)
+    assert lib.hdrreg_register_merge_host_workspace_size(2592, 1944, 1, 0, C.byref(p)) == 0
+    assert lib.hdrreg_register_merge_host_workspace_size(2592, 1944, 0, 2, C.byref(p)) == 0
+    assert lib.hdrreg_register_merge_host(None, 3, 64, 64, 1, 2, C.byref(p), None, 0, None) == 1
+    assert lib.hdrreg_register_merge_host(None, 0, 64, 64, 1, 0, C.byref(p), None, 0, None) == 1
+    f = hd.Frame(None, None, None)
+    st = (hd.Stack * 1)()
+    st[0].ref = C.pointer(f)
+    assert lib.hdrreg_register_merge_host(st, 1, 64, 64, 1, 2, C.byref(p), None, 0, None) == 1
+    assert b"stack 0" in lib.hdrreg_last_error()
+    assert lib.hdrreg_register_merge_host(None, 0, 64, 64, 1, 2, C.byref(p), None, 0, None) == 6
