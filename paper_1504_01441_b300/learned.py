@@ -196,9 +196,35 @@ def evaluate(prepared: List[Prepared], theta, p: hdrreg.Params, fallback_ratio: 
             "refine": refine}
 
 
+def time_network(reps: int, h: int = 486, w: int = 648):
+    """Device time (us per call) of the inference form and of the training forward of the
+    network on one quarter-resolution input of a 2592 x 1944 frame (trained parameters,
+    random input), each call timed with CUDA events over `reps` calls after three."""
+    import torch
+    theta = np.load(THETA_FILE)
+    x = torch.tensor(np.random.default_rng(1).uniform(-1, 1, (1, h, w, 2)),
+                     dtype=torch.bfloat16).cuda()
+    net = hdrreg.Predictor(1, h, w, theta)
+    out = {}
+    for name, fn in (("infer_us", lambda: net.infer(x)), ("forward_us", lambda: net.forward(x))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = round(a.elapsed_time(b) * 1e3 / max(reps, 1), 2)
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
+    ap.add_argument("--time-network", type=int, default=0, metavar="REPS",
+                    help="only time the network (inference and training forward) and exit")
     ap.add_argument("--out", default=THETA_FILE)
     ap.add_argument("--train-stacks", type=int, default=16)
     ap.add_argument("--eval-stacks", type=int, default=2)
@@ -208,6 +234,9 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--log", default=None)
     args = ap.parse_args()
+    if args.time_network:
+        print(json.dumps(time_network(args.time_network)))
+        return
     p = hdrreg.params_from_dict(synth.method_params(32, 6))
     t0 = time.perf_counter()
     train_set = [prepare(s, p) for s in make_stacks(args.train_stacks, 0)]
