@@ -10,7 +10,9 @@
 // memory; the five Gaussian moments are separable (row pass, column pass). To
 // avoid the FP32 cancellation of E[x^2] - mu^2, each row segment's moments are
 // taken about its own centre pixel and the column pass re-centres them exactly
-// onto the output pixel, so flat windows only ever sum small numbers.
+// onto the output pixel, so flat windows only ever sum small numbers. The two
+// images' moment chains run side by side as packed FP32x2 operations (each
+// component rounds as its scalar form would).
 #include <math.h>
 
 #include "hdrreg_internal.cuh"
@@ -178,38 +180,47 @@ __device__ __forceinline__ float norm_map(const MergeSrcDev& s, float z)
     return fmaf(f, b - a, a);
 }
 
-__global__ void __launch_bounds__(256) k_merge(const uint8_t* __restrict__ ref_y,
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__global__ void __launch_bounds__(256, 3) k_merge(const uint8_t* __restrict__ ref_y,
                                                const uint8_t* __restrict__ ref_u,
                                                const uint8_t* __restrict__ ref_v, int w, int h,
                                                MergeArgs args, float* __restrict__ oy,
                                                float* __restrict__ ou, float* __restrict__ ov,
                                                float* __restrict__ q_out)
 {
-    __shared__ float X[kIn][kIn + 1];
-    __shared__ float Y[kIn][kIn + 1];
-    __shared__ float Hm[5][kIn][kTile + 1];
+    // the reference (X) and the normalized warped source (Y) interleaved: every step of the
+    // two moment chains is one packed FP32x2 instruction
+    __shared__ float2 XY[kIn][kIn];
+    __shared__ float2 H1[kIn][kTile];   // (sum g a, sum g b) of each row segment
+    __shared__ float2 H2[kIn][kTile];   // (sum g a^2, sum g b^2)
+    __shared__ float H11[kIn][kTile + 1];  // sum g a b
     __shared__ float Wk[kTile][kTile + 1];
-    const int tid = threadIdx.x;
+    __shared__ float Ns[kTile][kTile + 1], Ds[kTile][kTile + 1], Zs[kTile][kTile + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
     const bool chroma = ref_u != nullptr && ou != nullptr;
     const int cw = w / 2, ch = h / 2;
+    const float2 neg1 = f2(-1.f, -1.f);
+    const float2 gsum2 = f2(args.gsum, args.gsum);
 
     // this thread's 4 luma pixels: (tx, ty + 8 k); its chroma pixel: (tid % 16, tid / 16)
     const int tx = tid % kTile, ty0 = tid / kTile;
-    float num[4], den[4];
+    // per-pixel numerator / denominator of the merge live in shared memory (this thread's
+    // own entries only), so the column pass loop keeps no arrays in registers
+#pragma unroll
     for (int k = 0; k < 4; k++) {
         const int x = x0 + tx, y = y0 + ty0 + 8 * k;
-        num[k] = 0.f;
-        den[k] = 0.f;
+        float nu = 0.f, de = 0.f;
         if (x < w && y < h) {
             const float z = (float)ref_y[(size_t)y * w + x];
             const float wr = well_exposed(z, args.we_k);
-            num[k] = wr * z;
-            den[k] = wr;
-            Wk[ty0 + 8 * k][tx] = wr;
-        } else {
-            Wk[ty0 + 8 * k][tx] = 0.f;
+            nu = wr * z;
+            de = wr;
         }
+        Ns[ty0 + 8 * k][tx] = nu;
+        Ds[ty0 + 8 * k][tx] = de;
+        Wk[ty0 + 8 * k][tx] = de;
     }
     const int cx = x0 / 2 + tid % 16, cy = y0 / 2 + tid / 16;
     const bool c_ok = chroma && cx < cw && cy < ch && (tid % 16) < kTile / 2;
@@ -226,74 +237,97 @@ __global__ void __launch_bounds__(256) k_merge(const uint8_t* __restrict__ ref_y
 
     for (int k = 0; k < args.nsrc; k++) {
         const MergeSrcDev s = args.src[k];
+        // every global load of this source up front (one round trip): the 42 x 42 halo
+        // (warp w: rows w + 8 r, columns lane and lane + 32), this thread's own 4 source
+        // pixels, its chroma pixel
+        uint8_t hr[12];
+        float hy[12];
+#pragma unroll
+        for (int q = 0; q < 12; q++) {
+            const int yy = warp + 8 * (q >> 1), xx = lane + 32 * (q & 1);
+            hr[q] = 0;
+            hy[q] = 0.f;
+            if (yy < kIn && xx < kIn) {
+                const int gy = clampi(y0 - kHalo + yy, 0, h - 1);
+                const int gx = clampi(x0 - kHalo + xx, 0, w - 1);
+                const size_t o = (size_t)gy * w + gx;
+                hr[q] = s.ref_n[o];
+                hy[q] = s.y[o];
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+            const int x = x0 + tx, y = y0 + ty0 + 8 * kk;
+            Zs[ty0 + 8 * kk][tx] = (x < w && y < h) ? s.y[(size_t)y * w + x] : 0.f;
+        }
+        float su = 0.f, sv = 0.f;
+        if (c_ok) {
+            const size_t o = (size_t)cy * cw + cx;
+            su = s.u[o];
+            sv = s.v[o];
+        }
         __syncthreads();
-        for (int i = tid; i < kIn * kIn; i += 256) {
-            const int yy = i / kIn, xx = i % kIn;
-            const int gx = clampi(x0 - kHalo + xx, 0, w - 1), gy = clampi(y0 - kHalo + yy, 0, h - 1);
-            const size_t o = (size_t)gy * w + gx;
-            X[yy][xx] = (float)s.ref_n[o];
-            Y[yy][xx] = norm_map(s, s.y[o]);
+#pragma unroll
+        for (int q = 0; q < 12; q++) {
+            const int yy = warp + 8 * (q >> 1), xx = lane + 32 * (q & 1);
+            if (yy < kIn && xx < kIn) XY[yy][xx] = f2((float)hr[q], norm_map(s, hy[q]));
         }
         __syncthreads();
         // Row pass: moments of each 11-tap row segment about its own centre pixel
-        // (a = x - x_c): M1 = sum g a, M2 = sum g a^2, M11 = sum g a b.
+        // (a = x - x_c, b = y - y_c): M1 = sum g (a, b), M2 = sum g (a^2, b^2), M11 = sum g a b.
         for (int i = tid; i < kIn * kTile; i += 256) {
             const int yy = i / kTile, xx = i % kTile;
-            const float cxv = X[yy][xx + kHalo], cyv = Y[yy][xx + kHalo];
-            float mx = 0.f, my = 0.f, mxx = 0.f, myy = 0.f, mxy = 0.f;
+            const float2 c = XY[yy][xx + kHalo];
+            float2 m1 = f2(0.f, 0.f), m2 = f2(0.f, 0.f);
+            float m11 = 0.f;
 #pragma unroll
             for (int d = 0; d <= 2 * kHalo; d++) {
-                const float gw = args.g[d];
-                const float a = X[yy][xx + d] - cxv, b = Y[yy][xx + d] - cyv;
-                const float ga = gw * a, gb = gw * b;
-                mx += ga;
-                my += gb;
-                mxx = fmaf(ga, a, mxx);
-                myy = fmaf(gb, b, myy);
-                mxy = fmaf(ga, b, mxy);
+                const float2 g2 = f2(args.g[d], args.g[d]);
+                const float2 ab = __ffma2_rn(c, neg1, XY[yy][xx + d]);
+                const float2 gab = __fmul2_rn(g2, ab);
+                m1 = __fadd2_rn(m1, gab);
+                m2 = __ffma2_rn(gab, ab, m2);
+                m11 = fmaf(gab.x, ab.y, m11);
             }
-            Hm[0][yy][xx] = mx;
-            Hm[1][yy][xx] = my;
-            Hm[2][yy][xx] = mxx;
-            Hm[3][yy][xx] = myy;
-            Hm[4][yy][xx] = mxy;
+            H1[yy][xx] = m1;
+            H2[yy][xx] = m2;
+            H11[yy][xx] = m11;
         }
         __syncthreads();
         const float C1 = (0.01f * 255.f) * (0.01f * 255.f), C2 = (0.03f * 255.f) * (0.03f * 255.f);
+#pragma unroll 1
         for (int kk = 0; kk < 4; kk++) {
             const int ly = ty0 + 8 * kk;
             const int x = x0 + tx, y = y0 + ly;
             // Column pass: re-centre every row's moments from its centre c_r onto the output
             // pixel's value c (delta = c_r - c): sum g (a + delta)^k expands exactly, so the
             // window moments stay small numbers wherever the window is flat.
-            const float cxv = X[ly + kHalo][tx + kHalo], cyv = Y[ly + kHalo][tx + kHalo];
-            float mx = 0.f, my = 0.f, mxx = 0.f, myy = 0.f, mxy = 0.f;
+            const float2 c = XY[ly + kHalo][tx + kHalo];
+            float2 a1 = f2(0.f, 0.f), a2 = f2(0.f, 0.f);
+            float a11 = 0.f;
 #pragma unroll
             for (int d = 0; d <= 2 * kHalo; d++) {
-                const float gw = args.g[d];
-                const float dx = X[ly + d][tx + kHalo] - cxv, dy = Y[ly + d][tx + kHalo] - cyv;
-                const float m1x = Hm[0][ly + d][tx], m1y = Hm[1][ly + d][tx];
-                const float r1x = fmaf(dx, args.gsum, m1x), r1y = fmaf(dy, args.gsum, m1y);
-                const float r2x = Hm[2][ly + d][tx] + dx * (m1x + r1x);
-                const float r2y = Hm[3][ly + d][tx] + dy * (m1y + r1y);
-                const float r11 = Hm[4][ly + d][tx] + fmaf(dy, m1x, dx * r1y);
-                mx = fmaf(gw, r1x, mx);
-                my = fmaf(gw, r1y, my);
-                mxx = fmaf(gw, r2x, mxx);
-                myy = fmaf(gw, r2y, myy);
-                mxy = fmaf(gw, r11, mxy);
+                const float2 g2 = f2(args.g[d], args.g[d]);
+                const float2 dd = __ffma2_rn(c, neg1, XY[ly + d][tx + kHalo]);
+                const float2 m1 = H1[ly + d][tx];
+                const float2 r1 = __ffma2_rn(dd, gsum2, m1);
+                const float2 r2 = __ffma2_rn(dd, __fadd2_rn(m1, r1), H2[ly + d][tx]);
+                const float r11 = H11[ly + d][tx] + fmaf(dd.y, m1.x, dd.x * r1.y);
+                a1 = __ffma2_rn(g2, r1, a1);
+                a2 = __ffma2_rn(g2, r2, a2);
+                a11 = fmaf(args.g[d], r11, a11);
             }
-            const float vx = mxx - mx * mx, vy = myy - my * my, cxy = mxy - mx * my;
-            const float ux = cxv + mx, uy = cyv + my;
+            const float vx = a2.x - a1.x * a1.x, vy = a2.y - a1.y * a1.y, cxy = a11 - a1.x * a1.y;
+            const float ux = c.x + a1.x, uy = c.y + a1.y;
             const float ssim = ((2.f * ux * uy + C1) * (2.f * cxy + C2)) /
                                ((ux * ux + uy * uy + C1) * (vx + vy + C2));
             const float q = ssim > 0.f ? ssim : 0.f;
             float wk = 0.f;
             if (x < w && y < h) {
-                const float z = s.y[(size_t)y * w + x];
+                const float z = Zs[ly][tx];
                 wk = well_exposed(z, args.we_k) * q * clip_taper(z);
-                num[kk] = fmaf(wk, z * s.inv_ratio, num[kk]);
-                den[kk] += wk;
+                Ns[ly][tx] = fmaf(wk, z * s.inv_ratio, Ns[ly][tx]);
+                Ds[ly][tx] += wk;
                 if (q_out) q_out[(size_t)k * w * h + (size_t)y * w + x] = q;
             }
             Wk[ly][tx] = wk;
@@ -303,15 +337,15 @@ __global__ void __launch_bounds__(256) k_merge(const uint8_t* __restrict__ ref_y
             const int lx = 2 * (tid % 16), ly = 2 * (tid / 16);
             const float wb =
                 ((Wk[ly][lx] + Wk[ly][lx + 1]) + (Wk[ly + 1][lx] + Wk[ly + 1][lx + 1])) * 0.25f;
-            const size_t o = (size_t)cy * cw + cx;
-            cnu = fmaf(wb, (s.u[o] - 128.f) * s.inv_ratio, cnu);
-            cnv = fmaf(wb, (s.v[o] - 128.f) * s.inv_ratio, cnv);
+            cnu = fmaf(wb, (su - 128.f) * s.inv_ratio, cnu);
+            cnv = fmaf(wb, (sv - 128.f) * s.inv_ratio, cnv);
             cden += wb;
         }
     }
+#pragma unroll
     for (int k = 0; k < 4; k++) {
         const int x = x0 + tx, y = y0 + ty0 + 8 * k;
-        if (x < w && y < h) oy[(size_t)y * w + x] = num[k] / den[k];
+        if (x < w && y < h) oy[(size_t)y * w + x] = Ns[ty0 + 8 * k][tx] / Ds[ty0 + 8 * k][tx];
     }
     if (c_ok) {
         const size_t o = (size_t)cy * cw + cx;
