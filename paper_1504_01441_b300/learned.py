@@ -196,6 +196,30 @@ def evaluate(prepared: List[Prepared], theta, p: hdrreg.Params, fallback_ratio: 
             "refine": refine}
 
 
+OPS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "predictor_operating_point.json")
+
+
+def search_cost(refine: int, fallback_rate: float, radius: int = 6) -> float:
+    """SSD offsets per tile of the search with a prediction: the refinement window, plus
+    the full window on the tiles that fall back."""
+    return (2 * refine + 1) ** 2 + fallback_rate * (2 * radius + 1) ** 2
+
+
+def calibrate(prepared: List[Prepared], theta, p: hdrreg.Params, bound: float = 0.5,
+              refines=(1, 2, 3, 4), ratios=(1.5, 1.25, 1.0, 0.9, 0.8)):
+    """Every (refine, fallback ratio) on the prepared stacks -> (points, the cheapest point
+    whose mean distance to the plain matches is <= bound, by search_cost; None if none)."""
+    pts = []
+    for r in refines:
+        for fr in ratios:
+            q = evaluate(prepared, theta, p, fallback_ratio=fr, refine=r)
+            pts.append({"refine": r, "ratio": fr, "epe_px": round(q["epe_px"], 4),
+                        "fallback_rate": round(q["fallback_rate"], 4),
+                        "cost": round(search_cost(r, q["fallback_rate"], p.radius), 2)})
+    ok = [t for t in pts if t["epe_px"] <= bound]
+    return pts, (min(ok, key=lambda t: (t["cost"], t["refine"])) if ok else None)
+
+
 def time_network(reps: int, h: int = 486, w: int = 648):
     """Device time (us per call) of the inference form and of the training forward of the
     network on one quarter-resolution input of a 2592 x 1944 frame (trained parameters,
@@ -225,6 +249,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--time-network", type=int, default=0, metavar="REPS",
                     help="only time the network (inference and training forward) and exit")
+    ap.add_argument("--calibrate", type=int, default=0, metavar="STACKS",
+                    help="choose the operating point meeting --bound on STACKS held-out stacks")
+    ap.add_argument("--bound", type=float, default=0.5)
+    ap.add_argument("--ops-out", default=OPS_FILE)
     ap.add_argument("--out", default=THETA_FILE)
     ap.add_argument("--train-stacks", type=int, default=16)
     ap.add_argument("--eval-stacks", type=int, default=2)
@@ -236,6 +264,21 @@ def main():
     args = ap.parse_args()
     if args.time_network:
         print(json.dumps(time_network(args.time_network)))
+        return
+    if args.calibrate:
+        # held-out stacks shaped like the headline workload (seeds apart from training,
+        # evaluation and the bench's stacks)
+        p = hdrreg.params_from_dict(synth.method_params(32, 6))
+        theta = torch.tensor(np.load(THETA_FILE)).cuda()
+        stacks = [synth.make_stack(synth.FIVE_MP, synth.stack_seed(4, 3000 + i))
+                  for i in range(args.calibrate)]
+        prep = [prepare(st, p) for st in stacks]
+        pts, best = calibrate(prep, theta, p, bound=args.bound)
+        rep = {"bound_px": args.bound, "stacks": args.calibrate, "chosen": best, "points": pts,
+               "spec": "2592x1944 YUV420, r = 4, sigma 1.5, +-4 px fields, seeds 4:3000+"}
+        with open(args.ops_out, "w") as f:
+            json.dump(rep, f, indent=1)
+        print(json.dumps({"chosen": best}))
         return
     p = hdrreg.params_from_dict(synth.method_params(32, 6))
     t0 = time.perf_counter()

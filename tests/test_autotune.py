@@ -117,3 +117,24 @@ def test_multi_argument_errors():
     arr[0].s.ref = C.pointer(f)
     assert lib.hdrreg_register_merge_multi(arr, 1, 2, None, 0, None) == 1   # NULL planes
     assert b"stack 0" in lib.hdrreg_last_error()
+
+
+def test_learned_operating_point_is_the_cheapest_within_the_bound(monkeypatch):
+    from paper_1504_01441_b300 import learned
+    assert learned.search_cost(1, 0.0) == 9 and learned.search_cost(0, 1.0) == 1 + 169
+    table = {(1, 1.5): (2.4, 0.09), (1, 1.0): (1.0, 0.58), (2, 1.0): (0.45, 0.60),
+             (4, 1.0): (0.47, 0.51), (4, 1.5): (0.9, 0.08)}
+
+    def fake(prep, theta, p, fallback_ratio, refine):
+        e, fb = table.get((refine, fallback_ratio), (9.0, 0.0))
+        return {"epe_px": e, "fallback_rate": fb}
+    monkeypatch.setattr(learned, "evaluate", fake)
+
+    class P:
+        radius = 6
+    pts, best = learned.calibrate([], None, P(), refines=(1, 2, 4), ratios=(1.5, 1.0))
+    assert len(pts) == 6
+    # (2, 1.0): 25 + 0.60 * 169 = 126.4 < (4, 1.0): 81 + 0.51 * 169 = 167.2
+    assert (best["refine"], best["ratio"]) == (2, 1.0)
+    _, none = learned.calibrate([], None, P(), refines=(1,), ratios=(1.5,), bound=0.5)
+    assert none is None
