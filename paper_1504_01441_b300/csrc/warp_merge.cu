@@ -182,137 +182,221 @@ __device__ __forceinline__ float norm_map(const MergeSrcDev& s, float z)
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-__global__ void __launch_bounds__(256, 3) k_merge(const uint8_t* __restrict__ ref_y,
-                                               const uint8_t* __restrict__ ref_u,
-                                               const uint8_t* __restrict__ ref_v, int w, int h,
-                                               MergeArgs args, float* __restrict__ oy,
-                                               float* __restrict__ ou, float* __restrict__ ov,
-                                               float* __restrict__ q_out)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
 {
-    // the reference (X) and the normalized warped source (Y) interleaved: every step of the
-    // two moment chains is one packed FP32x2 instruction
-    __shared__ float2 XY[kIn][kIn];
-    __shared__ float2 H1[kIn][kTile];   // (sum g a, sum g b) of each row segment
-    __shared__ float2 H2[kIn][kTile];   // (sum g a^2, sum g b^2)
-    __shared__ float H11[kIn][kTile + 1];  // sum g a b
-    __shared__ float Wk[kTile][kTile + 1];
-    __shared__ float Ns[kTile][kTile + 1], Ds[kTile][kTile + 1], Zs[kTile][kTile + 1];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
-    const bool chroma = ref_u != nullptr && ou != nullptr;
-    const int cw = w / 2, ch = h / 2;
-    const float2 neg1 = f2(-1.f, -1.f);
-    const float2 gsum2 = f2(args.gsum, args.gsum);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
 
-    // this thread's 4 luma pixels: (tx, ty + 8 k); its chroma pixel: (tid % 16, tid / 16)
-    const int tx = tid % kTile, ty0 = tid / kTile;
-    // per-pixel numerator / denominator of the merge live in shared memory (this thread's
-    // own entries only), so the column pass loop keeps no arrays in registers
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int x = x0 + tx, y = y0 + ty0 + 8 * k;
-        float nu = 0.f, de = 0.f;
-        if (x < w && y < h) {
-            const float z = (float)ref_y[(size_t)y * w + x];
-            const float wr = well_exposed(z, args.we_k);
-            nu = wr * z;
-            de = wr;
+// Raw inputs of one (tile, source) unit, staged ahead of their use. Columns: Rn holds
+// ref_n at x0 - 16 .. x0 + 47, Ys the warped source luma at x0 - 8 .. x0 + 39, both for
+// rows y0 - 5 .. y0 + 36; Ry the reference luma of the tile; Ru, Rv, Su, Sv the tile's
+// 16 x 16 chroma of the reference and of the warped source.
+struct alignas(16) MergeStage {
+    uint8_t Rn[kIn][64];
+    float Ys[kIn][48];
+    uint8_t Ry[kTile][kTile];
+    uint8_t Ru[kTile / 2][kTile / 2], Rv[kTile / 2][kTile / 2];
+    float Su[kTile / 2][kTile / 2], Sv[kTile / 2][kTile / 2];
+};
+
+struct MergeSmem {
+    MergeStage st[2];
+    float2 XY[kIn][kIn];   // the reference (X) and the normalized warped source (Y)
+    float2 H1[kIn][kTile];  // (sum g a, sum g b) of each row segment
+    float2 H2[kIn][kTile];  // (sum g a^2, sum g b^2)
+    float H11[kIn][kTile + 1];  // sum g a b
+    float Wk[kTile][kTile + 1];
+    float Ns[kTile][kTile + 1], Ds[kTile][kTile + 1];
+};
+
+// Stage unit (tile t, source k): 16-byte async copies for interior tiles when every
+// plane allows them, else plain loads with clamp-to-edge (and the same layout).
+__device__ __forceinline__ void merge_stage(MergeStage& S, const MergeArgs& args,
+                                            const uint8_t* __restrict__ ref_y,
+                                            const uint8_t* __restrict__ ref_u,
+                                            const uint8_t* __restrict__ ref_v, int w, int h,
+                                            bool chroma, int tiles_x, int t, int k, bool async_ok)
+{
+    const int tid = threadIdx.x;
+    const int x0 = (t % tiles_x) * kTile, y0 = (t / tiles_x) * kTile;
+    const MergeSrcDev& s = args.src[k];
+    const int cw = w / 2, ch = h / 2, cx0 = x0 / 2, cy0 = y0 / 2;
+    const bool interior = async_ok && x0 >= 16 && x0 + 48 <= w && y0 >= kHalo &&
+                          y0 + kTile + kHalo <= h;
+    if (interior) {
+        // Rn: 42 rows x 4 chunks; Ys: 42 rows x 12 chunks
+        for (int i = tid; i < kIn * 4; i += 256) {
+            const int r = i >> 2, c = i & 3;
+            cp_async16(&S.Rn[r][c * 16], s.ref_n + (size_t)(y0 - kHalo + r) * w + x0 - 16 + c * 16);
         }
-        Ns[ty0 + 8 * k][tx] = nu;
-        Ds[ty0 + 8 * k][tx] = de;
-        Wk[ty0 + 8 * k][tx] = de;
-    }
-    const int cx = x0 / 2 + tid % 16, cy = y0 / 2 + tid / 16;
-    const bool c_ok = chroma && cx < cw && cy < ch && (tid % 16) < kTile / 2;
-    float cnu = 0.f, cnv = 0.f, cden = 0.f;
-    __syncthreads();
-    if (c_ok) {
-        const int lx = 2 * (tid % 16), ly = 2 * (tid / 16);
-        const float wb = ((Wk[ly][lx] + Wk[ly][lx + 1]) + (Wk[ly + 1][lx] + Wk[ly + 1][lx + 1])) * 0.25f;
-        const size_t o = (size_t)cy * cw + cx;
-        cnu = wb * ((float)ref_u[o] - 128.f);
-        cnv = wb * ((float)ref_v[o] - 128.f);
-        cden = wb;
-    }
-
-    for (int k = 0; k < args.nsrc; k++) {
-        const MergeSrcDev s = args.src[k];
-        // every global load of this source up front (one round trip): the 42 x 42 halo
-        // (warp w: rows w + 8 r, columns lane and lane + 32), this thread's own 4 source
-        // pixels, its chroma pixel
-        uint8_t hr[12];
-        float hy[12];
-#pragma unroll
-        for (int q = 0; q < 12; q++) {
-            const int yy = warp + 8 * (q >> 1), xx = lane + 32 * (q & 1);
-            hr[q] = 0;
-            hy[q] = 0.f;
-            if (yy < kIn && xx < kIn) {
-                const int gy = clampi(y0 - kHalo + yy, 0, h - 1);
-                const int gx = clampi(x0 - kHalo + xx, 0, w - 1);
-                const size_t o = (size_t)gy * w + gx;
-                hr[q] = s.ref_n[o];
-                hy[q] = s.y[o];
+        for (int i = tid; i < kIn * 12; i += 256) {
+            const int r = i / 12, c = i - r * 12;
+            cp_async16(&S.Ys[r][c * 4], s.y + (size_t)(y0 - kHalo + r) * w + x0 - 8 + c * 4);
+        }
+        if (k == 0 && tid < 64) {
+            const int r = tid >> 1, c = tid & 1;
+            cp_async16(&S.Ry[r][c * 16], ref_y + (size_t)(y0 + r) * w + x0 + c * 16);
+        }
+        if (chroma) {
+            if (k == 0 && tid < 32) {
+                const int r = tid & 15;
+                const uint8_t* src = (tid < 16 ? ref_u : ref_v) + (size_t)(cy0 + r) * cw + cx0;
+                cp_async16(tid < 16 ? &S.Ru[r][0] : &S.Rv[r][0], src);
+            }
+            if (tid >= 64 && tid < 192) {
+                const int q = tid - 64, pl = q >> 6, r = (q >> 2) & 15, c = q & 3;
+                const float* src = (pl ? s.v : s.u) + (size_t)(cy0 + r) * cw + cx0 + c * 4;
+                cp_async16(pl ? &S.Sv[r][c * 4] : &S.Su[r][c * 4], src);
             }
         }
-#pragma unroll
-        for (int kk = 0; kk < 4; kk++) {
-            const int x = x0 + tx, y = y0 + ty0 + 8 * kk;
-            Zs[ty0 + 8 * kk][tx] = (x < w && y < h) ? s.y[(size_t)y * w + x] : 0.f;
+        return;
+    }
+    for (int i = tid; i < kIn * 64; i += 256) {
+        const int r = i >> 6, c = i & 63;
+        const int gy = clampi(y0 - kHalo + r, 0, h - 1), gx = clampi(x0 - 16 + c, 0, w - 1);
+        S.Rn[r][c] = s.ref_n[(size_t)gy * w + gx];
+    }
+    for (int i = tid; i < kIn * 48; i += 256) {
+        const int r = i / 48, c = i - r * 48;
+        const int gy = clampi(y0 - kHalo + r, 0, h - 1), gx = clampi(x0 - 8 + c, 0, w - 1);
+        S.Ys[r][c] = s.y[(size_t)gy * w + gx];
+    }
+    if (k == 0)
+        for (int i = tid; i < kTile * kTile; i += 256) {
+            const int r = i >> 5, c = i & 31;
+            const int gy = y0 + r < h ? y0 + r : h - 1, gx = x0 + c < w ? x0 + c : w - 1;
+            S.Ry[r][c] = ref_y[(size_t)gy * w + gx];
         }
-        float su = 0.f, sv = 0.f;
-        if (c_ok) {
-            const size_t o = (size_t)cy * cw + cx;
-            su = s.u[o];
-            sv = s.v[o];
+    if (chroma && cw > 0 && ch > 0) {
+        const int r = tid >> 4, c = tid & 15;
+        const int gy = cy0 + r < ch ? cy0 + r : ch - 1, gx = cx0 + c < cw ? cx0 + c : cw - 1;
+        const size_t o = (size_t)gy * cw + gx;
+        if (k == 0) {
+            S.Ru[r][c] = ref_u[o];
+            S.Rv[r][c] = ref_v[o];
+        }
+        S.Su[r][c] = s.u[o];
+        S.Sv[r][c] = s.v[o];
+    }
+}
+
+// Persistent CTAs over (tile, source) units in tile order; the next unit's inputs are
+// staged (async copies) while the current one computes.
+__global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ ref_y,
+                                                  const uint8_t* __restrict__ ref_u,
+                                                  const uint8_t* __restrict__ ref_v, int w, int h,
+                                                  MergeArgs args, float* __restrict__ oy,
+                                                  float* __restrict__ ou, float* __restrict__ ov,
+                                                  float* __restrict__ q_out, int async_ok)
+{
+    extern __shared__ __align__(16) uint8_t merge_smem[];
+    MergeSmem& M = *reinterpret_cast<MergeSmem*>(merge_smem);
+    const int tid = threadIdx.x;
+    const bool chroma = ref_u != nullptr && ou != nullptr;
+    const int cw = w / 2, ch = h / 2;
+    const int tiles_x = (w + kTile - 1) / kTile, tiles_y = (h + kTile - 1) / kTile;
+    const int ntiles = tiles_x * tiles_y, ns = args.nsrc;
+    const float2 neg1 = f2(-1.f, -1.f);
+    const float2 gsum2 = f2(args.gsum, args.gsum);
+    const float C1 = (0.01f * 255.f) * (0.01f * 255.f), C2 = (0.03f * 255.f) * (0.03f * 255.f);
+    // this thread's 4 luma pixels: (tx, ty + 8 k); its chroma pixel: (tid % 16, tid / 16)
+    const int tx = tid % kTile, ty0 = tid / kTile;
+    const int ccx = tid % 16, ccy = tid / 16;
+
+    const int my_units = blockIdx.x < ntiles ? ((ntiles - 1 - blockIdx.x) / gridDim.x + 1) * ns : 0;
+    if (my_units == 0) return;
+    merge_stage(M.st[0], args, ref_y, ref_u, ref_v, w, h, chroma, tiles_x, blockIdx.x, 0, async_ok);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    float cnu = 0.f, cnv = 0.f, cden = 0.f;
+    for (int u = 0; u < my_units; u++) {
+        const int t = blockIdx.x + (u / ns) * gridDim.x, k = u % ns;
+        const int x0 = (t % tiles_x) * kTile, y0 = (t / tiles_x) * kTile;
+        if (u + 1 < my_units) {
+            const int t1 = blockIdx.x + ((u + 1) / ns) * gridDim.x, k1 = (u + 1) % ns;
+            merge_stage(M.st[(u + 1) & 1], args, ref_y, ref_u, ref_v, w, h, chroma, tiles_x, t1, k1,
+                        async_ok);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        const MergeStage& S = M.st[u & 1];
+        const MergeSrcDev& s = args.src[k];
+        const int cx = x0 / 2 + ccx, cy = y0 / 2 + ccy;
+        const bool c_ok = chroma && cx < cw && cy < ch;
+        if (k == 0) {  // the reference's own weights open the sums
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int ly = ty0 + 8 * q;
+                const int x = x0 + tx, y = y0 + ly;
+                float nu = 0.f, de = 0.f;
+                if (x < w && y < h) {
+                    const float z = (float)S.Ry[ly][tx];
+                    de = well_exposed(z, args.we_k);
+                    nu = de * z;
+                }
+                M.Ns[ly][tx] = nu;
+                M.Ds[ly][tx] = de;
+                M.Wk[ly][tx] = de;
+            }
+        }
+        for (int i = tid; i < kIn * kIn; i += 256) {
+            const int yy = i / kIn, xx = i - yy * kIn;
+            M.XY[yy][xx] = f2((float)S.Rn[yy][xx + 11], norm_map(s, S.Ys[yy][xx + 3]));
         }
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 12; q++) {
-            const int yy = warp + 8 * (q >> 1), xx = lane + 32 * (q & 1);
-            if (yy < kIn && xx < kIn) XY[yy][xx] = f2((float)hr[q], norm_map(s, hy[q]));
+        if (k == 0) {
+            cnu = cnv = cden = 0.f;
+            if (c_ok) {
+                const int lx = 2 * ccx, ly = 2 * ccy;
+                const float wb =
+                    ((M.Wk[ly][lx] + M.Wk[ly][lx + 1]) + (M.Wk[ly + 1][lx] + M.Wk[ly + 1][lx + 1])) * 0.25f;
+                cnu = wb * ((float)S.Ru[ccy][ccx] - 128.f);
+                cnv = wb * ((float)S.Rv[ccy][ccx] - 128.f);
+                cden = wb;
+            }
         }
-        __syncthreads();
         // Row pass: moments of each 11-tap row segment about its own centre pixel
         // (a = x - x_c, b = y - y_c): M1 = sum g (a, b), M2 = sum g (a^2, b^2), M11 = sum g a b.
         for (int i = tid; i < kIn * kTile; i += 256) {
             const int yy = i / kTile, xx = i % kTile;
-            const float2 c = XY[yy][xx + kHalo];
+            const float2 c = M.XY[yy][xx + kHalo];
             float2 m1 = f2(0.f, 0.f), m2 = f2(0.f, 0.f);
             float m11 = 0.f;
 #pragma unroll
             for (int d = 0; d <= 2 * kHalo; d++) {
                 const float2 g2 = f2(args.g[d], args.g[d]);
-                const float2 ab = __ffma2_rn(c, neg1, XY[yy][xx + d]);
+                const float2 ab = __ffma2_rn(c, neg1, M.XY[yy][xx + d]);
                 const float2 gab = __fmul2_rn(g2, ab);
                 m1 = __fadd2_rn(m1, gab);
                 m2 = __ffma2_rn(gab, ab, m2);
                 m11 = fmaf(gab.x, ab.y, m11);
             }
-            H1[yy][xx] = m1;
-            H2[yy][xx] = m2;
-            H11[yy][xx] = m11;
+            M.H1[yy][xx] = m1;
+            M.H2[yy][xx] = m2;
+            M.H11[yy][xx] = m11;
         }
         __syncthreads();
-        const float C1 = (0.01f * 255.f) * (0.01f * 255.f), C2 = (0.03f * 255.f) * (0.03f * 255.f);
 #pragma unroll 1
-        for (int kk = 0; kk < 4; kk++) {
-            const int ly = ty0 + 8 * kk;
+        for (int q = 0; q < 4; q++) {
+            const int ly = ty0 + 8 * q;
             const int x = x0 + tx, y = y0 + ly;
             // Column pass: re-centre every row's moments from its centre c_r onto the output
             // pixel's value c (delta = c_r - c): sum g (a + delta)^k expands exactly, so the
             // window moments stay small numbers wherever the window is flat.
-            const float2 c = XY[ly + kHalo][tx + kHalo];
+            const float2 c = M.XY[ly + kHalo][tx + kHalo];
             float2 a1 = f2(0.f, 0.f), a2 = f2(0.f, 0.f);
             float a11 = 0.f;
 #pragma unroll
             for (int d = 0; d <= 2 * kHalo; d++) {
                 const float2 g2 = f2(args.g[d], args.g[d]);
-                const float2 dd = __ffma2_rn(c, neg1, XY[ly + d][tx + kHalo]);
-                const float2 m1 = H1[ly + d][tx];
+                const float2 dd = __ffma2_rn(c, neg1, M.XY[ly + d][tx + kHalo]);
+                const float2 m1 = M.H1[ly + d][tx];
                 const float2 r1 = __ffma2_rn(dd, gsum2, m1);
-                const float2 r2 = __ffma2_rn(dd, __fadd2_rn(m1, r1), H2[ly + d][tx]);
-                const float r11 = H11[ly + d][tx] + fmaf(dd.y, m1.x, dd.x * r1.y);
+                const float2 r2 = __ffma2_rn(dd, __fadd2_rn(m1, r1), M.H2[ly + d][tx]);
+                const float r11 = M.H11[ly + d][tx] + fmaf(dd.y, m1.x, dd.x * r1.y);
                 a1 = __ffma2_rn(g2, r1, a1);
                 a2 = __ffma2_rn(g2, r2, a2);
                 a11 = fmaf(args.g[d], r11, a11);
@@ -321,37 +405,41 @@ __global__ void __launch_bounds__(256, 3) k_merge(const uint8_t* __restrict__ re
             const float ux = c.x + a1.x, uy = c.y + a1.y;
             const float ssim = ((2.f * ux * uy + C1) * (2.f * cxy + C2)) /
                                ((ux * ux + uy * uy + C1) * (vx + vy + C2));
-            const float q = ssim > 0.f ? ssim : 0.f;
+            const float qv = ssim > 0.f ? ssim : 0.f;
             float wk = 0.f;
             if (x < w && y < h) {
-                const float z = Zs[ly][tx];
-                wk = well_exposed(z, args.we_k) * q * clip_taper(z);
-                Ns[ly][tx] = fmaf(wk, z * s.inv_ratio, Ns[ly][tx]);
-                Ds[ly][tx] += wk;
-                if (q_out) q_out[(size_t)k * w * h + (size_t)y * w + x] = q;
+                const float z = S.Ys[ly + kHalo][tx + 8];
+                wk = well_exposed(z, args.we_k) * qv * clip_taper(z);
+                M.Ns[ly][tx] = fmaf(wk, z * s.inv_ratio, M.Ns[ly][tx]);
+                M.Ds[ly][tx] += wk;
+                if (q_out) q_out[(size_t)k * w * h + (size_t)y * w + x] = qv;
             }
-            Wk[ly][tx] = wk;
+            M.Wk[ly][tx] = wk;
         }
         __syncthreads();
         if (c_ok) {
-            const int lx = 2 * (tid % 16), ly = 2 * (tid / 16);
+            const int lx = 2 * ccx, ly = 2 * ccy;
             const float wb =
-                ((Wk[ly][lx] + Wk[ly][lx + 1]) + (Wk[ly + 1][lx] + Wk[ly + 1][lx + 1])) * 0.25f;
-            cnu = fmaf(wb, (su - 128.f) * s.inv_ratio, cnu);
-            cnv = fmaf(wb, (sv - 128.f) * s.inv_ratio, cnv);
+                ((M.Wk[ly][lx] + M.Wk[ly][lx + 1]) + (M.Wk[ly + 1][lx] + M.Wk[ly + 1][lx + 1])) * 0.25f;
+            cnu = fmaf(wb, (S.Su[ccy][ccx] - 128.f) * s.inv_ratio, cnu);
+            cnv = fmaf(wb, (S.Sv[ccy][ccx] - 128.f) * s.inv_ratio, cnv);
             cden += wb;
         }
-    }
+        if (k == ns - 1) {
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int x = x0 + tx, y = y0 + ty0 + 8 * k;
-        if (x < w && y < h) oy[(size_t)y * w + x] = Ns[ty0 + 8 * k][tx] / Ds[ty0 + 8 * k][tx];
+            for (int q = 0; q < 4; q++) {
+                const int x = x0 + tx, y = y0 + ty0 + 8 * q;
+                if (x < w && y < h) oy[(size_t)y * w + x] = M.Ns[ty0 + 8 * q][tx] / M.Ds[ty0 + 8 * q][tx];
+            }
+            if (c_ok) {
+                const size_t o = (size_t)cy * cw + cx;
+                ou[o] = cnu / cden;
+                ov[o] = cnv / cden;
+            }
+        }
+        __syncthreads();  // the staging buffer and the sums are reused by the next unit
     }
-    if (c_ok) {
-        const size_t o = (size_t)cy * cw + cx;
-        ou[o] = cnu / cden;
-        ov[o] = cnv / cden;
-    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 }  // namespace
@@ -396,9 +484,20 @@ void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref
     }
     a.gsum = (float)fsum;
     a.we_k = (float)(1.0 / (2.0 * we_sigma * we_sigma));
-    dim3 grid((w + kTile - 1) / kTile, (h + kTile - 1) / kTile);
+    bool async_ok = (w % 32) == 0;  // 16-byte rows for u8 luma and chroma planes
+    auto al = [](const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; };
+    async_ok = async_ok && al(ref_y) && al(ref_u) && al(ref_v);
+    for (int k = 0; k < nsrc; k++)
+        async_ok = async_ok && al(srcs[k].y) && al(srcs[k].u) && al(srcs[k].v) && al(srcs[k].ref_n);
+    const int ntiles = ((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile);
+    const size_t smem = sizeof(MergeSmem);
+    ensure_smem((const void*)k_merge, smem);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
     note_launch();
-    k_merge<<<grid, 256, 0, s>>>(ref_y, ref_u, ref_v, w, h, a, oy, ou, ov, q_out);
+    k_merge<<<grid, 256, smem, s>>>(ref_y, ref_u, ref_v, w, h, a, oy, ou, ov, q_out, async_ok ? 1 : 0);
 }
 
 }  // namespace hdrreg
