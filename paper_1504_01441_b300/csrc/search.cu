@@ -8,10 +8,15 @@
 // image of the region (Sec. 2.2 notes they come cheaply from integral images),
 // built one row, then one column, per thread. The search centre is evaluated in
 // FP32 with a certified interval and in binary64 only when that interval
-// straddles a rounding boundary. The SSD of four pixels is one __vabsdiffu4 + one
-// unsigned __dp4a (exact: |a-b|^2 <= 65025, a 31x31 patch sums to < 2^26); the
-// window words of four neighbouring offsets are funnel shifts by 0, 8, 16, 24 bits
-// of the same two aligned words, so a thread takes four offsets per load. Costs
+// straddles a rounding boundary. The SSD is computed as sum a^2 + sum b_d^2 -
+// 2 sum a b_d in 32-bit unsigned integers (exact: a 31x31 patch sums to < 2^26): the
+// patch energy once, the window energies from sliding box sums, and the cross term
+// of four pixels as one unsigned __dp4a; the window words of four neighbouring
+// offsets are funnel shifts by 0, 8, 16, 24 bits of the same two aligned words, so a
+// thread takes four offsets per load. A tile's CTA is a chain of short dependent
+// phases (staging, integral image, corner pick, centre, window, SSD, argmin), so the
+// kernel is bounded for eight resident CTAs per SM (32 registers; the few spills cost
+// less than the latency they hide). Costs
 // and argmins are exact integers; the argmin key (cost << 16 | row-major index of
 // d) is reduced with warp shuffles.
 #include "hdrreg_internal.cuh"
@@ -80,7 +85,7 @@ __device__ __forceinline__ void stage_block(const uint8_t* __restrict__ img, int
 // shared-memory layout sizes (host and device agree through this helper)
 struct SearchSmem {
     int E, RS, RPW, IS, WS, WW, P, PWc;
-    size_t off_region, off_ii, off_win, off_patch, off_ssd, total;
+    size_t off_region, off_ii, off_win, off_patch, off_ssd, off_hs, total;
     __host__ __device__ SearchSmem(const SearchGeom& g)
     {
         E = g.grid_half * g.step + (g.quad > g.patch_half ? g.quad : g.patch_half);
@@ -102,11 +107,13 @@ struct SearchSmem {
         o += (size_t)P * PWc * 4;
         off_ssd = o;
         o += (size_t)(2 * g.radius + 1) * (2 * g.radius + 1) * 4;
+        off_hs = o;                            // row box sums of squares, WS x (2R+1)
+        o += (size_t)WS * (2 * g.radius + 1) * 4;
         total = o;
     }
 };
 
-__global__ void __launch_bounds__(kThreads) k_local_search(
+__global__ void __launch_bounds__(kThreads, 8) k_local_search(
     const uint8_t* __restrict__ ref, const uint8_t* __restrict__ src, const double* __restrict__ H,
     SearchGeom g, int32_t* __restrict__ corner_xy, int32_t* __restrict__ match_xy,
     uint32_t* __restrict__ cost_out, uint8_t* __restrict__ valid_out,
@@ -124,6 +131,8 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
     uint32_t* win = reinterpret_cast<uint32_t*>(smem + L.off_win);
     uint32_t* patch = reinterpret_cast<uint32_t*>(smem + L.off_patch);
     uint32_t* ssd = reinterpret_cast<uint32_t*>(smem + L.off_ssd);
+    uint32_t* hsq = reinterpret_cast<uint32_t*>(smem + L.off_hs);
+    __shared__ uint32_t s_a2;
 
     const int t = blockIdx.x;
     const int tx = t % g.ntx, ty = t / g.ntx;
@@ -247,7 +256,13 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
             }
         }
     }
-    const uint32_t tail = (P & 3) ? ((1u << (8 * (P & 3))) - 1u) : 0xFFFFFFFFu;
+    __syncthreads();
+    if (warp == 0) {  // sum of squares of the patch (its words are zero past column P)
+        uint32_t a2 = 0;
+        for (int i = lane; i < P * PWc; i += 32) a2 = __dp4a(patch[i], patch[i], a2);
+        for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(kFull, a2, o);
+        if (lane == 0) s_a2 = a2;
+    }
     // Pass 1 of the learned search: offsets [-r, r]^2 around the rounded prediction; the
     // plain search (and the fallback) is one pass over [-R, R]^2 around the centre.
     bool learned = ps.pred != nullptr;
@@ -261,8 +276,38 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
     for (;;) {
         // ---- stage the source window (byte 0 of a row = column ccx - RR - hp)
         const int side_d = 2 * RR + 1, nd = side_d * side_d, nq = (side_d + 3) >> 2;
-        stage_block(src, g.w, g.h, ccx - RR - hp, ccy - RR - hp, 2 * RR + P, 2 * RR + P, win, L.WW);
-        for (int i = tid; i < nd; i += kThreads) ssd[i] = 0u;
+        const int ws = 2 * RR + P;
+        stage_block(src, g.w, g.h, ccx - RR - hp, ccy - RR - hp, ws, ws, win, L.WW);
+        __syncthreads();
+        // ---- sum of squares of every window position: SSD(d) = sum a^2 + sum b_d^2 -
+        //      2 sum a b_d, exact in 32-bit unsigned arithmetic (every term < 2^32).
+        //      Row box sums (one window row per thread, sliding over dx), then column
+        //      box sums (one dx per thread, sliding over dy) start ssd at a^2 + b_d^2.
+        if (tid < ws) {
+            const uint32_t* wr = win + tid * L.WW;
+            auto sq = [&](int c) {
+                const uint32_t b = (wr[c >> 2] >> (8 * (c & 3))) & 255u;
+                return b * b;
+            };
+            uint32_t run = 0;
+            for (int c = 0; c < P; c++) run += sq(c);
+            hsq[tid * side_d] = run;
+            for (int dx = 1; dx < side_d; dx++) {
+                run += sq(dx + P - 1) - sq(dx - 1);
+                hsq[tid * side_d + dx] = run;
+            }
+        }
+        __syncthreads();
+        if (tid < side_d) {
+            uint32_t run = 0;
+            for (int r = 0; r < P; r++) run += hsq[r * side_d + tid];
+            const uint32_t a2 = s_a2;
+            ssd[tid] = a2 + run;
+            for (int dy = 1; dy < side_d; dy++) {
+                run += hsq[(dy + P - 1) * side_d + tid] - hsq[(dy - 1) * side_d + tid];
+                ssd[dy * side_d + tid] = a2 + run;
+            }
+        }
         __syncthreads();
 
         // ---- SSD over d in [-RR, RR]^2, exact unsigned integers. A thread takes four
@@ -282,26 +327,21 @@ __global__ void __launch_bounds__(kThreads) k_local_search(
                     const uint32_t* wr = win + (dy + v) * L.WW + dq;
                     uint32_t cur = wr[0];
 #pragma unroll 8
-                    for (int j = 0; j < PWc; j++) {
+                    for (int j = 0; j < PWc; j++) {  // cross terms sum a b_d
                         const uint32_t nxt = wr[j + 1], pv = pr[j];
-                        const uint32_t m = j == PWc - 1 ? tail : 0xFFFFFFFFu;
-                        uint32_t d;
-                        d = __vabsdiffu4(pv, cur & m);
-                        acc0 = __dp4a(d, d, acc0);
-                        d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 8) & m);
-                        acc1 = __dp4a(d, d, acc1);
-                        d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 16) & m);
-                        acc2 = __dp4a(d, d, acc2);
-                        d = __vabsdiffu4(pv, __funnelshift_r(cur, nxt, 24) & m);
-                        acc3 = __dp4a(d, d, acc3);
+                        acc0 = __dp4a(pv, cur, acc0);
+                        acc1 = __dp4a(pv, __funnelshift_r(cur, nxt, 8), acc1);
+                        acc2 = __dp4a(pv, __funnelshift_r(cur, nxt, 16), acc2);
+                        acc3 = __dp4a(pv, __funnelshift_r(cur, nxt, 24), acc3);
                         cur = nxt;
                     }
                 }
+                // ssd -= 2 sum a b_d (modulo 2^32; the final value is the exact SSD)
                 const int dx0 = 4 * dq, base = dy * side_d + dx0;
-                atomicAdd(&ssd[base], acc0);
-                if (dx0 + 1 < side_d) atomicAdd(&ssd[base + 1], acc1);
-                if (dx0 + 2 < side_d) atomicAdd(&ssd[base + 2], acc2);
-                if (dx0 + 3 < side_d) atomicAdd(&ssd[base + 3], acc3);
+                atomicAdd(&ssd[base], 0u - 2u * acc0);
+                if (dx0 + 1 < side_d) atomicAdd(&ssd[base + 1], 0u - 2u * acc1);
+                if (dx0 + 2 < side_d) atomicAdd(&ssd[base + 2], 0u - 2u * acc2);
+                if (dx0 + 3 < side_d) atomicAdd(&ssd[base + 3], 0u - 2u * acc3);
             }
         }
         __syncthreads();
