@@ -171,7 +171,7 @@ struct PyrArgs {
 
 __global__ void __launch_bounds__(256) k_pyramid(PyrArgs a)
 {
-    extern __shared__ uint8_t sm[];
+    extern __shared__ __align__(16) uint8_t sm[];
     __shared__ uint8_t lut[256];
     const int f = blockIdx.z;
     build_lut(lut, a.lut[f]);
@@ -179,21 +179,45 @@ __global__ void __launch_bounds__(256) k_pyramid(PyrArgs a)
     const int S = a.S;
     const int x0 = blockIdx.x * S, y0 = blockIdx.y * S;
     uint8_t* cur = sm;
-    // level 0: S x S, zero outside the frame
-    for (int i = threadIdx.x; i < S * S / 4; i += blockDim.x) {
-        const int yy = (i * 4) / S, xx = (i * 4) % S;
-        const int gy = y0 + yy;
-        uint32_t word = 0;
-        for (int k = 0; k < 4; k++) {
-            const int gx = x0 + xx + k;
-            uint32_t v = 0;
-            if (gx < a.w && gy < a.h) {
-                v = lut[a.in0[f][(size_t)gy * a.w + gx]];
-                if (a.out0[f]) a.out0[f][(size_t)gy * a.w + gx] = (uint8_t)v;
+    // level 0: S x S, zero outside the frame; 16 pixels per item, one 16-byte load and
+    // store where the row segment lies inside the frame and the addresses are aligned
+    const uint8_t* in = a.in0[f];
+    uint8_t* out0 = a.out0[f];
+    const bool vec = (a.w & 15) == 0 && ((uintptr_t)in & 15) == 0 &&
+                     (out0 == nullptr || ((uintptr_t)out0 & 15) == 0);
+    for (int i = threadIdx.x; i < S * S / 16; i += blockDim.x) {
+        const int yy = i / (S / 16), xx = (i % (S / 16)) * 16;
+        const int gy = y0 + yy, gx0 = x0 + xx;
+        uint32_t wd[4];
+        if (vec && gy < a.h && gx0 + 16 <= a.w) {
+            const size_t o = (size_t)gy * a.w + gx0;
+            const uint4 v = *reinterpret_cast<const uint4*>(in + o);
+            const uint32_t src[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                uint32_t r = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) r |= (uint32_t)lut[(src[q] >> (8 * k)) & 255u] << (8 * k);
+                wd[q] = r;
             }
-            word |= v << (8 * k);
+            if (out0) *reinterpret_cast<uint4*>(out0 + o) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                uint32_t r = 0;
+                for (int k = 0; k < 4; k++) {
+                    const int gx = gx0 + 4 * q + k;
+                    uint32_t v = 0;
+                    if (gx < a.w && gy < a.h) {
+                        v = lut[in[(size_t)gy * a.w + gx]];
+                        if (out0) out0[(size_t)gy * a.w + gx] = (uint8_t)v;
+                    }
+                    r |= v << (8 * k);
+                }
+                wd[q] = r;
+            }
         }
-        reinterpret_cast<uint32_t*>(cur)[i] = word;
+        *reinterpret_cast<uint4*>(cur + yy * S + xx) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
     }
     __syncthreads();
     int side = S;
@@ -202,14 +226,40 @@ __global__ void __launch_bounds__(256) k_pyramid(PyrArgs a)
         uint8_t* nxt = cur + side * side;
         const int lw = a.w >> l, lh = a.h >> l;
         const int bx = (x0 >> l), by = (y0 >> l);
-        for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) {
-            const int yy = i / ns, xx = i % ns;
-            const int s = cur[(2 * yy) * side + 2 * xx] + cur[(2 * yy) * side + 2 * xx + 1] +
-                          cur[(2 * yy + 1) * side + 2 * xx] + cur[(2 * yy + 1) * side + 2 * xx + 1];
-            const uint8_t v = (uint8_t)((s + 2) >> 2);
-            nxt[i] = v;
-            const int gx = bx + xx, gy = by + yy;
-            if (gx < lw && gy < lh) a.lv[f][l][(size_t)gy * lw + gx] = v;
+        uint8_t* lvo = a.lv[f][l];
+        const bool vec4 = (lw & 3) == 0 && ((uintptr_t)lvo & 3) == 0 && (ns & 3) == 0;
+        if (vec4) {  // four output pixels per item, one 4-byte store
+            for (int i = threadIdx.x; i < ns * ns / 4; i += blockDim.x) {
+                const int yy = i / (ns / 4), xx = (i % (ns / 4)) * 4;
+                const uint8_t* r0 = cur + (2 * yy) * side + 2 * xx;
+                const uint8_t* r1 = r0 + side;
+                uint32_t word = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int s = r0[2 * k] + r0[2 * k + 1] + r1[2 * k] + r1[2 * k + 1];
+                    word |= (uint32_t)((s + 2) >> 2) << (8 * k);
+                }
+                *reinterpret_cast<uint32_t*>(nxt + yy * ns + xx) = word;
+                const int gx = bx + xx, gy = by + yy;
+                if (gy < lh) {
+                    if (gx + 4 <= lw) {
+                        *reinterpret_cast<uint32_t*>(lvo + (size_t)gy * lw + gx) = word;
+                    } else {
+                        for (int k = 0; k < 4 && gx + k < lw; k++)
+                            lvo[(size_t)gy * lw + gx + k] = (uint8_t)(word >> (8 * k));
+                    }
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) {
+                const int yy = i / ns, xx = i % ns;
+                const int s = cur[(2 * yy) * side + 2 * xx] + cur[(2 * yy) * side + 2 * xx + 1] +
+                              cur[(2 * yy + 1) * side + 2 * xx] + cur[(2 * yy + 1) * side + 2 * xx + 1];
+                const uint8_t v = (uint8_t)((s + 2) >> 2);
+                nxt[i] = v;
+                const int gx = bx + xx, gy = by + yy;
+                if (gx < lw && gy < lh) lvo[(size_t)gy * lw + gx] = v;
+            }
         }
         __syncthreads();
         cur = nxt;
