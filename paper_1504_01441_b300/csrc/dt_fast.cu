@@ -235,6 +235,28 @@ __device__ __forceinline__ Aff seg_scan(Aff mine, Aff (*tot)[kCols], int col)
     return compose(pre, exc);
 }
 
+// ------------------------------------------------------ corner records
+// One record per level-0 tile for the first row pass: {x, y, residual u, residual v}
+// of its kept corner (y = -1 without one). The residual is q - H(p) (q - p when the
+// full displacement is propagated), evaluated in binary64 and rounded to FP32 once.
+__global__ void k_flow_corner_records(FlowCorners fc, int w, int h, int4* __restrict__ rec)
+{
+    const int n = fc.ntx * fc.nty;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int4 r = make_int4(0, -1, 0, 0);
+        if ((fc.mask[t >> 5] >> (t & 31)) & 1u) {
+            const int cx = fc.corner_xy[2 * t], cy = fc.corner_xy[2 * t + 1];
+            double bx = (double)cx, by = (double)cy;
+            bool ok = true;
+            if (!fc.full) ok = project_px(fc.H, cx, cy, w, h, bx, by);
+            if (ok)
+                r = make_int4(cx, cy, __float_as_int((float)((double)fc.match_xy[2 * t] - bx)),
+                              __float_as_int((float)((double)fc.match_xy[2 * t + 1] - by)));
+        }
+        rec[t] = r;
+    }
+}
+
 // ---------------------------------------------------------------- row pass
 // Persistent, double-buffered row pass: each CTA walks
 // rows y = blockIdx.x + k * gridDim.x; while row k computes, row k+1 is loading
@@ -245,7 +267,8 @@ __global__ void __launch_bounds__(kRowNT, 3) k_dt_rows_pipe(float* __restrict__ 
                                                          float* __restrict__ P2,
                                                          const uint8_t* __restrict__ guide,
                                                          int w, int h, DtLut lut_in,
-                                                         FlowCorners fc, int* err)
+                                                         FlowCorners fc,
+                                                         const int4* __restrict__ rec, int* err)
 {
     extern __shared__ __align__(128) float sm[];
     __shared__ float lut[256];
@@ -277,9 +300,18 @@ __global__ void __launch_bounds__(kRowNT, 3) k_dt_rows_pipe(float* __restrict__ 
     uint32_t ph0 = 0, ph1 = 0;
     int y = blockIdx.x;
     if (y < h) issue(y, 0);
+    // first pass: this thread's corner record (tile column tid) of the current row's tile
+    // row, loaded one row ahead
+    auto rec_of = [&](int yy) {
+        const int ty = yy / fc.tile;
+        return (kSparse && yy < h && ty < fc.nty && tid < fc.ntx) ? rec[ty * fc.ntx + tid]
+                                                                  : make_int4(0, -1, 0, 0);
+    };
+    int4 rc = rec_of(y);
     for (int k = 0; y < h; y += gridDim.x, k++) {
         const int b = k & 1;
         const int yn = y + gridDim.x;
+        const int4 rc_next = rec_of(yn);
         if (yn < h) {
             if (tid == 0) bulk_wait_read();  // the store of row k-1 has left buffer 1-b
             issue(yn, 1 - b);
@@ -310,20 +342,11 @@ __global__ void __launch_bounds__(kRowNT, 3) k_dt_rows_pipe(float* __restrict__ 
             const int ty = y / fc.tile;
             if (ty < fc.nty) {
                 for (int tx = tid; tx < fc.ntx; tx += kRowNT) {
-                    const int t = ty * fc.ntx + tx;
-                    if (!((fc.mask[t >> 5] >> (t & 31)) & 1u)) continue;
-                    if (fc.corner_xy[2 * t + 1] != y) continue;
-                    const int cx = fc.corner_xy[2 * t];
-                    double bx = (double)cx, by = (double)y;
-                    if (!fc.full) {
-                        double xs, ys;
-                        if (!project_px(fc.H, cx, y, w, h, xs, ys)) continue;
-                        bx = xs;
-                        by = ys;
-                    }
-                    s0[cx] = (float)((double)fc.match_xy[2 * t] - bx);
-                    s1[cx] = (float)((double)fc.match_xy[2 * t + 1] - by);
-                    s2[cx] = 1.f;
+                    const int4 c = tx == tid ? rc : rec[ty * fc.ntx + tx];
+                    if (c.y != y) continue;
+                    s0[c.x] = __int_as_float(c.z);
+                    s1[c.x] = __int_as_float(c.w);
+                    s2[c.x] = 1.f;
                 }
             }
             __syncthreads();
@@ -367,6 +390,7 @@ __global__ void __launch_bounds__(kRowNT, 3) k_dt_rows_pipe(float* __restrict__ 
             bulk_store(P2 + row, s2, w * 4);
             bulk_commit();
         }
+        rc = rc_next;
     }
     if (tid == 0) bulk_wait_read();
 }
@@ -711,7 +735,8 @@ void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int 
 
 template <int LM>
 void launch_rows_pipe(int first, float* P0, float* P1, float* P2, const uint8_t* guide, int w,
-                      int h, const DtLut& lut, const FlowCorners& fc, int* err, cudaStream_t s)
+                      int h, const DtLut& lut, const FlowCorners& fc, const int4* rec, int* err,
+                      cudaStream_t s)
 {
     const size_t smem = 2 * ((size_t)3 * kRowNT * LM * 4 + (size_t)kRowNT * LM);
     const int per_sm = (int)((225 * 1024) / (smem + 2048));
@@ -719,10 +744,12 @@ void launch_rows_pipe(int first, float* P0, float* P1, float* P2, const uint8_t*
     note_launch();
     if (first) {
         ensure_smem((const void*)k_dt_rows_pipe<LM, true>, smem);
-        k_dt_rows_pipe<LM, true><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, lut, fc, err);
+        k_dt_rows_pipe<LM, true><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, lut, fc, rec,
+                                                             err);
     } else {
         ensure_smem((const void*)k_dt_rows_pipe<LM, false>, smem);
-        k_dt_rows_pipe<LM, false><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, lut, fc, err);
+        k_dt_rows_pipe<LM, false><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, lut, fc,
+                                                              rec, err);
     }
 }
 
@@ -742,11 +769,15 @@ bool flow_fast_supported(int w, int h, const uint8_t* guide, const float* fu, co
 
 // The six passes of the flow on the fast path; `ws` holds the three planes and,
 // after them, the error word.
+// Records of the first row pass: at most one per 8 x 8 level-0 tile (tiles are >= 8 px).
+size_t corner_rec_bytes(int w, int h) { return align_up((size_t)(w / 8 + 1) * (h / 8 + 1) * 16, 256); }
+
 size_t flow_fast_extra_bytes(int w, int h)
 {
     const size_t ntile = (size_t)((h + kTR - 1) / kTR);
     const size_t wp = (size_t)((w + kTW - 1) / kTW) * kTW;
-    return align_up((size_t)kAgg * ntile * wp * 4, 256) + align_up((size_t)kCar * ntile * wp * 4, 256);
+    return align_up((size_t)kAgg * ntile * wp * 4, 256) + align_up((size_t)kCar * ntile * wp * 4, 256) +
+           corner_rec_bytes(w, h);
 }
 
 bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc, const DtLut* luts,
@@ -758,6 +789,15 @@ bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc,
     float* agg = static_cast<float*>(extra);
     float* car = reinterpret_cast<float*>(static_cast<uint8_t*>(extra) +
                                           align_up((size_t)kAgg * ntile * wp * 4, 256));
+    int4* rec = reinterpret_cast<int4*>(static_cast<uint8_t*>(extra) +
+                                        align_up((size_t)kAgg * ntile * wp * 4, 256) +
+                                        align_up((size_t)kCar * ntile * wp * 4, 256));
+    {
+        const int n = fc.ntx * fc.nty;
+        if ((size_t)n * 16 > corner_rec_bytes(w, h)) return false;
+        note_launch();
+        k_flow_corner_records<<<n > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(fc, w, h, rec);
+    }
     ColMaps mid, fin;
     if (!make_map(&mid.in[0], P0, w, h, 4) || !make_map(&mid.in[1], P1, w, h, 4) ||
         !make_map(&mid.in[2], P2, w, h, 4) || !make_map(&mid.guide, guide, w, h, 1, kGRows))
@@ -773,15 +813,15 @@ bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc,
         const DtLut& lut = luts[i];
         const int first = i == 0;
         switch (Lr) {
-            case 1: launch_rows_pipe<1>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
-            case 3: launch_rows_pipe<3>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
-            case 5: launch_rows_pipe<5>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
-            case 7: launch_rows_pipe<7>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
-            case 9: launch_rows_pipe<9>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
-            case 11: launch_rows_pipe<11>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
-            case 13: launch_rows_pipe<13>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
-            case 15: launch_rows_pipe<15>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
-            default: launch_rows_pipe<17>(first, P0, P1, P2, guide, w, h, lut, fc, err, s); break;
+            case 1: launch_rows_pipe<1>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 3: launch_rows_pipe<3>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 5: launch_rows_pipe<5>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 7: launch_rows_pipe<7>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 9: launch_rows_pipe<9>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 11: launch_rows_pipe<11>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 13: launch_rows_pipe<13>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 15: launch_rows_pipe<15>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            default: launch_rows_pipe<17>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
         }
         launch_cols_tiles((i == iters - 1) ? fin : mid, w, h, lut, i == iters - 1, (float)flow_eps,
                           agg, car, err, s);
