@@ -382,11 +382,9 @@ def measure_stages(torch, hdrreg, p, stack, dev, args):
     return {k: round(v, 2) for k, v in out.items()}
 
 
-# DRAM bytes of one flow call (2592 x 1944, 3 iterations) from the ncu capture in
-# profiles/dt_passes_5mp.md: first row pass 5.2 + 3.5 MB, two row passes 65.5 + 3.6 MB each,
-# three tile-map passes 65.5 + 0.7, three carry chains 2.9, three apply passes 67.5 + 3.9.
-FLOW_TRAFFIC = int((5.2 + 3.5 + 2 * (65.5 + 3.6) + 3 * (65.5 + 0.7) + 3 * 2.9 +
-                    3 * (67.5 + 3.9)) * 1e6)
+# DRAM bytes of one flow call (2592 x 1944, 3 iterations, 13 launches) from the ncu
+# capture summarised in profiles/flow_dram_5mp.md.
+FLOW_TRAFFIC = 555168000
 
 
 def measure_flow_roofline(stages, p):
@@ -397,8 +395,8 @@ def measure_flow_roofline(stages, p):
     return {"kernel": "flow: 6 domain-transform passes (row pass + 3-phase column pass)",
             "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "peak_source": src,
             "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": FLOW_TRAFFIC,
-            "traffic_source": "profiles/dt_passes_5mp.md: dram__bytes_read.sum + "
-                              "dram__bytes_write.sum of the stage's 11 launches (ncu, cold L2)",
+            "traffic_source": "profiles/flow_dram_5mp.md: dram__bytes_read.sum + "
+                              "dram__bytes_write.sum of the stage's 13 launches (ncu, cold L2)",
             "algorithmic_bytes_per_launch": algo, "us_per_launch": round(stages["flow"], 2),
             "timing": "CUDA graph replay of hdrreg_flow_upsample on one 5 MP pair"}
 
