@@ -707,7 +707,7 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
                     Hw, fu, fv, wy, chroma ? wu : nullptr, chroma ? wv : nullptr, s);
         if (diag) {
             note_launch();
-            k_diag<<<1, 256, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L,
+            k_diag<<<1, 1024, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L,
                                      lay.learned ? at(lay.fellback) : nullptr, diag + k);
         }
         md[k].y = wy;
