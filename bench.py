@@ -8,6 +8,7 @@ one CUDA graph. Prints one JSON line (see the keys below).
 
   python bench.py --gpus N --steps K --warmup W [--impl reference]
   python bench.py --workload mixed64    # 64 stacks of 1-12 MP, 2-3 frames, tuned (T, R)
+  python bench.py --workload sweep      # one pair per size, VGA .. 20 MP (scaling)
 
 Under torchrun each rank (one GPU) registers its own batch of stacks: stacks
 are independent, so the ranks are replicas with no data-path collective; the
@@ -32,6 +33,7 @@ WORKLOAD = "5mp_yuv420_pair"
 W, H = 2592, 1944
 MIXED = "mixed64"                       # command-line name of the mixed batch
 MIXED_NAME = "mixed64_1to12mp_yuv420"
+SWEEP = "sweep"
 MIXED_METRIC = "registered+merged output Mpix/s per B300 (64 stacks of 1-12 MP, 2-3 frames)"
 
 
@@ -48,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short run for a profiler")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED, SWEEP],
                     help="the 5 MP pair batch (default) or the mixed 1-12 MP batch")
     ap.add_argument("--stacks", type=int, default=64, help="stacks of the mixed batch")
     return ap.parse_args()
@@ -615,6 +617,54 @@ def measure_mixed_cpu_baseline(synth, stacks, table, n=4):
                       f"({mpix:.2f} output Mpix, {sec:.1f} s)"}
 
 
+# ------------------------------------------------------------ scaling sweep (f3)
+def run_sweep(args):
+    """Registration + merge time of one two-frame YUV420 pair per size, VGA to 20 MP (the
+    paper's runtime-vs-size claim, Sec. 4): the latency of one pair (its graph replayed
+    alone) and the throughput of `lanes` copies of it on concurrent lanes. value = the
+    log-log slope of the latency against the pixel count (1 = linear)."""
+    import math
+    stacks = synth_sweep()
+    import torch
+    from paper_1504_01441_b300 import autotune, hdrreg, synth
+    dev = torch.device("cuda", 0)
+    p = hdrreg.params_from_dict(synth.method_params(32, 6))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rows = []
+    for st in stacks:
+        lat = autotune.fused_time_us(st, p, reps=max(args.steps, 3), device=dev, flush=flush, lanes=1)
+        thr = autotune.fused_time_us(st, p, reps=max(args.steps, 3), device=dev, flush=flush,
+                                     lanes=args.lanes)
+        mp = st.width * st.height / 1e6
+        rows.append({"width": st.width, "height": st.height, "mpix": round(mp, 3),
+                     "latency_us": round(lat, 1), "batched_us_per_pair": round(thr, 1),
+                     "batched_mpix_s": round(mp / (thr / 1e6), 1)})
+        torch.cuda.empty_cache()
+    xs = [math.log(r["mpix"]) for r in rows]
+    ys = [math.log(r["latency_us"]) for r in rows]
+    zs = [math.log(r["batched_us_per_pair"]) for r in rows]
+
+    def slope(a, b):
+        ma, mb = sum(a) / len(a), sum(b) / len(b)
+        return sum((u - ma) * (v - mb) for u, v in zip(a, b)) / sum((u - ma) ** 2 for u in a)
+    line = {
+        "metric": "scaling: d log(latency) / d log(pixels), one 2-frame YUV420 pair, VGA..20 MP",
+        "value": round(slope(xs, ys), 3), "unit": "exponent (1 = linear)", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "scaling": "none", "vs_baseline": None, "data": "synthetic",
+        "dtype": "u8/i32 match, f64 fit, f32 flow/warp/merge",
+        "config": {"workload": "sweep_vga_to_20mp_yuv420_pair", "tile": 32, "radius": 6,
+                   "lanes": args.lanes, "l2": "L2 flushed (256 MB write) before every replay"},
+        "batched_slope": round(slope(xs, zs), 3), "sweep": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def synth_sweep():
+    from paper_1504_01441_b300 import synth
+    return synth.make_sweep_stacks()
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     ws, rank, local = dist_env()
@@ -695,6 +745,8 @@ def main():
         run_reference(args)
     elif args.workload == MIXED:
         run_mixed(args)
+    elif args.workload == SWEEP:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -262,7 +262,7 @@ __global__ void k_flow_corner_records(FlowCorners fc, int w, int h, int4* __rest
 // rows y = blockIdx.x + k * gridDim.x; while row k computes, row k+1 is loading
 // into the other buffer and row k-1 is storing.
 template <int LM, bool kSparse>
-__global__ void __launch_bounds__(kRowNT, 3) k_dt_rows_pipe(float* __restrict__ P0,
+__global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float* __restrict__ P0,
                                                          float* __restrict__ P1,
                                                          float* __restrict__ P2,
                                                          const uint8_t* __restrict__ guide,
@@ -763,7 +763,7 @@ bool flow_fast_supported(int w, int h, const uint8_t* guide, const float* fu, co
     if (w % 16 != 0 || w < 32 || h < 2) return false;
     if (((uintptr_t)guide % 16) != 0 || ((uintptr_t)fu % 16) != 0 || ((uintptr_t)fv % 16) != 0)
         return false;
-    if (row_L(w) > 17 || 2 * row_fast_smem(w) > kFastBudget) return false;
+    if (row_L(w) > 23 || 2 * row_fast_smem(w) > kFastBudget) return false;
     return encode_fn() != nullptr;
 }
 
@@ -821,7 +821,10 @@ bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc,
             case 11: launch_rows_pipe<11>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
             case 13: launch_rows_pipe<13>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
             case 15: launch_rows_pipe<15>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            default: launch_rows_pipe<17>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 17: launch_rows_pipe<17>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 19: launch_rows_pipe<19>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 21: launch_rows_pipe<21>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            default: launch_rows_pipe<23>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
         }
         launch_cols_tiles((i == iters - 1) ? fin : mid, w, h, lut, i == iters - 1, (float)flow_eps,
                           agg, car, err, s);

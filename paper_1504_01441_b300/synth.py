@@ -378,6 +378,32 @@ def make_mixed_stack(stack_index: int, config_index: int = 3, with_gt: bool = Fa
                       stack_seed(config_index, stack_index))
 
 
+# Sizes of the scaling sweep: 4:3 frames from VGA to 20 MP (widths multiples of 32).
+SWEEP_SIZES = ((640, 480), (1280, 960), (1600, 1200), (2048, 1536), (2592, 1944), (3264, 2448),
+               (4000, 3000), (4608, 3456), (5184, 3888))
+
+
+def sweep_spec(w: int, h: int) -> StackSpec:
+    """The headline pair recipe (ratio 4, noise 1.5 DN, +-4 px fields, 3 movers, YUV420)
+    at another size."""
+    return dataclasses.replace(FIVE_MP, width=w, height=h, with_gt=False)
+
+
+def make_sweep_stack(w: int, h: int) -> Stack:
+    return make_stack(sweep_spec(w, h), stack_seed(6, w))
+
+
+def make_sweep_stacks(sizes=SWEEP_SIZES, processes=None):
+    """make_sweep_stack for every size in a spawn-started process pool."""
+    import multiprocessing as mp
+    import os
+    n = processes or min(len(sizes), os.cpu_count() or 1)
+    if n <= 1:
+        return [make_sweep_stack(w, h) for w, h in sizes]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.starmap(make_sweep_stack, sizes)
+
+
 def make_stacks_parallel(jobs, processes=None):
     """make_mixed_stack over (stack_index, config_index, with_gt) jobs in a spawn-started
     process pool (safe after CUDA is initialized); returns the stacks in job order."""
