@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED, SWEEP],
                     help="the 5 MP pair batch (default) or the mixed 1-12 MP batch")
     ap.add_argument("--stacks", type=int, default=64, help="stacks of the mixed batch")
+    ap.add_argument("--preset", default="workload", choices=["workload", "paper"],
+                    help="the headline workload's parameters (T=32, R=6, ratio normalization) "
+                         "or the paper-exact preset (histogram equalization, R=10, the whole "
+                         "displacement propagated)")
     return ap.parse_args()
 
 
@@ -162,7 +166,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stacks = make_inputs(args.distinct)
-    p = hdrreg.params_from_dict(synth.method_params(32, 6))
+    if args.preset == "paper":
+        p = hdrreg.params_paper()
+    else:
+        p = hdrreg.params_from_dict(synth.method_params(32, 6))
     P = args.pairs
     # resident inputs: P distinct device buffers (contents cycle over the generated stacks)
     frames = []
@@ -215,7 +222,7 @@ def run_ours(args):
         roof = measure_flow_roofline(stages, p)
     # -- the learned level-0 search (row a-L) on the same resident pairs
     learned = None
-    if rank == 0 and not args.no_learned and not args.profile:
+    if rank == 0 and not args.no_learned and not args.profile and args.preset == "workload":
         learned = measure_learned(torch, hdrreg, synth, stacks, frames, p, dev, args)
     # -- end to end through the C ABI with host buffers (pinned), copies inside the timing
     e2e = None
@@ -223,7 +230,7 @@ def run_ours(args):
         e2e = measure_e2e(torch, hdrreg, p, stacks, dev, P, args)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.profile:
-        cpu = measure_cpu_baseline(synth, stacks[0])
+        cpu = measure_cpu_baseline(synth, stacks[0], cfg=p.as_dict())
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws,
@@ -232,7 +239,9 @@ def run_ours(args):
             "dtype": "u8/i32 match, f64 fit, f32 flow/warp/merge", "data": "synthetic",
             "config": {"workload": WORKLOAD, "width": W, "height": H, "format": "YUV420",
                        "frames": 2, "exposure_ratio": 4, "pairs_per_step": P,
-                       "distinct_stacks": len(stacks), "tile": 32, "radius": 6,
+                       "distinct_stacks": len(stacks), "tile": p.tile, "radius": p.radius,
+                       "preset": args.preset, "norm_mode": "histeq" if p.norm_mode else "ratio",
+                       "propagate_full": p.propagate_full,
                        "path": "plain (a1-a11)", "graph": True, "lanes": args.lanes,
                        "l2": f"inputs larger than L2: {P} resident pairs x 15.1 MB per step",
                        "parallelism": f"replicas x{ws}"},
@@ -346,9 +355,10 @@ def measure_stages(torch, hdrreg, p, stack, dev, args):
     refu = torch.from_numpy(stack.ref.u).to(dev)
     refv = torch.from_numpy(stack.ref.v).to(dev)
     out = {}
-    rn, sn, _ = hdrreg.normalize_exposure(ref, src, hdrreg.NORM_RATIO, stack.ratios[0])
+    mode = p.norm_mode
+    rn, sn, luts = hdrreg.normalize_exposure(ref, src, mode, stack.ratios[0])
     out["normalize"] = _graph_time_us(
-        torch, lambda: hdrreg.normalize_exposure(ref, src, hdrreg.NORM_RATIO, stack.ratios[0]), reps)
+        torch, lambda: hdrreg.normalize_exposure(ref, src, mode, stack.ratios[0]), reps)
     L = hdrreg.num_levels(W, H, p)
     out["pyramid"] = _graph_time_us(torch, lambda: (hdrreg.build_pyramid(rn, L),
                                                     hdrreg.build_pyramid(sn, L)), reps)
@@ -379,7 +389,7 @@ def measure_stages(torch, hdrreg, p, stack, dev, args):
         torch, lambda: hdrreg.flow_upsample(rn, res["cxy"], res["mxy"], res["mask"], res["H"], p), reps)
     wy, wu, wv = hdrreg.warp(src, srcu, srcv, res["H"], fu, fv)
     out["warp"] = _graph_time_us(torch, lambda: hdrreg.warp(src, srcu, srcv, res["H"], fu, fv), reps)
-    srcs = [dict(y=wy, u=wu, v=wv, ref_n=rn, ratio=stack.ratios[0])]
+    srcs = [dict(y=wy, u=wu, v=wv, ref_n=rn, ratio=stack.ratios[0], lut=luts[1])]
     out["merge"] = _graph_time_us(torch, lambda: hdrreg.merge(ref, refu, refv, srcs, p), reps)
     return {k: round(v, 2) for k, v in out.items()}
 
@@ -442,10 +452,10 @@ def measure_e2e(torch, hdrreg, p, stacks, dev, P, args):
             "api": "hdrreg_register_merge_host (pinned host planes in and out)"}
 
 
-def measure_cpu_baseline(synth, stack, runs=3):
+def measure_cpu_baseline(synth, stack, runs=3, cfg=None):
     import oracle
     oracle.build()
-    cfg = synth.method_params(32, 6)
+    cfg = cfg or synth.method_params(32, 6)
     t0 = time.perf_counter()
     for _ in range(runs):
         oracle.register_merge(stack.ref, stack.srcs, stack.ratios, cfg)

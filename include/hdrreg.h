@@ -63,8 +63,12 @@ typedef enum hdrreg_status {
 /*
  * Method parameters. hdrreg_params_default() fills the paper's values where
  * the paper gives them (Sec. 2.6: 21x21 patches, search radius 10, up to 5
- * levels, levels >= 100 px, candidate grid spacing T/16, sigma_s = 400) and
- * this library's readings of its silences elsewhere.
+ * levels, levels >= 100 px, candidate grid spacing T/16, sigma_s = 400; the
+ * frames' histograms equalized before matching, Sec. 3) and this library's
+ * readings of its silences elsewhere, among them that the flow carries the residual
+ * to the level-0 homography (dense map H0 + F). hdrreg_params_paper() is the same
+ * with the paper's literal propagation (the corners' whole displacement q - p is
+ * spread, Sec. 2.4; the homography is then used only to seed the matcher).
  */
 typedef struct hdrreg_params {
     int tile;             /* T: tile side in pixels of the level, 8..128, even          */
@@ -138,6 +142,7 @@ typedef struct hdrreg_diag {
 
 /* ---------------------------------------------------------------- misc */
 void hdrreg_params_default(hdrreg_params* p);
+void hdrreg_params_paper(hdrreg_params* p);
 const char* hdrreg_last_error(void);
 const char* hdrreg_version(void);
 /* Number of kernels this library has enqueued in this process (host counter,

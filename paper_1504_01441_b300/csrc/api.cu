@@ -229,7 +229,7 @@ void hdrreg_params_default(hdrreg_params* p)
     p->weed_iters = 512;
     p->weed_delta_min = 8;
     p->weed_delta_div = 20;
-    p->norm_mode = HDRREG_NORM_RATIO;
+    p->norm_mode = HDRREG_NORM_HISTEQ;
     p->dt_iters = 3;
     p->ssim_radius = 5;
     p->propagate_full = 0;
@@ -242,6 +242,13 @@ void hdrreg_params_default(hdrreg_params* p)
     p->weed_seed = 0x1504014410ull;
     p->predictor = nullptr;
     p->fallback_cost = 0u;
+}
+
+void hdrreg_params_paper(hdrreg_params* p)
+{
+    if (!p) return;
+    hdrreg_params_default(p);
+    p->propagate_full = 1;
 }
 
 hdrreg_status hdrreg_validate_params(const hdrreg_params* p)

@@ -78,22 +78,53 @@ void launch_lut2(const uint8_t* a, const uint8_t* b, uint8_t* an, uint8_t* bn, s
     k_lut2<<<grid, 256, 0, s>>>(a, b, an, bn, n, la, lb, vec);
 }
 
-// Per-frame 256-bin histograms (blockIdx.y = frame), accumulated in shared
-// memory, then added to hist[frame * 256 + v] (zeroed by the caller).
+// Per-frame 256-bin histograms (blockIdx.y = frame): 16 pixels per load where the frame
+// allows it and a sub-histogram per warp in shared memory (fewer warps contend for a bin);
+// the block's bins are added to
+// hist[frame * 256 + v] (zeroed by the caller).
 __global__ void __launch_bounds__(256) k_histograms(const uint8_t* __restrict__ a,
                                                     const uint8_t* __restrict__ b, size_t n,
                                                     uint32_t* __restrict__ hist)
 {
-    __shared__ uint32_t hs[256];
+    __shared__ uint32_t hs[8][256];
     const uint8_t* in = blockIdx.y ? b : a;
-    for (int v = threadIdx.x; v < 256; v += blockDim.x) hs[v] = 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int v = threadIdx.x; v < 8 * 256; v += blockDim.x) hs[v >> 8][v & 255] = 0;
     __syncthreads();
+    auto add = [&](uint32_t v, bool on) {
+        if (on) atomicAdd(&hs[warp][v], 1u);
+    };
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        atomicAdd(&hs[in[i]], 1u);
+    const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t done = 0;
+    if (((uintptr_t)in & 15) == 0) {
+        const size_t nv = n / 16;
+        const uint4* in4 = reinterpret_cast<const uint4*>(in);
+        const size_t rounds = (nv + stride - 1) / stride;  // the same for every lane of a warp
+        for (size_t r = 0; r < rounds; r++) {
+            const size_t i = first + r * stride;
+            const bool ok = i < nv;
+            const uint4 q = ok ? in4[i] : make_uint4(0, 0, 0, 0);
+            const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 16; k++) add((wd[k >> 2] >> (8 * (k & 3))) & 255u, ok);
+        }
+        done = nv * 16;
+    }
+    const size_t rest = n - done;
+    const size_t rounds = (rest + stride - 1) / stride;
+    for (size_t r = 0; r < rounds; r++) {
+        const size_t i = done + first + r * stride;
+        const bool ok = i < n;
+        add(ok ? in[i] : 0u, ok);
+    }
     __syncthreads();
-    for (int v = threadIdx.x; v < 256; v += blockDim.x)
-        if (hs[v]) atomicAdd(&hist[blockIdx.y * 256 + v], hs[v]);
+    for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int wv = 0; wv < 8; wv++) t += hs[wv][v];
+        if (t) atomicAdd(&hist[blockIdx.y * 256 + v], t);
+    }
 }
 
 __global__ void k_write_luts(LutSpec a, LutSpec b, uint8_t* __restrict__ luts)
@@ -119,41 +150,46 @@ void launch_histograms(const uint8_t* a, const uint8_t* b, size_t n, uint32_t* h
 }
 
 // Equalization maps of both frames: lut[v] = round((cdf[v]-cdf_min)*255/(N-cdf_min)),
-// integer arithmetic, halves up; identity for a constant frame.
-__global__ void k_histeq_luts(const uint32_t* __restrict__ hist, long long n,
-                              uint8_t* __restrict__ luts)
+// integer arithmetic, halves up; identity for a constant frame. One block of 256 threads
+// per frame: thread v holds bin v; the CDF is a block-wide inclusive prefix sum, cdf_min
+// the count of the first nonzero bin.
+__global__ void __launch_bounds__(256) k_histeq_luts(const uint32_t* __restrict__ hist,
+                                                     long long n, uint8_t* __restrict__ luts)
 {
-    const int f = threadIdx.x;  // one thread per frame: 256 sequential steps
-    if (f >= 2) return;
-    const uint32_t* hg = hist + f * 256;
-    long long cdf_min = 0;
-    for (int v = 0; v < 256; v++)
-        if (hg[v]) {
-            long long run = 0;
-            for (int u = 0; u <= v; u++) run += hg[u];
-            cdf_min = run;
-            break;
-        }
-    const long long den = n - cdf_min;
-    long long run = 0;
-    for (int v = 0; v < 256; v++) {
-        run += hg[v];
-        uint8_t out;
-        if (den <= 0) {
-            out = (uint8_t)v;
-        } else {
-            long long num = run - cdf_min;
-            if (num < 0) num = 0;
-            out = (uint8_t)((num * 255 + den / 2) / den);
-        }
-        luts[f * 256 + v] = out;
+    __shared__ long long wsum[8];
+    __shared__ int vmin;
+    const int f = blockIdx.x, v = threadIdx.x, warp = v >> 5, lane = v & 31;
+    const uint32_t hv = hist[f * 256 + v];
+    if (v == 0) vmin = 256;
+    long long inc = hv;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += u;
     }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (hv) atomicMin(&vmin, v);
+    long long pre = 0;
+    for (int k = 0; k < warp; k++) pre += wsum[k];
+    __syncthreads();
+    const long long cdf = pre + inc;
+    const long long cdf_min = vmin < 256 ? (long long)hist[f * 256 + vmin] : 0;
+    const long long den = n - cdf_min;
+    uint8_t out;
+    if (den <= 0) {
+        out = (uint8_t)v;
+    } else {
+        long long num = cdf - cdf_min;
+        if (num < 0) num = 0;
+        out = (uint8_t)((num * 255 + den / 2) / den);
+    }
+    luts[f * 256 + v] = out;
 }
 
 void launch_histeq_luts(const uint32_t* hist, size_t n, uint8_t* luts, cudaStream_t s)
 {
     note_launch();
-    k_histeq_luts<<<1, 32, 0, s>>>(hist, (long long)n, luts);
+    k_histeq_luts<<<2, 256, 0, s>>>(hist, (long long)n, luts);
 }
 
 // Pyramid: one block per S x S tile of level 0 (S = max(64, 2^(levels-1))).

@@ -21,7 +21,7 @@ STATUS = {0: "OK", 1: "E_INVALID_ARG", 2: "E_CUDA", 3: "E_DEGENERATE", 4: "E_TIM
           5: "E_UNSUPPORTED", 6: "E_WORKSPACE"}
 
 EXPORTS = [
-    "hdrreg_params_default", "hdrreg_last_error", "hdrreg_version", "hdrreg_launch_count",
+    "hdrreg_params_default", "hdrreg_params_paper", "hdrreg_last_error", "hdrreg_version", "hdrreg_launch_count",
     "hdrreg_num_levels",
     "hdrreg_validate_params", "hdrreg_num_tiles", "hdrreg_normalize_workspace_size",
     "hdrreg_normalize_exposure", "hdrreg_pyramid_bytes", "hdrreg_build_pyramid",
@@ -116,6 +116,7 @@ def lib():
         L.hdrreg_version.restype = C.c_char_p
         L.hdrreg_launch_count.restype = C.c_ulonglong
         L.hdrreg_params_default.argtypes = [C.POINTER(Params)]
+        L.hdrreg_params_paper.argtypes = [C.POINTER(Params)]
         L.hdrreg_validate_params.argtypes = [C.POINTER(Params)]
         L.hdrreg_num_levels.argtypes = [i, i, C.POINTER(Params)]
         L.hdrreg_num_tiles.argtypes = [i, i, i]
@@ -201,6 +202,16 @@ def params(**over) -> Params:
     for k, v in over.items():
         if not hasattr(p, k):
             raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def params_paper(**over) -> Params:
+    """The paper-exact preset: the defaults with the corners' whole displacement spread by
+    the flow (Sec. 2.4), with overrides."""
+    p = Params()
+    lib().hdrreg_params_paper(C.byref(p))
+    for k, v in over.items():
         setattr(p, k, v)
     return p
 

@@ -147,3 +147,14 @@ def test_host_staged_batch_sizes_and_errors(hd):
     assert lib.hdrreg_register_merge_host(st, 1, 64, 64, 1, 2, C.byref(p), None, 0, None) == 1
     assert b"stack 0" in lib.hdrreg_last_error()
     assert lib.hdrreg_register_merge_host(None, 0, 64, 64, 1, 2, C.byref(p), None, 0, None) == 6
+
+
+def test_paper_preset_and_defaults(hd):
+    d, p = hd.params(), hd.params_paper()
+    # the paper equalizes the frames' histograms before matching (Sec. 3)
+    assert d.norm_mode == hd.NORM_HISTEQ and p.norm_mode == hd.NORM_HISTEQ
+    # the preset spreads the corners' whole displacement (Sec. 2.4); the default the residual
+    assert d.propagate_full == 0 and p.propagate_full == 1
+    dd, pd = d.as_dict(), p.as_dict()
+    assert {k for k in dd if dd[k] != pd[k]} == {"propagate_full"}
+    assert hd.lib().hdrreg_validate_params(C.byref(p)) == 0

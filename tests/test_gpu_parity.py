@@ -493,3 +493,13 @@ def test_fused_batch_equals_single_calls_and_captures(hd, orc):
 
 def test_fused_histeq_mode(hd, orc, small_yuv_stack):
     _fused_case(hd, orc, small_yuv_stack, cfg(norm_mode=1))
+
+
+@pytest.mark.parametrize("which", ["small", "5mp"])
+def test_fused_paper_preset(hd, orc, small_yuv_stack, five_mp, which):
+    # the paper-exact preset end to end: histogram equalization, radius 10, 5 levels, the
+    # corners' whole displacement spread by the flow (warp by p + F)
+    stack = small_yuv_stack if which == "small" else five_mp
+    c = hd.params_paper(tile=16 if which == "small" else 32).as_dict()
+    _, diags = _fused_case(hd, orc, stack, c)
+    assert diags[0].valid > 0
