@@ -73,6 +73,7 @@ class StackSpec:
     mover_size: int = 64
     mover_shift: float = 16.0
     with_gt: bool = True
+    scene_gain: float = 1.0   # scales every primitive's luma (a dark scene: < 1)
 
 
 # The two single-stack workloads: a VGA luma pair (T=16, R=4) and the paper's
@@ -183,28 +184,29 @@ class _Geometry:
 
 
 def _draw_scene(rng: np.random.Generator, w: int, h: int, spec: StackSpec):
-    bg = rng.uniform(0.0, 40.0)
+    g = spec.scene_gain
+    bg = rng.uniform(0.0, 40.0) * g
     blobs = []
     for _ in range(spec.n_blobs):
         cx, cy = rng.uniform(0, w), rng.uniform(0, h)
         s = rng.uniform(4.0, max(w / 20.0, 4.5))
-        a = 255.0 * rng.uniform() ** 2.5
-        cu, cv = rng.uniform(-20, 20), rng.uniform(-20, 20)
+        a = 255.0 * rng.uniform() ** 2.5 * g
+        cu, cv = rng.uniform(-20, 20) * g, rng.uniform(-20, 20) * g
         blobs.append((cx, cy, s, a, cu, cv))
     rects = []
     for _ in range(spec.n_rects):
         rw = rng.uniform(8.0, max(w / 8.0, 9.0))
         rh = rng.uniform(8.0, max(w / 8.0, 9.0))
         x0, y0 = rng.uniform(-rw / 2, w - rw / 2), rng.uniform(-rh / 2, h - rh / 2)
-        a = 255.0 * rng.uniform() ** 2.5
-        cu, cv = rng.uniform(-20, 20), rng.uniform(-20, 20)
+        a = 255.0 * rng.uniform() ** 2.5 * g
+        cu, cv = rng.uniform(-20, 20) * g, rng.uniform(-20, 20) * g
         rects.append((x0, y0, x0 + rw, y0 + rh, a, cu, cv))
     movers = []
     for _ in range(spec.movers):
         m = spec.mover_size
         x0, y0 = rng.uniform(m, max(w - 2 * m, m + 1)), rng.uniform(m, max(h - 2 * m, m + 1))
-        a = 255.0 * rng.uniform() ** 2.5
-        cu, cv = rng.uniform(-20, 20), rng.uniform(-20, 20)
+        a = 255.0 * rng.uniform() ** 2.5 * g
+        cu, cv = rng.uniform(-20, 20) * g, rng.uniform(-20, 20) * g
         movers.append((x0, y0, x0 + m, y0 + m, a, cu, cv))
     return bg, blobs, rects, movers
 
@@ -376,6 +378,14 @@ def mixed_spec(stack_index: int, config_index: int = 3, with_gt: bool = False) -
 def make_mixed_stack(stack_index: int, config_index: int = 3, with_gt: bool = False) -> Stack:
     return make_stack(mixed_spec(stack_index, config_index, with_gt),
                       stack_seed(config_index, stack_index))
+
+
+def dark_spec(stops: int, width: int = 640, height: int = 480) -> StackSpec:
+    """A scene 2^stops darker than the headline one, seen by a dark reference (values
+    mostly below 255 / 2^stops, noise 1 DN) and a source 2^stops brighter (a normal
+    exposure): the reference lies `stops` stops under the source."""
+    return StackSpec(width, height, ratios=((2 ** stops, 1),), noise_sigma=1.0, field_amp=3.0,
+                     movers=1, chroma=False, scene_gain=1.0 / 2 ** stops)
 
 
 # Sizes of the scaling sweep: 4:3 frames from VGA to 20 MP (widths multiples of 32).

@@ -503,3 +503,12 @@ def test_fused_paper_preset(hd, orc, small_yuv_stack, five_mp, which):
     c = hd.params_paper(tile=16 if which == "small" else 32).as_dict()
     _, diags = _fused_case(hd, orc, stack, c)
     assert diags[0].valid > 0
+
+
+@pytest.mark.parametrize("stops,mode", [(4, 0), (6, 0), (6, 1)])
+def test_fused_dark_reference(hd, orc, stops, mode):
+    # a reference 4-6 stops under the source (values of a few DN): same bits for the level
+    # homographies, merge within 1e-4, with ratio and histogram-equalization normalization
+    from paper_1504_01441_b300 import synth
+    st = synth.make_stack(synth.dark_spec(stops), synth.stack_seed(7, stops))
+    _fused_case(hd, orc, st, cfg(16, 4, norm_mode=mode))
