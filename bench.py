@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED, SWEEP],
                     help="the 5 MP pair batch (default) or the mixed 1-12 MP batch")
     ap.add_argument("--stacks", type=int, default=64, help="stacks of the mixed batch")
+    ap.add_argument("--output", default="merge", choices=["merge", "fusion"],
+                    help="the fused call's output: the irradiance merge (a11) or the "
+                         "error-tolerant exposure fusion of Sec. 2.5 (output_mode 1)")
     ap.add_argument("--preset", default="workload", choices=["workload", "paper"],
                     help="the headline workload's parameters (T=32, R=6, ratio normalization) "
                          "or the paper-exact preset (histogram equalization, R=10, the whole "
@@ -170,6 +173,7 @@ def run_ours(args):
         p = hdrreg.params_paper()
     else:
         p = hdrreg.params_from_dict(synth.method_params(32, 6))
+    p.output_mode = 1 if args.output == "fusion" else 0
     P = args.pairs
     # resident inputs: P distinct device buffers (contents cycle over the generated stacks)
     frames = []
@@ -222,7 +226,8 @@ def run_ours(args):
         roof = measure_flow_roofline(stages, p)
     # -- the learned level-0 search (row a-L) on the same resident pairs
     learned = None
-    if rank == 0 and not args.no_learned and not args.profile and args.preset == "workload":
+    if (rank == 0 and not args.no_learned and not args.profile and args.preset == "workload"
+            and args.output == "merge"):
         learned = measure_learned(torch, hdrreg, synth, stacks, frames, p, dev, args)
     # -- end to end through the C ABI with host buffers (pinned), copies inside the timing
     e2e = None
@@ -241,6 +246,7 @@ def run_ours(args):
                        "frames": 2, "exposure_ratio": 4, "pairs_per_step": P,
                        "distinct_stacks": len(stacks), "tile": p.tile, "radius": p.radius,
                        "preset": args.preset, "norm_mode": "histeq" if p.norm_mode else "ratio",
+                       "output": args.output,
                        "propagate_full": p.propagate_full,
                        "path": "plain (a1-a11)", "graph": True, "lanes": args.lanes,
                        "l2": f"inputs larger than L2: {P} resident pairs x 15.1 MB per step",
@@ -391,6 +397,9 @@ def measure_stages(torch, hdrreg, p, stack, dev, args):
     out["warp"] = _graph_time_us(torch, lambda: hdrreg.warp(src, srcu, srcv, res["H"], fu, fv), reps)
     srcs = [dict(y=wy, u=wu, v=wv, ref_n=rn, ratio=stack.ratios[0], lut=luts[1])]
     out["merge"] = _graph_time_us(torch, lambda: hdrreg.merge(ref, refu, refv, srcs, p), reps)
+    q = hdrreg.merge(ref, refu, refv, srcs, p, want_q=True)[3]
+    fsrc = [dict(y=wy, u=wu, v=wv, q=q[0])]
+    out["fuse"] = _graph_time_us(torch, lambda: hdrreg.fuse(ref, refu, refv, fsrc), reps)
     return {k: round(v, 2) for k, v in out.items()}
 
 

@@ -86,7 +86,10 @@ typedef struct hdrreg_params {
     int dt_iters;         /* domain-transform iterations, 1..8                          */
     int ssim_radius;      /* SSIM Gaussian window radius; must be 5                     */
     int propagate_full;   /* 0: flow = residual to H0 (dense map H0+F); 1: q - p (H ignored) */
-    int reserved0;
+    int output_mode;      /* fused call's output: 0 the irradiance merge (a11); 1 the
+                             error-tolerant exposure fusion of Sec. 2.5 (contrast x
+                             well-exposedness x SSIM, hdrreg_fuse); 2 the same without the
+                             contrast factor                                           */
     double weed_eps;      /* inlier distance, pixels of the level                       */
     double sigma_s;       /* domain-transform spatial sigma                             */
     double sigma_r;       /* domain-transform range sigma, on a [0,1] intensity scale   */
@@ -460,6 +463,32 @@ size_t hdrreg_register_merge_batch_workspace_size(int w, int h, int nsrc, int la
 hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count, int w, int h,
                                           int nsrc, int lanes, const hdrreg_params* p,
                                           void* workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------- f1: error-tolerant exposure fusion (Sec. 2.5)
+ * The paper's output image: the exposure fusion of Mertens et al. (2007) over the
+ * reference and the warped sources, with each source's SSIM map as a fourth weight
+ * (colour saturation has no luma counterpart and is left out). Per luma pixel and frame:
+ * W = C * WE(Z) * Q + 1e-12 (C omitted when use_contrast = 0), C = |4 I - its 4
+ * neighbours| of I = Z / 255 (edges replicated), WE(z) = exp(-(z/255 - 0.5)^2 /
+ * (2 we_sigma^2)), Q = the source's SSIM map (1 for the reference), normalized over the
+ * frames. The images (Z / 255; chroma (c - 128) / 255 with the 2x2 means of the luma
+ * weights) are blended in Laplacian pyramids weighted by the Gaussian pyramids of the
+ * weights (Burt and Adelson: [1 4 6 4 1] / 16 with clamped coordinates, floor(log2
+ * min(w, h)) levels) and collapsed. out: 255 x the result (FP32; chroma as signed
+ * offsets, like the merge's). ref: u8 planes; srcs: warped FP32 planes (0..255) and the
+ * SSIM map (FP32 w x h, as hdrreg_merge writes it). All device pointers; the library
+ * allocates nothing. Workspace: hdrreg_fuse_workspace_size(w, h, nsrc, chroma).
+ */
+typedef struct hdrreg_fuse_src {
+    const float* y;
+    const float* u;
+    const float* v;
+    const float* q;
+} hdrreg_fuse_src;
+size_t hdrreg_fuse_workspace_size(int w, int h, int nsrc, int chroma);
+hdrreg_status hdrreg_fuse(const hdrreg_frame* ref, int w, int h, int nsrc,
+                          const hdrreg_fuse_src* srcs, int use_contrast, double we_sigma,
+                          hdrreg_planes_f32* out, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------- a1-a11 fused, a batch of stacks in host memory
  * The paper has no counterpart. hdrreg_register_merge_batch for stacks whose planes

@@ -115,6 +115,7 @@ struct FusedLayout {
     int wq = 0, hq = 0, pho = 0, pwo = 0;
     size_t xq = 0, pred = 0, cnn = 0, fellback = 0;
     size_t wy[kMaxSources], wu[kMaxSources], wv[kMaxSources], refn[kMaxSources];
+    size_t q = 0, fuse = 0;  // output_mode != 0
     size_t total;
     FusedLayout(int w, int h, int ns, const hdrreg_params* p)
     {
@@ -162,6 +163,11 @@ struct FusedLayout {
             wu[k] = lay.add((size_t)(w / 2) * (h / 2) * 4);
             wv[k] = lay.add((size_t)(w / 2) * (h / 2) * 4);
             refn[k] = lay.add((size_t)w * h);
+        }
+        q = fuse = 0;
+        if (p->output_mode != 0) {  // exposure fusion: the SSIM maps and the pyramids
+            q = lay.add((size_t)ns * w * h * 4);
+            fuse = lay.add(fuse_ws_bytes(w, h, ns + 1, true));
         }
         total = lay.total;
     }
@@ -284,6 +290,8 @@ hdrreg_status hdrreg_validate_params(const hdrreg_params* p)
         return fail(HDRREG_E_INVALID_ARG, "predictor_refine must be in [0, radius]");
     if (p->propagate_full != 0 && p->propagate_full != 1)
         return fail(HDRREG_E_INVALID_ARG, "propagate_full must be 0 or 1");
+    if (p->output_mode < 0 || p->output_mode > 2)
+        return fail(HDRREG_E_INVALID_ARG, "output_mode must be 0, 1 or 2");
     if (!(p->weed_eps > 0) || !(p->sigma_s > 0) || !(p->sigma_r > 0) || !(p->ssim_sigma > 0) ||
         !(p->we_sigma > 0) || !(p->flow_eps >= 0))
         return fail(HDRREG_E_INVALID_ARG,
@@ -727,10 +735,20 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
         md[k].mode = p->norm_mode;
         if ((st = launch_status("register_merge(register)"))) return st;
     }
-    // ---- a10 + a11
+    // ---- a10 + a11 (with output_mode != 0 the merge also leaves the SSIM maps, which the
+    //      exposure fusion of Sec. 2.5 then uses; its result replaces the merge's)
+    float* qmaps = p->output_mode ? reinterpret_cast<float*>(at(lay.q)) : nullptr;
     launch_merge(ref->y, chroma ? ref->u : nullptr, chroma ? ref->v : nullptr, w, h, nsrc, md,
                  p->ssim_sigma, p->we_sigma, out->y, chroma ? out->u : nullptr,
-                 chroma ? out->v : nullptr, nullptr, s);
+                 chroma ? out->v : nullptr, qmaps, s);
+    if (p->output_mode) {
+        FuseSrcDev fs[kMaxSources];
+        for (int k = 0; k < nsrc; k++)
+            fs[k] = FuseSrcDev{md[k].y, md[k].u, md[k].v, qmaps + (size_t)k * w * h};
+        launch_fuse(ref->y, chroma ? ref->u : nullptr, chroma ? ref->v : nullptr, w, h, nsrc, fs,
+                    p->output_mode == 1, p->we_sigma, out->y, chroma ? out->u : nullptr,
+                    chroma ? out->v : nullptr, at(lay.fuse), s);
+    }
     return launch_status("register_merge(merge)");
 }
 
@@ -1033,6 +1051,41 @@ hdrreg_status hdrreg_register_merge_batch(const hdrreg_stack* stacks, int count,
                       cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
     }
     return st;
+}
+
+// -------------------------------------------------------------------- f1
+size_t hdrreg_fuse_workspace_size(int w, int h, int nsrc, int chroma)
+{
+    if (bad_dims(w, h) || nsrc < 1 || nsrc > kMaxSources) return 0;
+    return fuse_ws_bytes(w, h, nsrc + 1, chroma != 0);
+}
+
+hdrreg_status hdrreg_fuse(const hdrreg_frame* ref, int w, int h, int nsrc,
+                          const hdrreg_fuse_src* srcs, int use_contrast, double we_sigma,
+                          hdrreg_planes_f32* out, void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!ref || !ref->y || !srcs || !out || !out->y)
+        return fail(HDRREG_E_INVALID_ARG, "fuse: NULL pointer");
+    if (bad_dims(w, h)) return fail(HDRREG_E_INVALID_ARG, "fuse: bad size %dx%d", w, h);
+    if (nsrc < 1 || nsrc > kMaxSources)
+        return fail(HDRREG_E_INVALID_ARG, "fuse: nsrc must be in [1, %d]", kMaxSources);
+    if (!(we_sigma > 0)) return fail(HDRREG_E_INVALID_ARG, "fuse: we_sigma must be > 0");
+    const bool chroma = ref->u && ref->v && out->u && out->v;
+    if (chroma && ((w & 1) || (h & 1)))
+        return fail(HDRREG_E_INVALID_ARG, "fuse: YUV420 needs even width and height");
+    FuseSrcDev fs[kMaxSources];
+    for (int k = 0; k < nsrc; k++) {
+        if (!srcs[k].y || !srcs[k].q || (chroma && (!srcs[k].u || !srcs[k].v)))
+            return fail(HDRREG_E_INVALID_ARG, "fuse: NULL plane of source %d", k);
+        fs[k] = FuseSrcDev{srcs[k].y, srcs[k].u, srcs[k].v, srcs[k].q};
+    }
+    const size_t need = fuse_ws_bytes(w, h, nsrc + 1, chroma);
+    if (!workspace || ws_bytes < need)
+        return fail(HDRREG_E_WORKSPACE, "fuse: workspace of %zu bytes required", need);
+    launch_fuse(ref->y, chroma ? ref->u : nullptr, chroma ? ref->v : nullptr, w, h, nsrc, fs,
+                use_contrast != 0, we_sigma, out->y, chroma ? out->u : nullptr,
+                chroma ? out->v : nullptr, workspace, static_cast<cudaStream_t>(stream));
+    return launch_status("fuse");
 }
 
 // Per-lane layout of the host-staged batch: the fused workspace, then device copies of

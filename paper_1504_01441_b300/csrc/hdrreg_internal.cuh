@@ -476,6 +476,18 @@ struct MergeSrcDev {
     int mode;
 };
 constexpr int kMaxSources = 4;
+
+// Exposure fusion (fuse.cu, row f1): a registered source's warped planes and SSIM map.
+struct FuseSrcDev {
+    const float* y;
+    const float* u;
+    const float* v;
+    const float* q;
+};
+size_t fuse_ws_bytes(int w, int h, int nframes, bool chroma);
+void launch_fuse(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v, int w, int h,
+                 int nsrc, const FuseSrcDev* srcs, int use_contrast, double we_sigma, float* oy,
+                 float* ou, float* ov, void* ws, cudaStream_t s);
 void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v, int w, int h,
                   int nsrc, const MergeSrcDev* srcs, double ssim_sigma, double we_sigma,
                   float* oy, float* ou, float* ov, float* q_out, cudaStream_t s);

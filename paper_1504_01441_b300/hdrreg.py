@@ -32,6 +32,7 @@ EXPORTS = [
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
     "hdrreg_register_merge_multi_workspace_size", "hdrreg_register_merge_multi",
     "hdrreg_register_merge_host_workspace_size", "hdrreg_register_merge_host",
+    "hdrreg_fuse_workspace_size", "hdrreg_fuse",
     "hdrreg_gemm_bf16", "hdrreg_cnn_workspace_size", "hdrreg_cnn_out_dims", "hdrreg_cnn_forward",
     "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_cnn_activation",
     "hdrreg_cnn_infer_workspace_size", "hdrreg_cnn_infer", "hdrreg_predictor_input",
@@ -57,7 +58,7 @@ class Params(C.Structure):
         ("quad", C.c_int), ("corner_thresh", C.c_int), ("weed_iters", C.c_int),
         ("weed_delta_min", C.c_int), ("weed_delta_div", C.c_int), ("norm_mode", C.c_int),
         ("dt_iters", C.c_int), ("ssim_radius", C.c_int), ("propagate_full", C.c_int),
-        ("reserved0", C.c_int),
+        ("output_mode", C.c_int),
         ("weed_eps", C.c_double), ("sigma_s", C.c_double), ("sigma_r", C.c_double),
         ("ssim_sigma", C.c_double), ("we_sigma", C.c_double), ("flow_eps", C.c_double),
         ("weed_seed", C.c_uint64), ("predictor", C.c_void_p), ("fallback_cost", C.c_uint32),
@@ -66,7 +67,7 @@ class Params(C.Structure):
 
     def as_dict(self) -> Dict:
         return {n: getattr(self, n) for n, _ in self._fields_
-                if n not in ("reserved0", "predictor", "fallback_cost", "predictor_refine")}
+                if n not in ("predictor", "fallback_cost", "predictor_refine")}
 
 
 class Frame(C.Structure):
@@ -86,6 +87,10 @@ class Stack(C.Structure):
     _fields_ = [("ref", C.POINTER(Frame)), ("srcs", C.POINTER(Frame)),
                 ("ratio_num", C.POINTER(C.c_int)), ("ratio_den", C.POINTER(C.c_int)),
                 ("out", PlanesF32), ("diag", C.c_void_p)]
+
+
+class FuseSrc(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("u", C.c_void_p), ("v", C.c_void_p), ("q", C.c_void_p)]
 
 
 class StackEx(C.Structure):
@@ -154,6 +159,10 @@ def lib():
         L.hdrreg_register_merge_batch_workspace_size.argtypes = [i, i, i, i, C.POINTER(Params)]
         L.hdrreg_register_merge_batch.argtypes = [C.POINTER(Stack), i, i, i, i, i,
                                                   C.POINTER(Params), vp, sz, vp]
+        L.hdrreg_fuse_workspace_size.restype = sz
+        L.hdrreg_fuse_workspace_size.argtypes = [i, i, i, i]
+        L.hdrreg_fuse.argtypes = [C.POINTER(Frame), i, i, i, C.POINTER(FuseSrc), i, C.c_double,
+                                  C.POINTER(PlanesF32), vp, sz, vp]
         L.hdrreg_register_merge_host_workspace_size.restype = sz
         L.hdrreg_register_merge_host_workspace_size.argtypes = [i, i, i, i, C.POINTER(Params)]
         L.hdrreg_register_merge_host.argtypes = [C.POINTER(Stack), i, i, i, i, i,
@@ -400,6 +409,29 @@ def merge(ref_y, ref_u, ref_v, sources: Sequence[Dict], p: Params, want_q=False,
     _check(lib().hdrreg_merge(C.byref(f), w, h, k, arr, C.byref(p), C.byref(o), _ptr(q),
                               _stream(stream)))
     return oy, ou, ov, q
+
+
+# ---------------------------------------------------------------- f1
+def fuse(ref_y, ref_u, ref_v, sources: Sequence[Dict], use_contrast=True, we_sigma=0.2,
+         stream=None):
+    """Error-tolerant exposure fusion (Sec. 2.5). sources: dicts with y, u, v (warped FP32)
+    and q (SSIM map FP32, as merge(want_q=True) returns). -> (Y, U - 128, V - 128) FP32."""
+    import torch
+    h, w = ref_y.shape
+    chroma = ref_u is not None
+    k = len(sources)
+    arr = (FuseSrc * k)(*[FuseSrc(_ptr(s["y"]), _ptr(s.get("u")), _ptr(s.get("v")), _ptr(s["q"]))
+                          for s in sources])
+    oy = _empty((h, w), torch.float32, ref_y)
+    ou = _empty((h // 2, w // 2), torch.float32, ref_y) if chroma else None
+    ov = _empty((h // 2, w // 2), torch.float32, ref_y) if chroma else None
+    n = lib().hdrreg_fuse_workspace_size(w, h, k, int(chroma))
+    ws = _empty((max(n, 1),), torch.uint8, ref_y)
+    f = Frame(_ptr(ref_y), _ptr(ref_u), _ptr(ref_v))
+    o = PlanesF32(_ptr(oy), _ptr(ou), _ptr(ov))
+    _check(lib().hdrreg_fuse(C.byref(f), w, h, k, arr, int(use_contrast), C.c_double(we_sigma),
+                             C.byref(o), _ptr(ws), n, _stream(stream)))
+    return oy, ou, ov
 
 
 # ---------------------------------------------------------------- fused

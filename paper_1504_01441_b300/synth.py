@@ -352,7 +352,7 @@ def method_params(tile: int = 32, radius: int = 6, **over) -> dict:
              grid_half=4, quad=10, corner_thresh=2, weed_iters=512, weed_delta_min=8,
              weed_delta_div=20, norm_mode=0, dt_iters=3, ssim_radius=5, propagate_full=0,
              weed_eps=1.5, sigma_s=400.0, sigma_r=0.5, ssim_sigma=1.5, we_sigma=0.2,
-             flow_eps=1e-20, weed_seed=0x1504014410)
+             flow_eps=1e-20, weed_seed=0x1504014410, output_mode=0)
     p.update(over)
     return p
 

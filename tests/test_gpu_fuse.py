@@ -1,0 +1,92 @@
+"""GPU: the error-tolerant exposure fusion (row f1) against the oracle (oracle/fusion.py).
+
+The fusion step on identical inputs (reference planes, warped FP32 planes, SSIM maps)
+must match within 1e-4 in the max norm relative to max(|oracle|, 1) -- the FP32
+pyramids against float64. The fused call with output_mode 1 is compared with the oracle's
+registration (its warped planes and SSIM maps) followed by the oracle's fusion.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_01441_b300 import build, hdrreg
+    build.build()
+    return hdrreg
+
+
+def rel_err(gpu, orc):
+    g = np.asarray(gpu, np.float64)
+    o = np.asarray(orc, np.float64)
+    return float(np.abs(g - o).max() / max(np.abs(o).max(), 1.0))
+
+
+def d(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return (t.to(dtype) if dtype is not None else t).cuda()
+
+
+@pytest.mark.parametrize("w,h,nsrc,contrast,chroma", [(334, 250, 1, True, True),
+                                                       (256, 192, 2, True, True),
+                                                       (161, 97, 1, False, False),
+                                                       (640, 480, 2, False, True)])
+def test_fuse_step_matches_oracle(hd, w, h, nsrc, contrast, chroma):
+    from oracle import fusion as F
+    from paper_1504_01441_b300 import synth
+    rng = np.random.default_rng(w + h + nsrc)
+    ry = rng.integers(0, 256, (h, w), dtype=np.uint8)
+    ru = rng.integers(0, 256, (h // 2, w // 2), dtype=np.uint8) if chroma else None
+    rv = rng.integers(0, 256, (h // 2, w // 2), dtype=np.uint8) if chroma else None
+    srcs, warped, qs = [], [], []
+    for _ in range(nsrc):
+        y = rng.uniform(0, 255, (h, w)).astype(np.float32)
+        u = rng.uniform(0, 255, (h // 2, w // 2)).astype(np.float32) if chroma else None
+        v = rng.uniform(0, 255, (h // 2, w // 2)).astype(np.float32) if chroma else None
+        q = rng.uniform(0, 1, (h, w)).astype(np.float32)
+        srcs.append(dict(y=d(y), u=d(u) if chroma else None, v=d(v) if chroma else None, q=d(q)))
+        warped.append((y, u, v))
+        qs.append(q)
+    gy, gu, gv = hd.fuse(d(ry), d(ru) if chroma else None, d(rv) if chroma else None, srcs,
+                         use_contrast=contrast)
+    oy, ou, ov = F.fuse(ry, ru, rv, warped, qs, use_contrast=contrast)
+    torch.cuda.synchronize()
+    e = rel_err(gy.cpu().numpy(), oy)
+    print(f"y {e:.2e}")
+    assert e <= REL
+    if chroma:
+        assert rel_err(gu.cpu().numpy(), ou) <= REL
+        assert rel_err(gv.cpu().numpy(), ov) <= REL
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_fused_call_with_exposure_fusion(hd, orc, small_yuv_stack, mode):
+    from oracle import fusion as F
+    from paper_1504_01441_b300 import synth
+    st = small_yuv_stack
+    c = synth.method_params(16, 4, output_mode=mode)
+    p = hd.params_from_dict(c)
+    (y, u, v), rm = hd.register_merge((d(st.ref.y), d(st.ref.u), d(st.ref.v)),
+                                      [(d(f.y), d(f.u), d(f.v)) for f in st.srcs], st.ratios, p)
+    torch.cuda.synchronize()
+    out = orc.register_merge(st.ref, st.srcs, st.ratios, c, want_intermediates=True)
+    diag = rm.diagnostics()
+    warped, qs = [], []
+    for k, f in enumerate(st.srcs):
+        assert np.array_equal(np.array(diag[k].H0[:]).view(np.uint64),
+                              out["H0"][k].reshape(9).view(np.uint64))
+        wy, wu, wv = orc.warp(f.y, f.u, f.v, out["H0"][k], out["flow_u"][k], out["flow_v"][k])
+        warped.append((wy, wu, wv))
+        qs.append(out["q"][k])
+    oy, ou, ov = F.fuse(st.ref.y, st.ref.u, st.ref.v, warped, qs, use_contrast=(mode == 1))
+    for name, g, o in (("y", y, oy), ("u", u, ou), ("v", v, ov)):
+        e = rel_err(g.cpu().numpy(), o)
+        print(f"{name} {e:.2e}")
+        assert e <= REL, name
