@@ -141,8 +141,8 @@ struct FusedLayout {
         hist = lay.add(2 * 256 * 4);
         luts = lay.add((size_t)kMaxSources * 512);
         flow = lay.add(flow_ws_bytes(w, h));
-        fu = lay.add((size_t)w * h * 4);
-        fv = lay.add((size_t)w * h * 4);
+        fu = lay.add((size_t)flow_pitch(w) * h * 4);  // flow planes at the flow's padded pitch
+        fv = lay.add((size_t)flow_pitch(w) * h * 4);
         // one network output cell per 32 x 32 tile (8 x 8 quarter-resolution pixels)
         learned = p->predictor != nullptr && L >= 3 && p->tile == 32 && (w >> 2) >= 8 &&
                   (h >> 2) >= 8;
@@ -496,7 +496,7 @@ hdrreg_status hdrreg_flow_upsample(const uint8_t* guide_n, int w, int h, const i
     FlowCorners fc{corner_xy, match_xy, mask_bits, H, w / p->tile, h / p->tile, p->tile,
                    p->propagate_full};
     launch_flow(guide_n, w, h, fc, p->sigma_s, p->sigma_r, p->dt_iters, p->flow_eps, flow_u,
-                flow_v, workspace, static_cast<cudaStream_t>(stream));
+                flow_v, w, workspace, static_cast<cudaStream_t>(stream));
     return launch_status("flow");
 }
 
@@ -512,7 +512,7 @@ hdrreg_status hdrreg_warp(const hdrreg_frame* src, int w, int h, const double* H
     if (chroma && ((w & 1) || (h & 1)))
         return fail(HDRREG_E_INVALID_ARG, "warp: YUV420 needs even width and height");
     launch_warp(src->y, chroma ? src->u : nullptr, chroma ? src->v : nullptr, w, h, H, flow_u,
-                flow_v, out->y, chroma ? out->u : nullptr, chroma ? out->v : nullptr,
+                flow_v, w, out->y, chroma ? out->u : nullptr, chroma ? out->v : nullptr,
                 static_cast<cudaStream_t>(stream));
     return launch_status("warp");
 }
@@ -713,13 +713,13 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
         FlowCorners fc{corner, match, mask, Hs, w / p->tile, h / p->tile, p->tile,
                        p->propagate_full};
         launch_flow(ref0, w, h, fc, p->sigma_s, p->sigma_r, p->dt_iters, p->flow_eps, fu, fv,
-                    at(lay.flow), s);
+                    flow_pitch(w), at(lay.flow), s);
         // ---- a9: warp the source frame
         float* wy = reinterpret_cast<float*>(at(lay.wy[k]));
         float* wu = reinterpret_cast<float*>(at(lay.wu[k]));
         float* wv = reinterpret_cast<float*>(at(lay.wv[k]));
         launch_warp(srcs[k].y, chroma ? srcs[k].u : nullptr, chroma ? srcs[k].v : nullptr, w, h,
-                    Hw, fu, fv, wy, chroma ? wu : nullptr, chroma ? wv : nullptr, s);
+                    Hw, fu, fv, flow_pitch(w), wy, chroma ? wu : nullptr, chroma ? wv : nullptr, s);
         if (diag) {
             note_launch();
             k_diag<<<1, 1024, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L,

@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
                                                          float* __restrict__ P1,
                                                          float* __restrict__ P2,
                                                          const uint8_t* __restrict__ guide,
-                                                         int w, int h, DtLut lut_in,
-                                                         FlowCorners fc,
+                                                         int w, int h, int ppitch, int gpitch,
+                                                         DtLut lut_in, FlowCorners fc,
                                                          const int4* __restrict__ rec, int* err)
 {
     extern __shared__ __align__(128) float sm[];
@@ -283,18 +283,19 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
         mbar_init(&bar[1]);
     }
     __syncthreads();
-    const uint32_t bytes = (kSparse ? 0u : 3u * (uint32_t)w * 4u) + (uint32_t)w;
+    // whole padded rows (pitches are multiples of 16 bytes); columns >= w are never used
+    const uint32_t bytes = (kSparse ? 0u : 3u * (uint32_t)ppitch * 4u) + (uint32_t)gpitch;
     auto issue = [&](int y, int b) {
         if (tid == 0) {
             float* B = sm + b * kBuf;
-            const size_t row = (size_t)y * w;
+            const size_t row = (size_t)y * ppitch;
             mbar_expect(&bar[b], bytes);
             if (!kSparse) {
-                bulk_load(B, P0 + row, w * 4, &bar[b]);
-                bulk_load(B + Wp, P1 + row, w * 4, &bar[b]);
-                bulk_load(B + 2 * Wp, P2 + row, w * 4, &bar[b]);
+                bulk_load(B, P0 + row, ppitch * 4, &bar[b]);
+                bulk_load(B + Wp, P1 + row, ppitch * 4, &bar[b]);
+                bulk_load(B + 2 * Wp, P2 + row, ppitch * 4, &bar[b]);
             }
-            bulk_load(B + 3 * Wp, guide + row, w, &bar[b]);
+            bulk_load(B + 3 * Wp, guide + (size_t)y * gpitch, gpitch, &bar[b]);
         }
     };
     uint32_t ph0 = 0, ph1 = 0;
@@ -384,10 +385,10 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
-            const size_t row = (size_t)y * w;
-            bulk_store(P0 + row, s0, w * 4);
-            bulk_store(P1 + row, s1, w * 4);
-            bulk_store(P2 + row, s2, w * 4);
+            const size_t row = (size_t)y * ppitch;
+            bulk_store(P0 + row, s0, ppitch * 4);
+            bulk_store(P1 + row, s1, ppitch * 4);
+            bulk_store(P2 + row, s2, ppitch * 4);
             bulk_commit();
         }
         rc = rc_next;
@@ -672,13 +673,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 2D tensor map over a w x h plane with 32 x `rows` boxes (4-byte FP32 or 1-byte u8 elements)
-bool make_map(CUtensorMap* m, const void* base, int w, int h, int esize, int rows = kTR)
+// 2D tensor map over a w x h plane (row pitch `pitch` elements) with 32 x `rows` boxes
+// (4-byte FP32 or 1-byte u8 elements)
+bool make_map(CUtensorMap* m, const void* base, int w, int h, int esize, int rows, int pitch)
 {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
-    const cuuint64_t strides[1] = {(cuuint64_t)w * esize};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * esize};
     const cuuint32_t box[2] = {(cuuint32_t)kTW, (cuuint32_t)rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType t =
@@ -735,8 +737,8 @@ void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int 
 
 template <int LM>
 void launch_rows_pipe(int first, float* P0, float* P1, float* P2, const uint8_t* guide, int w,
-                      int h, const DtLut& lut, const FlowCorners& fc, const int4* rec, int* err,
-                      cudaStream_t s)
+                      int h, int ppitch, int gpitch, const DtLut& lut, const FlowCorners& fc,
+                      const int4* rec, int* err, cudaStream_t s)
 {
     const size_t smem = 2 * ((size_t)3 * kRowNT * LM * 4 + (size_t)kRowNT * LM);
     const int per_sm = (int)((225 * 1024) / (smem + 2048));
@@ -744,12 +746,12 @@ void launch_rows_pipe(int first, float* P0, float* P1, float* P2, const uint8_t*
     note_launch();
     if (first) {
         ensure_smem((const void*)k_dt_rows_pipe<LM, true>, smem);
-        k_dt_rows_pipe<LM, true><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, lut, fc, rec,
-                                                             err);
+        k_dt_rows_pipe<LM, true><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, ppitch,
+                                                             gpitch, lut, fc, rec, err);
     } else {
         ensure_smem((const void*)k_dt_rows_pipe<LM, false>, smem);
-        k_dt_rows_pipe<LM, false><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, lut, fc,
-                                                              rec, err);
+        k_dt_rows_pipe<LM, false><<<grid, kRowNT, smem, s>>>(P0, P1, P2, guide, w, h, ppitch,
+                                                              gpitch, lut, fc, rec, err);
     }
 }
 
@@ -757,12 +759,11 @@ void launch_rows_pipe(int first, float* P0, float* P1, float* P2, const uint8_t*
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
 
-bool flow_fast_supported(int w, int h, const uint8_t* guide, const float* fu, const float* fv)
+// Sizes the fast path handles (the caller provides 16-byte-aligned bases and pitches: the
+// guide's pitch a multiple of 16, the planes' and the flow planes' multiples of 4).
+bool flow_fast_supported(int w, int h)
 {
-    // TMA: 16-byte aligned bases and row pitches (w % 16 for the u8 guide)
-    if (w % 16 != 0 || w < 32 || h < 2) return false;
-    if (((uintptr_t)guide % 16) != 0 || ((uintptr_t)fu % 16) != 0 || ((uintptr_t)fv % 16) != 0)
-        return false;
+    if (w < 32 || h < 2) return false;
     if (row_L(w) > 23 || 2 * row_fast_smem(w) > kFastBudget) return false;
     return encode_fn() != nullptr;
 }
@@ -780,10 +781,14 @@ size_t flow_fast_extra_bytes(int w, int h)
            corner_rec_bytes(w, h);
 }
 
-bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc, const DtLut* luts,
-                      int iters, double flow_eps, float* flow_u, float* flow_v, float* P0,
-                      float* P1, float* P2, int* err, void* extra, cudaStream_t s)
+bool launch_flow_fast(const uint8_t* guide, int gpitch, int w, int h, const FlowCorners& fc,
+                      const DtLut* luts, int iters, double flow_eps, float* flow_u, float* flow_v,
+                      int fpitch, float* P0, float* P1, float* P2, int ppitch, int* err,
+                      void* extra, cudaStream_t s)
 {
+    if (gpitch % 16 != 0 || ppitch % 4 != 0 || fpitch % 4 != 0 || gpitch < w || ppitch < w ||
+        fpitch < w)
+        return false;
     const size_t ntile = (size_t)((h + kTR - 1) / kTR);
     const size_t wp = (size_t)((w + kTW - 1) / kTW) * kTW;
     float* agg = static_cast<float*>(extra);
@@ -799,32 +804,34 @@ bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc,
         k_flow_corner_records<<<n > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(fc, w, h, rec);
     }
     ColMaps mid, fin;
-    if (!make_map(&mid.in[0], P0, w, h, 4) || !make_map(&mid.in[1], P1, w, h, 4) ||
-        !make_map(&mid.in[2], P2, w, h, 4) || !make_map(&mid.guide, guide, w, h, 1, kGRows))
+    if (!make_map(&mid.in[0], P0, w, h, 4, kTR, ppitch) || !make_map(&mid.in[1], P1, w, h, 4, kTR, ppitch) ||
+        !make_map(&mid.in[2], P2, w, h, 4, kTR, ppitch) ||
+        !make_map(&mid.guide, guide, w, h, 1, kGRows, gpitch))
         return false;
     mid.out[0] = mid.in[0];
     mid.out[1] = mid.in[1];
     mid.out[2] = mid.in[2];
     fin = mid;
-    if (!make_map(&fin.out[0], flow_u, w, h, 4) || !make_map(&fin.out[1], flow_v, w, h, 4))
+    if (!make_map(&fin.out[0], flow_u, w, h, 4, kTR, fpitch) ||
+        !make_map(&fin.out[1], flow_v, w, h, 4, kTR, fpitch))
         return false;
     const int Lr = row_L(w);
     for (int i = 0; i < iters; i++) {
         const DtLut& lut = luts[i];
         const int first = i == 0;
         switch (Lr) {
-            case 1: launch_rows_pipe<1>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 3: launch_rows_pipe<3>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 5: launch_rows_pipe<5>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 7: launch_rows_pipe<7>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 9: launch_rows_pipe<9>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 11: launch_rows_pipe<11>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 13: launch_rows_pipe<13>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 15: launch_rows_pipe<15>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 17: launch_rows_pipe<17>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 19: launch_rows_pipe<19>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            case 21: launch_rows_pipe<21>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
-            default: launch_rows_pipe<23>(first, P0, P1, P2, guide, w, h, lut, fc, rec, err, s); break;
+            case 1: launch_rows_pipe<1>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 3: launch_rows_pipe<3>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 5: launch_rows_pipe<5>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 7: launch_rows_pipe<7>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 9: launch_rows_pipe<9>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 11: launch_rows_pipe<11>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 13: launch_rows_pipe<13>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 15: launch_rows_pipe<15>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 17: launch_rows_pipe<17>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 19: launch_rows_pipe<19>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            case 21: launch_rows_pipe<21>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
+            default: launch_rows_pipe<23>(first, P0, P1, P2, guide, w, h, ppitch, gpitch, lut, fc, rec, err, s); break;
         }
         launch_cols_tiles((i == iters - 1) ? fin : mid, w, h, lut, i == iters - 1, (float)flow_eps,
                           agg, car, err, s);

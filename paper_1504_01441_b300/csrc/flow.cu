@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kNT) k_dt_cols(float* __restrict__ P0, float* 
                                                  const uint8_t* __restrict__ guide, int w, int h,
                                                  int L, int vec, DtLut lut_in, int final_pass,
                                                  float flow_eps, float* __restrict__ Fu,
-                                                 float* __restrict__ Fv)
+                                                 float* __restrict__ Fv, int fpitch)
 {
     constexpr int NSEG = kNT / SW;
     extern __shared__ __align__(16) float sm[];
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kNT) k_dt_cols(float* __restrict__ P0, float* 
             v.y = n.y >= flow_eps ? b.y / n.y : 0.f;
             v.z = n.z >= flow_eps ? b.z / n.z : 0.f;
             v.w = n.w >= flow_eps ? b.w / n.w : 0.f;
-            const size_t off = (size_t)r * w + xs0;
+            const size_t off = (size_t)r * fpitch + xs0;
             *reinterpret_cast<float4*>(Fu + off) = u;
             *reinterpret_cast<float4*>(Fv + off) = v;
         }
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kNT) k_dt_cols(float* __restrict__ P0, float* 
             if (cc < ncols) {
                 const float n = s2[r * SW + cc];
                 const bool ok = n >= flow_eps;
-                const size_t off = (size_t)r * w + xs0 + cc;
+                const size_t off = (size_t)r * fpitch + xs0 + cc;
                 Fu[off] = ok ? s0[r * SW + cc] / n : 0.f;
                 Fv[off] = ok ? s1[r * SW + cc] / n : 0.f;
             }
@@ -455,7 +455,7 @@ size_t row_smem(int w)
 
 template <int SW>
 void launch_cols(float* P0, float* P1, float* P2, const uint8_t* guide, int w, int h,
-                 const DtLut& lut, int final_pass, float eps, float* Fu, float* Fv,
+                 const DtLut& lut, int final_pass, float eps, float* Fu, float* Fv, int fpitch,
                  cudaStream_t s)
 {
     constexpr int NSEG = kNT / SW;
@@ -466,11 +466,11 @@ void launch_cols(float* P0, float* P1, float* P2, const uint8_t* guide, int w, i
     // vector staging needs every strip row start aligned: planes (workspace) and the
     // caller's guide / flow planes
     const uintptr_t al = (uintptr_t)guide | (uintptr_t)Fu | (uintptr_t)Fv;
-    const int vec = (w % SW == 0) && (w % 4 == 0) && (al % 4 == 0) &&
+    const int vec = (w % SW == 0) && (w % 4 == 0) && (fpitch % 4 == 0) && (al % 4 == 0) &&
                     (((uintptr_t)Fu | (uintptr_t)Fv) % 16 == 0);
     note_launch();
     k_dt_cols<SW><<<grid, kNT, smem, s>>>(P0, P1, P2, guide, w, h, L, vec, lut, final_pass, eps,
-                                          Fu, Fv);
+                                          Fu, Fv, fpitch);
 }
 
 }  // namespace
@@ -493,25 +493,55 @@ int flow_supported(int w, int h)
     return w >= 1 && h >= 1 && row_smem(w) <= kSmemBudget && pick_sw(h) != 0;
 }
 
+int flow_pitch(int w) { return (w + 15) / 16 * 16; }
+
+// Three FP32 planes at the padded pitch, the error word, the fast path's tile maps and
+// corner records, and a copy of the guide at the padded pitch (for widths whose rows
+// are not 16-byte aligned).
 size_t flow_ws_bytes(int w, int h)
 {
-    return 3 * align_up((size_t)w * h * 4, 256) + 256 + flow_fast_extra_bytes(w, h);
+    const size_t pp = (size_t)flow_pitch(w);
+    return 3 * align_up(pp * h * 4, 256) + 256 + flow_fast_extra_bytes(w, h) +
+           align_up(pp * h, 256);
 }
+
+namespace {
+__global__ void k_copy_rows(const uint8_t* __restrict__ in, int w, int h, uint8_t* __restrict__ out,
+                            int pitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x < pitch) out[(size_t)y * pitch + x] = x < w ? in[(size_t)y * w + x] : 0;
+}
+}  // namespace
 
 void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, double sigma_s,
                  double sigma_r, int iters, double flow_eps, float* flow_u, float* flow_v,
-                 void* ws, cudaStream_t s)
+                 int fpitch, void* ws, cudaStream_t s)
 {
-    const size_t plane = align_up((size_t)w * h * 4, 256);
+    const int pp = flow_pitch(w);
+    const size_t plane = align_up((size_t)pp * h * 4, 256);
     float* P0 = static_cast<float*>(ws);
     float* P1 = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + plane);
     float* P2 = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + 2 * plane);
     int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + 3 * plane);
-    if (iters <= kMaxDtIters && flow_fast_supported(w, h, guide, flow_u, flow_v)) {
+    uint8_t* extra = static_cast<uint8_t*>(ws) + 3 * plane + 256;
+    uint8_t* gcopy = extra + flow_fast_extra_bytes(w, h);
+    const bool out_ok = fpitch % 4 == 0 && ((uintptr_t)flow_u % 16) == 0 &&
+                        ((uintptr_t)flow_v % 16) == 0;
+    if (iters <= kMaxDtIters && out_ok && flow_fast_supported(w, h)) {
+        // the guide at a 16-byte-aligned pitch: the caller's rows, or a padded copy
+        const uint8_t* g = guide;
+        int gp = w;
+        if ((w % 16) != 0 || ((uintptr_t)guide % 16) != 0) {
+            note_launch();
+            k_copy_rows<<<dim3((pp + 255) / 256, h), 256, 0, s>>>(guide, w, h, gcopy, pp);
+            g = gcopy;
+            gp = pp;
+        }
         DtLut luts[kMaxDtIters];
         for (int i = 0; i < iters; i++) luts[i] = make_dt_lut(sigma_s, sigma_r, iters, i);
-        if (launch_flow_fast(guide, w, h, fc, luts, iters, flow_eps, flow_u, flow_v, P0, P1, P2,
-                             err, static_cast<uint8_t*>(ws) + 3 * plane + 256, s))
+        if (launch_flow_fast(g, gp, w, h, fc, luts, iters, flow_eps, flow_u, flow_v, fpitch, P0, P1,
+                             P2, pp, err, extra, s))
             return;
     }
     const int Lr = odd_up((w + kNT - 1) / kNT);
@@ -530,9 +560,11 @@ void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, doub
             k_dt_rows<false><<<h, kNT, rs, s>>>(P0, P1, P2, guide, w, h, Lr, gmode, lut, fc);
         const int fin = i == iters - 1;
         if (sw == 4)
-            launch_cols<4>(P0, P1, P2, guide, w, h, lut, fin, (float)flow_eps, flow_u, flow_v, s);
+            launch_cols<4>(P0, P1, P2, guide, w, h, lut, fin, (float)flow_eps, flow_u, flow_v,
+                           fpitch, s);
         else
-            launch_cols<2>(P0, P1, P2, guide, w, h, lut, fin, (float)flow_eps, flow_u, flow_v, s);
+            launch_cols<2>(P0, P1, P2, guide, w, h, lut, fin, (float)flow_eps, flow_u, flow_v,
+                           fpitch, s);
     }
 }
 

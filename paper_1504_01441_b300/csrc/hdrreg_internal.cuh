@@ -450,20 +450,22 @@ struct DtLut {  // per-iteration link weights a_i^(1 + (sigma_s/sigma_r) d / 255
     float w[256];
 };
 DtLut make_dt_lut(double sigma_s, double sigma_r, int iters, int i);
-bool flow_fast_supported(int w, int h, const uint8_t* guide, const float* fu, const float* fv);
+bool flow_fast_supported(int w, int h);  // sizes only; pitches and alignment checked by the caller
 size_t flow_fast_extra_bytes(int w, int h);
-bool launch_flow_fast(const uint8_t* guide, int w, int h, const FlowCorners& fc, const DtLut* luts,
-                      int iters, double flow_eps, float* flow_u, float* flow_v, float* P0,
-                      float* P1, float* P2, int* err, void* extra, cudaStream_t s);
+bool launch_flow_fast(const uint8_t* guide, int gpitch, int w, int h, const FlowCorners& fc,
+                      const DtLut* luts, int iters, double flow_eps, float* flow_u, float* flow_v,
+                      int fpitch, float* P0, float* P1, float* P2, int ppitch, int* err,
+                      void* extra, cudaStream_t s);
 size_t flow_ws_bytes(int w, int h);
+int flow_pitch(int w);  // padded pitch (elements) of the flow's internal planes
 void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, double sigma_s,
                  double sigma_r, int iters, double flow_eps, float* flow_u, float* flow_v,
-                 void* ws, cudaStream_t s);
+                 int fpitch, void* ws, cudaStream_t s);
 int flow_supported(int w, int h);
 
 void launch_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_v, int w, int h,
-                 const double* H, const float* fu, const float* fv, float* oy, float* ou,
-                 float* ov, cudaStream_t s);
+                 const double* H, const float* fu, const float* fv, int fpitch, float* oy,
+                 float* ou, float* ov, cudaStream_t s);
 
 struct MergeSrcDev {
     const float* y;

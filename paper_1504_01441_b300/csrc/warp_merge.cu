@@ -79,8 +79,9 @@ __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
                                               const uint8_t* __restrict__ sv, int w, int h,
                                               const double* __restrict__ H,
                                               const float* __restrict__ fu,
-                                              const float* __restrict__ fv, float* __restrict__ oy,
-                                              float* __restrict__ ou, float* __restrict__ ov)
+                                              const float* __restrict__ fv, int fpitch,
+                                              float* __restrict__ oy, float* __restrict__ ou,
+                                              float* __restrict__ ov)
 {
     __shared__ WarpCoef cs;
     if (threadIdx.x == 0) prep_coef(H, w, cs);
@@ -95,10 +96,10 @@ __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
         for (int i = 0; i < 2; i++) {
             const int x = 2 * bx + i, y = 2 * by + j;
             if (x >= w || y >= h) continue;
-            const size_t o = (size_t)y * w + x;
+            const size_t o = (size_t)y * w + x, of = (size_t)y * fpitch + x;
             float dx, dy;
             h_disp(c, x, y, w, h, dx, dy);
-            const float tx = dx + fu[o], ty = dy + fv[o];
+            const float tx = dx + fu[of], ty = dy + fv[of];
             stx += tx;
             sty += ty;
             oy[o] = bilerp(sy, w, h, x, y, tx, ty);
@@ -445,13 +446,13 @@ __global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ re
 }  // namespace
 
 void launch_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_v, int w, int h,
-                 const double* H, const float* fu, const float* fv, float* oy, float* ou,
-                 float* ov, cudaStream_t s)
+                 const double* H, const float* fu, const float* fv, int fpitch, float* oy,
+                 float* ou, float* ov, cudaStream_t s)
 {
     const long long nb = (long long)((w + 1) / 2) * ((h + 1) / 2);
     const int grid = (int)((nb + 255) / 256);
     note_launch();
-    k_warp<<<grid, 256, 0, s>>>(src_y, src_u, src_v, w, h, H, fu, fv, oy, ou, ov);
+    k_warp<<<grid, 256, 0, s>>>(src_y, src_u, src_v, w, h, H, fu, fv, fpitch, oy, ou, ov);
 }
 
 void launch_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,

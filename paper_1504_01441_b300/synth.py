@@ -359,8 +359,7 @@ def method_params(tile: int = 32, radius: int = 6, **over) -> dict:
 
 def mixed_spec(stack_index: int, config_index: int = 3, with_gt: bool = False) -> StackSpec:
     """One stack of the mixed batch workload: luma area U(1, 12) MP, aspect 4:3 or 16:9
-    (sensor-like sizes: width a multiple of 32, even height), 2 or 3 frames, YUV420, noise
-    1.5 DN, +-4 px local field, 3 movers. The
+    (even sides), 2 or 3 frames, YUV420, noise 1.5 DN, +-4 px local field, 3 movers. The
     reference is the darkest frame; every other frame draws its ratio from {2, 4, 8}.
     The draws come from their own PCG64 stream seeded by the stack's seed, so a stack's
     shape does not depend on which other stacks are made."""
@@ -369,7 +368,7 @@ def mixed_spec(stack_index: int, config_index: int = 3, with_gt: bool = False) -
     aspect = (4.0 / 3.0) if rng.uniform() < 0.5 else (16.0 / 9.0)
     nsrc = 1 if rng.uniform() < 0.5 else 2
     ratios = tuple((int(rng.choice((2, 4, 8))), 1) for _ in range(nsrc))
-    w = 32 * int(round(math.sqrt(area * aspect) / 32.0))
+    w = 2 * int(round(math.sqrt(area * aspect) / 2.0))
     h = 2 * int(round(w / aspect / 2.0))
     return StackSpec(w, h, ratios=ratios, noise_sigma=1.5, field_amp=4.0, movers=3,
                      chroma=True, with_gt=with_gt)

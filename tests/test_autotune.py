@@ -41,8 +41,8 @@ def test_candidate_grid_is_valid_for_the_library():
 def test_mixed_workload_recipe():
     specs = [synth.mixed_spec(i) for i in range(64)]
     areas = [s.width * s.height / 1e6 for s in specs]
-    assert all(0.97 <= a <= 12.1 for a in areas)
-    assert all(s.width % 32 == 0 and s.height % 2 == 0 and s.chroma for s in specs)
+    assert all(0.99 <= a <= 12.02 for a in areas)
+    assert all(s.width % 2 == 0 and s.height % 2 == 0 and s.chroma for s in specs)
     aspects = [s.width / s.height for s in specs]
     assert all(min(abs(a - 4 / 3), abs(a - 16 / 9)) < 0.01 for a in aspects)
     n43 = sum(abs(a - 4 / 3) < 0.01 for a in aspects)
