@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
     constexpr int Wp = kRowNT * LM;          // floats per plane buffer
     constexpr int kBuf = 3 * Wp + Wp / 4;    // floats per buffer (3 planes + guide bytes)
     const int tid = threadIdx.x;
-    lut[tid] = lut_in.w[tid];
+    for (int i = tid; i < 256; i += blockDim.x) lut[i] = lut_in.w[i];
     if (tid == 0) {
         mbar_init(&bar[0]);
         mbar_init(&bar[1]);
@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
         float* s2 = s0 + 2 * Wp;
         const uint8_t* g = reinterpret_cast<const uint8_t*>(s0 + 3 * Wp);
         const int x0 = tid * LM;
+        bool empty = false;  // a row without corners filters to zeros: nothing to compute
         if (kSparse) {  // the planes of the first pass: residuals at this row's corners, else 0
 #pragma unroll
             for (int i = 0; i < LM; i++) {
@@ -341,6 +342,7 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
             }
             __syncthreads();
             const int ty = y / fc.tile;
+            int mine = 0;
             if (ty < fc.nty) {
                 for (int tx = tid; tx < fc.ntx; tx += kRowNT) {
                     const int4 c = tx == tid ? rc : rec[ty * fc.ntx + tx];
@@ -348,10 +350,12 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
                     s0[c.x] = __int_as_float(c.z);
                     s1[c.x] = __int_as_float(c.w);
                     s2[c.x] = 1.f;
+                    mine = 1;
                 }
             }
-            __syncthreads();
+            empty = !__syncthreads_or(mine);
         }
+        if (!empty) {
         float v[3][LM];
         float wl[LM + 1];
 #pragma unroll
@@ -382,6 +386,7 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
                 s2[x] = v[2][i];
             }
         }
+        }  // !empty
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -448,7 +453,7 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
     __shared__ Aff4 agg[kTSeg][kTW];
     __shared__ __align__(8) uint64_t bar[2];
     const int tid = threadIdx.x, lane = tid & 31, sg = tid >> 5;
-    lut[tid] = lut_in.w[tid];
+    for (int i = tid; i < 256; i += blockDim.x) lut[i] = lut_in.w[i];
     if (tid == 0) {
         mbar_init(&bar[0]);
         mbar_init(&bar[1]);
