@@ -9,6 +9,7 @@ one CUDA graph. Prints one JSON line (see the keys below).
   python bench.py --gpus N --steps K --warmup W [--impl reference]
   python bench.py --workload mixed64    # 64 stacks of 1-12 MP, 2-3 frames, tuned (T, R)
   python bench.py --workload sweep      # one pair per size, VGA .. 20 MP (scaling)
+  python bench.py --workload learned12  # 32 three-frame 12 MP stacks, learned level-0 search
 
 Under torchrun each rank (one GPU) registers its own batch of stacks: stacks
 are independent, so the ranks are replicas with no data-path collective; the
@@ -34,6 +35,8 @@ W, H = 2592, 1944
 MIXED = "mixed64"                       # command-line name of the mixed batch
 MIXED_NAME = "mixed64_1to12mp_yuv420"
 SWEEP = "sweep"
+SCALE12 = "learned12"
+SCALE12_NAME = "learned_batched_32x12mp_3frame_yuv420"
 MIXED_METRIC = "registered+merged output Mpix/s per B300 (64 stacks of 1-12 MP, 2-3 frames)"
 
 
@@ -50,9 +53,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short run for a profiler")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED, SWEEP],
-                    help="the 5 MP pair batch (default) or the mixed 1-12 MP batch")
-    ap.add_argument("--stacks", type=int, default=64, help="stacks of the mixed batch")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED, SWEEP, SCALE12],
+                    help="the 5 MP pair batch (default), the mixed 1-12 MP batch, the size "
+                         "sweep, or 12 MP three-frame stacks with the learned search")
+    ap.add_argument("--stacks", type=int, default=64,
+                    help="stacks of the mixed batch (of the learned 12 MP batch: 32 unless set)")
     ap.add_argument("--output", default="merge", choices=["merge", "fusion"],
                     help="the fused call's output: the irradiance merge (a11) or the "
                          "error-tolerant exposure fusion of Sec. 2.5 (output_mode 1)")
@@ -558,7 +563,7 @@ def run_mixed(args):
         buckets = {}
         for s, p in zip(stacks, params):
             b = autotune.bucket_of(s.width, s.height, table["buckets_mp"])
-            buckets.setdefault(b, [p.tile, p.radius, 0])[2] += 1
+            buckets.setdefault(b, [p.tile, p.radius, p.search_threads or 256, 0])[3] += 1
         line = {
             "metric": MIXED_METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -569,7 +574,7 @@ def run_mixed(args):
                        "registered_mpix_per_step": round(reg_mpix, 3),
                        "input_bytes_per_step": in_bytes,
                        "buckets_mp": table["buckets_mp"],
-                       "picks_T_R_count": {str(table["buckets_mp"][b]): v
+                       "picks_T_R_B_count": {str(table["buckets_mp"][b]): v
                                            for b, v in sorted(buckets.items())},
                        "picks_source": picks_src, "graph": True, "lanes": args.lanes,
                        "l2": f"inputs larger than L2: {in_bytes / 1e9:.2f} GB resident per step",
@@ -627,7 +632,7 @@ def measure_mixed_cpu_baseline(synth, stacks, table, n=4):
     sub = sorted(stacks, key=lambda s: s.width * s.height)[:n]
     t0 = time.perf_counter()
     for s in sub:
-        t, r = table["picks"][autotune.bucket_of(s.width, s.height, table["buckets_mp"])]
+        t, r, _ = autotune.pick_of(table, s.width, s.height)
         oracle.register_merge(s.ref, s.srcs, s.ratios, synth.method_params(t, r))
     sec = time.perf_counter() - t0
     mpix = sum(s.width * s.height for s in sub) / 1e6
@@ -677,6 +682,175 @@ def run_sweep(args):
         "batched_slope": round(slope(xs, zs), 3), "sweep": rows,
     }
     print(json.dumps(line), flush=True)
+
+
+def _time_graph(torch, runner, frames, stream, warmup, steps):
+    """-> (ms per replay of runner(frames) captured as one CUDA graph, the graph, the
+    library launches it holds)."""
+    from paper_1504_01441_b300 import hdrreg
+    runner(frames, stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    n0 = hdrreg.launch_count()
+    with torch.cuda.graph(g, stream=stream):
+        runner(frames, stream=stream)
+    launches = hdrreg.launch_count() - n0
+    with torch.cuda.stream(stream):
+        for _ in range(max(warmup, 0)):
+            g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            g.replay()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps, g, launches
+
+
+def run_scale12(args):
+    """Learned + batched at scale: 32 three-frame 4000 x 3000 YUV420 stacks (exposures 1/4,
+    1, 4 of the reference's; +-8 px fields; 5 movers) per step through the batched fused
+    call with the learned level-0 search, one CUDA graph, at the default operating point
+    (refine 1, fallback above 1.5 x the median plain cost) and at the calibrated one; the
+    plain path on the same stacks; the host-staged form (e2e); and one training step of
+    the predictor (64 crops of 256 x 256 full-resolution pixels: forward, backward and
+    Adam, all in the library's kernels)."""
+    ws, rank, local = dist_env()
+    n = args.stacks if args.stacks != 64 else 32
+    t_gen = time.perf_counter()
+    from paper_1504_01441_b300 import synth as _s
+    stacks = _s.make_scale12_stacks(n)          # spawn pool, before CUDA starts
+    t_gen = time.perf_counter() - t_gen
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1504_01441_b300 import hdrreg, learned as L, synth
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w, h = stacks[0].width, stacks[0].height
+    p = hdrreg.params_from_dict(synth.method_params(32, 6))
+
+    def up(a):
+        return torch.from_numpy(a).to(dev)
+    frames = [((up(s.ref.y), up(s.ref.u), up(s.ref.v)),
+               [(up(f.y), up(f.u), up(f.v)) for f in s.srcs], list(s.ratios)) for s in stacks]
+    stream = torch.cuda.Stream(device=dev)
+    plain = hdrreg.RegisterMergeBatch(w, h, 2, p, True, slots=n, lanes=args.lanes, device=dev)
+    ms_plain, g, _ = _time_graph(torch, plain, frames, stream, args.warmup, args.steps)
+    del g, plain
+    theta = torch.tensor(np.load(L.THETA_FILE)).to(dev)
+    # quality and thresholds from the first source (exposure 1/4) of the first two stacks
+    prep = [L.prepare(s, p) for s in stacks[:2]]
+    med = float(torch.cat([P.cost[P.valid.bool()] for P in prep]).double().median().item())
+    points = [("default", 1, 1.5)]
+    if os.path.exists(L.OPS_FILE):
+        ch = json.load(open(L.OPS_FILE)).get("chosen")
+        if ch:
+            points.append(("at_bound", ch["refine"], ch["ratio"]))
+    legs, clk_sum, launches, pl_default = {}, None, 0, None
+    for name, refine, ratio in points:
+        q = L.evaluate(prep, theta, p, fallback_ratio=ratio, refine=refine)
+        pl = hdrreg.params_from_dict(p.as_dict())
+        pl.predictor = theta.data_ptr()
+        pl.fallback_cost = int(ratio * med)
+        pl.predictor_refine = refine
+        lrn = hdrreg.RegisterMergeBatch(w, h, 2, pl, True, slots=n, lanes=args.lanes, device=dev)
+        with ClockSampler(local) as clk:
+            ms, g, per_step = _time_graph(torch, lrn, frames, stream, args.warmup, args.steps)
+        if ws > 1:
+            ms = max_over_ranks(torch, dist, ms, dev)
+        fb = sum(d.fallbacks for i in range(n) for d in lrn.diagnostics(i))
+        val = sum(d.valid for i in range(n) for d in lrn.diagnostics(i))
+        legs[name] = {"value": round(ws * n * w * h / 1e6 / (ms / 1e3), 2), "unit": "Mpix/s",
+                      "ms_per_step": round(ms, 3), "refine": refine, "fallback_ratio": ratio,
+                      "fallback_cost": pl.fallback_cost,
+                      "fallback_rate": round(fb / max(val, 1), 4),
+                      "epe_vs_plain_px": round(q["epe_px"], 3),
+                      "epe_vs_plain_median_px": round(q["epe_median_px"], 3),
+                      "meets_0.5px_vs_plain": bool(q["epe_px"] <= 0.5)}
+        if name == "default":
+            clk_sum, pl_default = clk.summary(), pl
+            launches = args.steps * per_step
+        del g, lrn
+    del prep
+    # host-staged (pinned host planes in and out), default operating point
+    hin = [[torch.from_numpy(a).pin_memory() for a in
+            (s.ref.y, s.ref.u, s.ref.v) + tuple(x for f in s.srcs for x in (f.y, f.u, f.v))]
+           for s in stacks]
+    hout = [[torch.empty((h, w), dtype=torch.float32).pin_memory(),
+             torch.empty((h // 2, w // 2), dtype=torch.float32).pin_memory(),
+             torch.empty((h // 2, w // 2), dtype=torch.float32).pin_memory()] for _ in stacks]
+    batch = [((x[0], x[1], x[2]), [(x[3], x[4], x[5]), (x[6], x[7], x[8])], list(s.ratios))
+             for x, s in zip(hin, stacks)]
+    host = hdrreg.RegisterMergeHost(w, h, 2, pl_default, lanes=args.lanes, device=dev)
+    for _ in range(2):
+        host(batch, hout, stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    K = max(3, args.steps // 2)
+    for _ in range(K):
+        host(batch, hout, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = a.elapsed_time(b) / K
+    del host
+    # one training step: 64 crops of 64 x 64 quarter-resolution pixels (256 x 256 full)
+    net = hdrreg.Predictor(64, 64, 64, theta.cpu().numpy(), device=dev)
+    x = torch.empty((64, 64, 64, 2), dtype=torch.bfloat16, device=dev).uniform_(-1, 1)
+    label = torch.zeros((64, net.ho, net.wo, 2), dtype=torch.float32, device=dev)
+    valid = torch.ones((64, net.ho, net.wo), dtype=torch.uint8, device=dev)
+
+    def train_step():
+        net.forward(x, stream=stream)
+        net.backward(x, label, valid, stream=stream)
+        net.adam(1e-4, stream=stream)
+    for _ in range(3):
+        train_step()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(10):
+        train_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(b) / 10
+    out_mpix = n * w * h / 1e6
+    d = legs["default"]
+    if rank == 0:
+        line = {
+            "metric": "registered+merged output Mpix/s per B300, learned level-0 search "
+                      f"({n} three-frame 12 MP stacks)",
+            "value": d["value"], "unit": "Mpix/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": d["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/i32 match, bf16 net, f64 fit, f32 flow/warp/merge",
+            "data": "synthetic",
+            "config": {"workload": SCALE12_NAME, "stacks": n, "width": w, "height": h,
+                       "frames": 3, "exposures": "1/4, 1 (reference), 4", "field_px": 8,
+                       "movers": 5, "tile": 32, "radius": 6, "lanes": args.lanes,
+                       "graph": True, "l2": f"inputs larger than L2 ({n} resident stacks)",
+                       "generation_s": round(t_gen, 1), "parallelism": f"replicas x{ws}"},
+            "learned": legs,
+            "plain": {"value": round(ws * out_mpix / (ms_plain / 1e3), 2), "unit": "Mpix/s",
+                      "ms_per_step": round(ms_plain, 3)},
+            "quality_sample": "first source (exposure 1/4) of the first 2 stacks",
+            "e2e": {"value": round(out_mpix / (ms_e2e / 1e3), 2), "unit": "Mpix/s",
+                    "h2d_bytes_per_step": sum(t.numel() for x in hin for t in x),
+                    "d2h_bytes_per_step": sum(t.numel() * 4 for x in hout for t in x),
+                    "ms_per_step": round(ms_e2e, 3),
+                    "api": "hdrreg_register_merge_host, default operating point"},
+            "train_step_ms": round(train_ms, 3),
+            "train_step": "64 crops of 64x64x2 quarter-resolution inputs (256x256 full): "
+                          "forward, backward, Adam",
+            "gpu_launches": launches, "clocks": clk_sum,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 def synth_sweep():
@@ -732,7 +906,7 @@ def run_reference_mixed(args, ws):
              {"buckets_mp": list(autotune.BUCKETS_MP), "picks": [autotune.DEFAULT] * 4})
 
     def run(s):
-        t, r = table["picks"][autotune.bucket_of(s.width, s.height, table["buckets_mp"])]
+        t, r, _ = autotune.pick_of(table, s.width, s.height)
         oracle.register_merge(s.ref, s.srcs, s.ratios, synth.method_params(t, r))
 
     for i in range(max(args.warmup, 0)):
@@ -766,6 +940,8 @@ def main():
         run_mixed(args)
     elif args.workload == SWEEP:
         run_sweep(args)
+    elif args.workload == SCALE12:
+        run_scale12(args)
     else:
         run_ours(args)
 

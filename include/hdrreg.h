@@ -103,6 +103,9 @@ typedef struct hdrreg_params {
                                predicted match exceeds this falls back to the full search */
     int32_t predictor_refine; /* learned search: offsets [-r, r]^2 around the rounded
                                prediction are tried before the fallback test, 0..radius */
+    int32_t search_threads; /* threads per tile CTA of the SSD search (one CTA per tile):
+                               0 (= 256), 64, 128 or 256; a launch shape only, the
+                               results do not depend on it                              */
 } hdrreg_params;
 
 /* A YUV420 (or luma-only: u = v = NULL) 8-bit frame, device pointers. */

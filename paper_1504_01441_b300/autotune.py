@@ -1,4 +1,5 @@
-"""Tile size T and search radius R per image-size bucket for batches of mixed stacks.
+"""Tile size T, search radius R and search block shape B per image-size bucket for
+batches of mixed stacks.
 
 The paper runs one tile size and one search radius for its 5 MP pairs (Sec. 2.6,
 Sec. 3). A batch that mixes 1-12 MP stacks can do better per size: small images
@@ -15,10 +16,13 @@ bucket:
     source image;
 
 and keeps the fastest candidate whose error is no larger than that of the default
-(T = 32, R = 6). The selection rule and the bucket lookup are plain host code
-(`pick`, `bucket_of`); measuring needs the GPU. `python -m
+(T = 32, R = 6). A second stage then times the chosen (T, R) with each block shape of
+the tile search -- B threads per tile CTA, 64, 128 or 256 -- and keeps the fastest;
+the search's results are exact integers that do not depend on B, so the error stays
+that of the first stage. The selection rules and the bucket lookup are plain host code
+(`pick`, `pick_block`, `bucket_of`, `pick_of`); measuring needs the GPU. `python -m
 paper_1504_01441_b300.autotune` writes the table next to this file, where
-`load_table` finds it.
+`load_table` finds it (`--blocks-only` re-runs the second stage on an existing table).
 """
 from __future__ import annotations
 
@@ -30,6 +34,8 @@ BUCKETS_MP = (2.0, 4.0, 8.0, 12.0)          # upper bounds of the luma-area buck
 TILES = (16, 24, 32, 48)
 RADII = (3, 4, 5, 6, 7, 8)
 DEFAULT = (32, 6)
+BLOCKS = (64, 128, 256)                     # threads per tile CTA of the search
+DEFAULT_BLOCK = 256
 TABLE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_table.json")
 
 
@@ -57,12 +63,27 @@ def pick(results: Dict[Tuple[int, int], Tuple[float, float]],
     return min(ok, key=lambda kv: (kv[1][0], kv[0]))[0]
 
 
+def pick_block(times: Dict[int, float]) -> int:
+    """times: block shape B -> time. The fastest; ties go to the smaller B."""
+    if not times:
+        raise ValueError("no block shape was measured")
+    return min(times.items(), key=lambda kv: (kv[1], kv[0]))[0]
+
+
+def pick_of(table: Dict, w: int, h: int) -> Tuple[int, int, int]:
+    """(T, R, B) of a w x h stack's bucket; a table without block shapes gives B = 0 (the
+    library's default, 256)."""
+    pk = tuple(table["picks"][bucket_of(w, h, table["buckets_mp"])])
+    return (pk[0], pk[1], pk[2] if len(pk) > 2 else 0)
+
+
 def params_for(w: int, h: int, table: Dict, **over):
-    """Library parameters of a w x h stack: the method's defaults with the (T, R) of
+    """Library parameters of a w x h stack: the method's defaults with the (T, R, B) of
     its bucket from a tuning table (as returned by load_table)."""
     from . import hdrreg, synth
-    t, r = table["picks"][bucket_of(w, h, table["buckets_mp"])]
-    return hdrreg.params_from_dict(synth.method_params(tile=t, radius=r, **over))
+    t, r, b = pick_of(table, w, h)
+    return hdrreg.params_from_dict(synth.method_params(tile=t, radius=r, search_threads=b,
+                                                       **over))
 
 
 def load_table(path: str = TABLE_FILE) -> Dict:
@@ -176,20 +197,53 @@ def tuning_jobs(per_bucket: int = 2, buckets: Sequence[float] = BUCKETS_MP):
     return jobs
 
 
+def _by_bucket(stacks, buckets):
+    groups: List[list] = [[] for _ in buckets]
+    for st in stacks:
+        groups[bucket_of(st.width, st.height, buckets)].append(st)
+    return groups
+
+
+def tune_blocks(stacks, picks: Sequence[Sequence[int]], blocks: Sequence[int] = BLOCKS,
+                reps: int = 5, buckets: Sequence[float] = BUCKETS_MP, device="cuda", log=None,
+                flush=None):
+    """Second stage: the (T, R) pick of every bucket timed with each block shape of the
+    search; -> ([T, R, B] per bucket, {bucket: {B: us}})."""
+    import torch
+    from . import hdrreg, synth
+    if flush is None:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    out, meas = [], []
+    for b, group in enumerate(_by_bucket(stacks, buckets)):
+        t, r = picks[b][0], picks[b][1]
+        if not group:
+            out.append([t, r, DEFAULT_BLOCK])
+            meas.append({})
+            continue
+        times = {}
+        for nt in blocks:
+            p = hdrreg.params_from_dict(synth.method_params(tile=t, radius=r, search_threads=nt))
+            times[nt] = sum(fused_time_us(st, p, reps, device, flush) for st in group) / len(group)
+            if log:
+                log(f"bucket <= {buckets[b]} MP: T={t} R={r} B={nt}: {times[nt]:.1f} us")
+        out.append([t, r, pick_block(times)])
+        meas.append({str(k): round(v, 2) for k, v in times.items()})
+    return out, meas
+
+
 def tune(stacks, cands: Optional[Sequence[Tuple[int, int]]] = None, reps: int = 5,
-         buckets: Sequence[float] = BUCKETS_MP, device="cuda", log=None) -> Dict:
-    """Measure every candidate on the stacks of each bucket; -> table dict."""
+         buckets: Sequence[float] = BUCKETS_MP, device="cuda", log=None,
+         blocks: Sequence[int] = BLOCKS) -> Dict:
+    """Measure every candidate on the stacks of each bucket, then the block shapes of
+    the pick; -> table dict."""
     import torch
     from . import hdrreg, synth
     cands = list(cands or candidates())
     if DEFAULT not in cands:
         cands.append(DEFAULT)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-    by_bucket: List[list] = [[] for _ in buckets]
-    for st in stacks:
-        by_bucket[bucket_of(st.width, st.height, buckets)].append(st)
     picks, meas = [], []
-    for b, group in enumerate(by_bucket):
+    for b, group in enumerate(_by_bucket(stacks, buckets)):
         if not group:
             picks.append(DEFAULT)
             meas.append({})
@@ -204,8 +258,9 @@ def tune(stacks, cands: Optional[Sequence[Tuple[int, int]]] = None, reps: int = 
                 log(f"bucket <= {buckets[b]} MP: T={t} R={r}: {us:.1f} us, EPE {epe:.4f} px")
         picks.append(pick(res))
         meas.append({f"{t},{r}": [round(v[0], 2), round(v[1], 5)] for (t, r), v in res.items()})
-    return {"buckets_mp": list(buckets), "picks": [list(x) for x in picks],
-            "default": list(DEFAULT), "measurements": meas,
+    picks3, bmeas = tune_blocks(stacks, picks, blocks, reps, buckets, device, log, flush)
+    return {"buckets_mp": list(buckets), "picks": picks3,
+            "default": list(DEFAULT), "measurements": meas, "block_measurements": bmeas,
             "stacks": [[st.width, st.height, len(st.srcs), st.seed] for st in stacks],
             "device": torch.cuda.get_device_name(device), "reps": reps, "lanes": 4}
 
@@ -216,10 +271,19 @@ def main():
     ap.add_argument("--per-bucket", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--out", default=TABLE_FILE)
+    ap.add_argument("--blocks-only", action="store_true",
+                    help="keep the (T, R) picks of the existing table; time the block shapes")
     a = ap.parse_args()
     from . import synth
     stacks = synth.make_stacks_parallel(tuning_jobs(a.per_bucket))   # before any CUDA call
-    table = tune(stacks, reps=a.reps, log=lambda m: print(m, flush=True))
+    log = lambda m: print(m, flush=True)
+    if a.blocks_only:
+        table = load_table()
+        picks3, bmeas = tune_blocks(stacks, table["picks"], reps=a.reps,
+                                    buckets=table["buckets_mp"], log=log)
+        table["picks"], table["block_measurements"] = picks3, bmeas
+    else:
+        table = tune(stacks, reps=a.reps, log=log)
     with open(a.out, "w") as f:
         json.dump(table, f, indent=1)
     print(json.dumps({"picks": table["picks"], "buckets_mp": table["buckets_mp"]}))

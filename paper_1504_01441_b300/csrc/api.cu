@@ -93,6 +93,7 @@ static SearchGeom make_geom(int w, int h, const hdrreg_params* p)
     g.ntx = w / p->tile;
     g.nty = h / p->tile;
     g.corner_thr = (long long)p->corner_thresh * p->quad * p->quad;
+    g.threads = p->search_threads ? p->search_threads : 256;
     return g;
 }
 
@@ -288,6 +289,9 @@ hdrreg_status hdrreg_validate_params(const hdrreg_params* p)
         return fail(HDRREG_E_INVALID_ARG, "ssim_radius must be %d", kSsimRadius);
     if (p->predictor && (p->predictor_refine < 0 || p->predictor_refine > p->radius))
         return fail(HDRREG_E_INVALID_ARG, "predictor_refine must be in [0, radius]");
+    if (p->search_threads != 0 && p->search_threads != 64 && p->search_threads != 128 &&
+        p->search_threads != 256)
+        return fail(HDRREG_E_INVALID_ARG, "search_threads must be 0, 64, 128 or 256");
     if (p->propagate_full != 0 && p->propagate_full != 1)
         return fail(HDRREG_E_INVALID_ARG, "propagate_full must be 0 or 1");
     if (p->output_mode < 0 || p->output_mode > 2)

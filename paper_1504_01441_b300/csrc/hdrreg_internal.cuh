@@ -378,6 +378,7 @@ void launch_pyramid(const uint8_t* in0, int w, int h, int levels, LutSpec lut, u
 struct SearchGeom {
     int w, h, tile, radius, patch_half, grid_half, quad, step, ntx, nty;
     long long corner_thr;
+    int threads;  // threads per tile CTA of the search: 64, 128 or 256
 };
 // Learned level-0 search (row a-L): predicted displacement per tile and the fallback rule.
 struct PredSearch {

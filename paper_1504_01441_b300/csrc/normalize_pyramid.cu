@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_histograms(const uint8_t* __restrict__ 
 {
     __shared__ uint32_t hs[8][256];
     const uint8_t* in = blockIdx.y ? b : a;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     for (int v = threadIdx.x; v < 8 * 256; v += blockDim.x) hs[v >> 8][v & 255] = 0;
     __syncthreads();
     auto add = [&](uint32_t v, bool on) {
@@ -323,7 +323,7 @@ void launch_pyramid2(const uint8_t* const in0[2], int w, int h, int levels, cons
     size_t smem = 0;
     for (int side = a.S, l = 0; l < levels; l++, side /= 2) smem += (size_t)side * side;
     dim3 grid((w + a.S - 1) / a.S, (h + a.S - 1) / a.S, nframes);
-    if (smem > 48 * 1024) ensure_smem((const void*)k_pyramid, smem);
+    ensure_smem((const void*)k_pyramid, smem);  // static + dynamic may pass 48 KB
     note_launch();
     k_pyramid<<<grid, 256, smem, s>>>(a);
 }

@@ -25,8 +25,8 @@ namespace hdrreg {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+// Threads per tile CTA: a template parameter (64, 128 or 256, chosen per workload by
+// search_threads); every loop below strides by it, and the results do not depend on it.
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -54,6 +54,7 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v)
 // floor(32 / pw) rows per step. Blocks inside the plane of a 4-byte aligned buffer
 // read two aligned words per output word (the last read stays inside the buffer by
 // the explicit bound below).
+template <int NWARPS>
 __device__ __forceinline__ void stage_block(const uint8_t* __restrict__ img, int w, int h, int x0,
                                             int y0, int cols, int rows, uint32_t* dst, int pw)
 {
@@ -63,7 +64,7 @@ __device__ __forceinline__ void stage_block(const uint8_t* __restrict__ img, int
     const bool fast = ((uintptr_t)img & 3u) == 0 && x0 >= 0 && y0 >= 0 && x0 + cols <= w &&
                       y0 + rows <= h &&
                       (size_t)(y0 + rows - 1) * w + x0 + 4 * (size_t)pw + 4 <= (size_t)w * h;
-    for (int r = warp * rpw + sub; r < rows; r += kWarps * rpw) {
+    for (int r = warp * rpw + sub; r < rows; r += NWARPS * rpw) {
         uint32_t word;
         if (fast) {
             const size_t off = (size_t)(y0 + r) * w + x0 + 4 * j;
@@ -113,12 +114,14 @@ struct SearchSmem {
     }
 };
 
-__global__ void __launch_bounds__(kThreads, 8) k_local_search(
+template <int NT>
+__global__ void __launch_bounds__(NT, 2048 / NT) k_local_search(
     const uint8_t* __restrict__ ref, const uint8_t* __restrict__ src, const double* __restrict__ H,
     SearchGeom g, int32_t* __restrict__ corner_xy, int32_t* __restrict__ match_xy,
     uint32_t* __restrict__ cost_out, uint8_t* __restrict__ valid_out,
     uint32_t* __restrict__ mask_zero, PredSearch ps)
 {
+    constexpr int kWarps = NT / 32;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t red[kWarps];
     __shared__ float hs[18];  // (float)H, |(float)H|
@@ -148,10 +151,9 @@ __global__ void __launch_bounds__(kThreads, 8) k_local_search(
         hs[9 + tid] = fabsf(f);
     }
     // ---- stage the reference region (clamp-to-edge) and its integral image
-    stage_block(ref, g.w, g.h, ox, oy, L.RS, L.RS, region, L.RPW);
+    stage_block<kWarps>(ref, g.w, g.h, ox, oy, L.RS, L.RS, region, L.RPW);
     __syncthreads();
-    if (tid < IS) {  // row prefix sums, one row per thread (row 0 and column 0 zero)
-        const int r = tid;
+    for (int r = tid; r < IS; r += NT) {  // row prefix sums, one row per thread (row 0 and column 0 zero)
         int32_t* out = ii + r * IS;
         out[0] = 0;
         int run = 0;
@@ -173,11 +175,11 @@ __global__ void __launch_bounds__(kThreads, 8) k_local_search(
         }
     }
     __syncthreads();
-    if (tid < IS) {  // column prefix sums, one column per thread
+    for (int c = tid; c < IS; c += NT) {  // column prefix sums, one column per thread
         int run = 0;
         for (int r = 1; r < IS; r++) {
-            run += ii[r * IS + tid];
-            ii[r * IS + tid] = run;
+            run += ii[r * IS + c];
+            ii[r * IS + c] = run;
         }
     }
     __syncthreads();
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_local_search(
     //      ties -> lowest row-major candidate index
     const int K = g.grid_half, side = 2 * K + 1, q = g.quad;
     uint64_t best = 0;
-    for (int c = tid; c < side * side; c += kThreads) {
+    for (int c = tid; c < side * side; c += NT) {
         const int j = c / side - K, i = c % side - K;
         const int rx = L.E + g.step * i, ry = L.E + g.step * j;
         auto box = [&](int x0, int y0) {
@@ -277,35 +279,35 @@ __global__ void __launch_bounds__(kThreads, 8) k_local_search(
         // ---- stage the source window (byte 0 of a row = column ccx - RR - hp)
         const int side_d = 2 * RR + 1, nd = side_d * side_d, nq = (side_d + 3) >> 2;
         const int ws = 2 * RR + P;
-        stage_block(src, g.w, g.h, ccx - RR - hp, ccy - RR - hp, ws, ws, win, L.WW);
+        stage_block<kWarps>(src, g.w, g.h, ccx - RR - hp, ccy - RR - hp, ws, ws, win, L.WW);
         __syncthreads();
         // ---- sum of squares of every window position: SSD(d) = sum a^2 + sum b_d^2 -
         //      2 sum a b_d, exact in 32-bit unsigned arithmetic (every term < 2^32).
         //      Row box sums (one window row per thread, sliding over dx), then column
         //      box sums (one dx per thread, sliding over dy) start ssd at a^2 + b_d^2.
-        if (tid < ws) {
-            const uint32_t* wr = win + tid * L.WW;
+        for (int row = tid; row < ws; row += NT) {
+            const uint32_t* wr = win + row * L.WW;
             auto sq = [&](int c) {
                 const uint32_t b = (wr[c >> 2] >> (8 * (c & 3))) & 255u;
                 return b * b;
             };
             uint32_t run = 0;
             for (int c = 0; c < P; c++) run += sq(c);
-            hsq[tid * side_d] = run;
+            hsq[row * side_d] = run;
             for (int dx = 1; dx < side_d; dx++) {
                 run += sq(dx + P - 1) - sq(dx - 1);
-                hsq[tid * side_d + dx] = run;
+                hsq[row * side_d + dx] = run;
             }
         }
         __syncthreads();
-        if (tid < side_d) {
+        for (int dx = tid; dx < side_d; dx += NT) {
             uint32_t run = 0;
-            for (int r = 0; r < P; r++) run += hsq[r * side_d + tid];
+            for (int r = 0; r < P; r++) run += hsq[r * side_d + dx];
             const uint32_t a2 = s_a2;
-            ssd[tid] = a2 + run;
+            ssd[dx] = a2 + run;
             for (int dy = 1; dy < side_d; dy++) {
-                run += hsq[(dy + P - 1) * side_d + tid] - hsq[(dy - 1) * side_d + tid];
-                ssd[dy * side_d + tid] = a2 + run;
+                run += hsq[(dy + P - 1) * side_d + dx] - hsq[(dy - 1) * side_d + dx];
+                ssd[dy * side_d + dx] = a2 + run;
             }
         }
         __syncthreads();
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_local_search(
         {
             constexpr int kSplit = 4;
             const int rows_per = (P + kSplit - 1) / kSplit;
-            for (int item = tid; item < side_d * nq * kSplit; item += kThreads) {
+            for (int item = tid; item < side_d * nq * kSplit; item += NT) {
                 const int part = item % kSplit, rest = item / kSplit;
                 const int dq = rest % nq, dy = rest / nq;
                 const int v0 = part * rows_per, v1 = min(P, v0 + rows_per);
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_local_search(
         }
         __syncthreads();
         uint64_t bestk = ~0ull;
-        for (int di = tid; di < nd; di += kThreads) {
+        for (int di = tid; di < nd; di += NT) {
             const uint64_t key = ((uint64_t)ssd[di] << 16) | (uint64_t)di;
             bestk = key < bestk ? key : bestk;
         }
@@ -387,11 +389,19 @@ void launch_local_search(const uint8_t* ref, const uint8_t* src, const double* H
     const int n = g.ntx * g.nty;
     if (n <= 0) return;
     const SearchSmem L(g);
-    if (L.total > 48 * 1024) ensure_smem((const void*)k_local_search, L.total);
     const PredSearch ps = pred ? *pred : PredSearch{nullptr, 0, 0, 0u, nullptr};
     note_launch();
-    k_local_search<<<n, kThreads, L.total, s>>>(ref, src, H, g, corner_xy, match_xy, cost, valid,
-                                                mask_zero, ps);
+    auto go = [&](auto kern, int nt) {
+        ensure_smem((const void*)kern, L.total);  // static + dynamic may pass 48 KB
+        kern<<<n, nt, L.total, s>>>(ref, src, H, g, corner_xy, match_xy, cost, valid, mask_zero,
+                                    ps);
+    };
+    if (g.threads == 64)
+        go(k_local_search<64>, 64);
+    else if (g.threads == 128)
+        go(k_local_search<128>, 128);
+    else
+        go(k_local_search<256>, 256);
 }
 
 // Training label of every tile: match - search centre (Eq. 3), 0 without a corner.

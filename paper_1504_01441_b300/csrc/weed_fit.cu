@@ -515,7 +515,7 @@ void launch_weed_level(const WeedLevelArgs& a, cudaStream_t s)
     int blocks = (iters + 3) / 4;
     if (blocks < 1) blocks = 1;  // the fit still runs
     const size_t smem = weed_level_smem_bytes(a.n);
-    if (smem > 48 * 1024) ensure_smem((const void*)k_weed_level, smem);
+    ensure_smem((const void*)k_weed_level, smem);  // static + dynamic may pass 48 KB
     note_launch();
     k_weed_level<<<blocks, kLevelThreads, smem, s>>>(a, make_inlier_geom(a.w, a.eps));
 }
@@ -638,7 +638,7 @@ void launch_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_
     const int warps = (iters + 3) / 4;
     const int blocks = (warps + kWeedWarps - 1) / kWeedWarps;
     const size_t smem = (size_t)kWeedWarps * ((n + 31) / 32) * 4;
-    if (smem > 48 * 1024) ensure_smem((const void*)k_weed_iters, smem);
+    ensure_smem((const void*)k_weed_iters, smem);  // static + dynamic may pass 48 KB
     note_launch();
     k_weed_iters<<<blocks, kWeedThreads, smem, s>>>(n, w, delta_min, delta_div, seed, it0, it1,
                                                     mask, ws, make_inlier_geom(w, eps));

@@ -62,7 +62,7 @@ class Params(C.Structure):
         ("weed_eps", C.c_double), ("sigma_s", C.c_double), ("sigma_r", C.c_double),
         ("ssim_sigma", C.c_double), ("we_sigma", C.c_double), ("flow_eps", C.c_double),
         ("weed_seed", C.c_uint64), ("predictor", C.c_void_p), ("fallback_cost", C.c_uint32),
-        ("predictor_refine", C.c_int32),
+        ("predictor_refine", C.c_int32), ("search_threads", C.c_int32),
     ]
 
     def as_dict(self) -> Dict:

@@ -352,7 +352,7 @@ def method_params(tile: int = 32, radius: int = 6, **over) -> dict:
              grid_half=4, quad=10, corner_thresh=2, weed_iters=512, weed_delta_min=8,
              weed_delta_div=20, norm_mode=0, dt_iters=3, ssim_radius=5, propagate_full=0,
              weed_eps=1.5, sigma_s=400.0, sigma_r=0.5, ssim_sigma=1.5, we_sigma=0.2,
-             flow_eps=1e-20, weed_seed=0x1504014410, output_mode=0)
+             flow_eps=1e-20, weed_seed=0x1504014410, output_mode=0, search_threads=0)
     p.update(over)
     return p
 
@@ -385,6 +385,27 @@ def dark_spec(stops: int, width: int = 640, height: int = 480) -> StackSpec:
     exposure): the reference lies `stops` stops under the source."""
     return StackSpec(width, height, ratios=((2 ** stops, 1),), noise_sigma=1.0, field_amp=3.0,
                      movers=1, chroma=False, scene_gain=1.0 / 2 ** stops)
+
+
+# Learned + batched at scale: 4000 x 3000 three-frame stacks, exposures 1/4, 1 and 4 times
+# the reference's (the r = 1 frame is the reference), +-8 px local fields, 5 movers.
+SCALE12_SPEC = StackSpec(4000, 3000, ratios=((1, 4), (4, 1)), noise_sigma=1.5, field_amp=8.0,
+                         movers=5, chroma=True, with_gt=False)
+
+
+def make_scale12_stack(stack_index: int) -> Stack:
+    return make_stack(SCALE12_SPEC, stack_seed(5, stack_index))
+
+
+def make_scale12_stacks(n: int, processes=None):
+    """make_scale12_stack for stacks 0..n-1 in a spawn-started process pool."""
+    import multiprocessing as mp
+    import os
+    k = processes or min(n, os.cpu_count() or 1)
+    if k <= 1:
+        return [make_scale12_stack(i) for i in range(n)]
+    with mp.get_context("spawn").Pool(k) as pool:
+        return pool.map(make_scale12_stack, range(n))
 
 
 # Sizes of the scaling sweep: 4:3 frames from VGA to 20 MP (widths multiples of 32).

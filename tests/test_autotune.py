@@ -20,6 +20,24 @@ def test_pick_takes_the_fastest_candidate_no_worse_than_the_default():
         autotune.pick({(16, 3): (1.0, 0.1)})
 
 
+def test_pick_block_takes_the_fastest_shape():
+    assert autotune.pick_block({64: 30.0, 128: 25.0, 256: 27.0}) == 128
+    assert autotune.pick_block({64: 25.0, 128: 25.0, 256: 27.0}) == 64   # tie: smaller B
+    with pytest.raises(ValueError):
+        autotune.pick_block({})
+
+
+def test_every_block_shape_is_valid_for_the_library():
+    from paper_1504_01441_b300 import build, hdrreg
+    build.build()
+    for nt in (0,) + autotune.BLOCKS:
+        p = hdrreg.params_from_dict(synth.method_params(search_threads=nt))
+        assert hdrreg.lib().hdrreg_validate_params(C.byref(p)) == 0, nt
+    for nt in (32, 96, 512, -1):    # the C side sees the field where ctypes puts it
+        p = hdrreg.params_from_dict(synth.method_params(search_threads=nt))
+        assert hdrreg.lib().hdrreg_validate_params(C.byref(p)) == 1, nt
+
+
 def test_bucket_bounds():
     assert autotune.bucket_of(1000, 1000) == 0            # 1.0 MP
     assert autotune.bucket_of(2000, 1000) == 0            # exactly 2 MP
@@ -71,7 +89,11 @@ def test_params_for_uses_the_bucket_pick():
     assert (autotune.params_for(1600, 1200, table).tile,
             autotune.params_for(1600, 1200, table).radius) == (16, 3)
     p = autotune.params_for(4000, 3000, table)
-    assert (p.tile, p.radius, p.patch_half) == (48, 6, 10)
+    assert (p.tile, p.radius, p.patch_half, p.search_threads) == (48, 6, 10, 0)
+    table["picks"] = [(16, 3, 64), (24, 4, 128), (32, 5, 256), (48, 6, 128)]
+    assert autotune.pick_of(table, 1600, 1200) == (16, 3, 64)
+    p = autotune.params_for(4000, 3000, table)
+    assert (p.tile, p.radius, p.search_threads) == (48, 6, 128)
 
 
 def _stack_ex(hd, shapes):

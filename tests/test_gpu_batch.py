@@ -133,8 +133,8 @@ def test_mixed_workload_members_at_full_size(hd, orc):
     stacks = synth.make_stacks_parallel([(i, 3, False) for i in idx], processes=1)
     cfgs = []
     for s in stacks:
-        t, r = table["picks"][autotune.bucket_of(s.width, s.height, table["buckets_mp"])]
-        cfgs.append(synth.method_params(t, r))
+        t, r, b = autotune.pick_of(table, s.width, s.height)
+        cfgs.append(synth.method_params(t, r, search_threads=b))
     mm, outs = run_multi_case(hd, stacks, cfgs, lanes=2)
     check_against_oracle(orc, stacks[0], cfgs[0], outs[0], mm.diagnostics(0))
 
@@ -168,11 +168,13 @@ def test_tuner_on_a_small_candidate_set(hd, vga_stack):
     meas = table["measurements"][0]
     assert set(meas) == {"16,3", "16,4", "24,4", "32,6"}
     assert all(v[0] > 0 and 0 <= v[1] < 5 for v in meas.values())
-    t, r = table["picks"][0]
+    t, r, b = table["picks"][0]
     chosen = meas[f"{t},{r}"]
     assert chosen[1] <= meas["32,6"][1]
     assert all(v[0] >= chosen[0] for v in meas.values() if v[1] <= meas["32,6"][1])
-    assert table["picks"][1:] == [list(autotune.DEFAULT)] * 3     # buckets without stacks
+    bm = table["block_measurements"][0]
+    assert set(bm) == {"64", "128", "256"} and bm[str(b)] == min(bm.values())
+    assert table["picks"][1:] == [list(autotune.DEFAULT) + [256]] * 3   # buckets without stacks
 
 
 @pytest.mark.parametrize("lanes", [1, 3])

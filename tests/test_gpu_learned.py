@@ -71,14 +71,16 @@ def test_search_predicted_bit_exact(hd, orc, level_pair):
     grid = np.zeros((480 // 16 + 1, ntx + 3, 2), np.float32)  # wider than the tile grid
     grid[:30, :ntx] = pred.reshape(30, ntx, 2)
     for refine in (0, 1, 2):
-        gc, gm, gcost, gv, gfb = hd.local_search_predicted(dev(rn), dev(sn), dev(H.reshape(9)), p,
-                                                           dev(grid), thr, refine)
         om, oc, ofb = orc.search_predicted(rn, sn, H, c, cxy, valid, pred, thr, refine)
-        assert np.array_equal(gc.cpu().numpy(), cxy) and np.array_equal(gv.cpu().numpy(), valid)
-        assert np.array_equal(gm.cpu().numpy(), om), refine
-        assert np.array_equal(gcost.cpu().numpy().view(np.uint32), oc), refine
-        assert np.array_equal(gfb.cpu().numpy(), ofb), refine
         assert 0 < int(ofb.sum()) < int(valid.sum())  # both branches exercised
+        for nt in (0, 64, 128):    # every block shape of the search
+            p.search_threads = nt
+            gc, gm, gcost, gv, gfb = hd.local_search_predicted(dev(rn), dev(sn), dev(H.reshape(9)),
+                                                               p, dev(grid), thr, refine)
+            assert np.array_equal(gc.cpu().numpy(), cxy) and np.array_equal(gv.cpu().numpy(), valid)
+            assert np.array_equal(gm.cpu().numpy(), om), (refine, nt)
+            assert np.array_equal(gcost.cpu().numpy().view(np.uint32), oc), (refine, nt)
+            assert np.array_equal(gfb.cpu().numpy(), ofb), (refine, nt)
 
 
 def test_crops_are_the_covered_tiles(hd):

@@ -148,6 +148,24 @@ def test_local_search_bit_exact(hd, orc, vga, tile, radius, shape):
     assert _search_case(hd, orc, ref_n, src_n, H, c) > 0
 
 
+@pytest.mark.parametrize("threads", [64, 128])
+@pytest.mark.parametrize("tile,radius,shape,extra", [
+    (16, 4, (480, 640), {}), (48, 3, (250, 250), {}),
+    (128, 15, (300, 410), dict(grid_half=4, patch_half=15)),   # region side 86 > 64 threads
+    (8, 1, (60, 70), {})])
+def test_local_search_block_shapes_bit_exact(hd, orc, vga, tile, radius, shape, extra, threads):
+    # the search's CTA size is a launch shape only: every block shape gives the oracle's
+    # corners, matches and costs
+    from paper_1504_01441_b300 import synth
+    rng = np.random.default_rng(6)
+    gh = extra.pop("grid_half", min(4, tile // 2 // max(1, tile // 16) - 1))
+    c = cfg(tile, radius, grid_half=gh, search_threads=threads, **extra)
+    rn, sn = orc.normalize_ratio(vga.ref.y, vga.srcs[0].y, 4, 1)
+    h, w = shape
+    ref_n, src_n = np.ascontiguousarray(rn[:h, :w]), np.ascontiguousarray(sn[:h, :w])
+    assert _search_case(hd, orc, ref_n, src_n, synth.random_homography(rng), c) > 0
+
+
 def test_local_search_full_size_bit_exact(hd, orc, five_mp):
     from paper_1504_01441_b300 import synth
     rng = np.random.default_rng(5)
