@@ -10,6 +10,7 @@ one CUDA graph. Prints one JSON line (see the keys below).
   python bench.py --workload mixed64    # 64 stacks of 1-12 MP, 2-3 frames, tuned (T, R)
   python bench.py --workload sweep      # one pair per size, VGA .. 20 MP (scaling)
   python bench.py --workload learned12  # 32 three-frame 12 MP stacks, learned level-0 search
+  python bench.py --workload learned8px # 5 MP pairs with +-8 px fields, learned vs plain
 
 Under torchrun each rank (one GPU) registers its own batch of stacks: stacks
 are independent, so the ranks are replicas with no data-path collective; the
@@ -36,6 +37,8 @@ MIXED = "mixed64"                       # command-line name of the mixed batch
 MIXED_NAME = "mixed64_1to12mp_yuv420"
 SWEEP = "sweep"
 SCALE12 = "learned12"
+LEARNED8 = "learned8px"
+LEARNED8_NAME = "5mp_yuv420_pair_8px_fields"
 SCALE12_NAME = "learned_batched_32x12mp_3frame_yuv420"
 MIXED_METRIC = "registered+merged output Mpix/s per B300 (64 stacks of 1-12 MP, 2-3 frames)"
 
@@ -47,15 +50,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=16, help="stacks per step (inputs > L2)")
+    ap.add_argument("--search-threads", type=int, default=0, choices=[0, 64, 128, 256],
+                    help="threads per tile CTA of the search (0: the library default, 128)")
     ap.add_argument("--distinct", type=int, default=2, help="distinct generated stacks")
     ap.add_argument("--lanes", type=int, default=8, help="concurrent lanes of the batched call")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned level-0 search leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short run for a profiler")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED, SWEEP, SCALE12],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED, SWEEP, SCALE12, LEARNED8],
                     help="the 5 MP pair batch (default), the mixed 1-12 MP batch, the size "
-                         "sweep, or 12 MP three-frame stacks with the learned search")
+                         "sweep, 12 MP three-frame stacks with the learned search, or 5 MP "
+                         "pairs with +-8 px fields, learned vs plain")
     ap.add_argument("--stacks", type=int, default=64,
                     help="stacks of the mixed batch (of the learned 12 MP batch: 32 unless set)")
     ap.add_argument("--output", default="merge", choices=["merge", "fusion"],
@@ -179,6 +185,7 @@ def run_ours(args):
     else:
         p = hdrreg.params_from_dict(synth.method_params(32, 6))
     p.output_mode = 1 if args.output == "fusion" else 0
+    p.search_threads = args.search_threads
     P = args.pairs
     # resident inputs: P distinct device buffers (contents cycle over the generated stacks)
     frames = []
@@ -225,10 +232,12 @@ def run_ours(args):
     value = job_value(ws, mpix_step, ms_step)
 
     # -- dominant stage: the flow (6 domain-transform passes), timed alone on its stream
-    roof, stages = None, None
+    roof, stages, search_alu = None, None, None
     if rank == 0:
-        stages = measure_stages(torch, hdrreg, p, stacks[0], dev, args)
+        meta = {}
+        stages = measure_stages(torch, hdrreg, p, stacks[0], dev, args, meta)
         roof = measure_flow_roofline(stages, p)
+        search_alu = measure_search_alu(torch, hdrreg, stages, p, meta["valid_level0"], dev)
     # -- the learned level-0 search (row a-L) on the same resident pairs
     learned = None
     if (rank == 0 and not args.no_learned and not args.profile and args.preset == "workload"
@@ -250,6 +259,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "width": W, "height": H, "format": "YUV420",
                        "frames": 2, "exposure_ratio": 4, "pairs_per_step": P,
                        "distinct_stacks": len(stacks), "tile": p.tile, "radius": p.radius,
+                       "search_threads": p.search_threads or 128,
                        "preset": args.preset, "norm_mode": "histeq" if p.norm_mode else "ratio",
                        "output": args.output,
                        "propagate_full": p.propagate_full,
@@ -257,7 +267,8 @@ def run_ours(args):
                        "l2": f"inputs larger than L2: {P} resident pairs x 15.1 MB per step",
                        "parallelism": f"replicas x{ws}"},
             "gpu_launches": launches_per_step * K,
-            "roofline": roof, "stages_us": stages, "learned": learned, "cpu_baseline": cpu,
+            "roofline": roof, "search_alu": search_alu, "stages_us": stages, "learned": learned,
+            "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),
         }
@@ -356,8 +367,9 @@ def _graph_time_us(torch, fn, reps):
     return a.elapsed_time(b) * 1e3 / reps
 
 
-def measure_stages(torch, hdrreg, p, stack, dev, args):
-    """Per-stage device time on one resident 5 MP pair, each stage replayed as a graph."""
+def measure_stages(torch, hdrreg, p, stack, dev, args, meta=None):
+    """Per-stage device time on one resident 5 MP pair, each stage replayed as a graph.
+    meta (optional dict) receives the number of level-0 tiles with a corner."""
     reps = 5 if args.profile else 20
     ref = torch.from_numpy(stack.ref.y).to(dev)
     src = torch.from_numpy(stack.srcs[0].y).to(dev)
@@ -391,6 +403,8 @@ def measure_stages(torch, hdrreg, p, stack, dev, args):
     matcher()
     out["matcher"] = _graph_time_us(torch, matcher, reps)
     cxy, mxy, cost, valid = hdrreg.local_search(rn, sn, res["H"], p)
+    if meta is not None:
+        meta["valid_level0"] = int(valid.sum().item())
     out["search_level0"] = _graph_time_us(torch, lambda: hdrreg.local_search(rn, sn, res["H"], p), reps)
     out["weed_fit_level0"] = _graph_time_us(
         torch, lambda: hdrreg.weed_fit(cxy, mxy, valid, W, H, p, p.weed_seed, Hid,
@@ -411,6 +425,37 @@ def measure_stages(torch, hdrreg, p, stack, dev, args):
 # DRAM bytes of one flow call (2592 x 1944, 3 iterations, 13 launches) from the ncu
 # capture summarised in profiles/flow_dram_5mp.md.
 FLOW_TRAFFIC = 555168000
+
+
+def measure_search_alu(torch, hdrreg, stages, p, valid_tiles, dev):
+    """The level-0 SSD search against the measured __dp4a rate. Algorithmic work per
+    launch: the cross terms of SSD = sum a^2 + sum b^2 - 2 sum a b over (2R+1)^2 offsets
+    and (2h+1)^2 patch pixels of every tile with a corner, four byte products per
+    __dp4a. The rate is the probe's (hdrreg_probe_dp4a: 8 CTAs of 256 threads per SM,
+    eight independent chains per thread), median of 5 event-timed runs."""
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = 8 * sms, 4096
+    s = torch.cuda.Stream(device=dev)
+    for _ in range(3):
+        hdrreg.probe_dp4a(blocks, iters, sink, stream=s)
+    times = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        n = hdrreg.probe_dp4a(blocks, iters, sink, stream=s)
+        b.record(s)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    peak = n / (times[2] / 1e3) / 1e9
+    algo = valid_tiles * (2 * p.radius + 1) ** 2 * (2 * p.patch_half + 1) ** 2 / 4
+    achieved = algo / (stages["search_level0"] / 1e6) / 1e9
+    return {"kernel": "k_local_search (level 0)", "bound": "alu", "unit": "G dp4a/s",
+            "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "frac": round(achieved / peak, 4), "peak_source": "measured (hdrreg_probe_dp4a)",
+            "algorithmic_dp4a_per_launch": int(algo), "tiles_with_corner": valid_tiles,
+            "us_per_launch": stages["search_level0"]}
 
 
 def measure_flow_roofline(stages, p):
@@ -563,7 +608,7 @@ def run_mixed(args):
         buckets = {}
         for s, p in zip(stacks, params):
             b = autotune.bucket_of(s.width, s.height, table["buckets_mp"])
-            buckets.setdefault(b, [p.tile, p.radius, p.search_threads or 256, 0])[3] += 1
+            buckets.setdefault(b, [p.tile, p.radius, p.search_threads or 128, 0])[3] += 1
         line = {
             "metric": MIXED_METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -853,6 +898,63 @@ def run_scale12(args):
         dist.destroy_process_group()
 
 
+def run_learned8(args):
+    """5 MP YUV420 pairs as the headline workload but with +-8 px local fields: the plain
+    path and the learned level-0 search (default and calibrated operating points) on
+    `pairs` resident pairs per step, each replayed as one CUDA graph, with the learned
+    search's distance to the plain matches and both searches' distance to the generator's
+    truth."""
+    ws, rank, local = dist_env()
+    from paper_1504_01441_b300 import synth as _s
+    stacks = [_s.make_learned8_stack(i) for i in range(args.distinct)]
+    import torch
+    import torch.distributed as dist
+    from paper_1504_01441_b300 import hdrreg, synth
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    p = hdrreg.params_from_dict(synth.method_params(32, 6))
+    P = args.pairs
+    frames = []
+    for i in range(P):
+        s = stacks[i % len(stacks)]
+        ref = tuple(torch.from_numpy(a).to(dev) for a in (s.ref.y, s.ref.u, s.ref.v))
+        src = tuple(torch.from_numpy(a).to(dev) for a in (s.srcs[0].y, s.srcs[0].u, s.srcs[0].v))
+        frames.append((ref, [src], s.ratios))
+    stream = torch.cuda.Stream(device=dev)
+    plain = hdrreg.RegisterMergeBatch(W, H, 1, p, True, slots=P, lanes=args.lanes, device=dev)
+    with ClockSampler(local) as clk:
+        ms_plain, g, per_step = _time_graph(torch, plain, frames, stream, args.warmup, args.steps)
+    if ws > 1:
+        ms_plain = max_over_ranks(torch, dist, ms_plain, dev)
+    del g, plain
+    learned = measure_learned(torch, hdrreg, synth, stacks, frames, p, dev, args)
+    if rank == 0:
+        line = {
+            "metric": "registered+merged output Mpix/s per B300, learned level-0 search "
+                      "(5 MP pairs, +-8 px fields)",
+            "value": learned["value"], "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/i32 match, bf16 net, f64 fit, f32 flow/warp/merge",
+            "data": "synthetic",
+            "config": {"workload": LEARNED8_NAME, "width": W, "height": H, "format": "YUV420",
+                       "frames": 2, "exposure_ratio": 4, "field_px": 8, "movers": 3,
+                       "pairs_per_step": P, "distinct_stacks": len(stacks), "tile": 32,
+                       "radius": 6, "graph": True, "lanes": args.lanes,
+                       "l2": f"inputs larger than L2: {P} resident pairs x 15.1 MB per step",
+                       "parallelism": f"replicas x{ws}"},
+            "plain": {"value": round(ws * P * W * H / 1e6 / (ms_plain / 1e3), 2),
+                      "unit": "Mpix/s", "ms_per_step": round(ms_plain, 3),
+                      "gpu_launches_per_step": per_step},
+            "learned": learned, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def synth_sweep():
     from paper_1504_01441_b300 import synth
     return synth.make_sweep_stacks()
@@ -942,6 +1044,8 @@ def main():
         run_sweep(args)
     elif args.workload == SCALE12:
         run_scale12(args)
+    elif args.workload == LEARNED8:
+        run_learned8(args)
     else:
         run_ours(args)
 

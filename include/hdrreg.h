@@ -104,7 +104,7 @@ typedef struct hdrreg_params {
     int32_t predictor_refine; /* learned search: offsets [-r, r]^2 around the rounded
                                prediction are tried before the fallback test, 0..radius */
     int32_t search_threads; /* threads per tile CTA of the SSD search (one CTA per tile):
-                               0 (= 256), 64, 128 or 256; a launch shape only, the
+                               0 (= 128), 64, 128 or 256; a launch shape only, the
                                results do not depend on it                              */
 } hdrreg_params;
 
@@ -155,6 +155,14 @@ const char* hdrreg_version(void);
  * incremented at every launch; a graph captured from library calls replays the
  * launches counted while it was captured). */
 unsigned long long hdrreg_launch_count(void);
+/* Measurement aid for the SSD search's ALU roofline (Sec. 2.2: 8-bit products summed
+ * in 32-bit integers, issued as 4-way byte dot products): enqueues `blocks` CTAs of 256
+ * threads, each thread running `iters` rounds of 8 dependent-chain __dp4a operations
+ * (blocks * 256 * iters * 8 in total), on `stream`. The caller times it with events.
+ * sink: device uint32, written only if a chain's result hits an unused value (keeps the
+ * work live). blocks in [1, 2^20], iters in [1, 2^24]; E_INVALID_ARG otherwise, before
+ * any launch. */
+hdrreg_status hdrreg_probe_dp4a(int blocks, int iters, uint32_t* sink, void* stream);
 /* Number of pyramid levels for a w x h frame under p (host computation, Sec. 2.6). */
 int hdrreg_num_levels(int w, int h, const hdrreg_params* p);
 /* Check p; returns HDRREG_OK or HDRREG_E_INVALID_ARG (message in hdrreg_last_error). */

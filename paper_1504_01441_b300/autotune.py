@@ -35,7 +35,7 @@ TILES = (16, 24, 32, 48)
 RADII = (3, 4, 5, 6, 7, 8)
 DEFAULT = (32, 6)
 BLOCKS = (64, 128, 256)                     # threads per tile CTA of the search
-DEFAULT_BLOCK = 256
+DEFAULT_BLOCK = 128
 TABLE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_table.json")
 
 
@@ -72,7 +72,7 @@ def pick_block(times: Dict[int, float]) -> int:
 
 def pick_of(table: Dict, w: int, h: int) -> Tuple[int, int, int]:
     """(T, R, B) of a w x h stack's bucket; a table without block shapes gives B = 0 (the
-    library's default, 256)."""
+    library's default, 128)."""
     pk = tuple(table["picks"][bucket_of(w, h, table["buckets_mp"])])
     return (pk[0], pk[1], pk[2] if len(pk) > 2 else 0)
 

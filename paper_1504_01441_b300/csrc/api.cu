@@ -93,7 +93,7 @@ static SearchGeom make_geom(int w, int h, const hdrreg_params* p)
     g.ntx = w / p->tile;
     g.nty = h / p->tile;
     g.corner_thr = (long long)p->corner_thresh * p->quad * p->quad;
-    g.threads = p->search_threads ? p->search_threads : 256;
+    g.threads = p->search_threads ? p->search_threads : 128;
     return g;
 }
 

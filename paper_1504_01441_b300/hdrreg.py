@@ -37,7 +37,7 @@ EXPORTS = [
     "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_cnn_activation",
     "hdrreg_cnn_infer_workspace_size", "hdrreg_cnn_infer", "hdrreg_predictor_input",
     "hdrreg_tile_labels",
-    "hdrreg_predictor_crops", "hdrreg_local_search_predicted",
+    "hdrreg_predictor_crops", "hdrreg_local_search_predicted", "hdrreg_probe_dp4a",
 ]
 
 CNN_PARAMS = 119538
@@ -120,6 +120,7 @@ def lib():
         L.hdrreg_last_error.restype = C.c_char_p
         L.hdrreg_version.restype = C.c_char_p
         L.hdrreg_launch_count.restype = C.c_ulonglong
+        L.hdrreg_probe_dp4a.argtypes = [i, i, vp, vp]
         L.hdrreg_params_default.argtypes = [C.POINTER(Params)]
         L.hdrreg_params_paper.argtypes = [C.POINTER(Params)]
         L.hdrreg_validate_params.argtypes = [C.POINTER(Params)]
@@ -202,6 +203,12 @@ def version() -> str:
 def launch_count() -> int:
     """Kernels enqueued by the library so far in this process."""
     return int(lib().hdrreg_launch_count())
+
+
+def probe_dp4a(blocks: int, iters: int, sink, stream=None) -> int:
+    """Enqueue the integer dot-product rate probe; -> the number of __dp4a it issues."""
+    _check(lib().hdrreg_probe_dp4a(blocks, iters, _ptr(sink), _stream(stream)))
+    return blocks * 256 * iters * 8
 
 
 def params(**over) -> Params:

@@ -387,6 +387,16 @@ def dark_spec(stops: int, width: int = 640, height: int = 480) -> StackSpec:
                      movers=1, chroma=False, scene_gain=1.0 / 2 ** stops)
 
 
+# The learned search on 5 MP pairs with +-8 px local fields (the headline recipe otherwise).
+LEARNED8_SPEC = StackSpec(2592, 1944, ratios=((4, 1),), noise_sigma=1.5, field_amp=8.0,
+                          movers=3, chroma=True)
+
+
+def make_learned8_stack(stack_index: int) -> Stack:
+    """Seeds from index 50000 up: apart from the predictor's training stacks."""
+    return make_stack(LEARNED8_SPEC, stack_seed(4, 50000 + stack_index))
+
+
 # Learned + batched at scale: 4000 x 3000 three-frame stacks, exposures 1/4, 1 and 4 times
 # the reference's (the r = 1 frame is the reference), +-8 px local fields, 5 movers.
 SCALE12_SPEC = StackSpec(4000, 3000, ratios=((1, 4), (4, 1)), noise_sigma=1.5, field_amp=8.0,

@@ -100,6 +100,11 @@ def test_null_and_size_errors_return_before_any_launch(hd):
                                      C.byref(o), None, None) == 1
     assert lib.hdrreg_fit_homography(None, None, None, -1, 10, 10, None, None, None, None) == 1
     assert b"NULL" in lib.hdrreg_last_error() or b"range" in lib.hdrreg_last_error()
+    sink = C.c_uint32(0)
+    assert lib.hdrreg_probe_dp4a(0, 16, C.byref(sink), None) == 1
+    assert lib.hdrreg_probe_dp4a(148, 0, C.byref(sink), None) == 1
+    assert lib.hdrreg_probe_dp4a(148, 16, None, None) == 1
+    assert b"NULL" in lib.hdrreg_last_error()
 
 
 def test_batch_sizes_and_argument_errors(hd):

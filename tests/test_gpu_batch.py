@@ -174,7 +174,7 @@ def test_tuner_on_a_small_candidate_set(hd, vga_stack):
     assert all(v[0] >= chosen[0] for v in meas.values() if v[1] <= meas["32,6"][1])
     bm = table["block_measurements"][0]
     assert set(bm) == {"64", "128", "256"} and bm[str(b)] == min(bm.values())
-    assert table["picks"][1:] == [list(autotune.DEFAULT) + [256]] * 3   # buckets without stacks
+    assert table["picks"][1:] == [list(autotune.DEFAULT) + [128]] * 3   # buckets without stacks
 
 
 @pytest.mark.parametrize("lanes", [1, 3])

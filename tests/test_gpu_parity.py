@@ -530,3 +530,12 @@ def test_fused_dark_reference(hd, orc, stops, mode):
     from paper_1504_01441_b300 import synth
     st = synth.make_stack(synth.dark_spec(stops), synth.stack_seed(7, stops))
     _fused_case(hd, orc, st, cfg(16, 4, norm_mode=mode))
+
+
+def test_dp4a_rate_probe_runs(hd):
+    # the measurement aid of the search's ALU roofline: it launches, finishes, and counts
+    # the operations it issues
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    n = hd.probe_dp4a(148, 64, sink)
+    torch.cuda.synchronize()
+    assert n == 148 * 256 * 64 * 8
