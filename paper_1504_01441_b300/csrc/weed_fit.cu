@@ -31,7 +31,10 @@ namespace hdrreg {
 
 constexpr int kWeedWarps = 4;  // workspace path: warps per CTA, four iterations each
 constexpr int kWeedThreads = 32 * kWeedWarps;
-constexpr int kLevelWarps = 16;  // fused path: warps per CTA (four iterations per CTA)
+// Fused path: warps per CTA (four iterations per CTA). The CTA's time is set by the
+// binary64 chains of warp 0 (the four hypotheses) and of the last CTA (the fit); four
+// warps keep the register and thread footprint small for the kernels of other lanes.
+constexpr int kLevelWarps = 4;
 constexpr int kLevelThreads = 32 * kLevelWarps;
 constexpr int kFitSums = 23;
 
@@ -448,14 +451,17 @@ __global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a
     }
     __syncthreads();
 
-    // ---- four warps per iteration test the matches of a quarter of the words each
+    // ---- kLevelWarps / 4 warps per iteration test the matches of an equal share of the
+    //      words each
     const unsigned ok = s_ok;
     {
+        constexpr int kParts = kLevelWarps / 4;
+        static_assert(kLevelWarps % 4 == 0, "four iterations per CTA");
         const int i = warp & 3, part = warp >> 2;
         if ((ok >> i) & 1u) {
             InlierTest T;
             T.init(s_h[i]);
-            const int per = (nw + 3) >> 2;
+            const int per = (nw + kParts - 1) / kParts;
             const int w0 = part * per, w1 = min(nw, w0 + per);
             uint32_t* mine = bw + i * nw;
             int cnt = 0;
