@@ -174,9 +174,10 @@ struct FusedLayout {
     }
 };
 
-__global__ void k_diag(const double* H0, const uint8_t* valid, const uint32_t* mask, int n,
-                       const int32_t* fit_st, int levels, const uint8_t* fell_back,
-                       hdrreg_diag* d)
+__global__ void __launch_bounds__(256) k_diag(const double* H0, const uint8_t* valid,
+                                              const uint32_t* mask, int n, const int32_t* fit_st,
+                                              int levels, const uint8_t* fell_back,
+                                              hdrreg_diag* d)
 {
     __shared__ int sv, sk, sf;
     if (threadIdx.x == 0) {
@@ -188,12 +189,20 @@ __global__ void k_diag(const double* H0, const uint8_t* valid, const uint32_t* m
     int v = 0, k = 0, f = 0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         v += valid[t];
-        k += (mask[t >> 5] >> (t & 31)) & 1u;
         if (fell_back) f += fell_back[t];
     }
-    atomicAdd(&sv, v);
-    atomicAdd(&sk, k);
-    atomicAdd(&sf, f);
+    for (int wi = threadIdx.x; wi < (n + 31) / 32; wi += blockDim.x) {
+        const int bits = n - 32 * wi < 32 ? n - 32 * wi : 32;
+        k += __popc(mask[wi] & (bits == 32 ? ~0u : (1u << bits) - 1u));
+    }
+    v = __reduce_add_sync(0xffffffffu, v);
+    k = __reduce_add_sync(0xffffffffu, k);
+    f = __reduce_add_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sv, v);
+        atomicAdd(&sk, k);
+        atomicAdd(&sf, f);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 0; i < 9; i++) d->H0[i] = H0[i];
@@ -726,7 +735,7 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
                     Hw, fu, fv, flow_pitch(w), wy, chroma ? wu : nullptr, chroma ? wv : nullptr, s);
         if (diag) {
             note_launch();
-            k_diag<<<1, 1024, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L,
+            k_diag<<<1, 256, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L,
                                      lay.learned ? at(lay.fellback) : nullptr, diag + k);
         }
         md[k].y = wy;

@@ -432,7 +432,9 @@ struct WeedLevelArgs {
     int32_t* status;       // 0 fitted, 1 fewer than 4 matches, 2 singular
     unsigned* done;        // completion counter, zero on entry and left zero
 };
-constexpr size_t kWeedLevelSmemMax = 200 * 1024;
+// Dynamic shared memory of the one-launch weeding: up to 11,625 level tiles (a 4000 x
+// 3000 frame at T = 32); larger levels take the workspace path.
+constexpr size_t kWeedLevelSmemMax = 204 * 1024;
 size_t weed_level_smem_bytes(int n);
 bool weed_level_fits(int n);
 void launch_weed_level(const WeedLevelArgs& a, cudaStream_t s);

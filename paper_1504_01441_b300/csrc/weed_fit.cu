@@ -35,6 +35,9 @@ constexpr int kWeedThreads = 32 * kWeedWarps;
 // binary64 chains of warp 0 (the four hypotheses) and of the last CTA (the fit); four
 // warps keep the register and thread footprint small for the kernels of other lanes.
 constexpr int kLevelWarps = 4;
+constexpr int kHypWarps = 2;               // warps drawing and solving hypotheses, 4 each
+constexpr int kIterPerCta = 4 * kHypWarps;  // weeding iterations per CTA
+static_assert(kHypWarps < kLevelWarps, "some warps stage the coordinates");
 constexpr int kLevelThreads = 32 * kLevelWarps;
 constexpr int kFitSums = 23;
 
@@ -352,7 +355,7 @@ __device__ void fit_solve_warp(const __int128* S, int total, int w, const double
 size_t weed_level_smem_bytes(int n)
 {
     const size_t nn = n > 0 ? (size_t)n : 0, nw = (nn + 31) / 32;
-    return align_up(nn * 16, 16) + nw * 4 * 6 + 16;
+    return align_up(nn * 16, 16) + nw * 4 * (2 + kIterPerCta) + 16;
 }
 
 bool weed_level_fits(int n) { return weed_level_smem_bytes(n) <= kWeedLevelSmemMax; }
@@ -361,16 +364,16 @@ __global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ FitShared<kLevelWarps> fsh;
-    __shared__ double s_h[4][8];
+    __shared__ double s_h[kIterPerCta][8];
     __shared__ int wsum[kLevelWarps];
-    __shared__ int s_cnt[4];
+    __shared__ int s_cnt[kIterPerCta];
     __shared__ unsigned s_ok;
     __shared__ int last_s;
     const int n = a.n, nw = (n + 31) >> 5;
     float4* crd = reinterpret_cast<float4*>(smem);                        // [n] tile order
     uint32_t* vbits = reinterpret_cast<uint32_t*>(smem + align_up((size_t)n * 16, 16));
     int* vpref = reinterpret_cast<int*>(vbits + nw);                      // [nw + 1]
-    uint32_t* bw = reinterpret_cast<uint32_t*>(vpref + nw + 1);           // [4][nw]
+    uint32_t* bw = reinterpret_cast<uint32_t*>(vpref + nw + 1);           // [kIterPerCta][nw]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lg = ilog2_pow2(pow2_scale(a.w));
     const float invS = 1.0f / G.Sf;  // exact
@@ -381,7 +384,8 @@ __global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a
         const unsigned b = __ballot_sync(kFull, t < n && a.valid[t] != 0);
         if (lane == 0) vbits[wi] = b;
     }
-    if (tid < 4) s_cnt[tid] = 0;
+    if (tid < kIterPerCta) s_cnt[tid] = 0;
+    if (tid == 0) s_ok = 0;
     __syncthreads();
     {
         const int per = (nw + kLevelThreads - 1) / kLevelThreads;
@@ -405,16 +409,16 @@ __global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a
     }
     __syncthreads();
     const int nv = vpref[nw];
-    const long long it_base = (long long)a.it0 + 4LL * blockIdx.x;
+    const long long it_base = (long long)a.it0 + (long long)kIterPerCta * blockIdx.x;
 
-    // ---- warp 0: the four hypotheses (coordinates of the picks read from global);
-    //      warps 1.. : stage the coordinates of every valid match
-    if (warp == 0) {
+    // ---- warps 0 .. kHypWarps-1: four hypotheses each (coordinates of the picks read
+    //      from global); the other warps stage the coordinates of every valid match
+    if (warp < kHypWarps) {
         unsigned ok = 0;
         if (nv >= 4) {
             double x[8];
             ok = weed_hypotheses4(
-                a.seed, it_base, a.it1, nv, G.Sf, lg,
+                a.seed, it_base + 4 * warp, a.it1, nv, G.Sf, lg,
                 [&](int j) {
                     int lo = 0, hi = nw;  // vpref[lo] <= j < vpref[hi]
                     while (hi - lo > 1) {
@@ -428,15 +432,16 @@ __global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a
                 },
                 x);
             if ((lane & 7) == 0)
-                for (int k = 0; k < 8; k++) s_h[lane >> 3][k] = x[k];
+                for (int k = 0; k < 8; k++) s_h[4 * warp + (lane >> 3)][k] = x[k];
         }
-        if (lane == 0) s_ok = ok;
+        if (lane == 0 && ok) atomicOr(&s_ok, ok << (4 * warp));
     } else {
-        for (int t0 = tid - 32; t0 < n; t0 += 4 * (kLevelThreads - 32)) {
+        constexpr int kStage = kLevelThreads - 32 * kHypWarps;  // staging threads
+        for (int t0 = tid - 32 * kHypWarps; t0 < n; t0 += 4 * kStage) {
             int v[4], c0[4], c1[4], m0[4], m1[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const int t = t0 + u * (kLevelThreads - 32);
+                const int t = t0 + u * kStage;
                 const bool in = t < n;
                 v[u] = in ? a.valid[t] : 0;
                 c0[u] = in ? a.corner_xy[2 * t] : 0;
@@ -446,19 +451,23 @@ __global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a
             }
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                if (v[u]) crd[t0 + u * (kLevelThreads - 32)] = tilde4(c0[u], c1[u], m0[u], m1[u], a.w, a.h, invS);
+                if (v[u]) crd[t0 + u * kStage] = tilde4(c0[u], c1[u], m0[u], m1[u], a.w, a.h, invS);
         }
     }
     __syncthreads();
 
-    // ---- kLevelWarps / 4 warps per iteration test the matches of an equal share of the
-    //      words each
+    // ---- the iterations' inlier tests: iteration i on warps i mod kLevelWarps (each
+    //      over all words) when there are at least as many iterations as warps, else
+    //      kLevelWarps / kIterPerCta warps per iteration over equal shares of the words
     const unsigned ok = s_ok;
     {
-        constexpr int kParts = kLevelWarps / 4;
-        static_assert(kLevelWarps % 4 == 0, "four iterations per CTA");
-        const int i = warp & 3, part = warp >> 2;
-        if ((ok >> i) & 1u) {
+        constexpr int kParts = kLevelWarps > kIterPerCta ? kLevelWarps / kIterPerCta : 1;
+        constexpr int kStep = kLevelWarps > kIterPerCta ? kIterPerCta : kLevelWarps;
+        static_assert(kLevelWarps <= kIterPerCta || kLevelWarps % kIterPerCta == 0,
+                      "whole warps per iteration");
+        const int part = kLevelWarps > kIterPerCta ? warp / kIterPerCta : 0;
+        for (int i = warp % kStep; i < kIterPerCta; i += kStep) {
+            if (!((ok >> i) & 1u)) continue;
             InlierTest T;
             T.init(s_h[i]);
             const int per = (nw + kParts - 1) / kParts;
@@ -480,12 +489,12 @@ __global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a
     {
         const int delta = weed_delta(nv, a.delta_min, a.delta_div);
         unsigned acc = 0;
-        for (int i = 0; i < 4; i++)
+        for (int i = 0; i < kIterPerCta; i++)
             if (((ok >> i) & 1u) && s_cnt[i] > delta) acc |= 1u << i;
         if (acc) {
             for (int wi = tid; wi < nw; wi += kLevelThreads) {
                 uint32_t m = 0;
-                for (int i = 0; i < 4; i++)
+                for (int i = 0; i < kIterPerCta; i++)
                     if ((acc >> i) & 1u) m |= bw[i * nw + wi];
                 if (m) atomicOr(&a.mask[wi], m);
             }
@@ -518,7 +527,7 @@ __global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a
 void launch_weed_level(const WeedLevelArgs& a, cudaStream_t s)
 {
     const int iters = a.it1 > a.it0 ? a.it1 - a.it0 : 0;
-    int blocks = (iters + 3) / 4;
+    int blocks = (iters + kIterPerCta - 1) / kIterPerCta;
     if (blocks < 1) blocks = 1;  // the fit still runs
     const size_t smem = weed_level_smem_bytes(a.n);
     ensure_smem((const void*)k_weed_level, smem);  // static + dynamic may pass 48 KB
