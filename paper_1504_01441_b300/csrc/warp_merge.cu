@@ -83,13 +83,16 @@ __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
                                               float* __restrict__ oy, float* __restrict__ ou,
                                               float* __restrict__ ov)
 {
+    // The coefficients take a chain of binary64 operations (one thread, the others
+    // waiting), so the grid is sized to the resident CTAs and each CTA strides over
+    // many blocks: the chain runs once per CTA, not once per 256 blocks.
     __shared__ WarpCoef cs;
     if (threadIdx.x == 0) prep_coef(H, w, cs);
     __syncthreads();
     const WarpCoef c = cs;
     const int bw = (w + 1) / 2, bh = (h + 1) / 2;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= bw * bh) return;
+    const int nb = bw * bh;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nb; idx += gridDim.x * blockDim.x) {
     const int bx = idx % bw, by = idx / bw;
     float stx = 0.f, sty = 0.f;
     for (int j = 0; j < 2; j++)
@@ -112,6 +115,7 @@ __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
             ou[o] = bilerp(su, cw, ch, bx, by, tx, ty);
             ov[o] = bilerp(sv, cw, ch, bx, by, tx, ty);
         }
+    }
     }
 }
 
@@ -450,7 +454,11 @@ void launch_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_
                  float* ou, float* ov, cudaStream_t s)
 {
     const long long nb = (long long)((w + 1) / 2) * ((h + 1) / 2);
-    const int grid = (int)((nb + 255) / 256);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long need = (nb + 255) / 256, cap = 8LL * sms;  // 8 resident CTAs per SM
+    const int grid = (int)(need < cap ? need : cap);
     note_launch();
     k_warp<<<grid, 256, 0, s>>>(src_y, src_u, src_v, w, h, H, fu, fv, fpitch, oy, ou, ov);
 }
@@ -459,8 +467,11 @@ void launch_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, i
                             const double* H, void* out, cudaStream_t s)
 {
     const long long n = (long long)w * h;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long g = (n + 255) / 256;
-    if (g > 4096) g = 4096;
+    if (g > 8LL * sms) g = 8LL * sms;  // one binary64 coefficient chain per resident CTA
     note_launch();
     k_predictor_input<<<(int)g, 256, 0, s>>>(ref_q, src_q, w, h, H,
                                              static_cast<__nv_bfloat162*>(out));
