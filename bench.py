@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--search-threads", type=int, default=0, choices=[0, 64, 128, 256],
                     help="threads per tile CTA of the search (0: the library default, 128)")
     ap.add_argument("--distinct", type=int, default=2, help="distinct generated stacks")
-    ap.add_argument("--lanes", type=int, default=8, help="concurrent lanes of the batched call")
+    ap.add_argument("--lanes", type=int, default=16, help="concurrent lanes of the batched call "
+                    "(16: one pair per lane for the 16-pair step)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned level-0 search leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

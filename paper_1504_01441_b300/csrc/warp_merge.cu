@@ -384,30 +384,51 @@ __global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ re
             M.H11[yy][xx] = m11;
         }
         __syncthreads();
-#pragma unroll 1
-        for (int q = 0; q < 4; q++) {
-            const int ly = ty0 + 8 * q;
-            const int x = x0 + tx, y = y0 + ly;
-            // Column pass: re-centre every row's moments from its centre c_r onto the output
-            // pixel's value c (delta = c_r - c): sum g (a + delta)^k expands exactly, so the
-            // window moments stay small numbers wherever the window is flat.
-            const float2 c = M.XY[ly + kHalo][tx + kHalo];
-            float2 a1 = f2(0.f, 0.f), a2 = f2(0.f, 0.f);
-            float a11 = 0.f;
+        // Column pass: re-centre every row's moments from its centre c_r onto the output
+        // pixel's value c (delta = c_r - c): sum g (a + delta)^k expands exactly, so the
+        // window moments stay small numbers wherever the window is flat. A thread takes
+        // four consecutive output rows 4 ty0 .. 4 ty0 + 3 of column tx: each of the 14
+        // staged rows they span is read once and added, in tap order, to every output
+        // whose window holds it.
+        constexpr int kQ = 4, kSpan = kQ + 2 * kHalo;
+        const int lyb = kQ * ty0;
+        float2 cq[kQ], a1[kQ], a2[kQ];
+        float a11[kQ];
 #pragma unroll
-            for (int d = 0; d <= 2 * kHalo; d++) {
+        for (int q = 0; q < kQ; q++) {
+            cq[q] = M.XY[lyb + q + kHalo][tx + kHalo];
+            a1[q] = f2(0.f, 0.f);
+            a2[q] = f2(0.f, 0.f);
+            a11[q] = 0.f;
+        }
+#pragma unroll
+        for (int rr = 0; rr < kSpan; rr++) {
+            const float2 xy = M.XY[lyb + rr][tx + kHalo];
+            const float2 m1 = M.H1[lyb + rr][tx];
+            const float2 m2 = M.H2[lyb + rr][tx];
+            const float m11 = M.H11[lyb + rr][tx];
+#pragma unroll
+            for (int q = 0; q < kQ; q++) {
+                const int d = rr - q;
+                if (d < 0 || d > 2 * kHalo) continue;
                 const float2 g2 = f2(args.g[d], args.g[d]);
-                const float2 dd = __ffma2_rn(c, neg1, M.XY[ly + d][tx + kHalo]);
-                const float2 m1 = M.H1[ly + d][tx];
+                const float2 dd = __ffma2_rn(cq[q], neg1, xy);
                 const float2 r1 = __ffma2_rn(dd, gsum2, m1);
-                const float2 r2 = __ffma2_rn(dd, __fadd2_rn(m1, r1), M.H2[ly + d][tx]);
-                const float r11 = M.H11[ly + d][tx] + fmaf(dd.y, m1.x, dd.x * r1.y);
-                a1 = __ffma2_rn(g2, r1, a1);
-                a2 = __ffma2_rn(g2, r2, a2);
-                a11 = fmaf(args.g[d], r11, a11);
+                const float2 r2 = __ffma2_rn(dd, __fadd2_rn(m1, r1), m2);
+                const float r11 = m11 + fmaf(dd.y, m1.x, dd.x * r1.y);
+                a1[q] = __ffma2_rn(g2, r1, a1[q]);
+                a2[q] = __ffma2_rn(g2, r2, a2[q]);
+                a11[q] = fmaf(args.g[d], r11, a11[q]);
             }
-            const float vx = a2.x - a1.x * a1.x, vy = a2.y - a1.y * a1.y, cxy = a11 - a1.x * a1.y;
-            const float ux = c.x + a1.x, uy = c.y + a1.y;
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int ly = lyb + q;
+            const int x = x0 + tx, y = y0 + ly;
+            const float2 c = cq[q];
+            const float vx = a2[q].x - a1[q].x * a1[q].x, vy = a2[q].y - a1[q].y * a1[q].y,
+                        cxy = a11[q] - a1[q].x * a1[q].y;
+            const float ux = c.x + a1[q].x, uy = c.y + a1[q].y;
             const float ssim = ((2.f * ux * uy + C1) * (2.f * cxy + C2)) /
                                ((ux * ux + uy * uy + C1) * (vx + vy + C2));
             const float qv = ssim > 0.f ? ssim : 0.f;
