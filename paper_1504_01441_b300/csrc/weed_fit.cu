@@ -34,11 +34,12 @@ constexpr int kWeedThreads = 32 * kWeedWarps;
 // Fused path: warps per CTA (four iterations per CTA). The CTA's time is set by the
 // binary64 chains of warp 0 (the four hypotheses) and of the last CTA (the fit); four
 // warps keep the register and thread footprint small for the kernels of other lanes.
-constexpr int kLevelWarps = 4;
+// Two CTA shapes: four warps for small levels (the chains set the time; a small footprint
+// leaves the SMs to the other lanes), sixteen from kWideLevel tiles up (staging the matches
+// and testing them against eight hypotheses is then real work).
 constexpr int kHypWarps = 2;               // warps drawing and solving hypotheses, 4 each
 constexpr int kIterPerCta = 4 * kHypWarps;  // weeding iterations per CTA
-static_assert(kHypWarps < kLevelWarps, "some warps stage the coordinates");
-constexpr int kLevelThreads = 32 * kLevelWarps;
+constexpr int kNarrowWarps = 4, kWideWarps = 16, kWideLevel = 2048;
 constexpr int kFitSums = 23;
 
 __device__ __forceinline__ int ilog2_pow2(int s) { return 31 - __clz(s); }
@@ -360,8 +361,11 @@ size_t weed_level_smem_bytes(int n)
 
 bool weed_level_fits(int n) { return weed_level_smem_bytes(n) <= kWeedLevelSmemMax; }
 
-__global__ void __launch_bounds__(kLevelThreads, 1) k_weed_level(WeedLevelArgs a, InlierGeom G)
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 1) k_weed_level(WeedLevelArgs a, InlierGeom G)
 {
+    constexpr int kLevelWarps = NW, kLevelThreads = 32 * NW;
+    static_assert(kHypWarps < kLevelWarps, "some warps stage the coordinates");
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ FitShared<kLevelWarps> fsh;
     __shared__ double s_h[kIterPerCta][8];
@@ -530,9 +534,14 @@ void launch_weed_level(const WeedLevelArgs& a, cudaStream_t s)
     int blocks = (iters + kIterPerCta - 1) / kIterPerCta;
     if (blocks < 1) blocks = 1;  // the fit still runs
     const size_t smem = weed_level_smem_bytes(a.n);
-    ensure_smem((const void*)k_weed_level, smem);  // static + dynamic may pass 48 KB
     note_launch();
-    k_weed_level<<<blocks, kLevelThreads, smem, s>>>(a, make_inlier_geom(a.w, a.eps));
+    if (a.n >= kWideLevel) {
+        ensure_smem((const void*)k_weed_level<kWideWarps>, smem);  // static + dynamic may pass 48 KB
+        k_weed_level<kWideWarps><<<blocks, 32 * kWideWarps, smem, s>>>(a, make_inlier_geom(a.w, a.eps));
+    } else {
+        ensure_smem((const void*)k_weed_level<kNarrowWarps>, smem);
+        k_weed_level<kNarrowWarps><<<blocks, 32 * kNarrowWarps, smem, s>>>(a, make_inlier_geom(a.w, a.eps));
+    }
 }
 
 // ================================================== workspace weeding path
