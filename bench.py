@@ -866,6 +866,19 @@ def run_scale12(args):
     train_ms = a.elapsed_time(b) / 10
     out_mpix = n * w * h / 1e6
     d = legs["default"]
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.profile:
+        # the oracle's plain path on the first stack (two registrations of 12 MP, one run)
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.register_merge(stacks[0].ref, stacks[0].srcs, stacks[0].ratios,
+                              synth.method_params(32, 6))
+        sec = time.perf_counter() - t0
+        cpu = {"value": round(w * h / 1e6 / sec, 3), "unit": "Mpix/s", "cores": 1,
+               "kind": "oracle",
+               "sample": "one run of the oracle's whole plain path (a1-a11) on the first "
+                         "4000x3000 three-frame stack (output Mpix per second)"}
     if rank == 0:
         line = {
             "metric": "registered+merged output Mpix/s per B300, learned level-0 search "
@@ -892,7 +905,7 @@ def run_scale12(args):
             "train_step_ms": round(train_ms, 3),
             "train_step": "64 crops of 64x64x2 quarter-resolution inputs (256x256 full): "
                           "forward, backward, Adam",
-            "gpu_launches": launches, "clocks": clk_sum,
+            "gpu_launches": launches, "clocks": clk_sum, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -932,6 +945,10 @@ def run_learned8(args):
         ms_plain = max_over_ranks(torch, dist, ms_plain, dev)
     del g, plain
     learned = measure_learned(torch, hdrreg, synth, stacks, frames, p, dev, args)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.profile:
+        cpu = measure_cpu_baseline(synth, stacks[0])
+        cpu["sample"] += " (+-8 px fields)"
     if rank == 0:
         line = {
             "metric": "registered+merged output Mpix/s per B300, learned level-0 search "
@@ -949,7 +966,7 @@ def run_learned8(args):
             "plain": {"value": round(ws * P * W * H / 1e6 / (ms_plain / 1e3), 2),
                       "unit": "Mpix/s", "ms_per_step": round(ms_plain, 3),
                       "gpu_launches_per_step": per_step},
-            "learned": learned, "clocks": clk.summary(),
+            "learned": learned, "clocks": clk.summary(), "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
