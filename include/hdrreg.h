@@ -143,7 +143,9 @@ typedef struct hdrreg_diag {
     int32_t fit_status;      /* bit l set: level l kept the coarser homography              */
     int32_t fallbacks;       /* learned search: level-0 tiles that fell back to the full
                                 search; -1 on the plain path                                */
-    int32_t reserved[2];
+    int32_t flow_status;     /* 0; 1 if a bounded wait of the flow's pipelined passes ran out
+                                (the kernel then stops early and the flow is not valid)     */
+    int32_t reserved;
 } hdrreg_diag;
 
 /* ---------------------------------------------------------------- misc */

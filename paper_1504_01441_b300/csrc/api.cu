@@ -177,7 +177,7 @@ struct FusedLayout {
 __global__ void __launch_bounds__(256) k_diag(const double* H0, const uint8_t* valid,
                                               const uint32_t* mask, int n, const int32_t* fit_st,
                                               int levels, const uint8_t* fell_back,
-                                              hdrreg_diag* d)
+                                              const int* flow_err, hdrreg_diag* d)
 {
     __shared__ int sv, sk, sf;
     if (threadIdx.x == 0) {
@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(256) k_diag(const double* H0, const uint8_t* v
         for (int l = 0; l < levels; l++) bits |= (fit_st[l] != 0) << l;
         d->fit_status = bits;
         d->fallbacks = fell_back ? sf : -1;
-        d->reserved[0] = d->reserved[1] = 0;
+        d->flow_status = (flow_err && *flow_err) ? 1 : 0;
+        d->reserved = 0;
     }
 }
 
@@ -736,7 +737,8 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
         if (diag) {
             note_launch();
             k_diag<<<1, 256, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L,
-                                     lay.learned ? at(lay.fellback) : nullptr, diag + k);
+                                     lay.learned ? at(lay.fellback) : nullptr,
+                                     flow_error_word(at(lay.flow), w, h), diag + k);
         }
         md[k].y = wy;
         md[k].u = chroma ? wu : nullptr;

@@ -239,8 +239,11 @@ __device__ __forceinline__ Aff seg_scan(Aff mine, Aff (*tot)[kCols], int col)
 // One record per level-0 tile for the first row pass: {x, y, residual u, residual v}
 // of its kept corner (y = -1 without one). The residual is q - H(p) (q - p when the
 // full displacement is propagated), evaluated in binary64 and rounded to FP32 once.
-__global__ void k_flow_corner_records(FlowCorners fc, int w, int h, int4* __restrict__ rec)
+// Also zeroes the flow's error word (it is the first launch of the fast path).
+__global__ void k_flow_corner_records(FlowCorners fc, int w, int h, int4* __restrict__ rec,
+                                      int* __restrict__ err)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;
     const int n = fc.ntx * fc.nty;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         int4 r = make_int4(0, -1, 0, 0);
@@ -806,7 +809,7 @@ bool launch_flow_fast(const uint8_t* guide, int gpitch, int w, int h, const Flow
         const int n = fc.ntx * fc.nty;
         if ((size_t)n * 16 > corner_rec_bytes(w, h)) return false;
         note_launch();
-        k_flow_corner_records<<<n > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(fc, w, h, rec);
+        k_flow_corner_records<<<n > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(fc, w, h, rec, err);
     }
     ColMaps mid, fin;
     if (!make_map(&mid.in[0], P0, w, h, 4, kTR, ppitch) || !make_map(&mid.in[1], P1, w, h, 4, kTR, ppitch) ||

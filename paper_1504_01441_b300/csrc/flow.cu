@@ -514,6 +514,12 @@ __global__ void k_copy_rows(const uint8_t* __restrict__ in, int w, int h, uint8_
 }
 }  // namespace
 
+int* flow_error_word(void* ws, int w, int h)
+{
+    const size_t plane = align_up((size_t)flow_pitch(w) * h * 4, 256);
+    return reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + 3 * plane);
+}
+
 void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, double sigma_s,
                  double sigma_r, int iters, double flow_eps, float* flow_u, float* flow_v,
                  int fpitch, void* ws, cudaStream_t s)
@@ -523,7 +529,7 @@ void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, doub
     float* P0 = static_cast<float*>(ws);
     float* P1 = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + plane);
     float* P2 = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + 2 * plane);
-    int* err = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + 3 * plane);
+    int* err = flow_error_word(ws, w, h);
     uint8_t* extra = static_cast<uint8_t*>(ws) + 3 * plane + 256;
     uint8_t* gcopy = extra + flow_fast_extra_bytes(w, h);
     const bool out_ok = fpitch % 4 == 0 && ((uintptr_t)flow_u % 16) == 0 &&
@@ -544,6 +550,7 @@ void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, doub
                              P2, pp, err, extra, s))
             return;
     }
+    cudaMemsetAsync(err, 0, sizeof(int), s);  // the basic path has no waits that could set it
     const int Lr = odd_up((w + kNT - 1) / kNT);
     const size_t rs = row_smem(w);
     ensure_smem((const void*)k_dt_rows<true>, rs);

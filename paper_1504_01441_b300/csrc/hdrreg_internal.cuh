@@ -461,6 +461,9 @@ bool launch_flow_fast(const uint8_t* guide, int gpitch, int w, int h, const Flow
                       void* extra, cudaStream_t s);
 size_t flow_ws_bytes(int w, int h);
 int flow_pitch(int w);  // padded pitch (elements) of the flow's internal planes
+// The flow's error word inside its workspace (set by a bounded wait that ran out; zeroed
+// by every flow call).
+int* flow_error_word(void* ws, int w, int h);
 void launch_flow(const uint8_t* guide, int w, int h, const FlowCorners& fc, double sigma_s,
                  double sigma_r, int iters, double flow_eps, float* flow_u, float* flow_v,
                  int fpitch, void* ws, cudaStream_t s);

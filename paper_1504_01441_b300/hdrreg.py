@@ -101,7 +101,7 @@ class StackEx(C.Structure):
 class Diag(C.Structure):
     _fields_ = [("H0", C.c_double * 9), ("levels", C.c_int32), ("tiles", C.c_int32),
                 ("valid", C.c_int32), ("kept", C.c_int32), ("fit_status", C.c_int32),
-                ("fallbacks", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("fallbacks", C.c_int32), ("flow_status", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None

@@ -86,6 +86,12 @@ def test_sizes(hd):
     assert lib.hdrreg_normalize_workspace_size(0) == 0 and lib.hdrreg_normalize_workspace_size(1) > 0
 
 
+def test_diag_layout_matches_the_header(hd):
+    # hdrreg_diag: 9 binary64 then 8 int32 (levels .. fallbacks, flow_status, reserved)
+    assert C.sizeof(hd.Diag) == 9 * 8 + 8 * 4
+    assert hd.Diag.flow_status.offset == 9 * 8 + 6 * 4
+
+
 def test_null_and_size_errors_return_before_any_launch(hd):
     lib = hd.lib()
     p = hd.params()

@@ -434,6 +434,7 @@ def _fused_case(hd, orc, stack, c):
     for k, d in enumerate(diags):
         assert np.array_equal(np.array(d.H0[:]).view(np.uint64),
                               out["H0"][k].reshape(9).view(np.uint64)), f"H0 of source {k}"
+        assert d.flow_status == 0 and d.reserved == 0, f"flow status of source {k}"
     e = assert_rel(host(ey), out["y"], "fused merge y")
     if chroma:
         assert_rel(host(eu), out["u"], "fused merge u")
