@@ -75,6 +75,88 @@ __global__ void __launch_bounds__(256) k_fuse_level0(FuseL0 a, int w, int h)
     }
 }
 
+// The same weights for four consecutive pixels x4 .. x4 + 3 of row y (w a multiple of 4,
+// rows 4-element aligned): vector loads of the row and of its neighbours, the left and
+// right neighbours of the group as single loads; each pixel's arithmetic is weight_of's.
+__device__ __forceinline__ void load4(const uint8_t* __restrict__ p, float (&v)[4])
+{
+    const uchar4 c = *reinterpret_cast<const uchar4*>(p);
+    v[0] = (float)c.x;
+    v[1] = (float)c.y;
+    v[2] = (float)c.z;
+    v[3] = (float)c.w;
+}
+
+__device__ __forceinline__ void load4(const float* __restrict__ p, float (&v)[4])
+{
+    const float4 c = *reinterpret_cast<const float4*>(p);
+    v[0] = c.x;
+    v[1] = c.y;
+    v[2] = c.z;
+    v[3] = c.w;
+}
+
+template <typename T>
+__device__ __forceinline__ void weights4(const T* __restrict__ z, int x4, int y, int w, int h,
+                                         const FuseL0& a, float (&wk)[4])
+{
+    const size_t r = (size_t)y * w;
+    float c[4];
+    load4(z + r + x4, c);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const float t = c[j] * (1.f / 255.f) - 0.5f;
+        wk[j] = expf(-(t * t) * a.we_k);
+    }
+    if (a.use_contrast) {
+        const int yu = y > 0 ? y - 1 : 0, yd = y + 1 < h ? y + 1 : h - 1;
+        float u[4], d[4];
+        load4(z + (size_t)yu * w + x4, u);
+        load4(z + (size_t)yd * w + x4, d);
+        const float lft = (float)z[r + (x4 > 0 ? x4 - 1 : 0)];
+        const float rgt = (float)z[r + (x4 + 4 < w ? x4 + 4 : w - 1)];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float xl = j == 0 ? lft : c[j - 1], xr = j == 3 ? rgt : c[j + 1];
+            const float s = (xl + xr) + (u[j] + d[j]);
+            wk[j] *= fabsf(fmaf(4.f, c[j], -s)) * (1.f / 255.f);
+        }
+    }
+}
+
+template <int NF>
+__global__ void __launch_bounds__(256) k_fuse_level0_v4(FuseL0 a, int w, int h)
+{
+    const int x4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y;
+    if (x4 >= w) return;
+    const size_t i = (size_t)y * w + x4;
+    float wv[NF][4], tot[4];
+    weights4(a.ref_y, x4, y, w, h, a, wv[0]);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        wv[0][j] = wv[0][j] + 1e-12f;
+        tot[j] = wv[0][j];
+    }
+#pragma unroll
+    for (int f = 1; f < NF; f++) {
+        float q[4];
+        weights4(a.y[f - 1], x4, y, w, h, a, wv[f]);
+        load4(a.q[f - 1] + i, q);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            wv[f][j] = wv[f][j] * q[j] + 1e-12f;
+            tot[j] += wv[f][j];
+        }
+    }
+    float inv[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) inv[j] = 1.f / tot[j];
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+        *reinterpret_cast<float4*>(a.gw[f] + i) =
+            make_float4(wv[f][0] * inv[0], wv[f][1] * inv[1], wv[f][2] * inv[2], wv[f][3] * inv[3]);
+}
+
 // Level-0 chroma weights: 2x2 means of the normalized luma weights.
 struct FuseC0 {
     const float* gw_luma[kMaxSources + 1];
@@ -164,6 +246,43 @@ __device__ __forceinline__ float expand_at(const float* __restrict__ c, int wc, 
     return (row(ky - 1) + 6.f * row(ky) + row(ky + 1)) * 0.125f;
 }
 
+// The 3 x 3 coarse neighbourhood (clamped) of coarse pixel (kx, ky), and EXPAND at the
+// four fine pixels (2 kx + dx, 2 ky + dy) from it, e[dy][dx]: the same sums as expand_at,
+// shared by the four pixels of a 2 x 2 block.
+__device__ __forceinline__ void nbr3(const float* __restrict__ c, int wc, int hc, int kx, int ky,
+                                     float (&n)[3][3])
+{
+    const int x0 = clampi(kx - 1, 0, wc - 1), x1 = clampi(kx, 0, wc - 1), x2 = clampi(kx + 1, 0, wc - 1);
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        const float* cr = c + (size_t)clampi(ky - 1 + r, 0, hc - 1) * wc;
+        n[r][0] = cr[x0];
+        n[r][1] = cr[x1];
+        n[r][2] = cr[x2];
+    }
+}
+
+__device__ __forceinline__ void expand4(const float (&n)[3][3], float (&e)[2][2])
+{
+    float ev[3], od[3];  // each coarse row interpolated to an even and to an odd fine x
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        ev[r] = (n[r][0] + 6.f * n[r][1] + n[r][2]) * 0.125f;
+        od[r] = (n[r][1] + n[r][2]) * 0.5f;
+    }
+    e[0][0] = (ev[0] + 6.f * ev[1] + ev[2]) * 0.125f;
+    e[0][1] = (od[0] + 6.f * od[1] + od[2]) * 0.125f;
+    e[1][0] = (ev[1] + ev[2]) * 0.5f;
+    e[1][1] = (od[1] + od[2]) * 0.5f;
+}
+
+// Launch grid of the 2 x 2-block kernels: one thread per block of a w x h level.
+dim3 grid_blocks(int w, int h)
+{
+    const int bw = (w + 1) / 2, bh = (h + 1) / 2;
+    return dim3((unsigned)((bw + 255) / 256), (unsigned)bh, 1u);
+}
+
 // The finest level in one pass: O^0 = sum_f W_f (I_f - EXPAND(I_f^1)) + EXPAND(O^1) with
 // I_f read from the frames ((v + off) / 255); out = 255 O^0. Without a level 1 (single
 // level) O^0 = sum_f W_f I_f.
@@ -178,22 +297,43 @@ struct FinalArgs {
     int nf;
 };
 
+// One thread per 2 x 2 block of fine pixels: the EXPANDs of the block share one 3 x 3
+// coarse neighbourhood per plane.
 template <int NF>
 __global__ void __launch_bounds__(256) k_fuse_final0(FinalArgs a, int w, int h, int wc, int hc)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x < w) {
-        const size_t i = (size_t)y * w + x;
-        float acc = 0.f;
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y;
+    if (2 * bx >= w) return;
+    float e[NF + 1][2][2];
 #pragma unroll
-        for (int f = 0; f < NF; f++) {
-            float v = ((f == 0 ? (float)a.ref[i] : a.src[f == 0 ? 0 : f - 1][i]) + a.off) *
-                      (1.f / 255.f);
-            if (a.gi1[f]) v -= expand_at(a.gi1[f], wc, hc, x, y);
-            acc = fmaf(a.gw[f][i], v, acc);
+    for (int f = 0; f <= NF; f++) {
+        const float* c = f < NF ? a.gi1[f] : a.o1;
+        if (c) {
+            float n[3][3];
+            nbr3(c, wc, hc, bx, by, n);
+            expand4(n, e[f]);
         }
-        if (a.o1) acc += expand_at(a.o1, wc, hc, x, y);
-        a.out[i] = acc * 255.f;
+    }
+#pragma unroll
+    for (int dy = 0; dy < 2; dy++) {
+        const int y = 2 * by + dy;
+        if (y >= h) break;
+#pragma unroll
+        for (int dx = 0; dx < 2; dx++) {
+            const int x = 2 * bx + dx;
+            if (x >= w) break;
+            const size_t i = (size_t)y * w + x;
+            float acc = 0.f;
+#pragma unroll
+            for (int f = 0; f < NF; f++) {
+                float v = ((f == 0 ? (float)a.ref[i] : a.src[f == 0 ? 0 : f - 1][i]) + a.off) *
+                          (1.f / 255.f);
+                if (a.gi1[f]) v -= e[f][dy][dx];
+                acc = fmaf(a.gw[f][i], v, acc);
+            }
+            if (a.o1) acc += e[NF][dy][dx];
+            a.out[i] = acc * 255.f;
+        }
     }
 }
 
@@ -205,18 +345,44 @@ struct BlendArgs {
     int nf;
 };
 
+// One thread per 2 x 2 block (the EXPANDs share one coarse neighbourhood per frame).
 __global__ void __launch_bounds__(256) k_fuse_blend(BlendArgs a, int w, int h, int wc, int hc)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x < w) {
-        const size_t i = (size_t)y * w + x;
-        float acc = 0.f;
-        for (int f = 0; f < a.nf; f++) {
-            float lap = a.gi[f][i];
-            if (a.gi_up[f]) lap -= expand_at(a.gi_up[f], wc, hc, x, y);
-            acc = fmaf(a.gw[f][i], lap, acc);
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y;
+    if (2 * bx >= w) return;
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int f = 0; f < a.nf; f++) {
+        float e[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+        if (a.gi_up[f]) {
+            float n[3][3];
+            nbr3(a.gi_up[f], wc, hc, bx, by, n);
+            expand4(n, e);
         }
-        a.r[i] = acc;
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++) {
+            const int y = 2 * by + dy;
+            if (y >= h) break;
+#pragma unroll
+            for (int dx = 0; dx < 2; dx++) {
+                const int x = 2 * bx + dx;
+                if (x >= w) break;
+                const size_t i = (size_t)y * w + x;
+                float lap = a.gi[f][i];
+                if (a.gi_up[f]) lap -= e[dy][dx];
+                acc[dy][dx] = fmaf(a.gw[f][i], lap, acc[dy][dx]);
+            }
+        }
+    }
+#pragma unroll
+    for (int dy = 0; dy < 2; dy++) {
+        const int y = 2 * by + dy;
+        if (y >= h) break;
+#pragma unroll
+        for (int dx = 0; dx < 2; dx++) {
+            const int x = 2 * bx + dx;
+            if (x >= w) break;
+            a.r[(size_t)y * w + x] = acc[dy][dx];
+        }
     }
 }
 
@@ -227,12 +393,27 @@ __global__ void __launch_bounds__(256) k_fuse_collapse(float* __restrict__ r,
                                                        int wc, int hc, float* __restrict__ out,
                                                        float scale)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x < w) {
-        const size_t i = (size_t)y * w + x;
-        const float o = up ? r[i] + expand_at(up, wc, hc, x, y) : r[i];
-        if (out) out[i] = o * scale;
-        else r[i] = o;
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y;
+    if (2 * bx >= w) return;
+    float e[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    if (up) {
+        float n[3][3];
+        nbr3(up, wc, hc, bx, by, n);
+        expand4(n, e);
+    }
+#pragma unroll
+    for (int dy = 0; dy < 2; dy++) {
+        const int y = 2 * by + dy;
+        if (y >= h) break;
+#pragma unroll
+        for (int dx = 0; dx < 2; dx++) {
+            const int x = 2 * bx + dx;
+            if (x >= w) break;
+            const size_t i = (size_t)y * w + x;
+            const float o = up ? r[i] + e[dy][dx] : r[i];
+            if (out) out[i] = o * scale;
+            else r[i] = o;
+        }
     }
 }
 
@@ -372,11 +553,11 @@ static void blend_channel(const Pyr& P, int nf, float* const* gi, float* const* 
         b.r = r + P.off[l];
         const int wc = l + 1 < P.L ? P.W[l + 1] : 1, hc = l + 1 < P.L ? P.Hh[l + 1] : 1;
         note_launch();
-        k_fuse_blend<<<grid2(P.W[l], P.Hh[l]), 256, 0, s>>>(b, P.W[l], P.Hh[l], wc, hc);
+        k_fuse_blend<<<grid_blocks(P.W[l], P.Hh[l]), 256, 0, s>>>(b, P.W[l], P.Hh[l], wc, hc);
     }
     for (int l = (P.Lc < P.L ? P.Lc : P.L) - 1 - (P.Lc < P.L ? 0 : 1); l >= 1; l--) {
         note_launch();
-        k_fuse_collapse<<<grid2(P.W[l], P.Hh[l]), 256, 0, s>>>(
+        k_fuse_collapse<<<grid_blocks(P.W[l], P.Hh[l]), 256, 0, s>>>(
             r + P.off[l], r + P.off[l + 1], P.W[l], P.Hh[l], P.W[l + 1], P.Hh[l + 1], nullptr, 1.f);
     }
     FinalArgs fa{};
@@ -390,7 +571,7 @@ static void blend_channel(const Pyr& P, int nf, float* const* gi, float* const* 
         fa.gi1[f] = P.L > 1 ? gi[f] + P.off[1] : nullptr;
         if (f > 0) fa.src[f - 1] = src[f - 1];
     }
-    const dim3 g = grid2(P.W[0], P.Hh[0]);
+    const dim3 g = grid_blocks(P.W[0], P.Hh[0]);
     const int wc = P.L > 1 ? P.W[1] : 1, hc = P.L > 1 ? P.Hh[1] : 1;
     note_launch();
     switch (nf) {
@@ -497,12 +678,28 @@ void launch_fuse(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_
         sy[k] = srcs[k].y;
     }
     for (int f = 0; f < nf; f++) a.gw[f] = gw[f];
+    // four pixels per thread where every row of every plane starts 16-byte aligned (4 for
+    // the reference bytes)
+    bool v4 = (w % 4) == 0 && ((uintptr_t)ref_y % 4) == 0;
+    for (int k = 0; k < nsrc; k++)
+        v4 = v4 && ((uintptr_t)a.y[k] % 16) == 0 && ((uintptr_t)a.q[k] % 16) == 0;
+    for (int f = 0; f < nf; f++) v4 = v4 && ((uintptr_t)a.gw[f] % 16) == 0;
     note_launch();
-    switch (nf) {
-    case 2: k_fuse_level0<2><<<grid2(w, h), 256, 0, s>>>(a, w, h); break;
-    case 3: k_fuse_level0<3><<<grid2(w, h), 256, 0, s>>>(a, w, h); break;
-    case 4: k_fuse_level0<4><<<grid2(w, h), 256, 0, s>>>(a, w, h); break;
-    default: k_fuse_level0<5><<<grid2(w, h), 256, 0, s>>>(a, w, h); break;
+    if (v4) {
+        const dim3 g((unsigned)((w / 4 + 255) / 256), (unsigned)h);
+        switch (nf) {
+        case 2: k_fuse_level0_v4<2><<<g, 256, 0, s>>>(a, w, h); break;
+        case 3: k_fuse_level0_v4<3><<<g, 256, 0, s>>>(a, w, h); break;
+        case 4: k_fuse_level0_v4<4><<<g, 256, 0, s>>>(a, w, h); break;
+        default: k_fuse_level0_v4<5><<<g, 256, 0, s>>>(a, w, h); break;
+        }
+    } else {
+        switch (nf) {
+        case 2: k_fuse_level0<2><<<grid2(w, h), 256, 0, s>>>(a, w, h); break;
+        case 3: k_fuse_level0<3><<<grid2(w, h), 256, 0, s>>>(a, w, h); break;
+        case 4: k_fuse_level0<4><<<grid2(w, h), 256, 0, s>>>(a, w, h); break;
+        default: k_fuse_level0<5><<<grid2(w, h), 256, 0, s>>>(a, w, h); break;
+        }
     }
     const uint8_t* ry[1] = {ref_y};
     build_pyramids(pl, nf, ry, 1, sy, gi, gw, 0.f, s);
