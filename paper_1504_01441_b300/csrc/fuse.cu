@@ -187,6 +187,9 @@ struct PlaneSetT {
     float* out[kMaxPlanes];
 };
 
+// One thread per 2 x 2 block of outputs: the block's 7 x 7 input window is read once, each
+// input row filtered along x for both output columns, then along y for both output rows
+// (per output, the sums and their order are those of the one-output form).
 template <typename T>
 __global__ void __launch_bounds__(256) k_fuse_reduce(PlaneSetT<T> p, int wi, int hi, int wo, int ho,
                                                      float off, float scale)
@@ -194,22 +197,40 @@ __global__ void __launch_bounds__(256) k_fuse_reduce(PlaneSetT<T> p, int wi, int
     const float g[5] = {1.f / 16.f, 4.f / 16.f, 6.f / 16.f, 4.f / 16.f, 1.f / 16.f};
     const T* in = p.in[blockIdx.z];
     float* out = p.out[blockIdx.z];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x < wo) {
-        const size_t i = (size_t)y * wo + x;
-        int xs[5];
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y;
+    if (2 * bx >= wo) return;
+    int xs[7];
 #pragma unroll
-        for (int j = 0; j < 5; j++) xs[j] = clampi(2 * x + j - 2, 0, wi - 1);
-        float acc = 0.f;
+    for (int j = 0; j < 7; j++) xs[j] = clampi(4 * bx + j - 2, 0, wi - 1);
+    float s0[7], s1[7];  // row sums for output columns 2 bx and 2 bx + 1
 #pragma unroll
-        for (int r = 0; r < 5; r++) {
-            const T* row = in + (size_t)clampi(2 * y + r - 2, 0, hi - 1) * wi;
-            float s = 0.f;
+    for (int rr = 0; rr < 7; rr++) {
+        const T* row = in + (size_t)clampi(4 * by + rr - 2, 0, hi - 1) * wi;
+        float v[7];
 #pragma unroll
-            for (int j = 0; j < 5; j++) s = fmaf(g[j], ((float)row[xs[j]] + off) * scale, s);
-            acc = fmaf(g[r], s, acc);
+        for (int j = 0; j < 7; j++) v[j] = ((float)row[xs[j]] + off) * scale;
+        float a = 0.f, b = 0.f;
+#pragma unroll
+        for (int j = 0; j < 5; j++) {
+            a = fmaf(g[j], v[j], a);
+            b = fmaf(g[j], v[j + 2], b);
         }
-        out[i] = acc;
+        s0[rr] = a;
+        s1[rr] = b;
+    }
+#pragma unroll
+    for (int dy = 0; dy < 2; dy++) {
+        const int y = 2 * by + dy;
+        if (y >= ho) break;
+#pragma unroll
+        for (int dx = 0; dx < 2; dx++) {
+            const int x = 2 * bx + dx;
+            if (x >= wo) break;
+            float acc = 0.f;
+#pragma unroll
+            for (int r = 0; r < 5; r++) acc = fmaf(g[r], dx ? s1[r + 2 * dy] : s0[r + 2 * dy], acc);
+            out[(size_t)y * wo + x] = acc;
+        }
     }
 }
 
@@ -594,7 +615,9 @@ static void reduce_planes(const Pyr& P, int l, const T* const* in, float* const*
             ps.out[k] = out[b + k];
         }
         note_launch();
-        k_fuse_reduce<T><<<grid2(P.W[l + 1], P.Hh[l + 1], cnt), 256, 0, s>>>(
+        dim3 g = grid_blocks(P.W[l + 1], P.Hh[l + 1]);
+        g.z = (unsigned)cnt;
+        k_fuse_reduce<T><<<g, 256, 0, s>>>(
             ps, P.W[l], P.Hh[l], P.W[l + 1], P.Hh[l + 1], off, scale);
     }
 }
