@@ -37,6 +37,29 @@ struct FuseL0 {
     float we_k;  // 1 / (2 sigma^2)
 };
 
+// |4 z - (xl + xr) - (u + d)| / 255, the contrast of Sec. 2.5 in DN. On a linear ramp of a
+// warped (FP32) frame the exact value is 0, and the weights are then normalized against the
+// 1e-12 floor, so a plain FP32 evaluation (rounding error ~1e-5 DN) would decide them. The
+// sum is therefore formed without error (Knuth's two-sum), the difference 4 z - hi is exact
+// where it cancels (Sterbenz), and one rounding remains. For byte frames every step is exact
+// in FP32 already.
+__device__ __forceinline__ float two_sum(float a, float b, float& e)
+{
+    const float s = a + b, bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+__device__ __forceinline__ float contrast_dn(float zc, float xl, float xr, float u, float d, bool exact)
+{
+    if (exact) return fabsf(fmaf(4.f, zc, -((xl + xr) + (u + d))));
+    float e0, e1, e2;
+    const float a = two_sum(xl, xr, e0), b = two_sum(u, d, e1);
+    const float hi = two_sum(a, b, e2);
+    const float lo = (e0 + e1) + e2;
+    return fabsf(fmaf(4.f, zc, -hi) - lo);
+}
+
 template <typename T>
 __device__ __forceinline__ float weight_of(const T* __restrict__ z, size_t i, int x, int y, int w,
                                            int h, const FuseL0& a)
@@ -48,9 +71,9 @@ __device__ __forceinline__ float weight_of(const T* __restrict__ z, size_t i, in
         const int xl = x > 0 ? x - 1 : 0, xr = x + 1 < w ? x + 1 : w - 1;
         const int yu = y > 0 ? y - 1 : 0, yd = y + 1 < h ? y + 1 : h - 1;
         const size_t r = (size_t)y * w;
-        const float s = ((float)z[r + xl] + (float)z[r + xr]) +
-                        ((float)z[(size_t)yu * w + x] + (float)z[(size_t)yd * w + x]);
-        wk *= fabsf(fmaf(4.f, zc, -s)) * (1.f / 255.f);
+        wk *= contrast_dn(zc, (float)z[r + xl], (float)z[r + xr], (float)z[(size_t)yu * w + x],
+                          (float)z[(size_t)yd * w + x], sizeof(T) == 1) *
+              (1.f / 255.f);
     }
     return wk;
 }
@@ -118,8 +141,7 @@ __device__ __forceinline__ void weights4(const T* __restrict__ z, int x4, int y,
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const float xl = j == 0 ? lft : c[j - 1], xr = j == 3 ? rgt : c[j + 1];
-            const float s = (xl + xr) + (u[j] + d[j]);
-            wk[j] *= fabsf(fmaf(4.f, c[j], -s)) * (1.f / 255.f);
+            wk[j] *= contrast_dn(c[j], xl, xr, u[j], d[j], sizeof(T) == 1) * (1.f / 255.f);
         }
     }
 }

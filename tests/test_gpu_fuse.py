@@ -90,3 +90,27 @@ def test_fused_call_with_exposure_fusion(hd, orc, small_yuv_stack, mode):
         e = rel_err(g.cpu().numpy(), o)
         print(f"{name} {e:.2e}")
         assert e <= REL, name
+
+
+def test_fused_exposure_fusion_at_5mp(hd, orc):
+    # the fusion output of the fused call on the 2592 x 1944 YUV420 pair of the batch
+    # workload (T = 32, R = 6), against the oracle's registration followed by the oracle
+    # fusion: same H0 bits, planes within the parity tolerance
+    from oracle import fusion as F
+    from paper_1504_01441_b300 import synth
+    st = synth.make_stack(synth.FIVE_MP, synth.stack_seed(2, 0))
+    c = synth.method_params(32, 6, output_mode=1)
+    p = hd.params_from_dict(c)
+    (y, u, v), rm = hd.register_merge((d(st.ref.y), d(st.ref.u), d(st.ref.v)),
+                                      [(d(f.y), d(f.u), d(f.v)) for f in st.srcs], st.ratios, p)
+    torch.cuda.synchronize()
+    out = orc.register_merge(st.ref, st.srcs, st.ratios, c, want_intermediates=True)
+    f = st.srcs[0]
+    assert np.array_equal(np.array(rm.diagnostics()[0].H0[:]).view(np.uint64),
+                          out["H0"][0].reshape(9).view(np.uint64))
+    wy, wu, wv = orc.warp(f.y, f.u, f.v, out["H0"][0], out["flow_u"][0], out["flow_v"][0])
+    oy, ou, ov = F.fuse(st.ref.y, st.ref.u, st.ref.v, [(wy, wu, wv)], [out["q"][0]])
+    for name, g, o in (("y", y, oy), ("u", u, ou), ("v", v, ov)):
+        e = rel_err(g.cpu().numpy(), o)
+        print(f"{name} {e:.2e}")
+        assert e <= REL, name
