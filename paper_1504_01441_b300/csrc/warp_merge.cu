@@ -52,8 +52,9 @@ __device__ __forceinline__ void h_disp(const WarpCoef& c, int x, int y, int w, i
     }
     const float nx = fmaf(c.a0, u, fmaf(c.a1, v, c.a2)) - 0.5f * u * E;
     const float ny = fmaf(c.b0, u, fmaf(c.b1, v, c.b2)) - 0.5f * v * E;
-    dx = nx / D;
-    dy = ny / D;
+    const float r = __frcp_rn(D);  // one reciprocal for both components
+    dx = nx * r;
+    dy = ny * r;
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -95,7 +96,9 @@ __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nb; idx += gridDim.x * blockDim.x) {
     const int bx = idx % bw, by = idx / bw;
     float stx = 0.f, sty = 0.f;
+#pragma unroll
     for (int j = 0; j < 2; j++)
+#pragma unroll
         for (int i = 0; i < 2; i++) {
             const int x = 2 * bx + i, y = 2 * by + j;
             if (x >= w || y >= h) continue;
