@@ -484,6 +484,17 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
             if (!kApply) __syncthreads();             // all threads are done reading buffer 1-b
             issue(nx, 1 - b);
         }
+        // phase C: this item's six carries (written by the chain kernel), loaded before
+        // the wait for the tile so that their latency overlaps it
+        float cr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (kApply) {
+            const int xc = (item % ntx) * kTW + lane, tc = item / ntx;
+            if (xc < w) {
+                const size_t c0 = (size_t)xc * kCar * ntile + tc;
+#pragma unroll
+                for (int q = 0; q < 6; q++) cr[q] = __ldg(car + c0 + (size_t)q * ntile);
+            }
+        }
         const bool ok = __syncthreads_and(mbar_wait(&bar[b], b ? ph1 : ph0));
         if (b) ph1 ^= 1u; else ph0 ^= 1u;
         if (!ok) {
@@ -514,7 +525,6 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
         }
         const bool colok = x0 + lane < w;
         const size_t ao = (size_t)(x0 + lane) * kAgg * ntile + tile;  // agg[x][k][t]
-        const size_t co = (size_t)(x0 + lane) * kCar * ntile + tile;  // car[x][k][t]
         Aff m = sweep_fwd<kTLS>(v, wl, kTLS);
         agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
         __syncthreads();
@@ -564,8 +574,7 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
             }
             __syncthreads();  // agg reused by the next item
         } else {
-            Aff pre = colok ? Aff{0.f, car[co], car[co + ntile], car[co + 2 * ntile]}
-                            : Aff{0.f, 0.f, 0.f, 0.f};
+            Aff pre = Aff{0.f, cr[0], cr[1], cr[2]};  // zero carries outside the image
             for (int q = 0; q < sg; q++) {
                 const Aff4 a = agg[q][lane];
                 pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
@@ -575,8 +584,7 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
             m = sweep_bwd<kTLS>(v, wl, kTLS);
             agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
             __syncthreads();
-            Aff suf = colok ? Aff{0.f, car[co + 3 * ntile], car[co + 4 * ntile], car[co + 5 * ntile]}
-                            : Aff{0.f, 0.f, 0.f, 0.f};
+            Aff suf = Aff{0.f, cr[3], cr[4], cr[5]};
             for (int q = kTSeg - 1; q > sg; q--) {
                 const Aff4 a = agg[q][lane];
                 suf = compose(suf, Aff{a.A, a.B0, a.B1, a.B2});
