@@ -425,7 +425,7 @@ def measure_stages(torch, hdrreg, p, stack, dev, args, meta=None):
 
 # DRAM bytes of one flow call (2592 x 1944, 3 iterations, 13 launches) from the ncu
 # capture summarised in profiles/flow_dram_5mp.md.
-FLOW_TRAFFIC = 554760960
+FLOW_TRAFFIC = 554542336
 
 
 def measure_search_alu(torch, hdrreg, stages, p, valid_tiles, dev):
