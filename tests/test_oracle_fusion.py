@@ -89,3 +89,21 @@ def test_fuse_of_identical_frames_and_a_dominant_frame():
     y2 = rng.uniform(0, 255, (48, 64))
     fy, _, _ = F.fuse(y, None, None, [(y2, None, None)], [np.zeros((48, 64))])
     assert np.abs(fy - y).max() < 1e-6
+
+
+def test_contrast_vanishes_on_planes_and_the_floor_then_decides():
+    # the discrete Laplacian of a plane is 0 (up to binary64 rounding) away from the border,
+    # so on two planar frames with equal well-exposedness the normalized weights are set by
+    # the 1e-12 floor alone: one half each
+    y, x = np.mgrid[0:24, 0:32].astype(np.float64)
+    a = 40.0 + 1.75 * x + 0.5 * y
+    b = 90.0 + 0.25 * x - 1.125 * y
+    ca = F.contrast(a / 255.0)[1:-1, 1:-1]
+    cb = F.contrast(b / 255.0)[1:-1, 1:-1]
+    assert np.abs(ca).max() < 1e-14 and np.abs(cb).max() < 1e-14
+    w = F.weights([a, b], [None, np.ones_like(b)], use_contrast=True)
+    we_a, we_b = F.well_exposedness(a), F.well_exposedness(b)
+    inner = (slice(1, -1), slice(1, -1))
+    # contrast * well-exposedness is far below the floor, so the ratio is the floor's (1:1)
+    assert np.all(ca * we_a[inner] < 1e-13) and np.all(cb * we_b[inner] < 1e-13)
+    assert np.allclose(w[0][inner], 0.5, atol=1e-3) and np.allclose(w[0][inner] + w[1][inner], 1.0)
