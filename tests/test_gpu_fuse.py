@@ -114,3 +114,26 @@ def test_fused_exposure_fusion_at_5mp(hd, orc):
         e = rel_err(g.cpu().numpy(), o)
         print(f"{name} {e:.2e}")
         assert e <= REL, name
+
+
+def test_fuse_contrast_on_smooth_fp32_frames(hd):
+    # two smooth warped-like FP32 frames (planes with slopes of 1/3 and 1/7, rounded to
+    # FP32) and a flat reference: the contrasts are the rounding residue of the planes, a
+    # few 1e-6 DN, and the normalized weights are their ratio. The step call must evaluate
+    # |4 z - sum of the neighbours| on the FP32 values as the oracle does, not with FP32
+    # rounding of its own.
+    from oracle import fusion as F
+    h, w = 96, 128
+    y, x = np.mgrid[0:h, 0:w].astype(np.float64)
+    ref = np.full((h, w), 60, np.uint8)
+    s1 = (80.0 + x / 3.0 + y / 7.0).astype(np.float32)
+    s2 = (150.0 - x / 7.0 + y / 3.0).astype(np.float32)
+    q = np.full((h, w), 0.75, np.float32)
+    srcs = [dict(y=d(s), q=d(q)) for s in (s1, s2)]
+    gy, _, _ = hd.fuse(d(ref), None, None, srcs, use_contrast=True)
+    oy, _, _ = F.fuse(ref, None, None, [(s1, None, None), (s2, None, None)], [q, q],
+                      use_contrast=True)
+    torch.cuda.synchronize()
+    e = rel_err(gy.cpu().numpy(), oy)
+    print(f"y {e:.2e}")
+    assert e <= REL
