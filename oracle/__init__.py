@@ -17,19 +17,39 @@ import numpy as np
 _DIR = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_DIR, "hdrreg_oracle.c")
 _LIB = os.path.join(_DIR, "liboracle.so")
-_lib = None
+_LIB_OMP = os.path.join(_DIR, "liboracle_omp.so")
+_libs = {}
+_parallel = False
 
-CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-Wall", "-shared", "-fPIC"]
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-Wall",
+          "-Wno-unknown-pragmas", "-shared", "-fPIC"]
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (binary64 in the written order: no contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_DIR, "hdrreg_oracle.h"))):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile the oracle with gcc (binary64 in the written order: no contraction), once
+    serial (liboracle.so) and once with OpenMP over its independent loops
+    (liboracle_omp.so)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_DIR, "hdrreg_oracle.h")))
+    for out, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
+            tmp = out + ".tmp%d" % os.getpid()
+            subprocess.check_call(["gcc", *CFLAGS, *extra, "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, out)
     return _LIB
+
+
+def set_parallel(on: bool) -> None:
+    """Route every oracle call to the OpenMP build (True) or the serial one (False, the
+    default). The OpenMP build uses OMP_NUM_THREADS threads, else all cores."""
+    global _parallel
+    _parallel = bool(on)
+
+
+def threads() -> int:
+    """Threads the OpenMP build runs with (1 for the serial build)."""
+    if not _parallel:
+        return 1
+    return int(C.CDLL(_LIB_OMP).orc_max_threads())
 
 
 class Params(C.Structure):
@@ -56,11 +76,11 @@ def make_params(cfg: Dict) -> Params:
 
 
 def lib():
-    global _lib
-    if _lib is None:
+    path = _LIB_OMP if _parallel else _LIB
+    if path not in _libs:
         build()
-        _lib = C.CDLL(_LIB)
-    return _lib
+        _libs[path] = C.CDLL(path)
+    return _libs[path]
 
 
 def _p(a: Optional[np.ndarray]):
@@ -320,20 +340,44 @@ def bilinear(img, x, y):
     return f(_p(img), w, h, C.c_double(x), C.c_double(y))
 
 
-def warp(src_y, src_u, src_v, H0, flow_u, flow_v):
+def bilinear_clipped(img, x, y):
+    img = _u8(img)
+    h, w = img.shape
+    return bool(lib().orc_bilinear_clipped(_p(img), w, h, C.c_double(x), C.c_double(y)))
+
+
+def warp(src_y, src_u, src_v, H0, flow_u, flow_v, want_clip=False):
+    """(y, u, v) warped planes; with want_clip also the luma clip flags (uint8)."""
     src_y = _u8(src_y)
     h, w = src_y.shape
     H0 = _f64(H0).reshape(9)
     fu, fv = _f64(flow_u), _f64(flow_v)
     oy = np.zeros((h, w))
+    clip = np.zeros((h, w), np.uint8)
     chroma = src_u is not None
     su = _u8(src_u) if chroma else None
     sv = _u8(src_v) if chroma else None
     ou = np.zeros((h // 2, w // 2)) if chroma else None
     ov = np.zeros((h // 2, w // 2)) if chroma else None
     lib().orc_warp(_p(src_y), _p(su), _p(sv), w, h, _p(H0), _p(fu), _p(fv), _p(oy), _p(ou),
-                   _p(ov))
-    return oy, ou, ov
+                   _p(ov), _p(clip))
+    return (oy, ou, ov, clip) if want_clip else (oy, ou, ov)
+
+
+def clip_fragile(src_y, H0, flow_u, flow_v, delta=1e-3):
+    """Reference pixels whose clip decision (orc_bilinear_clipped at H0(p) + F(p)) is not
+    the same at every corner of the square of half-side ``delta`` pixels around the sample
+    position: there a position error below ``delta`` (a float32 flow, float32 evaluation
+    of H0) can flip the decision, so the merge weight of the sample is not determined by
+    the position to that accuracy. Returns a bool map."""
+    fu, fv = _f64(flow_u), _f64(flow_v)
+    base = warp(src_y, None, None, H0, fu, fv, want_clip=True)[3]
+    out = np.zeros(base.shape, bool)
+    for sx in (-delta, delta):
+        for sy in (-delta, delta):
+            c = warp(src_y, None, None, H0, fu + sx, fv + sy, want_clip=True)[3]
+            out |= c != base
+    return out
 
 
 # ---------------------------------------------------------------- a10
@@ -362,8 +406,10 @@ def well_exposedness(z, sigma=0.2):
     return f(C.c_double(z), C.c_double(sigma))
 
 
-def merge(ref_y, ref_u, ref_v, warped, qmaps, ratios, we_sigma=0.2):
-    """warped: list of (y, u, v) float arrays per source; ratios: list of floats t_k / t_ref."""
+def merge(ref_y, ref_u, ref_v, warped, qmaps, ratios, we_sigma=0.2, clips=None):
+    """warped: list of (y, u, v) float arrays per source; ratios: list of floats t_k / t_ref;
+    clips: per source the uint8 clip flags of the warped luma (``warp(..., want_clip=True)``),
+    or None to take a sample as clipped when its value is <= 0 or >= 255."""
     ref_y = _u8(ref_y)
     h, w = ref_y.shape
     chroma = ref_u is not None
@@ -378,8 +424,10 @@ def merge(ref_y, ref_u, ref_v, warped, qmaps, ratios, we_sigma=0.2):
     ou = np.zeros((h // 2, w // 2)) if chroma else None
     ov = np.zeros((h // 2, w // 2)) if chroma else None
     ru, rv = (_u8(ref_u), _u8(ref_v)) if chroma else (None, None)
+    cl = None if clips is None else [_u8(c) for c in clips]
     lib().orc_merge(w, h, _p(ref_y), _p(ru), _p(rv), k, arr(wy), arr(wu), arr(wv), arr(qs),
-                    _p(rat), C.c_double(we_sigma), _p(oy), _p(ou), _p(ov))
+                    arr(cl) if cl is not None else None, _p(rat), C.c_double(we_sigma), _p(oy),
+                    _p(ou), _p(ov))
     return oy, ou, ov
 
 
@@ -403,13 +451,15 @@ def register_merge(ref, srcs, ratios, cfg, want_intermediates=False):
     inter = {}
     if want_intermediates:
         inter = {n: [np.zeros((h, w)) for _ in range(k)] for n in ("warped_y", "flow_u", "flow_v", "q")}
+        inter["clip"] = [np.zeros((h, w), np.uint8) for _ in range(k)]
     prm = make_params(cfg)
     ru, rv = (_u8(ref.u), _u8(ref.v)) if chroma else (None, None)
     lib().orc_register_merge(
         w, h, _p(ry), _p(ru), _p(rv), k, arr(sy), arr(su), arr(sv), _p(num), _p(den),
         C.byref(prm), _p(oy), _p(ou), _p(ov), _p(H0),
         arr(inter["warped_y"]) if inter else None, arr(inter["flow_u"]) if inter else None,
-        arr(inter["flow_v"]) if inter else None, arr(inter["q"]) if inter else None)
+        arr(inter["flow_v"]) if inter else None, arr(inter["q"]) if inter else None,
+        arr(inter["clip"]) if inter else None)
     out = dict(y=oy, u=ou, v=ov, H0=H0.reshape(k, 3, 3))
     out.update(inter)
     return out

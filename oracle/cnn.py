@@ -144,9 +144,11 @@ def features(x):
     return np.stack(out, -1)
 
 
-def forward(theta, x, bf16=False, layers=LAYERS, feature_stage=True):
+def forward(theta, x, bf16=False, layers=LAYERS, feature_stage=True, perturb=None):
     """x [n, h, w, 2] -> (out [n, h/8, w/8, 2] (ceil at each stride), cache for backward).
-    feature_stage=False feeds x straight to the first layer (used by the gradient pins)."""
+    feature_stage=False feeds x straight to the first layer (used by the gradient pins).
+    perturb (tests only): a function applied to every layer's pre-activation, used to
+    measure how far the bfloat16 chain moves under accumulation-sized noise."""
     params = unpack(theta, layers)
     if bf16:
         params = [(bf16_round(W), np.asarray(b, np.float32).astype(np.float64)) for W, b in params]
@@ -159,6 +161,8 @@ def forward(theta, x, bf16=False, layers=LAYERS, feature_stage=True):
     acts = [x]
     for (W, b), (ci, co, k, s, r) in zip(params, layers):
         z = conv_forward(acts[-1], W, b, s)
+        if perturb is not None:
+            z = perturb(z)
         if r:
             z = np.maximum(z, 0.0)
             if bf16:

@@ -2,7 +2,12 @@
  * hdrreg_oracle.c -- CPU reference of the registration + merge path.
  *
  * TEST INFRASTRUCTURE ONLY (see hdrreg_oracle.h). Plain loops, FP64 and
- * int64/__int128, evaluated in the written order. Each function names the
+ * int64/__int128, evaluated in the written order. The loops over independent
+ * rows, columns, tiles and weeding iterations carry OpenMP pragmas: the serial
+ * build ignores them, the OpenMP build (liboracle_omp.so) runs them on all
+ * cores. Every output element is computed by the same operations in the same
+ * order either way, and the weeding union is order-free, so both builds give
+ * the same bits. Each function names the
  * passage of the paper (section / equation) it restates, plus the reading
  * taken where the paper is silent.
  */
@@ -95,6 +100,7 @@ int orc_num_levels(int w, int h, int levels_max, int min_size)
 void orc_downsample(const uint8_t* in, int w, int h, uint8_t* out)
 {
     int ow = w / 2, oh = h / 2;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < oh; y++)
         for (int x = 0; x < ow; x++) {
             int s = in[(long)(2 * y) * w + 2 * x] + in[(long)(2 * y) * w + 2 * x + 1] +
@@ -158,6 +164,7 @@ int orc_pick_corners(const uint8_t* img, int w, int h, const orc_params* p,
     int s = T / 16 > 1 ? T / 16 : 1;
     int ntx = w / T, nty = h / T;
     long thr = (long)p->corner_thresh * q * q;
+#pragma omp parallel for collapse(2) schedule(dynamic, 8)
     for (int ty = 0; ty < nty; ty++)
         for (int tx = 0; tx < ntx; tx++) {
             int t = ty * ntx + tx;
@@ -231,6 +238,7 @@ void orc_search(const uint8_t* ref_n, const uint8_t* src_n, int w, int h, const 
                 int32_t* center_xy, int32_t* match_xy, uint32_t* cost)
 {
     int R = p->radius, hp = p->patch_half;
+#pragma omp parallel for schedule(dynamic, 4)
     for (int t = 0; t < ntiles; t++) {
         int px = corner_xy[2 * t], py = corner_xy[2 * t + 1];
         int32_t cx = px, cy = py;
@@ -489,7 +497,6 @@ void orc_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* 
               uint32_t* mask_bits, int32_t* accepted_out)
 {
     int* V = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
-    uint8_t* inl = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
     int nv = 0;
     for (int t = 0; t < n; t++) if (valid[t]) V[nv++] = t;
     int accepted = 0;
@@ -497,6 +504,12 @@ void orc_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* 
         int delta = (nv + p->weed_delta_div - 1) / p->weed_delta_div;
         if (delta < p->weed_delta_min) delta = p->weed_delta_min;
         double S = (double)orc_pow2_scale(w);
+        /* the iterations are independent and M is their union (order-free), so they may
+         * run in any order: one inlier buffer per thread, the union by atomic OR */
+#pragma omp parallel
+        {
+        uint8_t* inl = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
+#pragma omp for reduction(+ : accepted) schedule(dynamic, 8)
         for (int it = iter_begin; it < iter_end; it++) {
             int pick[4];
             if (!orc_weed_sample(seed, it, nv, pick)) continue;
@@ -525,13 +538,17 @@ void orc_weed(const int32_t* corner_xy, const int32_t* match_xy, const uint8_t* 
             if (cnt > delta) {
                 accepted++;
                 for (int k = 0; k < nv; k++)
-                    if (inl[k]) mask_bits[V[k] >> 5] |= 1u << (V[k] & 31);
+                    if (inl[k]) {
+#pragma omp atomic
+                        mask_bits[V[k] >> 5] |= 1u << (V[k] & 31);
+                    }
             }
+        }
+        free(inl);
         }
     }
     if (accepted_out) *accepted_out = accepted;
     free(V);
-    free(inl);
 }
 
 /* ===================================================================== a7 */
@@ -722,6 +739,7 @@ void orc_dt_filter(double** P, int np, const uint8_t* g, int w, int h, double si
     for (int it = 0; it < iters; it++) {
         double sig, a;
         orc_dt_sigma(sigma_s, iters, it, &sig, &a);
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < h; y++) {
             const uint8_t* gr = g + (long)y * w;
             for (int x = 1; x < w; x++) {
@@ -741,6 +759,7 @@ void orc_dt_filter(double** P, int np, const uint8_t* g, int w, int h, double si
                 }
             }
         }
+#pragma omp parallel for schedule(static)
         for (int x = 0; x < w; x++) {
             for (int y = 1; y < h; y++) {
                 double d = 1.0 + ratio * fabs((double)g[(long)y * w + x] -
@@ -796,6 +815,7 @@ void orc_flow(const uint8_t* guide, int w, int h, int n, const int32_t* corner_x
     }
     double* planes[3] = {Pu, Pv, N};
     orc_dt_filter(planes, 3, guide, w, h, p->sigma_s, p->sigma_r, p->dt_iters);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < np; i++) {
         if (N[i] >= p->flow_eps) {
             flow_u[i] = Pu[i] / N[i];
@@ -827,18 +847,45 @@ double orc_bilinear(const uint8_t* img, int w, int h, double x, double y)
 }
 
 /*
+ * Does the bilinear sample at (x, y) draw on a clipped pixel? The frames are
+ * 8-bit (Sec. 2.1), so a pixel at 0 or 255 recorded only a bound on its
+ * irradiance, and any sample that gives such a pixel a nonzero weight inherits
+ * that bound. The taps with nonzero weight are the one at (floor x, floor y),
+ * always; its right neighbour when the x fraction is above zero; the tap below
+ * when the y fraction is above zero; and the diagonal one when both are.
+ * Returns 1 when one of them holds 0 or 255, else 0 (clamp-to-edge taps).
+ */
+int orc_bilinear_clipped(const uint8_t* img, int w, int h, double x, double y)
+{
+    double x0 = floor(x), y0 = floor(y);
+    int ix = (int)x0, iy = (int)y0;
+    int right = x - x0 > 0.0, below = y - y0 > 0.0;
+    int t[4], nt = 0;
+    t[nt++] = pix(img, w, h, ix, iy);
+    if (right) t[nt++] = pix(img, w, h, ix + 1, iy);
+    if (below) t[nt++] = pix(img, w, h, ix, iy + 1);
+    if (right && below) t[nt++] = pix(img, w, h, ix + 1, iy + 1);
+    for (int k = 0; k < nt; k++)
+        if (t[k] == 0 || t[k] == 255) return 1;
+    return 0;
+}
+
+/*
  * Warp the source to the reference (Sec. 2.4): reference pixel p samples the
  * source at M(p) = H0(p) + F(p) (bilinear, clamp-to-edge). Chroma (half
  * resolution, optional) samples at (Mbar(q) - 0.5) / 2, Mbar the mean of the
- * four luma positions of the 2x2 block of chroma pixel q.
+ * four luma positions of the 2x2 block of chroma pixel q. Optionally clip_y[p]
+ * = orc_bilinear_clipped at M(p): whether the luma sample draws on a pixel at
+ * 0 or 255.
  */
 void orc_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_v, int w, int h,
               const double H0[9], const double* flow_u, const double* flow_v,
-              double* out_y, double* out_u, double* out_v)
+              double* out_y, double* out_u, double* out_v, uint8_t* clip_y)
 {
     long np = (long)w * h;
     double* mx = (double*)malloc(sizeof(double) * (size_t)np);
     double* my = (double*)malloc(sizeof(double) * (size_t)np);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < h; y++)
         for (int x = 0; x < w; x++) {
             long i = (long)y * w + x;
@@ -847,9 +894,11 @@ void orc_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_v, 
             mx[i] = xs + flow_u[i];
             my[i] = ys + flow_v[i];
             out_y[i] = orc_bilinear(src_y, w, h, mx[i], my[i]);
+            if (clip_y) clip_y[i] = (uint8_t)orc_bilinear_clipped(src_y, w, h, mx[i], my[i]);
         }
     if (src_u && src_v && out_u && out_v) {
         int cw = w / 2, ch = h / 2;
+#pragma omp parallel for schedule(static)
         for (int j = 0; j < ch; j++)
             for (int i = 0; i < cw; i++) {
                 long a = (long)(2 * j) * w + 2 * i, b = a + w;
@@ -886,6 +935,7 @@ void orc_ssim(const double* X, const double* Y, int w, int h, double sigma, int 
     for (int k = 0; k < n * n; k++) g[k] /= gs;
     double C1 = (0.01 * 255.0) * (0.01 * 255.0);
     double C2 = (0.03 * 255.0) * (0.03 * 255.0);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < h; y++)
         for (int x = 0; x < w; x++) {
             double mx = 0.0, my = 0.0;
@@ -924,6 +974,7 @@ void orc_ghost_mask(const uint8_t* ref_n, const double* warped_y, int w, int h, 
     long np = (long)w * h;
     double* X = (double*)calloc((size_t)np, sizeof(double));
     double* Y = (double*)calloc((size_t)np, sizeof(double));
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < np; i++) {
         X[i] = (double)ref_n[i];
         double z = warped_y[i];
@@ -956,30 +1007,25 @@ double orc_well_exposedness(double z, double sigma)
 }
 
 /*
- * Clipping taper of a resampled source value: 0 at 0 and 255, rising linearly
- * to 1 over the 2 DN next to either end. A clipped sample carries no
- * irradiance; the ramp keeps the weight continuous in the sample value.
- */
-double orc_clip_taper(double z)
-{
-    double d = fmin(z, 255.0 - z) / 2.0;
-    return d <= 0.0 ? 0.0 : (d >= 1.0 ? 1.0 : d);
-}
-
-/*
  * Weighted irradiance merge (Sec. 2.5 weights; Sec. 3.1 irradiance map):
  * E(p) = sum_k w_k Z_k / r_k / sum_k w_k with r_ref = 1, w_ref = WE(Z_ref) and
- * for every warped source w_k = WE(Z_k) * Q_k * taper(Z_k) (orc_clip_taper).
- * Chroma U-128, V-128 is merged with the mean of the four luma weights of its
- * 2x2 block and the same 1/r_k.
+ * for every warped source w_k = WE(Z_k) * Q_k, or 0 where the sample is clipped:
+ * a clipped sample measured only a bound on the irradiance, so it carries none.
+ * clip[k][p] says whether source k's sample at p draws on a pixel at 0 or 255
+ * (orc_bilinear_clipped, written by orc_warp); without it (clip or clip[k]
+ * NULL) a sample is clipped when Z_k <= 0 or Z_k >= 255, the same test for a
+ * sample that sits on one pixel. Chroma U-128, V-128 is merged with the mean of
+ * the four luma weights of its 2x2 block and the same 1/r_k.
  */
 void orc_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v,
                int nsrc, const double* const* wy, const double* const* wu,
-               const double* const* wv, const double* const* q, const double* ratio,
-               double we_sigma, double* out_y, double* out_u, double* out_v)
+               const double* const* wv, const double* const* q,
+               const uint8_t* const* clip, const double* ratio, double we_sigma,
+               double* out_y, double* out_u, double* out_v)
 {
     long np = (long)w * h;
     double* wts = (double*)malloc(sizeof(double) * (size_t)np * (size_t)(nsrc + 1));
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < np; i++) {
         double z0 = (double)ref_y[i];
         double w0 = orc_well_exposedness(z0, we_sigma);
@@ -987,7 +1033,8 @@ void orc_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u, const u
         wts[i] = w0;
         for (int k = 0; k < nsrc; k++) {
             double z = wy[k][i];
-            double wk = orc_well_exposedness(z, we_sigma) * q[k][i] * orc_clip_taper(z);
+            int clipped = (clip && clip[k]) ? clip[k][i] != 0 : (z <= 0.0 || z >= 255.0);
+            double wk = clipped ? 0.0 : orc_well_exposedness(z, we_sigma) * q[k][i];
             wts[(long)(k + 1) * np + i] = wk;
             num += wk * (z / ratio[k]);
             den += wk;
@@ -996,6 +1043,7 @@ void orc_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u, const u
     }
     if (ref_u && ref_v && out_u && out_v) {
         int cw = w / 2, ch = h / 2;
+#pragma omp parallel for schedule(static)
         for (int j = 0; j < ch; j++)
             for (int i = 0; i < cw; i++) {
                 long a = (long)(2 * j) * w + 2 * i, b = a + w, c = (long)j * cw + i;
@@ -1023,8 +1071,8 @@ void orc_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u, const u
  * to the reference independently (n-1 runs, Sec. 2), then merged. Per source:
  * normalize (a1), pyramid matcher (a2-a7), sparse-to-dense flow guided by the
  * normalized reference (a8), warp (a9), ghost mask (a10); then the merge
- * (a11). Optional per-source outputs: H0 (9 doubles each), warped luma, flow
- * and mask. Returns 0.
+ * (a11). Optional per-source outputs: H0 (9 doubles each), warped luma, flow,
+ * mask and clip flags of the warped luma. Returns 0.
  */
 int orc_register_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u,
                        const uint8_t* ref_v, int nsrc, const uint8_t* const* src_y,
@@ -1033,12 +1081,13 @@ int orc_register_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u,
                        const orc_params* p, double* out_y, double* out_u, double* out_v,
                        double* H0_out, double* const* warped_y_out,
                        double* const* flow_u_out, double* const* flow_v_out,
-                       double* const* q_out)
+                       double* const* q_out, uint8_t* const* clip_out)
 {
     long np = (long)w * h;
     long nc = (long)(w / 2) * (h / 2);
     int chroma = ref_u && ref_v && out_u && out_v;
     double* wy[8] = {0}; double* wu[8] = {0}; double* wv[8] = {0}; double* qq[8] = {0};
+    uint8_t* cl[8] = {0};
     if (nsrc < 1 || nsrc > 8) return 1;
     double ratio[8] = {0};
     int ntmax = (w / p->tile) * (h / p->tile) + 1;
@@ -1076,8 +1125,9 @@ int orc_register_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u,
         wu[k] = chroma ? (double*)malloc(sizeof(double) * nc) : NULL;
         wv[k] = chroma ? (double*)malloc(sizeof(double) * nc) : NULL;
         qq[k] = (double*)malloc(sizeof(double) * np);
+        cl[k] = (uint8_t*)malloc((size_t)np);
         orc_warp(src_y[k], chroma ? src_u[k] : NULL, chroma ? src_v[k] : NULL, w, h, Huse, fu,
-                 fv, wy[k], wu[k], wv[k]);
+                 fv, wy[k], wu[k], wv[k], cl[k]);
         orc_ghost_mask(ref_n, wy[k], w, h, p->norm_mode, gain, lut_s, p->ssim_sigma,
                        p->ssim_radius, qq[k]);
         if (H0_out) memcpy(H0_out + 9 * k, H0, sizeof(H0));
@@ -1085,13 +1135,25 @@ int orc_register_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u,
         if (flow_u_out && flow_u_out[k]) memcpy(flow_u_out[k], fu, sizeof(double) * np);
         if (flow_v_out && flow_v_out[k]) memcpy(flow_v_out[k], fv, sizeof(double) * np);
         if (q_out && q_out[k]) memcpy(q_out[k], qq[k], sizeof(double) * np);
+        if (clip_out && clip_out[k]) memcpy(clip_out[k], cl[k], (size_t)np);
     }
     orc_merge(w, h, ref_y, chroma ? ref_u : NULL, chroma ? ref_v : NULL, nsrc,
               (const double* const*)wy, (const double* const*)wu, (const double* const*)wv,
-              (const double* const*)qq, ratio, p->we_sigma, out_y, chroma ? out_u : NULL,
+              (const double* const*)qq, (const uint8_t* const*)cl, ratio, p->we_sigma, out_y,
+              chroma ? out_u : NULL,
               chroma ? out_v : NULL);
-    for (int k = 0; k < nsrc; k++) { free(wy[k]); free(wu[k]); free(wv[k]); free(qq[k]); }
+    for (int k = 0; k < nsrc; k++) {
+        free(wy[k]); free(wu[k]); free(wv[k]); free(qq[k]); free(cl[k]);
+    }
     free(ref_n); free(src_n); free(cxy); free(mxy); free(cst); free(vld); free(msk);
     free(fu); free(fv);
     return 0;
 }
+
+/* Threads an OpenMP region of this build would use (1 in the serial build). */
+#ifdef _OPENMP
+#include <omp.h>
+int orc_max_threads(void) { return omp_get_max_threads(); }
+#else
+int orc_max_threads(void) { return 1; }
+#endif

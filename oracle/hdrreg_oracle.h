@@ -9,7 +9,8 @@
  *
  * Arithmetic: integer steps in int64 / __int128, everything else in IEEE
  * binary64 evaluated in the written order (compiled with -ffp-contract=off,
- * no fast-math). Single-threaded plain loops.
+ * no fast-math). Plain loops; the OpenMP build runs the independent ones on
+ * all cores with the same per-element arithmetic (bit-identical results).
  *
  * Conventions: images are row-major, tightly packed; pixel centres sit at
  * integer coordinates; "normalized" coordinates are those of Sec. 2.2 (Eq. 3):
@@ -118,9 +119,10 @@ void orc_flow(const uint8_t* guide, int w, int h, int n, const int32_t* corner_x
 
 /* ---- a9: warp ------------------------------------------------------------ */
 double orc_bilinear(const uint8_t* img, int w, int h, double x, double y);
+int  orc_bilinear_clipped(const uint8_t* img, int w, int h, double x, double y);
 void orc_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_v, int w, int h,
               const double H0[9], const double* flow_u, const double* flow_v,
-              double* out_y, double* out_u, double* out_v);
+              double* out_y, double* out_u, double* out_v, uint8_t* clip_y);
 
 /* ---- a10: SSIM ghost mask -------------------------------------------------- */
 void orc_ssim(const double* x, const double* y, int w, int h, double sigma, int radius,
@@ -130,11 +132,13 @@ void orc_ghost_mask(const uint8_t* ref_n, const double* warped_y, int w, int h, 
 
 /* ---- a11: weighted irradiance merge --------------------------------------- */
 double orc_well_exposedness(double z, double sigma);
-double orc_clip_taper(double z);
 void orc_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v,
                int nsrc, const double* const* wy, const double* const* wu,
-               const double* const* wv, const double* const* q, const double* ratio,
-               double we_sigma, double* out_y, double* out_u, double* out_v);
+               const double* const* wv, const double* const* q,
+               const uint8_t* const* clip, const double* ratio, double we_sigma,
+               double* out_y, double* out_u, double* out_v);
+
+int  orc_max_threads(void);
 
 /* ---- whole path for one stack (n-1 registrations, Sec. 2) ----------------- */
 int  orc_register_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u,
@@ -144,7 +148,7 @@ int  orc_register_merge(int w, int h, const uint8_t* ref_y, const uint8_t* ref_u
                         const orc_params* p, double* out_y, double* out_u, double* out_v,
                         double* H0_out, double* const* warped_y_out,
                         double* const* flow_u_out, double* const* flow_v_out,
-                        double* const* q_out);
+                        double* const* q_out, uint8_t* const* clip_out);
 
 #ifdef __cplusplus
 }

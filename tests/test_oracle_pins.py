@@ -575,6 +575,39 @@ def test_ghost_mask_ratio_gain_and_clamp(orc):
     assert q.min() >= 0.0
 
 
+def test_ghost_mask_histeq_identity_lut_equals_ratio_mode(orc):
+    # with the identity LUT the equalization branch maps a warped value z in [0, 255] to z,
+    # which the ratio branch with gain 1 does as well
+    rng = np.random.default_rng(21)
+    ref_n = rng.integers(0, 256, (26, 31)).astype(np.uint8)
+    wy = rng.uniform(0, 255, (26, 31))
+    wy[0, :5] = [0.0, 255.0, 254.75, 0.5, 127.0]
+    q1 = orc.ghost_mask(ref_n, wy, mode=1, src_lut=np.arange(256))
+    q0 = orc.ghost_mask(ref_n, wy, mode=0, gain=1.0)
+    assert np.array_equal(q1, q0)
+
+
+def test_ghost_mask_histeq_interpolates_the_lut(orc):
+    # lut[v] = min(2v, 255); warped values k + 0.25 must enter SSIM as the linear
+    # interpolation lut[k] + 0.25 (lut[k+1] - lut[k]), written out by hand:
+    # 2k + 0.5 below 127, 254.25 between 127 and 128 (254 -> 255), 255 from 128 on
+    rng = np.random.default_rng(22)
+    h, w = 24, 28
+    k = rng.integers(0, 255, (h, w))
+    k[0, :3] = [126, 127, 128]
+    wy = k + 0.25
+    lut = np.minimum(2 * np.arange(256), 255)
+    by_hand = np.where(k < 127, 2 * k + 0.5, np.where(k == 127, 254.25, 255.0))
+    ref_n = rng.integers(0, 256, (h, w)).astype(np.uint8)
+    q = orc.ghost_mask(ref_n, wy, mode=1, src_lut=lut)
+    want = np.maximum(orc.ssim(ref_n.astype(float), by_hand), 0.0)
+    assert np.abs(q - want).max() < 1e-12
+    # a nearest-level reading (lut at the rounded value) gives another mask
+    nearest = np.maximum(orc.ssim(ref_n.astype(float), lut[np.rint(wy).astype(int)].astype(float)),
+                         0.0)
+    assert np.abs(q - nearest).max() > 1e-3
+
+
 # --------------------------------------------------------------------- a11
 def test_well_exposedness_values(orc):
     assert orc.well_exposedness(127.5) == 1.0
@@ -656,21 +689,86 @@ def test_inlier_test_matches_reprojection_distance(orc):
     assert n_checked > 2900
 
 
-@pytest.mark.parametrize("z,taper", [(254.0, 0.5), (253.0, 1.0), (255.0, 0.0), (1.0, 0.5),
-                                     (0.0, 0.0), (128.0, 1.0), (254.5, 0.25)])
-def test_merge_source_weight_closed_form(orc, z, taper):
-    # one pixel, Q = 1: E = (w0 Z0 + w1 Z1/r) / (w0 + w1) -> w1 = w0 (Z0 - E) / (E - Z1/r)
+@pytest.mark.parametrize("z", [254.0, 253.0, 255.0, 1.0, 0.0, 128.0, 254.5, 0.25])
+def test_merge_source_weight_closed_form(orc, z):
+    # one pixel, Q = 1, no clip flags (a sample is clipped when its value is 0 or 255):
+    # E = (w0 Z0 + w1 Z1/r) / (w0 + w1) -> w1 = w0 (Z0 - E) / (E - Z1/r) must be WE(Z1)
+    # strictly inside (0, 255) and 0 at either end
     z0, r = 100, 2.0
     oy, _, _ = orc.merge(np.array([[z0]], np.uint8), None, None, [(np.array([[z]]), None, None)],
                          [np.ones((1, 1))], [r])
     e = oy[0, 0]
     w0 = orc.well_exposedness(float(z0))
-    want = orc.well_exposedness(z) * taper
+    want = orc.well_exposedness(z) if 0.0 < z < 255.0 else 0.0
     if want == 0.0:
         assert abs(e - z0) < 1e-12
     else:
         w1 = w0 * (z0 - e) / (e - z / r)
         assert abs(w1 - want) < 1e-9 * max(want, 1e-3)
+
+
+def test_bilinear_clipped_brute_force(orc):
+    # the taps that carry a nonzero bilinear weight, enumerated from the four weights
+    # (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy at positions on the grid, on half and
+    # quarter steps, off the image (clamped taps) and at random
+    rng = np.random.default_rng(19)
+    h, w = 9, 11
+    img = rng.integers(1, 255, (h, w)).astype(np.uint8)
+    img[rng.random((h, w)) < 0.2] = 255
+    img[rng.random((h, w)) < 0.1] = 0
+    pts = [(x, y) for x in np.arange(-1.0, w + 0.5, 0.25) for y in np.arange(-1.0, h + 0.5, 0.5)]
+    pts += [tuple(p) for p in rng.uniform(-1.0, w, (300, 2))]
+    n_true = 0
+    for x, y in pts:
+        x0, y0 = math.floor(x), math.floor(y)
+        fx, fy = x - x0, y - y0
+        wts = {(0, 0): (1 - fx) * (1 - fy), (1, 0): fx * (1 - fy), (0, 1): (1 - fx) * fy,
+               (1, 1): fx * fy}
+        want = any(wt > 0 and img[min(max(y0 + j, 0), h - 1), min(max(x0 + i, 0), w - 1)]
+                   in (0, 255) for (i, j), wt in wts.items())
+        assert orc.bilinear_clipped(img, x, y) == want, (x, y)
+        n_true += want
+    assert 0.2 * len(pts) < n_true < 0.9 * len(pts)
+
+
+def test_merge_half_pixel_shifted_clipped_ramp_gives_reference(orc):
+    # Noise-free pair on a linear scene: the reference sees Z_ref(x) = 2x, the source (twice
+    # the exposure) sees the scene half a pixel further on, src(q) = min(4q + 2, 255), and
+    # is warped back by that half pixel. Where both taps are unclipped the bilinear sample
+    # is exactly 4x = r Z_ref; from x = 64 on a tap is 255, so the sample is a clipped
+    # measurement and must carry no weight. So E = Z_ref at every pixel (x >= 1; x = 0
+    # samples the clamped edge). A value rule alone (clipped only at 255 exactly) would
+    # let the sample 254.5 at x = 64 through.
+    h, w = 6, 100
+    xs = np.tile(np.arange(w), (h, 1))
+    ref_y = (2 * xs).astype(np.uint8)
+    src_y = np.minimum(4 * xs + 2, 255).astype(np.uint8)
+    fu, fv = np.full((h, w), -0.5), np.zeros((h, w))
+    wy, _, _, clip = orc.warp(src_y, None, None, np.eye(3), fu, fv, want_clip=True)
+    assert wy[0, 64] == 254.5 and clip[0, 64] == 1 and clip[0, 63] == 0
+    q = np.ones((h, w))
+    oy, _, _ = orc.merge(ref_y, None, None, [(wy, None, None)], [q], [2.0], clips=[clip])
+    assert np.abs(oy[:, 1:] - ref_y[:, 1:]).max() <= 1e-12 * 255
+    by_value, _, _ = orc.merge(ref_y, None, None, [(wy, None, None)], [q], [2.0])
+    assert abs(by_value[0, 64] - 128.0) > 0.01
+
+
+def test_merge_dark_source_zeros_carry_no_weight(orc):
+    # A source a quarter of the reference's exposure, noise-free, identity geometry: where
+    # the reference is a multiple of 4 the source is exactly Z_ref / 4; where it is 1-3 the
+    # source rounds to 0, a clipped sample. E = Z_ref everywhere.
+    rng = np.random.default_rng(20)
+    h, w = 16, 20
+    ref_y = (4 * rng.integers(1, 63, (h, w))).astype(np.uint8)
+    small = rng.random((h, w)) < 0.3
+    ref_y[small] = rng.integers(1, 4, int(small.sum()))
+    src_y = np.where(small, 0, ref_y // 4).astype(np.uint8)
+    z = np.zeros((h, w))
+    wy, _, _, clip = orc.warp(src_y, None, None, np.eye(3), z, z, want_clip=True)
+    assert np.array_equal(clip.astype(bool), small)
+    oy, _, _ = orc.merge(ref_y, None, None, [(wy, None, None)], [np.ones((h, w))], [0.25],
+                         clips=[clip])
+    assert np.abs(oy - ref_y).max() <= 1e-12 * 255
 
 
 # --------------------------------------------------------------------- a-L (learned path)
