@@ -86,7 +86,8 @@ def prepare(stack, p: hdrreg.Params, device="cuda", keep_gt: bool = False) -> Pr
 
 
 def make_stacks(n: int, first_index: int, spec=TRAIN_SPEC):
-    return [synth.make_stack(spec, synth.stack_seed(4, first_index + i)) for i in range(n)]
+    return synth.make_spec_stacks_parallel(spec, [synth.stack_seed(4, first_index + i)
+                                                  for i in range(n)])
 
 
 def train(prepared: List[Prepared], steps: int, batch: int = 64, lr: float = 2e-3, seed: int = 0,
@@ -255,6 +256,11 @@ def main():
     ap.add_argument("--ops-out", default=OPS_FILE)
     ap.add_argument("--out", default=THETA_FILE)
     ap.add_argument("--train-stacks", type=int, default=16)
+    ap.add_argument("--stress-stacks", type=int, default=0,
+                    help="training stacks with +-8 px fields (STRESS_SPEC) besides the +-4 px ones")
+    ap.add_argument("--label-radius", type=int, default=6,
+                    help="search radius of the plain level-0 search that labels the training "
+                         "tiles (labels on its border are left out)")
     ap.add_argument("--eval-stacks", type=int, default=2)
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--batch", type=int, default=64)
@@ -281,11 +287,17 @@ def main():
         print(json.dumps({"chosen": best}))
         return
     p = hdrreg.params_from_dict(synth.method_params(32, 6))
+    p_label = hdrreg.params_from_dict(synth.method_params(32, args.label_radius))
     t0 = time.perf_counter()
-    train_set = [prepare(s, p) for s in make_stacks(args.train_stacks, 0)]
+    stacks = make_stacks(args.train_stacks, 0)
+    if args.stress_stacks:
+        stacks += make_stacks(args.stress_stacks, 4000, STRESS_SPEC)
+    train_set = [prepare(s, p_label) for s in stacks]
+    del stacks
     eval_set = [prepare(s, p, keep_gt=True) for s in make_stacks(args.eval_stacks, 1000)]
     t_data = time.perf_counter() - t0
-    theta, hist, t_train = train(train_set, args.steps, args.batch, args.lr, args.seed)
+    theta, hist, t_train = train(train_set, args.steps, args.batch, args.lr, args.seed,
+                                 label_bound=float(args.label_radius))
     m_train = evaluate(train_set[:2], theta, p)
     m_eval = {f"refine{r}_ratio{fr}": evaluate(eval_set, theta, p, fallback_ratio=fr, refine=r)
               for r in (0, 1) for fr in (1.0, 1.5)}
@@ -293,7 +305,8 @@ def main():
     m_eval["stress_refine1_ratio1.5"] = evaluate(stress, theta, p, fallback_ratio=1.5, refine=1)
     np.save(args.out, theta.cpu().numpy())
     rep = {"steps": args.steps, "batch": args.batch, "lr": args.lr, "seed": args.seed,
-           "train_stacks": args.train_stacks, "data_s": round(t_data, 1),
+           "train_stacks": args.train_stacks, "stress_stacks": args.stress_stacks,
+           "label_radius": args.label_radius, "data_s": round(t_data, 1),
            "train_s": round(t_train, 2), "ms_per_step": round(1e3 * t_train / args.steps, 3),
            "loss": hist[::10] + hist[-1:], "train_metrics": m_train, "eval_metrics": m_eval}
     print(json.dumps(rep))

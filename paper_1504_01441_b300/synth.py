@@ -457,6 +457,19 @@ def make_stacks_parallel(jobs, processes=None):
         return pool.starmap(make_mixed_stack, jobs)
 
 
+def make_spec_stacks_parallel(spec: StackSpec, seeds, processes=None):
+    """make_stack(spec, seed) for every seed in a spawn-started process pool; returns the
+    stacks in seed order."""
+    import multiprocessing as mp
+    import os
+    seeds = list(seeds)
+    n = processes or min(len(seeds), os.cpu_count() or 1)
+    if n <= 1:
+        return [make_stack(spec, sd) for sd in seeds]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.starmap(make_stack, [(spec, sd) for sd in seeds])
+
+
 WORKLOADS = {
     "vga_luma_pair": (VGA_LUMA, dict(tile=16, radius=4)),
     "5mp_yuv420_pair": (FIVE_MP, dict(tile=32, radius=6)),
