@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned level-0 search leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the mixed 64-stack batch leg of the default workload")
+    ap.add_argument("--staged", action="store_true",
+                    help="mixed batches: every stack's merge as one stage after all "
+                         "registrations (hdrreg_register_merge_staged) instead of on its lane")
     ap.add_argument("--profile", action="store_true", help="short run for a profiler")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, MIXED, SWEEP, SCALE12, LEARNED8],
                     help="the 5 MP pair batch (default), the mixed 1-12 MP batch, the size "
@@ -161,6 +166,22 @@ def flow_algorithmic_bytes(w, h, iters=3):
     return first + (2 * iters - 2) * middle + last
 
 
+PATH_BYTES_PER_PX = 165  # compulsory bytes per registered luma pixel of a1-a11 (the model)
+
+
+def path_roofline(reg_mpix_per_step, ms_step, what):
+    """The whole step against the per-pixel byte model of the path: 165 B per registered
+    luma pixel (normalization and pyramid ~4.7, matcher ~2.7, the six flow passes ~140,
+    warp and merge ~17), at the measured HBM bandwidth."""
+    peak, src = peaks()
+    model = reg_mpix_per_step * 1e6 * PATH_BYTES_PER_PX
+    ach = model / (ms_step / 1e3) / 1e9
+    return {"kernel": what, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+            "peak_source": src, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "model_bytes_per_registered_px": PATH_BYTES_PER_PX,
+            "algorithmic_bytes_per_step": int(model)}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -176,6 +197,12 @@ def run_ours(args):
     from paper_1504_01441_b300 import hdrreg, synth
 
     ws, rank, local = dist_env()
+    # the mixed batch's stacks are generated in a spawn pool before CUDA starts
+    mixed = None
+    if (rank == 0 and not args.no_batched and not args.profile and args.preset == "workload"
+            and args.output == "merge"):
+        t_gen = time.perf_counter()
+        mixed = (mixed_inputs(args.stacks), time.perf_counter() - t_gen)
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl")
@@ -248,6 +275,13 @@ def run_ours(args):
     e2e = None
     if rank == 0 and not args.no_e2e:
         e2e = measure_e2e(torch, hdrreg, p, stacks, dev, P, args)
+    # -- the mixed batch (64 stacks of 1-12 MP, 2-3 frames, tuned (T, R)) as one graph
+    batched = None
+    if mixed is not None:
+        del frames, runner
+        torch.cuda.empty_cache()
+        batched = measure_mixed(torch, hdrreg, mixed[0], dev, args, K)
+        batched["generation_s"] = round(mixed[1], 1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.profile:
         cpu = measure_cpu_baseline(synth, stacks[0], cfg=p.as_dict())
@@ -268,7 +302,11 @@ def run_ours(args):
                        "l2": f"inputs larger than L2: {P} resident pairs x 15.1 MB per step",
                        "parallelism": f"replicas x{ws}"},
             "gpu_launches": launches_per_step * K,
-            "roofline": roof, "search_alu": search_alu, "stages_us": stages, "learned": learned,
+            "roofline": roof,
+            "roofline_path": path_roofline(mpix_step, ms_step, "whole step: the batched fused "
+                                           "path over the step's pairs, per-pixel byte model"),
+            "search_alu": search_alu, "stages_us": stages, "learned": learned,
+            "batched": batched,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),
@@ -423,8 +461,8 @@ def measure_stages(torch, hdrreg, p, stack, dev, args, meta=None):
     return {k: round(v, 2) for k, v in out.items()}
 
 
-# DRAM bytes of one flow call (2592 x 1944, 3 iterations, 13 launches) from the ncu
-# capture summarised in profiles/flow_dram_5mp.md.
+# DRAM bytes of one flow call (2592 x 1944, 3 iterations, 13 launches): dram__bytes_read.sum
+# + dram__bytes_write.sum over the call's launches in one ncu capture (cold L2).
 FLOW_TRAFFIC = 554542336
 
 
@@ -432,19 +470,21 @@ def measure_search_alu(torch, hdrreg, stages, p, valid_tiles, dev):
     """The level-0 SSD search against the measured __dp4a rate. Algorithmic work per
     launch: the cross terms of SSD = sum a^2 + sum b^2 - 2 sum a b over (2R+1)^2 offsets
     and (2h+1)^2 patch pixels of every tile with a corner, four byte products per
-    __dp4a. The rate is the probe's (hdrreg_probe_dp4a: 8 CTAs of 256 threads per SM,
-    eight independent chains per thread), median of 5 event-timed runs."""
+    __dp4a. The rate is the probe's (the benchmark's own libhdrreg_probe.so: 8 CTAs of
+    256 threads per SM, eight independent chains per thread), median of 5 event-timed
+    runs."""
+    from paper_1504_01441_b300 import probe
     sink = torch.zeros(1, dtype=torch.int32, device=dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     blocks, iters = 8 * sms, 4096
     s = torch.cuda.Stream(device=dev)
     for _ in range(3):
-        hdrreg.probe_dp4a(blocks, iters, sink, stream=s)
+        probe.probe_dp4a(blocks, iters, sink, stream=s)
     times = []
     for _ in range(5):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)
-        n = hdrreg.probe_dp4a(blocks, iters, sink, stream=s)
+        n = probe.probe_dp4a(blocks, iters, sink, stream=s)
         b.record(s)
         b.synchronize()
         times.append(a.elapsed_time(b))
@@ -454,7 +494,7 @@ def measure_search_alu(torch, hdrreg, stages, p, valid_tiles, dev):
     achieved = algo / (stages["search_level0"] / 1e6) / 1e9
     return {"kernel": "k_local_search (level 0)", "bound": "alu", "unit": "G dp4a/s",
             "achieved": round(achieved, 1), "peak": round(peak, 1),
-            "frac": round(achieved / peak, 4), "peak_source": "measured (hdrreg_probe_dp4a)",
+            "frac": round(achieved / peak, 4), "peak_source": "measured (dp4a rate probe)",
             "algorithmic_dp4a_per_launch": int(algo), "tiles_with_corner": valid_tiles,
             "us_per_launch": stages["search_level0"]}
 
@@ -467,8 +507,8 @@ def measure_flow_roofline(stages, p):
     return {"kernel": "flow: 6 domain-transform passes (row pass + 3-phase column pass)",
             "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "peak_source": src,
             "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": FLOW_TRAFFIC,
-            "traffic_source": "profiles/flow_dram_5mp.md: dram__bytes_read.sum + "
-                              "dram__bytes_write.sum of the stage's 13 launches (ncu, cold L2)",
+            "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of the stage's "
+                              "13 launches in one ncu capture (cold L2)",
             "algorithmic_bytes_per_launch": algo, "us_per_launch": round(stages["flow"], 2),
             "timing": "CUDA graph replay of hdrreg_flow_upsample on one 5 MP pair"}
 
@@ -513,15 +553,33 @@ def measure_e2e(torch, hdrreg, p, stacks, dev, P, args):
 
 
 def measure_cpu_baseline(synth, stack, runs=3, cfg=None):
+    """The oracle's whole path on one pair on the host cores: the serial build (one
+    thread) and the OpenMP build (its independent loops over rows, columns, tiles and
+    weeding iterations on every core the process may use; same bits). `value` is the
+    OpenMP figure, `single_thread` the serial one."""
     import oracle
     oracle.build()
     cfg = cfg or synth.method_params(32, 6)
-    t0 = time.perf_counter()
-    for _ in range(runs):
-        oracle.register_merge(stack.ref, stack.srcs, stack.ratios, cfg)
-    sec = (time.perf_counter() - t0) / runs
-    return {"value": round(W * H / 1e6 / sec, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-            "sample": f"{runs} runs of the oracle's whole path (a1-a11) on one 2592x1944 YUV420 pair"}
+
+    def timed(parallel):
+        oracle.set_parallel(parallel)
+        try:
+            oracle.register_merge(stack.ref, stack.srcs, stack.ratios, cfg)  # warm the pages
+            t0 = time.perf_counter()
+            for _ in range(runs):
+                oracle.register_merge(stack.ref, stack.srcs, stack.ratios, cfg)
+            return (time.perf_counter() - t0) / runs, oracle.threads()
+        finally:
+            oracle.set_parallel(False)
+    sec1, _ = timed(False)
+    secn, nthreads = timed(True)
+    affinity = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None
+    sample = f"{runs} runs of the oracle's whole path (a1-a11) on one {W}x{H} YUV420 pair"
+    return {"value": round(W * H / 1e6 / secn, 3), "unit": "Mpix/s", "cores": nthreads,
+            "kind": "oracle", "build": "OpenMP (liboracle_omp.so)", "sample": sample,
+            "os_cpu_count": os.cpu_count(), "affinity_cpus": affinity,
+            "single_thread": {"value": round(W * H / 1e6 / sec1, 3), "unit": "Mpix/s",
+                              "cores": 1, "build": "serial (liboracle.so)"}}
 
 
 # ------------------------------------------------------------ mixed batch (a-B)
@@ -529,6 +587,60 @@ def mixed_inputs(n):
     """The mixed workload's stacks (generated in a spawn pool, before CUDA starts)."""
     from paper_1504_01441_b300 import synth
     return synth.make_stacks_parallel([(i, 3, False) for i in range(n)])
+
+
+def measure_mixed(torch, hdrreg, stacks, dev, args, K):
+    """The mixed batch (its stacks already generated) as one multi-shape batched call on
+    `lanes` lanes, captured once and replayed K times as a CUDA graph; each stack runs with
+    its size bucket's tuned (T, R, B)."""
+    from paper_1504_01441_b300 import autotune
+    if os.path.exists(autotune.TABLE_FILE):
+        table, picks_src = autotune.load_table(), "tune_table.json"
+    else:
+        table = {"buckets_mp": list(autotune.BUCKETS_MP), "picks": [autotune.DEFAULT] * 4}
+        picks_src = "default (no tuning table)"
+    params = [autotune.params_for(s.width, s.height, table) for s in stacks]
+
+    def up(a):
+        return torch.from_numpy(a).to(dev)
+    frames = [((up(s.ref.y), up(s.ref.u), up(s.ref.v)),
+               [(up(f.y), up(f.u), up(f.v)) for f in s.srcs], list(s.ratios)) for s in stacks]
+    shapes = [(s.width, s.height, len(s.srcs), p, True) for s, p in zip(stacks, params)]
+    runner = hdrreg.RegisterMergeMulti(shapes, lanes=args.lanes, device=dev, staged=args.staged)
+    stream = torch.cuda.Stream(device=dev)
+    runner(frames, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    n0 = hdrreg.launch_count()
+    with torch.cuda.graph(graph, stream=stream):
+        runner(frames, stream=stream)
+    launches = hdrreg.launch_count() - n0
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 0)):
+            graph.replay()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for _ in range(K):
+            graph.replay()
+        end.record(stream)
+        torch.cuda.synchronize()
+    ms_step = start.elapsed_time(end) / K
+    out_mpix = sum(s.width * s.height for s in stacks) / 1e6
+    reg_mpix = sum(s.width * s.height * len(s.srcs) for s in stacks) / 1e6
+    in_bytes = sum(s.width * s.height * 3 // 2 * (1 + len(s.srcs)) for s in stacks)
+    del graph, runner, frames
+    torch.cuda.empty_cache()
+    return {"workload": MIXED_NAME, "metric": MIXED_METRIC, "value": round(out_mpix / (ms_step / 1e3), 2),
+            "unit": "Mpix/s", "ms_per_step": round(ms_step, 3), "steps": K,
+            "stacks": len(stacks), "output_mpix_per_step": round(out_mpix, 3),
+            "registered_mpix_per_step": round(reg_mpix, 3), "input_bytes_per_step": in_bytes,
+            "picks_source": picks_src, "lanes": args.lanes, "graph": True,
+            "merge_schedule": "one stage after all registrations" if args.staged else "on each stack's lane",
+            "gpu_launches": launches * K,
+            "roofline_path": path_roofline(reg_mpix, ms_step, "whole step of the mixed batch, "
+                                           "per-pixel byte model")}
 
 
 def run_mixed(args):
@@ -558,7 +670,7 @@ def run_mixed(args):
     frames = [((up(s.ref.y), up(s.ref.u), up(s.ref.v)),
                [(up(f.y), up(f.u), up(f.v)) for f in s.srcs], list(s.ratios)) for s in stacks]
     shapes = [(s.width, s.height, len(s.srcs), p, True) for s, p in zip(stacks, params)]
-    runner = hdrreg.RegisterMergeMulti(shapes, lanes=args.lanes, device=dev)
+    runner = hdrreg.RegisterMergeMulti(shapes, lanes=args.lanes, device=dev, staged=args.staged)
     stream = torch.cuda.Stream(device=dev)
     runner(frames, stream=stream)
     torch.cuda.synchronize()
@@ -623,6 +735,8 @@ def run_mixed(args):
                        "picks_T_R_B_count": {str(table["buckets_mp"][b]): v
                                            for b, v in sorted(buckets.items())},
                        "picks_source": picks_src, "graph": True, "lanes": args.lanes,
+                       "merge_schedule": ("one stage after all registrations" if args.staged
+                                          else "on each stack's lane"),
                        "l2": f"inputs larger than L2: {in_bytes / 1e9:.2f} GB resident per step",
                        "generation_s": round(t_gen, 1), "parallelism": f"replicas x{ws}"},
             "gpu_launches": launches_per_step * K, "roofline": roof, "cpu_baseline": cpu,
@@ -1001,6 +1115,10 @@ def run_reference(args):
     learned8 = args.workload == LEARNED8
     stack = synth.make_learned8_stack(0) if learned8 else make_inputs(1)[0]
     cfg = synth.method_params(32, 6)
+    # the OpenMP build of the oracle on every host core the process may use (same bits
+    # as the serial build)
+    oracle.set_parallel(True)
+    cores = oracle.threads()
     for _ in range(max(args.warmup, 0)):
         oracle.register_merge(stack.ref, stack.srcs, stack.ratios, cfg)
     t0 = time.perf_counter()
@@ -1023,7 +1141,8 @@ def run_reference(args):
         "config": {"workload": LEARNED8_NAME if learned8 else WORKLOAD, "width": W, "height": H,
                    "format": "YUV420", "frames": 2, "exposure_ratio": 4, "tile": 32, "radius": 6,
                    "path": "plain (a1-a11)"},
-        "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": cores,
+                         "kind": "oracle", "build": "OpenMP (liboracle_omp.so)",
                          "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -1046,6 +1165,8 @@ def run_reference_mixed(args, ws):
         t, r, _ = autotune.pick_of(table, s.width, s.height)
         oracle.register_merge(s.ref, s.srcs, s.ratios, synth.method_params(t, r))
 
+    oracle.set_parallel(True)  # the OpenMP build on every host core (same bits as serial)
+    cores = oracle.threads()
     for i in range(max(args.warmup, 0)):
         run(stacks[i % 4])
     t0 = time.perf_counter()
@@ -1061,7 +1182,8 @@ def run_reference_mixed(args, ws):
         "ms_per_step": round(sec * 1e3 / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64/int64 (CPU oracle)",
         "data": "synthetic", "config": {"workload": MIXED_NAME, "stacks": args.stacks},
-        "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": cores,
+                         "kind": "oracle", "build": "OpenMP (liboracle_omp.so)",
                          "sample": "per step one of the 4 smallest stacks of the mixed batch"},
         "e2e": {"value": round(value, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},

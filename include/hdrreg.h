@@ -25,7 +25,8 @@
  *    cudaStream_t; NULL = legacy default stream), never synchronize the host,
  *    and can be captured into a CUDA graph. Scratch memory, where needed, is
  *    passed in as `workspace` of at least the size the matching *_workspace_size
- *    call returns (256-byte aligned).
+ *    call returns (256-byte aligned). hdrreg_weed_static, which takes no
+ *    workspace, is described on its own where it is declared.
  *  - Arguments are validated on the host before anything is launched; an
  *    invalid argument returns HDRREG_E_INVALID_ARG and launches nothing. A
  *    launch failure returns HDRREG_E_CUDA. hdrreg_last_error() returns a
@@ -131,6 +132,9 @@ typedef struct hdrreg_merge_src {
     const uint8_t* src_lut;  /* HISTEQ only: the source frame's 256-entry LUT (device)     */
     int ratio_num;           /* exposure ratio t_src / t_ref = num / den, both > 0          */
     int ratio_den;
+    const uint8_t* clip;     /* w x h, nonzero where the warped luma sample draws on a source
+                                pixel at 0 or 255 (hdrreg_warp's clip_out), or NULL: then a
+                                sample is clipped when its value is <= 0 or >= 255          */
 } hdrreg_merge_src;
 
 /* Per-source diagnostics written on the device by hdrreg_register_merge. */
@@ -157,14 +161,6 @@ const char* hdrreg_version(void);
  * incremented at every launch; a graph captured from library calls replays the
  * launches counted while it was captured). */
 unsigned long long hdrreg_launch_count(void);
-/* Measurement aid for the SSD search's ALU roofline (Sec. 2.2: 8-bit products summed
- * in 32-bit integers, issued as 4-way byte dot products): enqueues `blocks` CTAs of 256
- * threads, each thread running `iters` rounds of 8 dependent-chain __dp4a operations
- * (blocks * 256 * iters * 8 in total), on `stream`. The caller times it with events.
- * sink: device uint32, written only if a chain's result hits an unused value (keeps the
- * work live). blocks in [1, 2^20], iters in [1, 2^24]; E_INVALID_ARG otherwise, before
- * any launch. */
-hdrreg_status hdrreg_probe_dp4a(int blocks, int iters, uint32_t* sink, void* stream);
 /* Number of pyramid levels for a w x h frame under p (host computation, Sec. 2.6). */
 int hdrreg_num_levels(int w, int h, const hdrreg_params* p);
 /* Check p; returns HDRREG_OK or HDRREG_E_INVALID_ARG (message in hdrreg_last_error). */
@@ -230,11 +226,12 @@ hdrreg_status hdrreg_weed(const int32_t* corner_xy, const int32_t* match_xy, con
 
 /* ------------------------------------ a6 without caller-provided scratch
  * The paper has no counterpart: this is hdrreg_weed for callers that cannot
- * allocate device memory and therefore have no workspace to pass -- code that
- * runs while a stream is being captured in a mode that forbids cudaMalloc,
- * real-time pipelines that allow no allocation after start-up, or plugins
- * whose host owns all device memory. Same inputs, output and result as
- * hdrreg_weed; it allocates nothing and calls no allocating routine.
+ * allocate device memory and therefore have no workspace to pass -- real-time
+ * pipelines that allow no allocation after start-up, plugins whose host owns
+ * all device memory, or code that runs where the CUDA allocator may not be
+ * called. Same inputs, output and result as hdrreg_weed; it allocates nothing
+ * and calls no allocating routine. As there, mask_bits is OR-ed into: the
+ * caller zeroes it before the first iteration range.
  * Its scratch is a fixed array inside this library (about 160 KB on every GPU
  * that loads the library, kept until the process exits), so n must not exceed
  * HDRREG_WEED_STATIC_MAX_TILES (larger n returns HDRREG_E_INVALID_ARG and
@@ -302,18 +299,24 @@ hdrreg_status hdrreg_flow_upsample(const uint8_t* guide_n, int w, int h, const i
  * source at H(p) + flow(p), bilinear with clamp-to-edge taps. Chroma (when
  * src->u, src->v and out->u, out->v are all set; w, h even) samples at
  * (Mbar - 0.5) / 2 with Mbar the mean of the four luma positions of its 2x2
- * block. Outputs FP32 planes.
+ * block. Outputs FP32 planes. clip_out (optional, device, w x h bytes): 1 where
+ * the luma sample draws on a source pixel at 0 or 255 -- a tap with a nonzero
+ * bilinear weight: the one at (floor x, floor y) always, its right neighbour
+ * when the x fraction is above 0, the row below when the y fraction is above 0
+ * -- else 0. The merge gives such a sample no weight (Sec. 2.1: 8-bit frames,
+ * so a clipped pixel measured only a bound on its irradiance).
  */
 hdrreg_status hdrreg_warp(const hdrreg_frame* src, int w, int h, const double* H,
                           const float* flow_u, const float* flow_v, const hdrreg_planes_f32* out,
-                          void* stream);
+                          uint8_t* clip_out, void* stream);
 
 /* ------------------------------------------------ a10-a11: ghost mask + merge
  * Irradiance merge of the reference with nsrc warped sources (host array of
  * descriptors): E = sum_k w_k Z_k / r_k / sum_k w_k with r_ref = 1,
- * w_ref = WE(Z_ref), w_k = WE(Z_k) * max(0, SSIM(ref_n_k, N_k(Z_k))) * c(Z_k), where
- * c is 0 at 0 and 255 and rises linearly to 1 over the 2 DN next to either end
- * (clipped samples carry no irradiance). WE is the well-exposedness weight of exposure
+ * w_ref = WE(Z_ref), w_k = WE(Z_k) * max(0, SSIM(ref_n_k, N_k(Z_k))) for a
+ * sample that draws on no clipped pixel and w_k = 0 for one that does (the
+ * source's clip plane; clipped samples carry no irradiance). WE is the
+ * well-exposedness weight of exposure
  * fusion; SSIM uses a Gaussian window (ssim_sigma, radius 5) with clamp-to-edge;
  * N_k maps the warped source into the registration's normalized domain (RATIO:
  * min(255, g z) with g the gain its frame received; HISTEQ: its LUT,
@@ -540,6 +543,22 @@ size_t hdrreg_register_merge_multi_workspace_size(const hdrreg_stack_ex* stacks,
                                                   int lanes);
 hdrreg_status hdrreg_register_merge_multi(const hdrreg_stack_ex* stacks, int count, int lanes,
                                           void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------- extension: the same batch, merges as one stage
+ * The paper has no counterpart (it registers one stack at a time). As
+ * hdrreg_register_merge_multi, with the stacks' registrations (a1-a9) on the lanes and
+ * then, once every lane has joined `stream`, every stack's merge (a10-a11) in
+ * persistent launches that take tiles of any stack (up to 48 stacks per launch) instead
+ * of one merge per stack on its lane. Each stack's merge inputs (warped planes,
+ * normalized reference, LUTs) stay in the workspace until then. Results are identical to
+ * hdrreg_register_merge_multi. Stacks must ask for the irradiance merge (output_mode
+ * 0); HDRREG_E_UNSUPPORTED otherwise. Workspace:
+ * hdrreg_register_merge_staged_workspace_size(stacks, count, lanes).
+ */
+size_t hdrreg_register_merge_staged_workspace_size(const hdrreg_stack_ex* stacks, int count,
+                                                   int lanes);
+hdrreg_status hdrreg_register_merge_staged(const hdrreg_stack_ex* stacks, int count, int lanes,
+                                           void* workspace, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -115,7 +115,8 @@ struct FusedLayout {
     bool learned = false;  // level-0 search by the predictor (row a-L)
     int wq = 0, hq = 0, pho = 0, pwo = 0;
     size_t xq = 0, pred = 0, cnn = 0, fellback = 0;
-    size_t wy[kMaxSources], wu[kMaxSources], wv[kMaxSources], refn[kMaxSources];
+    size_t wy[kMaxSources], wu[kMaxSources], wv[kMaxSources], refn[kMaxSources],
+        clip[kMaxSources];
     size_t q = 0, fuse = 0;  // output_mode != 0
     size_t total;
     FusedLayout(int w, int h, int ns, const hdrreg_params* p)
@@ -164,6 +165,7 @@ struct FusedLayout {
             wu[k] = lay.add((size_t)(w / 2) * (h / 2) * 4);
             wv[k] = lay.add((size_t)(w / 2) * (h / 2) * 4);
             refn[k] = lay.add((size_t)w * h);
+            clip[k] = lay.add((size_t)w * h);
         }
         q = fuse = 0;
         if (p->output_mode != 0) {  // exposure fusion: the SSIM maps and the pyramids
@@ -517,7 +519,7 @@ hdrreg_status hdrreg_flow_upsample(const uint8_t* guide_n, int w, int h, const i
 // -------------------------------------------------------------------- a9
 hdrreg_status hdrreg_warp(const hdrreg_frame* src, int w, int h, const double* H,
                           const float* flow_u, const float* flow_v, const hdrreg_planes_f32* out,
-                          void* stream)
+                          uint8_t* clip_out, void* stream)
 {
     if (!src || !src->y || !H || !flow_u || !flow_v || !out || !out->y)
         return fail(HDRREG_E_INVALID_ARG, "warp: NULL pointer");
@@ -526,7 +528,7 @@ hdrreg_status hdrreg_warp(const hdrreg_frame* src, int w, int h, const double* H
     if (chroma && ((w & 1) || (h & 1)))
         return fail(HDRREG_E_INVALID_ARG, "warp: YUV420 needs even width and height");
     launch_warp(src->y, chroma ? src->u : nullptr, chroma ? src->v : nullptr, w, h, H, flow_u,
-                flow_v, w, out->y, chroma ? out->u : nullptr, chroma ? out->v : nullptr,
+                flow_v, w, out->y, chroma ? out->u : nullptr, chroma ? out->v : nullptr, clip_out,
                 static_cast<cudaStream_t>(stream));
     return launch_status("warp");
 }
@@ -549,6 +551,8 @@ static hdrreg_status merge_src_dev(const hdrreg_merge_src& m, int mode, bool chr
     d.inv_ratio = (float)((double)m.ratio_den / (double)m.ratio_num);
     d.gain = m.ratio_num < m.ratio_den ? (float)((double)m.ratio_den / (double)m.ratio_num) : 1.f;
     d.mode = mode;
+    d.clip = m.clip;
+    d.clip_sign = 0;
     return HDRREG_OK;
 }
 
@@ -614,13 +618,27 @@ static hdrreg_status rm_validate(const hdrreg_frame* ref, int w, int h, int nsrc
     return HDRREG_OK;
 }
 
+// Where the stage-major batch keeps one stack's merge inputs until its merge launch:
+// per source the normalized reference, the warped planes (clip flags in the luma's sign
+// bit) and the equalization LUTs; rm_enqueue fills md.
+struct StagedOut {
+    uint8_t* refn[kMaxSources];
+    float* wy[kMaxSources];
+    float* wu[kMaxSources];
+    float* wv[kMaxSources];
+    uint8_t* luts;  // 512 bytes per source
+    MergeSrcDev md[kMaxSources];
+};
+
 // Enqueue the whole path for one validated stack on stream s, using the workspace
-// laid out by `lay`.
+// laid out by `lay`. With `so` the merge inputs go to so's buffers and the merge is left
+// to the caller (so->md describes its sources).
 static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
                                 const hdrreg_frame* srcs, const int* ratio_num,
                                 const int* ratio_den, const hdrreg_params* p,
                                 const FusedLayout& lay, void* workspace,
-                                const hdrreg_planes_f32* out, hdrreg_diag* diag, cudaStream_t s)
+                                const hdrreg_planes_f32* out, hdrreg_diag* diag, cudaStream_t s,
+                                StagedOut* so = nullptr)
 {
     hdrreg_status st = HDRREG_OK;
     const bool chroma = ref->u && ref->v && out->u && out->v;
@@ -645,7 +663,8 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
     for (int k = 0; k < nsrc; k++) {
         // ---- a1 + a2: normalized level 0 (or an alias of the input) and the pyramids
         LutSpec lr{nullptr, 1, 1}, ls{nullptr, 1, 1};
-        uint8_t* luts_k = at(lay.luts) + 512 * k;
+        uint8_t* luts_k = so ? so->luts + 512 * k : at(lay.luts) + 512 * k;
+        uint8_t* refn_k = so ? so->refn[k] : at(lay.refn[k]);
         bool ref_identity = true, src_identity = true;
         float gain = 1.f;
         if (p->norm_mode == HDRREG_NORM_RATIO) {
@@ -665,7 +684,7 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
             ls = LutSpec{luts_k + 256, 1, 1};
             ref_identity = src_identity = false;
         }
-        const uint8_t* ref0 = ref_identity ? ref->y : at(lay.refn[k]);
+        const uint8_t* ref0 = ref_identity ? ref->y : refn_k;
         const uint8_t* src0 = src_identity ? srcs[k].y : at(lay.src_lv[0]);
         {
             uint8_t* rl[kMaxLevels] = {nullptr};
@@ -676,7 +695,7 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
             }
             const uint8_t* ins[2] = {ref->y, srcs[k].y};
             const LutSpec luts[2] = {lr, ls};
-            uint8_t* outs0[2] = {ref_identity ? nullptr : at(lay.refn[k]),
+            uint8_t* outs0[2] = {ref_identity ? nullptr : refn_k,
                                  src_identity ? nullptr : at(lay.src_lv[0])};
             uint8_t* const* lvs[2] = {rl, sl};
             launch_pyramid2(ins, w, h, L, luts, outs0, lvs, 2, s);
@@ -729,11 +748,16 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
         launch_flow(ref0, w, h, fc, p->sigma_s, p->sigma_r, p->dt_iters, p->flow_eps, fu, fv,
                     flow_pitch(w), at(lay.flow), s);
         // ---- a9: warp the source frame
-        float* wy = reinterpret_cast<float*>(at(lay.wy[k]));
-        float* wu = reinterpret_cast<float*>(at(lay.wu[k]));
-        float* wv = reinterpret_cast<float*>(at(lay.wv[k]));
+        float* wy = so ? so->wy[k] : reinterpret_cast<float*>(at(lay.wy[k]));
+        float* wu = so ? so->wu[k] : reinterpret_cast<float*>(at(lay.wu[k]));
+        float* wv = so ? so->wv[k] : reinterpret_cast<float*>(at(lay.wv[k]));
+        // the merge alone reads the warped luma: its clip flags ride in the sign bit; the
+        // exposure fusion reads the planes too, so there they get a plane of their own
+        const bool clip_sign = p->output_mode == 0;
+        uint8_t* clip = clip_sign ? nullptr : at(lay.clip[k]);
         launch_warp(srcs[k].y, chroma ? srcs[k].u : nullptr, chroma ? srcs[k].v : nullptr, w, h,
-                    Hw, fu, fv, flow_pitch(w), wy, chroma ? wu : nullptr, chroma ? wv : nullptr, s);
+                    Hw, fu, fv, flow_pitch(w), wy, chroma ? wu : nullptr, chroma ? wv : nullptr,
+                    clip, s, clip_sign);
         if (diag) {
             note_launch();
             k_diag<<<1, 256, 0, s>>>(Hs, valid, mask, lay.n0, fit_st, L,
@@ -748,8 +772,12 @@ static hdrreg_status rm_enqueue(const hdrreg_frame* ref, int w, int h, int nsrc,
         md[k].inv_ratio = (float)((double)ratio_den[k] / (double)ratio_num[k]);
         md[k].gain = gain;
         md[k].mode = p->norm_mode;
+        md[k].clip = clip;
+        md[k].clip_sign = clip_sign ? 1 : 0;
+        if (so) so->md[k] = md[k];
         if ((st = launch_status("register_merge(register)"))) return st;
     }
+    if (so) return HDRREG_OK;  // the caller merges
     // ---- a10 + a11 (with output_mode != 0 the merge also leaves the SSIM maps, which the
     //      exposure fusion of Sec. 2.5 then uses; its result replaces the merge's)
     float* qmaps = p->output_mode ? reinterpret_cast<float*>(at(lay.q)) : nullptr;
@@ -1319,6 +1347,145 @@ hdrreg_status hdrreg_register_merge_multi(const hdrreg_stack_ex* stacks, int cou
                       cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
     }
     return st;
+}
+
+}  // extern "C"
+
+namespace hdrreg {
+
+// Per-stack blocks of the stage-major batch: the merge inputs of every source.
+struct StagedPlan {
+    MultiPlan mp;
+    std::vector<size_t> off;  // per stack: start of its block (after the lane workspaces)
+    size_t total = 0;
+};
+
+static size_t staged_block(int w, int h, int nsrc)
+{
+    const size_t cpx = (size_t)(w / 2) * (h / 2);
+    return (size_t)nsrc * (align_up((size_t)w * h * 4, 256) + 2 * align_up(cpx * 4, 256) +
+                           align_up((size_t)w * h, 256)) + 512 * (size_t)nsrc;
+}
+
+static StagedPlan plan_staged(const hdrreg_stack_ex* st, int count, int lanes)
+{
+    StagedPlan sp;
+    sp.mp = plan_multi(st, count, lanes);
+    sp.total = sp.mp.total;
+    sp.off.assign(count, 0);
+    for (int i = 0; i < count; i++) {
+        sp.off[i] = sp.total;
+        sp.total += align_up(staged_block(st[i].w, st[i].h, st[i].nsrc), 256);
+    }
+    return sp;
+}
+
+static StagedOut staged_out(uint8_t* b, int w, int h, int nsrc)
+{
+    StagedOut so{};
+    const size_t cpx = (size_t)(w / 2) * (h / 2);
+    for (int k = 0; k < nsrc; k++) {
+        so.wy[k] = reinterpret_cast<float*>(b);
+        b += align_up((size_t)w * h * 4, 256);
+        so.wu[k] = reinterpret_cast<float*>(b);
+        b += align_up(cpx * 4, 256);
+        so.wv[k] = reinterpret_cast<float*>(b);
+        b += align_up(cpx * 4, 256);
+        so.refn[k] = b;
+        b += align_up((size_t)w * h, 256);
+    }
+    so.luts = b;
+    return so;
+}
+
+}  // namespace hdrreg
+
+extern "C" {
+
+size_t hdrreg_register_merge_staged_workspace_size(const hdrreg_stack_ex* stacks, int count,
+                                                   int lanes)
+{
+    if (!hdrreg_register_merge_multi_workspace_size(stacks, count, lanes)) return 0;
+    return plan_staged(stacks, count, lanes).total;
+}
+
+hdrreg_status hdrreg_register_merge_staged(const hdrreg_stack_ex* stacks, int count, int lanes,
+                                           void* workspace, size_t ws_bytes, void* stream)
+{
+    if (count < 0 || (count > 0 && !stacks))
+        return fail(HDRREG_E_INVALID_ARG, "register_merge_staged: bad stack array");
+    if (lanes < 1 || lanes > HDRREG_MAX_LANES)
+        return fail(HDRREG_E_INVALID_ARG, "register_merge_staged: lanes must be in [1, %d]",
+                    HDRREG_MAX_LANES);
+    for (int i = 0; i < count; i++) {
+        const hdrreg_stack_ex& k = stacks[i];
+        hdrreg_status st = rm_validate(k.s.ref, k.w, k.h, k.nsrc, k.s.srcs, k.s.ratio_num,
+                                       k.s.ratio_den, k.p, &k.s.out);
+        if (st) return fail(st, "register_merge_staged: stack %d: %s", i, hdrreg_last_error());
+        if (k.p->output_mode != 0)
+            return fail(HDRREG_E_UNSUPPORTED,
+                        "register_merge_staged: stack %d asks for the exposure fusion", i);
+    }
+    if (count == 0) return HDRREG_OK;
+    const StagedPlan sp = plan_staged(stacks, count, lanes);
+    if (!workspace || ws_bytes < sp.total)
+        return fail(HDRREG_E_WORKSPACE, "register_merge_staged: workspace of %zu bytes required",
+                    sp.total);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* base = static_cast<uint8_t*>(workspace);
+    std::vector<StagedOut> so(count);
+    for (int i = 0; i < count; i++)
+        so[i] = staged_out(base + sp.off[i], stacks[i].w, stacks[i].h, stacks[i].nsrc);
+    auto run = [&](int i, cudaStream_t q) {
+        const hdrreg_stack_ex& k = stacks[i];
+        const FusedLayout lay(k.w, k.h, k.nsrc, k.p);
+        return rm_enqueue(k.s.ref, k.w, k.h, k.nsrc, k.s.srcs, k.s.ratio_num, k.s.ratio_den, k.p,
+                          lay, base + sp.mp.lane_off[sp.mp.lane_of[i]], &k.s.out, k.s.diag, q,
+                          &so[i]);
+    };
+    hdrreg_status st = HDRREG_OK;
+    if (sp.mp.used == 1) {
+        for (int i = 0; i < count && !st; i++) st = run(i, s);
+    } else {
+        LaneSet* ls = nullptr;
+        if ((st = lane_set(&ls))) return st;
+        std::lock_guard<std::mutex> lock(lane_enqueue_mu);
+        cudaError_t e = cudaEventRecord(ls->fork, s);
+        for (int j = 0; j < sp.mp.used && e == cudaSuccess; j++)
+            e = cudaStreamWaitEvent(ls->stream[j], ls->fork, 0);
+        if (e != cudaSuccess)
+            return fail(HDRREG_E_CUDA, "register_merge_staged: fork: %s", cudaGetErrorString(e));
+        for (int i = 0; i < count && !st; i++) st = run(i, ls->stream[sp.mp.lane_of[i]]);
+        for (int j = 0; j < sp.mp.used; j++) {
+            cudaError_t e1 = cudaEventRecord(ls->join[j], ls->stream[j]);
+            cudaError_t e2 = cudaStreamWaitEvent(s, ls->join[j], 0);
+            if (!st && (e1 != cudaSuccess || e2 != cudaSuccess))
+                st = fail(HDRREG_E_CUDA, "register_merge_staged: join: %s",
+                          cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+        }
+    }
+    if (st) return st;
+    // every stack's merge in persistent launches over all their tiles
+    std::vector<MergeJob> jobs(count);
+    for (int i = 0; i < count; i++) {
+        const hdrreg_stack_ex& k = stacks[i];
+        const bool chroma = k.s.ref->u && k.s.ref->v && k.s.out.u && k.s.out.v;
+        MergeJob& J = jobs[i];
+        J.ref_y = k.s.ref->y;
+        J.ref_u = chroma ? k.s.ref->u : nullptr;
+        J.ref_v = chroma ? k.s.ref->v : nullptr;
+        J.w = k.w;
+        J.h = k.h;
+        J.nsrc = k.nsrc;
+        for (int q = 0; q < k.nsrc; q++) J.srcs[q] = so[i].md[q];
+        J.ssim_sigma = k.p->ssim_sigma;
+        J.we_sigma = k.p->we_sigma;
+        J.oy = k.s.out.y;
+        J.ou = chroma ? k.s.out.u : nullptr;
+        J.ov = chroma ? k.s.out.v : nullptr;
+    }
+    launch_merge_many(jobs.data(), count, s);
+    return launch_status("register_merge_staged(merge)");
 }
 
 }  // extern "C"

@@ -471,7 +471,7 @@ int flow_supported(int w, int h);
 
 void launch_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_v, int w, int h,
                  const double* H, const float* fu, const float* fv, int fpitch, float* oy,
-                 float* ou, float* ov, cudaStream_t s);
+                 float* ou, float* ov, uint8_t* clip, cudaStream_t s, bool clip_sign = false);
 
 struct MergeSrcDev {
     const float* y;
@@ -482,6 +482,8 @@ struct MergeSrcDev {
     float inv_ratio;     // 1 / r_k
     float gain;          // RATIO: gain of the source frame
     int mode;
+    const uint8_t* clip;  // w x h flags of samples that draw on a pixel at 0 or 255, or nullptr
+    int clip_sign;        // 1: y carries the flag in its sign bit (the fused path's own planes)
 };
 constexpr int kMaxSources = 4;
 
@@ -499,6 +501,20 @@ void launch_fuse(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_
 void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v, int w, int h,
                   int nsrc, const MergeSrcDev* srcs, double ssim_sigma, double we_sigma,
                   float* oy, float* ou, float* ov, float* q_out, cudaStream_t s);
+// One stack's merge for launch_merge_many (the stage-major batch schedule).
+struct MergeJob {
+    const uint8_t* ref_y;
+    const uint8_t* ref_u;
+    const uint8_t* ref_v;
+    int w, h, nsrc;
+    MergeSrcDev srcs[kMaxSources];
+    double ssim_sigma, we_sigma;
+    float* oy;
+    float* ou;
+    float* ov;
+};
+constexpr int kMergeBatchStacks = 48;  // stacks per persistent merge launch (parameter space)
+void launch_merge_many(const MergeJob* jobs, int count, cudaStream_t s);
 
 // ------------------------------------------ tensor-core GEMM (row a-L)
 // C[M x N] = A[M x K] * B[N x K]^T, bf16 K-major operands (16-byte aligned, ld % 8 == 0),

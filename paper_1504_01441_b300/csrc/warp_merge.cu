@@ -75,6 +75,32 @@ __device__ __forceinline__ float bilerp(const uint8_t* __restrict__ img, int w, 
     return fmaf(fy, bot - top, top);
 }
 
+// The same sample, plus whether it draws on a clipped pixel: a tap at 0 or 255 with a
+// nonzero weight -- (ix, iy) always, (ix + 1, iy) when fx > 0, (ix, iy + 1) when
+// fy > 0, (ix + 1, iy + 1) when both are.
+__device__ __forceinline__ float bilerp_clip(const uint8_t* __restrict__ img, int w, int h, int x,
+                                             int y, float tx, float ty, bool& clipped)
+{
+    const float fx0 = floorf(tx), fy0 = floorf(ty);
+    const float fx = tx - fx0, fy = ty - fy0;
+    const int ix = x + (int)fx0, iy = y + (int)fy0;
+    const int xa = clampi(ix, 0, w - 1), xb = clampi(ix + 1, 0, w - 1);
+    const size_t ra = (size_t)clampi(iy, 0, h - 1) * w, rb = (size_t)clampi(iy + 1, 0, h - 1) * w;
+    const unsigned ua = __ldg(img + ra + xa), ub = __ldg(img + ra + xb);
+    const unsigned uc = __ldg(img + rb + xa), ud = __ldg(img + rb + xb);
+    const bool right = fx > 0.f, below = fy > 0.f;
+    auto sat = [](unsigned v) { return v == 0u || v == 255u; };
+    clipped = sat(ua) || (right && sat(ub)) || (below && (sat(uc) || (right && sat(ud))));
+    const float a = (float)ua, b = (float)ub, c = (float)uc, d = (float)ud;
+    const float top = fmaf(fx, b - a, a);
+    const float bot = fmaf(fx, d - c, c);
+    return fmaf(fy, bot - top, top);
+}
+
+// kVec: the flow pitch and the width are even and the planes 8-byte aligned, so each
+// row pair of a 2x2 block moves as one float2 (flows in, warped luma out) and its two
+// clip flags as one 16-bit word.
+template <bool kVec>
 __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
                                               const uint8_t* __restrict__ su,
                                               const uint8_t* __restrict__ sv, int w, int h,
@@ -82,7 +108,8 @@ __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
                                               const float* __restrict__ fu,
                                               const float* __restrict__ fv, int fpitch,
                                               float* __restrict__ oy, float* __restrict__ ou,
-                                              float* __restrict__ ov)
+                                              float* __restrict__ ov,
+                                              uint8_t* __restrict__ clip, int clip_sign)
 {
     // The coefficients take a chain of binary64 operations (one thread, the others
     // waiting), so the grid is sized to the resident CTAs and each CTA strides over
@@ -95,21 +122,54 @@ __global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
     const int nb = bw * bh;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nb; idx += gridDim.x * blockDim.x) {
     const int bx = idx % bw, by = idx / bw;
+    const int x = 2 * bx;
+    const bool two = x + 1 < w;  // the block's right column exists
     float stx = 0.f, sty = 0.f;
 #pragma unroll
-    for (int j = 0; j < 2; j++)
+    for (int j = 0; j < 2; j++) {
+        const int y = 2 * by + j;
+        if (y >= h) continue;
+        const size_t o = (size_t)y * w + x, of = (size_t)y * fpitch + x;
+        float f[2][2];  // [u, v][column]
+        if (kVec) {
+            const float2 a = __ldg(reinterpret_cast<const float2*>(fu + of));
+            const float2 b = __ldg(reinterpret_cast<const float2*>(fv + of));
+            f[0][0] = a.x; f[0][1] = a.y; f[1][0] = b.x; f[1][1] = b.y;
+        } else {
+            f[0][0] = fu[of];
+            f[1][0] = fv[of];
+            f[0][1] = two ? fu[of + 1] : 0.f;
+            f[1][1] = two ? fv[of + 1] : 0.f;
+        }
+        float z[2];
+        bool cl[2] = {false, false};
 #pragma unroll
         for (int i = 0; i < 2; i++) {
-            const int x = 2 * bx + i, y = 2 * by + j;
-            if (x >= w || y >= h) continue;
-            const size_t o = (size_t)y * w + x, of = (size_t)y * fpitch + x;
+            z[i] = 0.f;
+            if (i == 1 && !two) continue;
             float dx, dy;
-            h_disp(c, x, y, w, h, dx, dy);
-            const float tx = dx + fu[of], ty = dy + fv[of];
+            h_disp(c, x + i, y, w, h, dx, dy);
+            const float tx = dx + f[0][i], ty = dy + f[1][i];
             stx += tx;
             sty += ty;
-            oy[o] = bilerp(sy, w, h, x, y, tx, ty);
+            z[i] = bilerp_clip(sy, w, h, x + i, y, tx, ty, cl[i]);
+            // clip_sign: the flag travels in the sign bit of the (non-negative) sample
+            if (clip_sign && cl[i]) z[i] = __int_as_float(__float_as_int(z[i]) | (int)0x80000000);
         }
+        if (kVec) {
+            *reinterpret_cast<float2*>(oy + o) = make_float2(z[0], z[1]);
+            if (clip)
+                *reinterpret_cast<uint16_t*>(clip + o) =
+                    (uint16_t)((cl[0] ? 1u : 0u) | (cl[1] ? 256u : 0u));
+        } else {
+            oy[o] = z[0];
+            if (clip) clip[o] = cl[0] ? 1 : 0;
+            if (two) {
+                oy[o + 1] = z[1];
+                if (clip) clip[o + 1] = cl[1] ? 1 : 0;
+            }
+        }
+    }
     if (su && ou) {
         const int cw = w / 2, ch = h / 2;
         if (bx < cw && by < ch) {
@@ -163,14 +223,6 @@ __device__ __forceinline__ float well_exposed(float z, float k)
 {
     const float t = z * (1.f / 255.f) - 0.5f;
     return expf(-(t * t) * k);
-}
-
-// 0 at 0 and 255, linear to 1 over the 2 DN next to either end: clipped samples
-// carry no irradiance and the weight stays continuous in the sample value.
-__device__ __forceinline__ float clip_taper(float z)
-{
-    const float d = fminf(z, 255.f - z) * 0.5f;
-    return fminf(fmaxf(d, 0.f), 1.f);
 }
 
 __device__ __forceinline__ float norm_map(const MergeSrcDev& s, float z)
@@ -291,46 +343,101 @@ __device__ __forceinline__ void merge_stage(MergeStage& S, const MergeArgs& args
     }
 }
 
-// Persistent CTAs over (tile, source) units in tile order; the next unit's inputs are
-// staged (async copies) while the current one computes.
-__global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ ref_y,
-                                                  const uint8_t* __restrict__ ref_u,
-                                                  const uint8_t* __restrict__ ref_v, int w, int h,
-                                                  MergeArgs args, float* __restrict__ oy,
-                                                  float* __restrict__ ou, float* __restrict__ ov,
-                                                  float* __restrict__ q_out, int async_ok)
+// One stack's merge as the kernel sees it: its planes, sizes, sources and weights.
+struct MergeStackDev {
+    const uint8_t* ref_y;
+    const uint8_t* ref_u;  // nullptr: luma only
+    const uint8_t* ref_v;
+    float* oy;
+    float* ou;
+    float* ov;
+    float* q_out;          // optional SSIM maps (nsrc planes of w x h)
+    int w, h, tiles_x;
+    int item_begin;        // first item (32 x 32 tile) of this stack in the launch's item list
+    int async_ok;          // every plane allows 16-byte asynchronous row copies
+    MergeArgs a;
+};
+
+// The stacks of one launch; their tiles are numbered consecutively, stack after stack.
+template <int NS>
+struct MergeBatch {
+    int nstacks, nitems;
+    MergeStackDev st[NS];
+};
+
+template <int NS>
+__device__ __forceinline__ int stack_of(const MergeBatch<NS>& B, int item)
+{
+    int s = 0;
+    while (s + 1 < B.nstacks && B.st[s + 1].item_begin <= item) s++;
+    return s;
+}
+
+// Persistent CTAs over (tile, source) units: items (tiles of any stack of the launch)
+// i = blockIdx.x + j * gridDim.x, and within an item every source of its stack in order;
+// the next unit's inputs are staged (async copies) while the current one computes.
+template <int NS>
+__global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeBatch<NS> B)
 {
     extern __shared__ __align__(16) uint8_t merge_smem[];
     MergeSmem& M = *reinterpret_cast<MergeSmem*>(merge_smem);
     const int tid = threadIdx.x;
-    const bool chroma = ref_u != nullptr && ou != nullptr;
-    const int cw = w / 2, ch = h / 2;
-    const int tiles_x = (w + kTile - 1) / kTile, tiles_y = (h + kTile - 1) / kTile;
-    const int ntiles = tiles_x * tiles_y, ns = args.nsrc;
     const float2 neg1 = f2(-1.f, -1.f);
-    const float2 gsum2 = f2(args.gsum, args.gsum);
     const float C1 = (0.01f * 255.f) * (0.01f * 255.f), C2 = (0.03f * 255.f) * (0.03f * 255.f);
     // this thread's 4 luma pixels: (tx, ty + 8 k); its chroma pixel: (tid % 16, tid / 16)
     const int tx = tid % kTile, ty0 = tid / kTile;
     const int ccx = tid % 16, ccy = tid / 16;
 
-    const int my_units = blockIdx.x < ntiles ? ((ntiles - 1 - blockIdx.x) / gridDim.x + 1) * ns : 0;
-    if (my_units == 0) return;
-    merge_stage(M.st[0], args, ref_y, ref_u, ref_v, w, h, chroma, tiles_x, blockIdx.x, 0, async_ok);
+    int item = blockIdx.x;
+    if (item >= B.nitems) return;
+    int si = stack_of(B, item), k = 0, buf = 0;
+    {
+        const MergeStackDev& D = B.st[si];
+        merge_stage(M.st[0], D.a, D.ref_y, D.ref_u, D.ref_v, D.w, D.h,
+                    D.ref_u != nullptr && D.ou != nullptr, D.tiles_x, item - D.item_begin, 0,
+                    D.async_ok);
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
     float cnu = 0.f, cnv = 0.f, cden = 0.f;
-    for (int u = 0; u < my_units; u++) {
-        const int t = blockIdx.x + (u / ns) * gridDim.x, k = u % ns;
-        const int x0 = (t % tiles_x) * kTile, y0 = (t / tiles_x) * kTile;
-        if (u + 1 < my_units) {
-            const int t1 = blockIdx.x + ((u + 1) / ns) * gridDim.x, k1 = (u + 1) % ns;
-            merge_stage(M.st[(u + 1) & 1], args, ref_y, ref_u, ref_v, w, h, chroma, tiles_x, t1, k1,
-                        async_ok);
+    for (;;) {
+        // the unit after this one: the next source of the item, or the CTA's next item
+        int nitem = item, nsi = si, nk = k + 1;
+        if (nk >= B.st[si].a.nsrc) {
+            nitem = item + gridDim.x;
+            nk = 0;
+            nsi = nitem < B.nitems ? stack_of(B, nitem) : si;
+        }
+        const bool more = nitem < B.nitems;
+        if (more) {
+            const MergeStackDev& Dn = B.st[nsi];
+            merge_stage(M.st[buf ^ 1], Dn.a, Dn.ref_y, Dn.ref_u, Dn.ref_v, Dn.w, Dn.h,
+                        Dn.ref_u != nullptr && Dn.ou != nullptr, Dn.tiles_x, nitem - Dn.item_begin,
+                        nk, Dn.async_ok);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();
-        const MergeStage& S = M.st[u & 1];
+        const MergeStackDev& D = B.st[si];
+        const MergeArgs& args = D.a;
+        const uint8_t* __restrict__ ref_y = D.ref_y;
+        float* __restrict__ oy = D.oy;
+        float* __restrict__ ou = D.ou;
+        float* __restrict__ ov = D.ov;
+        float* __restrict__ q_out = D.q_out;
+        const int w = D.w, h = D.h, ns = args.nsrc;
+        const bool chroma = D.ref_u != nullptr && ou != nullptr;
+        const int cw = w / 2, ch = h / 2;
+        const int t = item - D.item_begin;
+        const int x0 = (t % D.tiles_x) * kTile, y0 = (t / D.tiles_x) * kTile;
+        const float2 gsum2 = f2(args.gsum, args.gsum);
+        // total weight of a window as the column pass accumulates it (row weight gsum, taps
+        // in order)
+        float s0 = 0.f;
+#pragma unroll
+        for (int d = 0; d <= 2 * kSsimRadius; d++) s0 = fmaf(args.g[d], args.gsum, s0);
+        const float2 s02 = f2(s0, s0);
+        (void)ref_y;
+        const MergeStage& S = M.st[buf];
         const MergeSrcDev& s = args.src[k];
         const int cx = x0 / 2 + ccx, cy = y0 / 2 + ccy;
         const bool c_ok = chroma && cx < cw && cy < ch;
@@ -352,7 +459,8 @@ __global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ re
         }
         for (int i = tid; i < kIn * kIn; i += 256) {
             const int yy = i / kIn, xx = i - yy * kIn;
-            M.XY[yy][xx] = f2((float)S.Rn[yy][xx + 11], norm_map(s, S.Ys[yy][xx + 3]));
+            const float zy = S.Ys[yy][xx + 3];
+            M.XY[yy][xx] = f2((float)S.Rn[yy][xx + 11], norm_map(s, s.clip_sign ? fabsf(zy) : zy));
         }
         __syncthreads();
         if (k == 0) {
@@ -387,19 +495,21 @@ __global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ re
             M.H11[yy][xx] = m11;
         }
         __syncthreads();
-        // Column pass: re-centre every row's moments from its centre c_r onto the output
-        // pixel's value c (delta = c_r - c): sum g (a + delta)^k expands exactly, so the
-        // window moments stay small numbers wherever the window is flat. A thread takes
-        // four consecutive output rows 4 ty0 .. 4 ty0 + 3 of column tx: each of the 14
-        // staged rows they span is read once and added, in tap order, to every output
-        // whose window holds it.
+        // Column pass: a thread takes four consecutive output rows 4 ty0 .. 4 ty0 + 3 of
+        // column tx. Each of the 14 staged rows they span is read once, its moments are
+        // re-centred from its centre c_r onto the value c_t of the thread's first output
+        // pixel (delta = c_r - c_t: sum g (a + delta)^k expands exactly), and added, in tap
+        // order, to every output whose window holds it. The four sums are then re-centred
+        // once more, from c_t onto each output's own value, with the same expansion and
+        // the window's total weight S0. Every centre is a pixel inside the output's window
+        // (c_t at most three rows away), so flat windows only ever sum small numbers.
         constexpr int kQ = 4, kSpan = kQ + 2 * kHalo;
         const int lyb = kQ * ty0;
-        float2 cq[kQ], a1[kQ], a2[kQ];
+        const float2 ct = M.XY[lyb + kHalo][tx + kHalo];
+        float2 a1[kQ], a2[kQ];
         float a11[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; q++) {
-            cq[q] = M.XY[lyb + q + kHalo][tx + kHalo];
             a1[q] = f2(0.f, 0.f);
             a2[q] = f2(0.f, 0.f);
             a11[q] = 0.f;
@@ -410,15 +520,15 @@ __global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ re
             const float2 m1 = M.H1[lyb + rr][tx];
             const float2 m2 = M.H2[lyb + rr][tx];
             const float m11 = M.H11[lyb + rr][tx];
+            const float2 dd = __ffma2_rn(ct, neg1, xy);
+            const float2 r1 = __ffma2_rn(dd, gsum2, m1);
+            const float2 r2 = __ffma2_rn(dd, __fadd2_rn(m1, r1), m2);
+            const float r11 = m11 + fmaf(dd.y, m1.x, dd.x * r1.y);
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
                 const int d = rr - q;
                 if (d < 0 || d > 2 * kHalo) continue;
                 const float2 g2 = f2(args.g[d], args.g[d]);
-                const float2 dd = __ffma2_rn(cq[q], neg1, xy);
-                const float2 r1 = __ffma2_rn(dd, gsum2, m1);
-                const float2 r2 = __ffma2_rn(dd, __fadd2_rn(m1, r1), m2);
-                const float r11 = m11 + fmaf(dd.y, m1.x, dd.x * r1.y);
                 a1[q] = __ffma2_rn(g2, r1, a1[q]);
                 a2[q] = __ffma2_rn(g2, r2, a2[q]);
                 a11[q] = fmaf(args.g[d], r11, a11[q]);
@@ -428,17 +538,28 @@ __global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ re
         for (int q = 0; q < kQ; q++) {
             const int ly = lyb + q;
             const int x = x0 + tx, y = y0 + ly;
-            const float2 c = cq[q];
-            const float vx = a2[q].x - a1[q].x * a1[q].x, vy = a2[q].y - a1[q].y * a1[q].y,
-                        cxy = a11[q] - a1[q].x * a1[q].y;
+            const float2 c = M.XY[ly + kHalo][tx + kHalo];
+            // from c_t onto c: delta = c_t - c
+            const float2 dq = __ffma2_rn(c, neg1, ct);
+            const float2 b1 = __ffma2_rn(dq, s02, a1[q]);
+            const float2 b2 = __ffma2_rn(dq, __fadd2_rn(a1[q], b1), a2[q]);
+            const float b11 = a11[q] + fmaf(dq.y, a1[q].x, dq.x * b1.y);
+            a1[q] = b1;
+            const float vx = b2.x - b1.x * b1.x, vy = b2.y - b1.y * b1.y,
+                        cxy = b11 - b1.x * b1.y;
             const float ux = c.x + a1[q].x, uy = c.y + a1[q].y;
             const float ssim = ((2.f * ux * uy + C1) * (2.f * cxy + C2)) /
                                ((ux * ux + uy * uy + C1) * (vx + vy + C2));
             const float qv = ssim > 0.f ? ssim : 0.f;
             float wk = 0.f;
             if (x < w && y < h) {
-                const float z = S.Ys[ly + kHalo][tx + 8];
-                wk = well_exposed(z, args.we_k) * qv * clip_taper(z);
+                const float zs = S.Ys[ly + kHalo][tx + 8];
+                const float z = s.clip_sign ? fabsf(zs) : zs;
+                // a sample that draws on a pixel at 0 or 255 carries no irradiance
+                const bool clipped = s.clip_sign ? signbit(zs)
+                                     : (s.clip ? __ldg(s.clip + (size_t)y * w + x) != 0
+                                               : (z <= 0.f || z >= 255.f));
+                wk = clipped ? 0.f : well_exposed(z, args.we_k) * qv;
                 M.Ns[ly][tx] = fmaf(wk, z * s.inv_ratio, M.Ns[ly][tx]);
                 M.Ds[ly][tx] += wk;
                 if (q_out) q_out[(size_t)k * w * h + (size_t)y * w + x] = qv;
@@ -467,6 +588,11 @@ __global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ re
             }
         }
         __syncthreads();  // the staging buffer and the sums are reused by the next unit
+        if (!more) break;
+        item = nitem;
+        si = nsi;
+        k = nk;
+        buf ^= 1;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -475,7 +601,7 @@ __global__ void __launch_bounds__(256, 2) k_merge(const uint8_t* __restrict__ re
 
 void launch_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_v, int w, int h,
                  const double* H, const float* fu, const float* fv, int fpitch, float* oy,
-                 float* ou, float* ov, cudaStream_t s)
+                 float* ou, float* ov, uint8_t* clip, cudaStream_t s, bool clip_sign)
 {
     const long long nb = (long long)((w + 1) / 2) * ((h + 1) / 2);
     int dev = 0, sms = 148;
@@ -484,7 +610,15 @@ void launch_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_
     const long long need = (nb + 255) / 256, cap = 8LL * sms;  // 8 resident CTAs per SM
     const int grid = (int)(need < cap ? need : cap);
     note_launch();
-    k_warp<<<grid, 256, 0, s>>>(src_y, src_u, src_v, w, h, H, fu, fv, fpitch, oy, ou, ov);
+    auto al8 = [](const void* p) { return p == nullptr || ((uintptr_t)p & 7u) == 0; };
+    const bool vec = (w % 2) == 0 && (fpitch % 2) == 0 && al8(fu) && al8(fv) && al8(oy) &&
+                     (clip == nullptr || ((uintptr_t)clip & 1u) == 0);
+    if (vec)
+        k_warp<true><<<grid, 256, 0, s>>>(src_y, src_u, src_v, w, h, H, fu, fv, fpitch, oy, ou, ov,
+                                          clip, clip_sign ? 1 : 0);
+    else
+        k_warp<false><<<grid, 256, 0, s>>>(src_y, src_u, src_v, w, h, H, fu, fv, fpitch, oy, ou,
+                                           ov, clip, clip_sign ? 1 : 0);
 }
 
 void launch_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, int h,
@@ -501,11 +635,14 @@ void launch_predictor_input(const uint8_t* ref_q, const uint8_t* src_q, int w, i
                                              static_cast<__nv_bfloat162*>(out));
 }
 
-void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v, int w, int h,
-                  int nsrc, const MergeSrcDev* srcs, double ssim_sigma, double we_sigma,
-                  float* oy, float* ou, float* ov, float* q_out, cudaStream_t s)
+// The weights and flags of one stack's merge.
+static MergeStackDev merge_stack(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v,
+                                 int w, int h, int nsrc, const MergeSrcDev* srcs,
+                                 double ssim_sigma, double we_sigma, float* oy, float* ou,
+                                 float* ov, float* q_out)
 {
-    MergeArgs a;
+    MergeStackDev D;
+    MergeArgs& a = D.a;
     a.nsrc = nsrc;
     for (int k = 0; k < nsrc; k++) a.src[k] = srcs[k];
     double gs[2 * kSsimRadius + 1], tot = 0.0;
@@ -525,15 +662,63 @@ void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref
     async_ok = async_ok && al(ref_y) && al(ref_u) && al(ref_v);
     for (int k = 0; k < nsrc; k++)
         async_ok = async_ok && al(srcs[k].y) && al(srcs[k].u) && al(srcs[k].v) && al(srcs[k].ref_n);
-    const int ntiles = ((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile);
-    const size_t smem = sizeof(MergeSmem);
-    ensure_smem((const void*)k_merge, smem);
+    D.ref_y = ref_y;
+    D.ref_u = ref_u;
+    D.ref_v = ref_v;
+    D.oy = oy;
+    D.ou = ou;
+    D.ov = ov;
+    D.q_out = q_out;
+    D.w = w;
+    D.h = h;
+    D.tiles_x = (w + kTile - 1) / kTile;
+    D.item_begin = 0;
+    D.async_ok = async_ok ? 1 : 0;
+    return D;
+}
+
+static int merge_grid(int nitems)
+{
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
+    return nitems < 2 * sms ? nitems : 2 * sms;
+}
+
+void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v, int w, int h,
+                  int nsrc, const MergeSrcDev* srcs, double ssim_sigma, double we_sigma,
+                  float* oy, float* ou, float* ov, float* q_out, cudaStream_t s)
+{
+    MergeBatch<1> B;
+    B.nstacks = 1;
+    B.st[0] = merge_stack(ref_y, ref_u, ref_v, w, h, nsrc, srcs, ssim_sigma, we_sigma, oy, ou, ov,
+                          q_out);
+    B.nitems = B.st[0].tiles_x * ((h + kTile - 1) / kTile);
+    const size_t smem = sizeof(MergeSmem);
+    ensure_smem((const void*)k_merge<1>, smem);
     note_launch();
-    k_merge<<<grid, 256, smem, s>>>(ref_y, ref_u, ref_v, w, h, a, oy, ou, ov, q_out, async_ok ? 1 : 0);
+    k_merge<1><<<merge_grid(B.nitems), 256, smem, s>>>(B);
+}
+
+// Several stacks' merges in persistent launches of up to kMergeBatchStacks stacks each.
+void launch_merge_many(const MergeJob* jobs, int count, cudaStream_t s)
+{
+    const size_t smem = sizeof(MergeSmem);
+    ensure_smem((const void*)k_merge<kMergeBatchStacks>, smem);
+    for (int first = 0; first < count; first += kMergeBatchStacks) {
+        MergeBatch<kMergeBatchStacks> B;
+        B.nstacks = count - first < kMergeBatchStacks ? count - first : kMergeBatchStacks;
+        B.nitems = 0;
+        for (int j = 0; j < B.nstacks; j++) {
+            const MergeJob& J = jobs[first + j];
+            B.st[j] = merge_stack(J.ref_y, J.ref_u, J.ref_v, J.w, J.h, J.nsrc, J.srcs, J.ssim_sigma,
+                                  J.we_sigma, J.oy, J.ou, J.ov, nullptr);
+            B.st[j].item_begin = B.nitems;
+            B.nitems += B.st[j].tiles_x * ((J.h + kTile - 1) / kTile);
+        }
+        note_launch();
+        k_merge<kMergeBatchStacks><<<merge_grid(B.nitems), 256, smem, s>>>(B);
+    }
 }
 
 }  // namespace hdrreg

@@ -31,13 +31,14 @@ EXPORTS = [
     "hdrreg_register_merge_workspace_size", "hdrreg_register_merge",
     "hdrreg_register_merge_batch_workspace_size", "hdrreg_register_merge_batch",
     "hdrreg_register_merge_multi_workspace_size", "hdrreg_register_merge_multi",
+    "hdrreg_register_merge_staged_workspace_size", "hdrreg_register_merge_staged",
     "hdrreg_register_merge_host_workspace_size", "hdrreg_register_merge_host",
     "hdrreg_fuse_workspace_size", "hdrreg_fuse",
     "hdrreg_gemm_bf16", "hdrreg_cnn_workspace_size", "hdrreg_cnn_out_dims", "hdrreg_cnn_forward",
     "hdrreg_cnn_backward", "hdrreg_cnn_adam", "hdrreg_cnn_activation",
     "hdrreg_cnn_infer_workspace_size", "hdrreg_cnn_infer", "hdrreg_predictor_input",
     "hdrreg_tile_labels",
-    "hdrreg_predictor_crops", "hdrreg_local_search_predicted", "hdrreg_probe_dp4a",
+    "hdrreg_predictor_crops", "hdrreg_local_search_predicted",
 ]
 
 CNN_PARAMS = 119538
@@ -80,7 +81,8 @@ class PlanesF32(C.Structure):
 
 class MergeSrc(C.Structure):
     _fields_ = [("y", C.c_void_p), ("u", C.c_void_p), ("v", C.c_void_p), ("ref_n", C.c_void_p),
-                ("src_lut", C.c_void_p), ("ratio_num", C.c_int), ("ratio_den", C.c_int)]
+                ("src_lut", C.c_void_p), ("ratio_num", C.c_int), ("ratio_den", C.c_int),
+                ("clip", C.c_void_p)]
 
 
 class Stack(C.Structure):
@@ -120,7 +122,6 @@ def lib():
         L.hdrreg_last_error.restype = C.c_char_p
         L.hdrreg_version.restype = C.c_char_p
         L.hdrreg_launch_count.restype = C.c_ulonglong
-        L.hdrreg_probe_dp4a.argtypes = [i, i, vp, vp]
         L.hdrreg_params_default.argtypes = [C.POINTER(Params)]
         L.hdrreg_params_paper.argtypes = [C.POINTER(Params)]
         L.hdrreg_validate_params.argtypes = [C.POINTER(Params)]
@@ -147,7 +148,8 @@ def lib():
         L.hdrreg_flow_workspace_size.argtypes = [i, i]
         L.hdrreg_flow_upsample.argtypes = [vp, i, i, vp, vp, vp, i, vp, C.POINTER(Params), vp,
                                            vp, vp, sz, vp]
-        L.hdrreg_warp.argtypes = [C.POINTER(Frame), i, i, vp, vp, vp, C.POINTER(PlanesF32), vp]
+        L.hdrreg_warp.argtypes = [C.POINTER(Frame), i, i, vp, vp, vp, C.POINTER(PlanesF32), vp,
+                                  vp]
         L.hdrreg_merge.argtypes = [C.POINTER(Frame), i, i, i, C.POINTER(MergeSrc),
                                    C.POINTER(Params), C.POINTER(PlanesF32), vp, vp]
         L.hdrreg_register_merge_workspace_size.restype = sz
@@ -171,6 +173,9 @@ def lib():
         L.hdrreg_register_merge_multi_workspace_size.restype = sz
         L.hdrreg_register_merge_multi_workspace_size.argtypes = [C.POINTER(StackEx), i, i]
         L.hdrreg_register_merge_multi.argtypes = [C.POINTER(StackEx), i, i, vp, sz, vp]
+        L.hdrreg_register_merge_staged_workspace_size.restype = sz
+        L.hdrreg_register_merge_staged_workspace_size.argtypes = [C.POINTER(StackEx), i, i]
+        L.hdrreg_register_merge_staged.argtypes = [C.POINTER(StackEx), i, i, vp, sz, vp]
         L.hdrreg_gemm_bf16.argtypes = [vp, i, vp, i, i, i, i, vp, i, vp, vp]
         L.hdrreg_cnn_workspace_size.restype = sz
         L.hdrreg_cnn_workspace_size.argtypes = [i, i, i]
@@ -203,12 +208,6 @@ def version() -> str:
 def launch_count() -> int:
     """Kernels enqueued by the library so far in this process."""
     return int(lib().hdrreg_launch_count())
-
-
-def probe_dp4a(blocks: int, iters: int, sink, stream=None) -> int:
-    """Enqueue the integer dot-product rate probe; -> the number of __dp4a it issues."""
-    _check(lib().hdrreg_probe_dp4a(blocks, iters, _ptr(sink), _stream(stream)))
-    return blocks * 256 * iters * 8
 
 
 def params(**over) -> Params:
@@ -382,23 +381,26 @@ def flow_upsample(guide_n, corner_xy, match_xy, mask, H, p: Params, stream=None)
 
 
 # ---------------------------------------------------------------- a9
-def warp(src_y, src_u, src_v, H, flow_u, flow_v, stream=None):
+def warp(src_y, src_u, src_v, H, flow_u, flow_v, stream=None, want_clip=False):
+    """-> (y, u, v) FP32 planes, and with want_clip the uint8 clip flags of the luma samples"""
     import torch
     h, w = src_y.shape
     oy = _empty((h, w), torch.float32, src_y)
+    clip = _empty((h, w), torch.uint8, src_y) if want_clip else None
     chroma = src_u is not None
     ou = _empty((h // 2, w // 2), torch.float32, src_y) if chroma else None
     ov = _empty((h // 2, w // 2), torch.float32, src_y) if chroma else None
     f = Frame(_ptr(src_y), _ptr(src_u), _ptr(src_v))
     o = PlanesF32(_ptr(oy), _ptr(ou), _ptr(ov))
     _check(lib().hdrreg_warp(C.byref(f), w, h, _ptr(H), _ptr(flow_u), _ptr(flow_v), C.byref(o),
-                             _stream(stream)))
-    return oy, ou, ov
+                             _ptr(clip), _stream(stream)))
+    return (oy, ou, ov, clip) if want_clip else (oy, ou, ov)
 
 
 # ---------------------------------------------------------------- a10-a11
 def merge(ref_y, ref_u, ref_v, sources: Sequence[Dict], p: Params, want_q=False, stream=None):
-    """sources: dicts with y, u, v (warped FP32), ref_n (u8), ratio (num, den), lut (HISTEQ)."""
+    """sources: dicts with y, u, v (warped FP32), ref_n (u8), ratio (num, den), lut (HISTEQ),
+    clip (optional uint8 clip flags of the warped luma, as warp(want_clip=True) returns)."""
     import torch
     h, w = ref_y.shape
     chroma = ref_u is not None
@@ -406,7 +408,7 @@ def merge(ref_y, ref_u, ref_v, sources: Sequence[Dict], p: Params, want_q=False,
     arr = (MergeSrc * k)()
     for i, s in enumerate(sources):
         arr[i] = MergeSrc(_ptr(s["y"]), _ptr(s.get("u")), _ptr(s.get("v")), _ptr(s["ref_n"]),
-                          _ptr(s.get("lut")), s["ratio"][0], s["ratio"][1])
+                          _ptr(s.get("lut")), s["ratio"][0], s["ratio"][1], _ptr(s.get("clip")))
     oy = _empty((h, w), torch.float32, ref_y)
     ou = _empty((h // 2, w // 2), torch.float32, ref_y) if chroma else None
     ov = _empty((h // 2, w // 2), torch.float32, ref_y) if chroma else None
@@ -734,13 +736,18 @@ class RegisterMergeMulti:
     `lanes` concurrent lanes. `shapes` lists (w, h, nsrc, params, chroma) per stack slot;
     the object owns the workspace and each slot's output planes and diagnostics."""
 
-    def __init__(self, shapes, lanes: int = 4, device="cuda"):
+    def __init__(self, shapes, lanes: int = 4, device="cuda", staged: bool = False):
+        """staged: run the merges of all stacks as one stage after every registration
+        (hdrreg_register_merge_staged) instead of each on its stack's lane."""
         import torch
         self.shapes = [(int(w), int(h), int(n), p, bool(c)) for w, h, n, p, c in shapes]
         self.lanes = lanes
+        self.staged = staged
         self._params = [C.pointer(p) for _, _, _, p, _ in self.shapes]
         arr = self._array(len(self.shapes))
-        n = lib().hdrreg_register_merge_multi_workspace_size(arr, len(self.shapes), lanes)
+        size_fn = (lib().hdrreg_register_merge_staged_workspace_size if staged else
+                   lib().hdrreg_register_merge_multi_workspace_size)
+        n = size_fn(arr, len(self.shapes), lanes)
         if n == 0:
             raise HdrregError(1, "bad shape, lanes or parameters for register_merge_multi")
         self.ws = torch.empty((n,), dtype=torch.uint8, device=device)
@@ -787,8 +794,8 @@ class RegisterMergeMulti:
             arr[i].s.out = PlanesF32(_ptr(o[0]), _ptr(o[1]), _ptr(o[2]))
             arr[i].s.diag = _ptr(self.diag[i])
             keep.append((fr, fs, num, den))
-        _check(lib().hdrreg_register_merge_multi(arr, k, self.lanes, _ptr(self.ws),
-                                                 self.ws.numel(), _stream(stream)))
+        fn = lib().hdrreg_register_merge_staged if self.staged else lib().hdrreg_register_merge_multi
+        _check(fn(arr, k, self.lanes, _ptr(self.ws), self.ws.numel(), _stream(stream)))
         self._keep = keep
         return self.outs
 

@@ -101,16 +101,11 @@ def test_null_and_size_errors_return_before_any_launch(hd):
                                          None) == 1
     f = hd.Frame(None, None, None)
     o = hd.PlanesF32(None, None, None)
-    assert lib.hdrreg_warp(C.byref(f), 64, 64, None, None, None, C.byref(o), None) == 1
+    assert lib.hdrreg_warp(C.byref(f), 64, 64, None, None, None, C.byref(o), None, None) == 1
     assert lib.hdrreg_register_merge(C.byref(f), 64, 64, 1, None, None, None, C.byref(p), None, 0,
                                      C.byref(o), None, None) == 1
     assert lib.hdrreg_fit_homography(None, None, None, -1, 10, 10, None, None, None, None) == 1
     assert b"NULL" in lib.hdrreg_last_error() or b"range" in lib.hdrreg_last_error()
-    sink = C.c_uint32(0)
-    assert lib.hdrreg_probe_dp4a(0, 16, C.byref(sink), None) == 1
-    assert lib.hdrreg_probe_dp4a(148, 0, C.byref(sink), None) == 1
-    assert lib.hdrreg_probe_dp4a(148, 16, None, None) == 1
-    assert b"NULL" in lib.hdrreg_last_error()
 
 
 def test_batch_sizes_and_argument_errors(hd):
@@ -169,3 +164,18 @@ def test_paper_preset_and_defaults(hd):
     dd, pd = d.as_dict(), p.as_dict()
     assert {k for k in dd if dd[k] != pd[k]} == {"propagate_full"}
     assert hd.lib().hdrreg_validate_params(C.byref(p)) == 0
+
+
+def test_rate_probe_is_a_separate_library():
+    # the benchmark's dp4a rate probe lives in its own library, not in the C ABI of the
+    # registration library; its argument checks return before any launch
+    from paper_1504_01441_b300 import build, probe
+    build.build()
+    import ctypes as C2
+    main = C2.CDLL(build.LIB)
+    assert not hasattr(main, "hdrreg_probe_dp4a")
+    lib = probe.lib()
+    sink = C2.c_uint32(0)
+    assert lib.hdrreg_probe_dp4a(0, 16, C2.byref(sink), None) == 1
+    assert lib.hdrreg_probe_dp4a(148, 0, C2.byref(sink), None) == 1
+    assert lib.hdrreg_probe_dp4a(148, 16, None, None) == 1

@@ -13,9 +13,10 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from tolerance import check_merged
+
 pytestmark = pytest.mark.gpu
 
-REL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -36,24 +37,13 @@ def dev_stack(s):
             [(dev(f.y), dev(f.u), dev(f.v)) for f in s.srcs], list(s.ratios))
 
 
-def rel_err(gpu, orc):
-    g = np.asarray(gpu, np.float64)
-    o = np.asarray(orc, np.float64)
-    return float(np.abs(g - o).max() / max(np.abs(o).max(), 1.0))
-
-
 def check_against_oracle(orc, stack, c, outs, diags):
-    out = orc.register_merge(stack.ref, stack.srcs, stack.ratios, c)
+    out = orc.register_merge(stack.ref, stack.srcs, stack.ratios, c, want_intermediates=True)
     for k, d in enumerate(diags):
         assert np.array_equal(np.array(d.H0[:]).view(np.uint64),
                               out["H0"][k].reshape(9).view(np.uint64)), f"H0 of source {k}"
     torch.cuda.synchronize()
-    for name, g in zip("yuv", outs):
-        if g is None:
-            continue
-        e = rel_err(g.cpu().numpy(), out[name])
-        print(f"{name}: max-norm relative error {e:.3e}")
-        assert e <= REL, name
+    check_merged(orc, stack, out, c, outs)
 
 
 def run_multi_case(hd, stacks, cfgs, lanes):
@@ -104,6 +94,48 @@ def test_multi_shapes_equal_single_calls_and_captures(hd, orc):
     mm, outs = run_multi_case(hd, stacks, cfgs, lanes=3)
     check_against_oracle(orc, stacks[1], cfgs[1], outs[1], mm.diagnostics(1))
     check_against_oracle(orc, stacks[3], cfgs[3], outs[3], mm.diagnostics(3))
+
+
+def test_staged_merges_equal_the_lane_form_and_capture(hd):
+    # the same mixed stacks with every merge as one stage after all registrations
+    # (persistent launches over the tiles of every stack): the same bits as the lane form,
+    # eagerly and replayed from a CUDA graph
+    from paper_1504_01441_b300 import synth
+    specs = [synth.StackSpec(320, 240, ratios=((4, 1),), movers=1, chroma=True),
+             synth.StackSpec(352, 288, ratios=((2, 1), (8, 1)), movers=1, chroma=True),
+             synth.StackSpec(256, 192, ratios=((1, 4), (4, 1)), movers=1, chroma=False),
+             synth.StackSpec(482, 322, ratios=((4, 1),), movers=1, chroma=True)]
+    stacks = [synth.make_stack(sp, 190 + i) for i, sp in enumerate(specs)]
+    params = [hd.params_from_dict(synth.method_params(t, r))
+              for t, r in [(16, 4), (24, 3), (16, 3), (16, 5)]]
+    params[1].norm_mode = hd.NORM_HISTEQ
+    dstacks = [dev_stack(s) for s in stacks]
+    shapes = [(s.width, s.height, len(s.srcs), p, s.ref.u is not None)
+              for s, p in zip(stacks, params)]
+    lanes_form = hd.RegisterMergeMulti(shapes, lanes=3)
+    want = [[t.clone() if t is not None else None for t in o] for o in lanes_form(dstacks)]
+    staged = hd.RegisterMergeMulti(shapes, lanes=3, staged=True)
+    outs = staged(dstacks)
+    torch.cuda.synchronize()
+    for i, (o, w_) in enumerate(zip(outs, want)):
+        for a, b in zip(o, w_):
+            assert (a is None and b is None) or torch.equal(a, b), f"stack {i}"
+        assert ([d.H0[:] for d in staged.diagnostics(i)] ==
+                [d.H0[:] for d in lanes_form.diagnostics(i)])
+    for o in outs:
+        for t in o:
+            if t is not None:
+                t.zero_()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        staged(dstacks, stream=s)
+    with torch.cuda.stream(s):
+        g.replay()
+    torch.cuda.synchronize()
+    for i, (o, w_) in enumerate(zip(outs, want)):
+        for a, b in zip(o, w_):
+            assert (a is None and b is None) or torch.equal(a, b), f"stack {i} (graph replay)"
 
 
 def test_multi_one_lane_and_more_lanes_than_stacks(hd):

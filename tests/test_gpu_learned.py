@@ -7,6 +7,8 @@ import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
+
+from tolerance import check_merged
 pytestmark = pytest.mark.gpu
 
 
@@ -43,7 +45,11 @@ def test_predictor_input_matches_oracle(hd, orc, level_pair):
     x = hd.predictor_input(dev(rq), dev(sq), dev(H.reshape(9))).float().cpu().numpy()
     want = orc.predictor_input(rq, sq, H)
     assert x.shape == want.shape
-    assert np.abs(x - want).max() <= 1.0 / 64
+    # values in [-1, 1] stored as bfloat16: half a unit in the last place is at most 2^-9
+    # (for |v| in [0.5, 1)), plus the FP32 evaluation of the sample (~1e-6)
+    err = np.abs(x - want).max()
+    print(f"predictor input max error {err:.3e} (bound {2.0 ** -9 + 1e-5:.3e})")
+    assert err <= 2.0 ** -9 + 1e-5
 
 
 def test_tile_labels_bit_exact(hd, orc, level_pair):
@@ -199,21 +205,20 @@ def test_fused_learned_path_equals_its_step_calls(hd):
 def test_learned_merge_error_against_the_oracle_at_8px_fields(hd, orc):
     # The merge error of the learned path against the float64 oracle, on one 5 MP YUV420
     # pair with +-8 px local fields. The plain fused call is at parity with the oracle
-    # (max-norm error <= 1e-4 of the largest value). The learned call (default operating
+    # (per element within 1e-4 * max(|oracle|, 1)). The learned call (default operating
     # point: r = 1, fallback above 1.5 x the median plain cost) changes level-0 matches,
     # so its merged image is held to the oracle's plain merge by an error budget instead:
     # the mean absolute luma difference and the share of pixels more than 2 DN apart.
     from paper_1504_01441_b300 import learned, synth
     st = synth.make_learned8_stack(0)
     c = cfg(32, 6)
-    want = orc.register_merge(st.ref, st.srcs, st.ratios, c)
+    want = orc.register_merge(st.ref, st.srcs, st.ratios, c, want_intermediates=True)
     p = hd.params_from_dict(c)
     ref = (dev(st.ref.y), dev(st.ref.u), dev(st.ref.v))
     srcs = [(dev(st.srcs[0].y), dev(st.srcs[0].u), dev(st.srcs[0].v))]
     (y0, u0, v0), _ = hd.register_merge(ref, srcs, st.ratios, p)
-    for name, g in zip("yuv", (y0, u0, v0)):
-        e = np.abs(g.cpu().numpy() - want[name]).max() / max(np.abs(want[name]).max(), 1.0)
-        assert e <= 1e-4, name
+    torch.cuda.synchronize()
+    check_merged(orc, st, want, c, (y0, u0, v0), "plain fused merge")
     prep = learned.prepare(st, p)
     thr = int(1.5 * float(prep.cost[prep.valid.bool()].double().median().item()))
     theta = torch.tensor(np.load(learned.THETA_FILE)).cuda()
@@ -229,3 +234,48 @@ def test_learned_merge_error_against_the_oracle_at_8px_fields(hd, orc):
     assert 0 < d.fallbacks < d.valid
     # measured on a B300: 0.113 DN and 0.38 % (fallback on 283 of 1853 tiles)
     assert mean_abs <= 0.25 and share2 <= 0.01
+
+
+def test_learned_search_gains_over_plain_beyond_the_search_radius(hd):
+    # What the trained network buys, against the generator's truth. On +-8 px fields (seeds
+    # apart from training) some tiles' true match lies outside the level-0 window: the truth
+    # at the corner minus the search centre (from the level-1 homography) exceeds R = 6 in x
+    # or y, so the plain search cannot reach it. The learned search (prediction, +-1
+    # refinement, plain search where the residual cost exceeds 1.5 x the median plain cost;
+    # the network was trained on labels of a radius-12 plain search) must land closer to the
+    # truth on those tiles, and over all tiles, than the plain search does.
+    from paper_1504_01441_b300 import learned, synth
+    p = hd.params_from_dict(cfg(32, 6))
+    theta = torch.tensor(np.load(learned.THETA_FILE)).cuda()
+    plain_far, learned_far, plain_all, learned_all, fell = [], [], [], [], 0
+    for i in range(2):
+        P = learned.prepare(synth.make_learned8_stack(i), p, keep_gt=True)
+        net = hd.Predictor(1, P.x.shape[0], P.x.shape[1], theta)
+        pred = net.infer(P.x.unsqueeze(0))[0]
+        thr = int(1.5 * float(P.cost[P.valid.bool()].double().median().item()))
+        c, m, _, v, fb = hd.local_search_predicted(P.ref_n, P.src_n, P.H1, p, pred, thr, refine=1)
+        ok = (v.bool() & P.valid.bool()).cpu().numpy()
+        corner = c.cpu().numpy()[ok].astype(np.int64)
+        gt = P.gt.cpu().numpy()
+        truth = np.stack([gt[0][corner[:, 1], corner[:, 0]], gt[1][corner[:, 1], corner[:, 0]]], 1)
+        mp = P.match.cpu().numpy()[ok].astype(np.float64)
+        ml = m.cpu().numpy()[ok].astype(np.float64)
+        centre = mp - P.label.cpu().numpy()[ok]        # label = plain match - search centre
+        far = (np.abs(truth - centre) > p.radius).any(1)
+        ep, el = np.hypot(*(mp - truth).T), np.hypot(*(ml - truth).T)
+        plain_far.append(ep[far])
+        learned_far.append(el[far])
+        plain_all.append(ep)
+        learned_all.append(el)
+        fell += int(fb.cpu().numpy()[ok].sum())
+    pf, lf = np.concatenate(plain_far), np.concatenate(learned_far)
+    pa, la = np.concatenate(plain_all), np.concatenate(learned_all)
+    print(f"tiles beyond the radius: {pf.size} of {pa.size}; end-point error against the "
+          f"generator's truth there: plain {pf.mean():.3f} px, learned {lf.mean():.3f} px; "
+          f"over all tiles: plain {pa.mean():.3f} px, learned {la.mean():.3f} px; "
+          f"fallback on {fell} tiles")
+    # measured on a B300 with the committed network: 167 of 3,730 tiles beyond the radius,
+    # plain 5.72 px, learned 5.07 px there; over all tiles plain 3.02 px, learned 1.69 px
+    assert pf.size >= 20
+    assert lf.mean() < 0.95 * pf.mean()   # beyond the window the plain search cannot reach
+    assert la.mean() < 0.75 * pa.mean()   # and over every tile with a corner

@@ -2,9 +2,8 @@
 
 Integer / index / FP64-decided outputs (normalized images, pyramids, corners,
 matches, SSD costs, weeding masks, level homographies) must be bit-exact. FP32
-outputs (flow, warp, SSIM mask, merge) must satisfy the tolerance of the
-spec: relative error <= 1e-4, measured in the max norm of each output
-plane, |gpu - oracle|_inf <= 1e-4 * max(|oracle|_inf, 1).
+outputs (flow, warp, SSIM mask, merge) must satisfy, element by element,
+|gpu - oracle| <= 1e-4 * max(|oracle|, 1) (tests/tolerance.py).
 """
 import math
 
@@ -13,9 +12,11 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from tolerance import (REL, check_end_to_end, check_merged, check_rel, chroma_exclude,
+                       flow_sensitivity, fused_fragile)
+
 pytestmark = pytest.mark.gpu
 
-REL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -44,25 +45,8 @@ def host(t):
     return t.cpu().numpy()
 
 
-def rel_err(gpu, orc):
-    g = np.asarray(gpu, np.float64)
-    o = np.asarray(orc, np.float64)
-    return float(np.abs(g - o).max() / max(np.abs(o).max(), 1.0))
-
-
-def assert_rel(gpu, orc, what, rel=REL):
-    g = np.asarray(gpu, np.float64)
-    o = np.asarray(orc, np.float64)
-    d = np.abs(g - o)
-    e = rel_err(g, o)
-    idx = np.unravel_index(int(np.argmax(d)), d.shape)
-    elem = d > rel * np.maximum(np.abs(o), 1.0)
-    msg = (f"{what}: max-norm relative error {e:.3e} (limit {rel:.0e}) at {idx}: gpu {g[idx]!r} "
-           f"oracle {o[idx]!r}; elements above {rel:.0e}*max(|oracle|,1): {int(elem.sum())} "
-           f"of {d.size}")
-    print(msg)
-    assert e <= rel, msg
-    return e
+def assert_rel(gpu, orc, what, rel=REL, exclude=None):
+    return check_rel(gpu, orc, what, rel=rel, exclude=exclude)
 
 
 def mask_bool(words, n):
@@ -360,9 +344,17 @@ def test_warp(hd, orc, small_yuv_stack, chroma):
     fu, fv = synth.random_flow(rng, w, h, 4.0)
     u = dev(s.u) if chroma else None
     v = dev(s.v) if chroma else None
-    oy, ou, ov = hd.warp(dev(s.y), u, v, dev(H.reshape(9)), dev(fu), dev(fv))
-    wy, wu, wv = orc.warp(s.y, s.u if chroma else None, s.v if chroma else None, H, fu, fv)
+    oy, ou, ov, clip = hd.warp(dev(s.y), u, v, dev(H.reshape(9)), dev(fu), dev(fv),
+                               want_clip=True)
+    wy, wu, wv, oclip = orc.warp(s.y, s.u if chroma else None, s.v if chroma else None, H, fu, fv,
+                                 want_clip=True)
     assert_rel(host(oy), wy, "warp y")
+    # the clip flags agree wherever the decision is not fragile at the float32 position error
+    frag = orc.clip_fragile(s.y, H, fu, fv)
+    differ = host(clip) != oclip
+    print(f"clip flags: {int(oclip.sum())} set, {int(frag.sum())} fragile, "
+          f"{int(differ.sum())} differ ({int((differ & frag).sum())} of them fragile)")
+    assert not (differ & ~frag).any() and frag.sum() <= 1e-3 * frag.size
     if chroma:
         assert_rel(host(ou), wu, "warp u")
         assert_rel(host(ov), wv, "warp v")
@@ -383,23 +375,25 @@ def _merge_case(hd, orc, stack, c, ratios):
     rng = np.random.default_rng(8)
     h, w = stack.ref.y.shape
     chroma = stack.ref.u is not None
-    srcs, osrcs, qs = [], [], []
+    srcs, osrcs, qs, clips = [], [], [], []
     for k, s in enumerate(stack.srcs):
         rn, _ = orc.normalize_ratio(stack.ref.y, s.y, *ratios[k])
         H = synth.random_homography(rng, scale=0.002, shift_n=0.002, persp=0.0001)
         fu, fv = synth.random_flow(rng, w, h, 1.0)
-        wy, wu, wv = orc.warp(s.y, s.u, s.v, H, fu, fv)
+        wy, wu, wv, clip = orc.warp(s.y, s.u, s.v, H, fu, fv, want_clip=True)
         wy, wu, wv = [None if a is None else a.astype(np.float32) for a in (wy, wu, wv)]
+        clips.append(clip)
         gain = ratios[k][1] / ratios[k][0] if ratios[k][0] < ratios[k][1] else 1.0
         qs.append(orc.ghost_mask(rn, wy, 0, gain))
         osrcs.append((wy, wu, wv))
         srcs.append(dict(y=dev(wy), u=dev(wu) if chroma else None, v=dev(wv) if chroma else None,
-                         ref_n=dev(rn), ratio=ratios[k]))
+                         ref_n=dev(rn), ratio=ratios[k], clip=dev(clip)))
     p = hd.params_from_dict(c)
     ey, eu, ev, q = hd.merge(dev(stack.ref.y), dev(stack.ref.u) if chroma else None,
                              dev(stack.ref.v) if chroma else None, srcs, p, want_q=True)
     oy, ou, ov = orc.merge(stack.ref.y, stack.ref.u, stack.ref.v, osrcs, qs,
-                           [r[0] / r[1] for r in ratios])
+                           [r[0] / r[1] for r in ratios], clips=clips)
+    assert sum(int(c.sum()) for c in clips) > 0
     for k in range(len(srcs)):
         assert_rel(host(q)[k], qs[k], f"ssim mask {k}")
     assert_rel(host(ey), oy, "merge y")
@@ -421,7 +415,10 @@ def test_merge_three_frames(hd, orc):
 
 
 # --------------------------------------------------------------------- fused
-def _fused_case(hd, orc, stack, c):
+def _fused_case(hd, orc, stack, c, propagated=False):
+    """propagated: hold the merged planes to the per-element rule plus the oracle's own
+    movement under the flow's tolerance (used where the propagated flow is the whole
+    displacement, tens of pixels, whose FP32 error moves the sample positions most)"""
     p = hd.params_from_dict(c)
     chroma = stack.ref.u is not None
     ref = (dev(stack.ref.y), dev(stack.ref.u) if chroma else None,
@@ -429,21 +426,29 @@ def _fused_case(hd, orc, stack, c):
     srcs = [(dev(s.y), dev(s.u) if chroma else None, dev(s.v) if chroma else None)
             for s in stack.srcs]
     (ey, eu, ev), rm = hd.register_merge(ref, srcs, stack.ratios, p)
-    out = orc.register_merge(stack.ref, stack.srcs, stack.ratios, c)
+    out = orc.register_merge(stack.ref, stack.srcs, stack.ratios, c, want_intermediates=True)
     diags = rm.diagnostics()
     for k, d in enumerate(diags):
         assert np.array_equal(np.array(d.H0[:]).view(np.uint64),
                               out["H0"][k].reshape(9).view(np.uint64)), f"H0 of source {k}"
         assert d.flow_status == 0 and d.reserved == 0, f"flow status of source {k}"
-    e = assert_rel(host(ey), out["y"], "fused merge y")
-    if chroma:
-        assert_rel(host(eu), out["u"], "fused merge u")
-        assert_rel(host(ev), out["v"], "fused merge v")
-    return e, diags
+    torch.cuda.synchronize()
+    if not propagated:
+        check_merged(orc, stack, out, c, (ey, eu, ev) if chroma else (ey,), "fused merge")
+        return diags
+    base, sens = flow_sensitivity(orc, stack, out, c)
+    assert np.array_equal(base[0], out["y"])  # the tail recomputation is the oracle's path
+    ex = fused_fragile(orc, stack, out, c)
+    for name, g, o, sn in zip("yuv", (ey, eu, ev), base, sens):
+        if o is not None:
+            check_end_to_end(host(g), o, sn, f"fused merge {name}",
+                             exclude=ex if name == "y" else chroma_exclude(ex),
+                             max_excluded_frac=1e-3 if name == "y" else 4e-3)
+    return diags
 
 
 def test_fused_vga_luma(hd, orc, vga):
-    _, diags = _fused_case(hd, orc, vga, cfg())
+    diags = _fused_case(hd, orc, vga, cfg())
     assert diags[0].levels == 3 and diags[0].valid > 300
 
 
@@ -455,7 +460,7 @@ def test_fused_three_frame_yuv(hd, orc):
 
 
 def test_fused_five_mp(hd, orc, five_mp):
-    _, diags = _fused_case(hd, orc, five_mp, cfg(32, 6))
+    diags = _fused_case(hd, orc, five_mp, cfg(32, 6))
     assert diags[0].levels == 5 and diags[0].tiles == 81 * 60
 
 
@@ -465,7 +470,7 @@ def test_fused_level_beyond_shared_memory_plan(hd, orc):
     spec = synth.StackSpec(1024, 768, ratios=((1, 4),), noise_sigma=1.0, field_amp=2.0,
                            movers=1, chroma=False)
     assert hd.lib().hdrreg_weed_fit_supported(12288) == 0
-    _, diags = _fused_case(hd, orc, synth.make_stack(spec, 55), cfg(8, 3, grid_half=3))
+    diags = _fused_case(hd, orc, synth.make_stack(spec, 55), cfg(8, 3, grid_half=3))
     assert diags[0].tiles == 12288
 
 
@@ -505,9 +510,10 @@ def test_fused_batch_equals_single_calls_and_captures(hd, orc):
     for i, (o, want) in enumerate(zip(outs, single)):
         for a, b in zip(o, want[:3]):
             assert torch.equal(a, b), f"stack {i} (graph replay)"
-    out = orc.register_merge(stacks[2].ref, stacks[2].srcs, stacks[2].ratios, c)
-    assert_rel(host(outs[2][0]), out["y"], "batched merge y")
-    assert_rel(host(outs[2][1]), out["u"], "batched merge u")
+    out = orc.register_merge(stacks[2].ref, stacks[2].srcs, stacks[2].ratios, c,
+                             want_intermediates=True)
+    torch.cuda.synchronize()
+    check_merged(orc, stacks[2], out, c, outs[2], "batched merge")
 
 
 def test_fused_histeq_mode(hd, orc, small_yuv_stack):
@@ -520,7 +526,7 @@ def test_fused_paper_preset(hd, orc, small_yuv_stack, five_mp, which):
     # corners' whole displacement spread by the flow (warp by p + F)
     stack = small_yuv_stack if which == "small" else five_mp
     c = hd.params_paper(tile=16 if which == "small" else 32).as_dict()
-    _, diags = _fused_case(hd, orc, stack, c)
+    diags = _fused_case(hd, orc, stack, c, propagated=True)
     assert diags[0].valid > 0
 
 
@@ -531,12 +537,3 @@ def test_fused_dark_reference(hd, orc, stops, mode):
     from paper_1504_01441_b300 import synth
     st = synth.make_stack(synth.dark_spec(stops), synth.stack_seed(7, stops))
     _fused_case(hd, orc, st, cfg(16, 4, norm_mode=mode))
-
-
-def test_dp4a_rate_probe_runs(hd):
-    # the measurement aid of the search's ALU roofline: it launches, finishes, and counts
-    # the operations it issues
-    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
-    n = hd.probe_dp4a(148, 64, sink)
-    torch.cuda.synchronize()
-    assert n == 148 * 256 * 64 * 8

@@ -1,6 +1,6 @@
 """hdrreg_weed_static: the weeding step for callers that cannot allocate device
-memory (for example code running under a stream capture that forbids
-cudaMalloc, or a real-time pipeline that allows no allocation after start-up).
+memory (for example a real-time pipeline that allows no allocation after
+start-up, or a plugin whose host owns all device memory).
 
 It keeps its scratch in a fixed array inside the library instead of a
 caller-provided workspace. This test calls it through the C ABI on two calls in
