@@ -59,20 +59,52 @@ __device__ __forceinline__ void h_disp(const WarpCoef& c, int x, int y, int w, i
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// bilinear sample at (x + t_x, y + t_y) with integer x, y and small offsets t
+// The four taps of a bilinear sample at (x + t_x, y + t_y) (integer x, y, small offsets t):
+// (ix, iy), (ix + 1, iy), (ix, iy + 1), (ix + 1, iy + 1) with clamp-to-edge reads, and the
+// fractions. Frames hold fewer than 2^31 pixels, so offsets are 32-bit; samples whose
+// footprint lies inside the frame (almost all) skip the clamps.
+struct Taps {
+    unsigned a, b, c, d;
+    float fx, fy;
+};
+
+__device__ __forceinline__ Taps taps_at(const uint8_t* __restrict__ img, int w, int h, int x,
+                                        int y, float tx, float ty)
+{
+    const float fx0 = floorf(tx), fy0 = floorf(ty);
+    Taps t;
+    t.fx = tx - fx0;
+    t.fy = ty - fy0;
+    const int ix = x + (int)fx0, iy = y + (int)fy0;
+    if ((unsigned)ix < (unsigned)(w - 1) && (unsigned)iy < (unsigned)(h - 1)) {
+        const uint8_t* p = img + (iy * w + ix);
+        t.a = __ldg(p);
+        t.b = __ldg(p + 1);
+        t.c = __ldg(p + w);
+        t.d = __ldg(p + w + 1);
+    } else {
+        const int xa = clampi(ix, 0, w - 1), xb = clampi(ix + 1, 0, w - 1);
+        const int ra = clampi(iy, 0, h - 1) * w, rb = clampi(iy + 1, 0, h - 1) * w;
+        t.a = __ldg(img + ra + xa);
+        t.b = __ldg(img + ra + xb);
+        t.c = __ldg(img + rb + xa);
+        t.d = __ldg(img + rb + xb);
+    }
+    return t;
+}
+
+__device__ __forceinline__ float lerp_taps(const Taps& t)
+{
+    const float a = (float)t.a, b = (float)t.b, c = (float)t.c, d = (float)t.d;
+    const float top = fmaf(t.fx, b - a, a);
+    const float bot = fmaf(t.fx, d - c, c);
+    return fmaf(t.fy, bot - top, top);
+}
+
 __device__ __forceinline__ float bilerp(const uint8_t* __restrict__ img, int w, int h, int x, int y,
                                         float tx, float ty)
 {
-    const float fx0 = floorf(tx), fy0 = floorf(ty);
-    const float fx = tx - fx0, fy = ty - fy0;
-    const int ix = x + (int)fx0, iy = y + (int)fy0;
-    const int xa = clampi(ix, 0, w - 1), xb = clampi(ix + 1, 0, w - 1);
-    const size_t ra = (size_t)clampi(iy, 0, h - 1) * w, rb = (size_t)clampi(iy + 1, 0, h - 1) * w;
-    const float a = __ldg(img + ra + xa), b = __ldg(img + ra + xb);
-    const float c = __ldg(img + rb + xa), d = __ldg(img + rb + xb);
-    const float top = fmaf(fx, b - a, a);
-    const float bot = fmaf(fx, d - c, c);
-    return fmaf(fy, bot - top, top);
+    return lerp_taps(taps_at(img, w, h, x, y, tx, ty));
 }
 
 // The same sample, plus whether it draws on a clipped pixel: a tap at 0 or 255 with a
@@ -81,27 +113,18 @@ __device__ __forceinline__ float bilerp(const uint8_t* __restrict__ img, int w, 
 __device__ __forceinline__ float bilerp_clip(const uint8_t* __restrict__ img, int w, int h, int x,
                                              int y, float tx, float ty, bool& clipped)
 {
-    const float fx0 = floorf(tx), fy0 = floorf(ty);
-    const float fx = tx - fx0, fy = ty - fy0;
-    const int ix = x + (int)fx0, iy = y + (int)fy0;
-    const int xa = clampi(ix, 0, w - 1), xb = clampi(ix + 1, 0, w - 1);
-    const size_t ra = (size_t)clampi(iy, 0, h - 1) * w, rb = (size_t)clampi(iy + 1, 0, h - 1) * w;
-    const unsigned ua = __ldg(img + ra + xa), ub = __ldg(img + ra + xb);
-    const unsigned uc = __ldg(img + rb + xa), ud = __ldg(img + rb + xb);
-    const bool right = fx > 0.f, below = fy > 0.f;
-    auto sat = [](unsigned v) { return v == 0u || v == 255u; };
-    clipped = sat(ua) || (right && sat(ub)) || (below && (sat(uc) || (right && sat(ud))));
-    const float a = (float)ua, b = (float)ub, c = (float)uc, d = (float)ud;
-    const float top = fmaf(fx, b - a, a);
-    const float bot = fmaf(fx, d - c, c);
-    return fmaf(fy, bot - top, top);
+    const Taps t = taps_at(img, w, h, x, y, tx, ty);
+    const bool right = t.fx > 0.f, below = t.fy > 0.f;
+    auto sat = [](unsigned v) { return v - 1u >= 254u; };  // v == 0 or v == 255
+    clipped = sat(t.a) || (right && sat(t.b)) || (below && (sat(t.c) || (right && sat(t.d))));
+    return lerp_taps(t);
 }
 
 // kVec: the flow pitch and the width are even and the planes 8-byte aligned, so each
 // row pair of a 2x2 block moves as one float2 (flows in, warped luma out) and its two
 // clip flags as one 16-bit word.
 template <bool kVec>
-__global__ void __launch_bounds__(256) k_warp(const uint8_t* __restrict__ sy,
+__global__ void __launch_bounds__(256, 5) k_warp(const uint8_t* __restrict__ sy,
                                               const uint8_t* __restrict__ su,
                                               const uint8_t* __restrict__ sv, int w, int h,
                                               const double* __restrict__ H,
@@ -607,12 +630,19 @@ void launch_warp(const uint8_t* src_y, const uint8_t* src_u, const uint8_t* src_
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long need = (nb + 255) / 256, cap = 8LL * sms;  // 8 resident CTAs per SM
-    const int grid = (int)(need < cap ? need : cap);
-    note_launch();
     auto al8 = [](const void* p) { return p == nullptr || ((uintptr_t)p & 7u) == 0; };
     const bool vec = (w % 2) == 0 && (fpitch % 2) == 0 && al8(fu) && al8(fv) && al8(oy) &&
                      (clip == nullptr || ((uintptr_t)clip & 1u) == 0);
+    const void* fn = vec ? (const void*)k_warp<true> : (const void*)k_warp<false>;
+    // the grid is the resident CTAs: each strides over many blocks, so the binary64
+    // coefficient chain runs once per CTA
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long need = (nb + 255) / 256, cap = (long long)per_sm * sms;
+    const int grid = (int)(need < cap ? need : cap);
+    note_launch();
     if (vec)
         k_warp<true><<<grid, 256, 0, s>>>(src_y, src_u, src_v, w, h, H, fu, fv, fpitch, oy, ou, ov,
                                           clip, clip_sign ? 1 : 0);
