@@ -26,7 +26,9 @@ import argparse
 import dataclasses
 import json
 import os
+import struct
 import time
+import zlib
 from typing import List
 
 import numpy as np
@@ -90,11 +92,59 @@ def make_stacks(n: int, first_index: int, spec=TRAIN_SPEC):
                                                   for i in range(n)])
 
 
+# Training checkpoint: a flat file of a fixed header, the FP32 parameters, the two Adam
+# moment vectors, the crop generator's state, and a CRC-32 of everything before it.
+CKPT_MAGIC = b"HDRRCKP1"
+_CKPT_HEAD = struct.Struct("<8sIIqqI")  # magic, version, parameters, Adam step, step, rng bytes
+
+
+def write_checkpoint(path: str, theta, m, v, adam_t: int, step: int, rng_state: bytes):
+    """Write a training checkpoint (atomically: a temporary file, then a rename).
+    theta, m, v: float32 vectors of the same length; adam_t: Adam's step counter; step: the
+    next training step to run; rng_state: the crop generator's state."""
+    arrs = [np.ascontiguousarray(np.asarray(a, np.float32)).reshape(-1) for a in (theta, m, v)]
+    if not arrs[0].size == arrs[1].size == arrs[2].size:
+        raise ValueError("theta, m and v must have the same length")
+    body = _CKPT_HEAD.pack(CKPT_MAGIC, 1, arrs[0].size, int(adam_t), int(step), len(rng_state))
+    body += b"".join(a.tobytes() for a in arrs) + bytes(rng_state)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "wb") as f:
+        f.write(body + struct.pack("<I", zlib.crc32(body)))
+    os.replace(tmp, path)
+
+
+def read_checkpoint(path: str) -> dict:
+    """-> dict(theta, m, v, adam_t, step, rng_state); ValueError if the file is not a
+    checkpoint, is truncated, or fails its checksum."""
+    data = open(path, "rb").read()
+    if len(data) < _CKPT_HEAD.size + 4:
+        raise ValueError(f"{path}: too short for a checkpoint")
+    magic, version, n, adam_t, step, nr = _CKPT_HEAD.unpack_from(data, 0)
+    if magic != CKPT_MAGIC or version != 1:
+        raise ValueError(f"{path}: not a predictor training checkpoint")
+    end = _CKPT_HEAD.size + 12 * n + nr
+    if len(data) != end + 4:
+        raise ValueError(f"{path}: size {len(data)} does not match its header ({end + 4})")
+    if struct.unpack_from("<I", data, end)[0] != zlib.crc32(data[:end]):
+        raise ValueError(f"{path}: checksum mismatch")
+    o = _CKPT_HEAD.size
+    vec = [np.frombuffer(data, np.float32, n, o + 4 * n * i).copy() for i in range(3)]
+    return dict(theta=vec[0], m=vec[1], v=vec[2], adam_t=adam_t, step=step,
+                rng_state=data[o + 12 * n:end])
+
+
 def train(prepared: List[Prepared], steps: int, batch: int = 64, lr: float = 2e-3, seed: int = 0,
-          theta=None, log_every: int = 50, augment: bool = True, label_bound: float = 6.0):
+          theta=None, log_every: int = 50, augment: bool = True, label_bound: float = 6.0,
+          checkpoint: str = None, checkpoint_every: int = 0, resume: str = None,
+          stop_at: int = None):
     """Adam on random crops (each under one of the 8 mirror/transpose symmetries when
     augment); crops of one batch come from all prepared stacks in turn; labels on the
-    border of the plain search (|d| >= label_bound, the search radius) are left out."""
+    border of the plain search (|d| >= label_bound, the search radius) are left out.
+    checkpoint / checkpoint_every: write a checkpoint after every that many steps (and
+    after the last); resume: continue from a checkpoint, which gives the same parameters,
+    bit for bit, as the run that was never interrupted (the crops come from the saved
+    generator state, the learning rate from the step number); stop_at: end after that
+    step of the `steps`-step schedule (a run in pieces)."""
     import torch
     from . import hdrreg as hd
     dev = prepared[0].x.device
@@ -103,6 +153,23 @@ def train(prepared: List[Prepared], steps: int, batch: int = 64, lr: float = 2e-
     if theta is None:
         pred.theta.copy_(torch.tensor(init_theta(seed)))
     g = torch.Generator(device="cpu").manual_seed(seed)
+    start = 0
+    if resume:
+        ck = read_checkpoint(resume)
+        if ck["theta"].size != pred.theta.numel():
+            raise ValueError(f"{resume}: {ck['theta'].size} parameters, the network has "
+                             f"{pred.theta.numel()}")
+        pred.theta.copy_(torch.from_numpy(ck["theta"]))
+        pred.m.copy_(torch.from_numpy(ck["m"]))
+        pred.v.copy_(torch.from_numpy(ck["v"]))
+        pred.t = ck["adam_t"]
+        g.set_state(torch.frombuffer(bytearray(ck["rng_state"]), dtype=torch.uint8))
+        start = ck["step"]
+
+    def save(next_step):
+        torch.cuda.synchronize()
+        write_checkpoint(checkpoint, pred.theta.cpu().numpy(), pred.m.cpu().numpy(),
+                         pred.v.cpu().numpy(), pred.t, next_step, g.get_state().numpy().tobytes())
     xb = torch.empty((batch, side, side, 2), dtype=torch.bfloat16, device=dev)
     lb = torch.empty((batch, CROP_TILES, CROP_TILES, 2), dtype=torch.float32, device=dev)
     vb = torch.empty((batch, CROP_TILES, CROP_TILES), dtype=torch.uint8, device=dev)
@@ -110,7 +177,8 @@ def train(prepared: List[Prepared], steps: int, batch: int = 64, lr: float = 2e-
            for i in range(len(prepared))]
     history = []
     t0 = time.perf_counter()
-    for step in range(steps):
+    end = steps if stop_at is None else min(steps, stop_at)
+    for step in range(start, end):
         o = 0
         for P, k in zip(prepared, per):
             if k == 0:
@@ -131,6 +199,9 @@ def train(prepared: List[Prepared], steps: int, batch: int = 64, lr: float = 2e-
         pred.adam(lr=lr * (1.0 - 0.9 * step / max(steps - 1, 1)))  # linear decay to 10%
         if step % log_every == 0 or step == steps - 1:
             history.append((step, float(loss.item())))
+        if checkpoint and ((checkpoint_every and (step + 1) % checkpoint_every == 0) or
+                           step == end - 1):
+            save(step + 1)
     torch.cuda.synchronize()
     if int(pred.status.item()) != 0:
         raise hd.HdrregError(2, "a tensor-core kernel timed out during training")
@@ -258,6 +329,11 @@ def main():
     ap.add_argument("--train-stacks", type=int, default=16)
     ap.add_argument("--stress-stacks", type=int, default=0,
                     help="training stacks with +-8 px fields (STRESS_SPEC) besides the +-4 px ones")
+    ap.add_argument("--checkpoint", default=None,
+                    help="write a training checkpoint to this file (every --checkpoint-every "
+                         "steps and at the end)")
+    ap.add_argument("--checkpoint-every", type=int, default=1000)
+    ap.add_argument("--resume", default=None, help="continue training from this checkpoint")
     ap.add_argument("--label-radius", type=int, default=6,
                     help="search radius of the plain level-0 search that labels the training "
                          "tiles (labels on its border are left out)")
@@ -297,7 +373,8 @@ def main():
     eval_set = [prepare(s, p, keep_gt=True) for s in make_stacks(args.eval_stacks, 1000)]
     t_data = time.perf_counter() - t0
     theta, hist, t_train = train(train_set, args.steps, args.batch, args.lr, args.seed,
-                                 label_bound=float(args.label_radius))
+                                 label_bound=float(args.label_radius), checkpoint=args.checkpoint,
+                                 checkpoint_every=args.checkpoint_every, resume=args.resume)
     m_train = evaluate(train_set[:2], theta, p)
     m_eval = {f"refine{r}_ratio{fr}": evaluate(eval_set, theta, p, fallback_ratio=fr, refine=r)
               for r in (0, 1) for fr in (1.0, 1.5)}

@@ -279,3 +279,19 @@ def test_learned_search_gains_over_plain_beyond_the_search_radius(hd):
     assert pf.size >= 20
     assert lf.mean() < 0.95 * pf.mean()   # beyond the window the plain search cannot reach
     assert la.mean() < 0.75 * pa.mean()   # and over every tile with a corner
+
+
+def test_training_resumes_from_a_checkpoint_bit_for_bit(hd, tmp_path):
+    # six Adam steps in one run against three steps, a checkpoint, and three more steps in
+    # a fresh predictor resumed from it: the same parameters, bit for bit
+    from paper_1504_01441_b300 import learned, synth
+    p = hd.params_from_dict(cfg(32, 6))
+    prep = [learned.prepare(synth.make_stack(synth.VGA_LUMA, synth.stack_seed(1)), p)]
+    whole, _, _ = learned.train(prep, 6, batch=8, seed=3, log_every=1)
+    ck = str(tmp_path / "ck.bin")
+    learned.train(prep, 6, batch=8, seed=3, log_every=1, checkpoint=ck, stop_at=3)
+    state = learned.read_checkpoint(ck)
+    assert state["step"] == 3 and state["adam_t"] == 3
+    assert not np.array_equal(state["theta"], whole.cpu().numpy())
+    resumed, _, _ = learned.train(prep, 6, batch=8, seed=3, log_every=1, resume=ck)
+    assert torch.equal(resumed, whole)
