@@ -15,6 +15,8 @@
 // component rounds as its scalar form would).
 #include <math.h>
 
+#include <cmath>
+
 #include "hdrreg_internal.cuh"
 
 namespace hdrreg {
@@ -238,14 +240,18 @@ struct MergeArgs {
     MergeSrcDev src[kMaxSources];
     float g[2 * kSsimRadius + 1];
     float gsum;  // sum of the FP32 taps (1 up to rounding)
+    float s0;    // total weight of a window as the column pass accumulates it: fma of each
+                 // tap with gsum, taps in order
     float we_k;  // 1 / (2 sigma^2)
     int nsrc;
 };
 
+// The exponent lies in [-k/4, 0] (k = 12.5 at sigma 0.2), where the fast exponential's
+// error is a few units in the last place: far below the merge's 1e-4 parity rule.
 __device__ __forceinline__ float well_exposed(float z, float k)
 {
     const float t = z * (1.f / 255.f) - 0.5f;
-    return expf(-(t * t) * k);
+    return __expf(-(t * t) * k);
 }
 
 __device__ __forceinline__ float norm_map(const MergeSrcDev& s, float z)
@@ -295,16 +301,36 @@ struct MergeSmem {
     float Ns[kTile][kTile + 1], Ds[kTile][kTile + 1];
 };
 
+// Tile t of a row-major grid tiles_x wide: (t mod tiles_x, t / tiles_x) from the FP32
+// reciprocal `inv` = 1 / tiles_x and one correction step (exact for t < 2^23).
+__device__ __forceinline__ void tile_xy(int t, int tiles_x, float inv, int& bx, int& by)
+{
+    int q = __float2int_rz((float)t * inv);
+    int r = t - q * tiles_x;
+    if (r < 0) {
+        q--;
+        r += tiles_x;
+    } else if (r >= tiles_x) {
+        q++;
+        r -= tiles_x;
+    }
+    bx = r;
+    by = q;
+}
+
 // Stage unit (tile t, source k): 16-byte async copies for interior tiles when every
 // plane allows them, else plain loads with clamp-to-edge (and the same layout).
 __device__ __forceinline__ void merge_stage(MergeStage& S, const MergeArgs& args,
                                             const uint8_t* __restrict__ ref_y,
                                             const uint8_t* __restrict__ ref_u,
                                             const uint8_t* __restrict__ ref_v, int w, int h,
-                                            bool chroma, int tiles_x, int t, int k, bool async_ok)
+                                            bool chroma, int tiles_x, float inv_tiles_x, int t,
+                                            int k, bool async_ok)
 {
     const int tid = threadIdx.x;
-    const int x0 = (t % tiles_x) * kTile, y0 = (t / tiles_x) * kTile;
+    int bx, by;
+    tile_xy(t, tiles_x, inv_tiles_x, bx, by);
+    const int x0 = bx * kTile, y0 = by * kTile;
     const MergeSrcDev& s = args.src[k];
     const int cw = w / 2, ch = h / 2, cx0 = x0 / 2, cy0 = y0 / 2;
     const bool interior = async_ok && x0 >= 16 && x0 + 48 <= w && y0 >= kHalo &&
@@ -376,6 +402,7 @@ struct MergeStackDev {
     float* ov;
     float* q_out;          // optional SSIM maps (nsrc planes of w x h)
     int w, h, tiles_x;
+    float inv_tiles_x;     // 1 / tiles_x
     int item_begin;        // first item (32 x 32 tile) of this stack in the launch's item list
     int async_ok;          // every plane allows 16-byte asynchronous row copies
     MergeArgs a;
@@ -417,7 +444,8 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
     {
         const MergeStackDev& D = B.st[si];
         merge_stage(M.st[0], D.a, D.ref_y, D.ref_u, D.ref_v, D.w, D.h,
-                    D.ref_u != nullptr && D.ou != nullptr, D.tiles_x, item - D.item_begin, 0,
+                    D.ref_u != nullptr && D.ou != nullptr, D.tiles_x, D.inv_tiles_x,
+                    item - D.item_begin, 0,
                     D.async_ok);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -434,7 +462,8 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
         if (more) {
             const MergeStackDev& Dn = B.st[nsi];
             merge_stage(M.st[buf ^ 1], Dn.a, Dn.ref_y, Dn.ref_u, Dn.ref_v, Dn.w, Dn.h,
-                        Dn.ref_u != nullptr && Dn.ou != nullptr, Dn.tiles_x, nitem - Dn.item_begin,
+                        Dn.ref_u != nullptr && Dn.ou != nullptr, Dn.tiles_x, Dn.inv_tiles_x,
+                        nitem - Dn.item_begin,
                         nk, Dn.async_ok);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -451,14 +480,11 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
         const bool chroma = D.ref_u != nullptr && ou != nullptr;
         const int cw = w / 2, ch = h / 2;
         const int t = item - D.item_begin;
-        const int x0 = (t % D.tiles_x) * kTile, y0 = (t / D.tiles_x) * kTile;
+        int tbx, tby;
+        tile_xy(t, D.tiles_x, D.inv_tiles_x, tbx, tby);
+        const int x0 = tbx * kTile, y0 = tby * kTile;
         const float2 gsum2 = f2(args.gsum, args.gsum);
-        // total weight of a window as the column pass accumulates it (row weight gsum, taps
-        // in order)
-        float s0 = 0.f;
-#pragma unroll
-        for (int d = 0; d <= 2 * kSsimRadius; d++) s0 = fmaf(args.g[d], args.gsum, s0);
-        const float2 s02 = f2(s0, s0);
+        const float2 s02 = f2(args.s0, args.s0);
         (void)ref_y;
         const MergeStage& S = M.st[buf];
         const MergeSrcDev& s = args.src[k];
@@ -506,6 +532,7 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
             float m11 = 0.f;
 #pragma unroll
             for (int d = 0; d <= 2 * kHalo; d++) {
+                if (d == kHalo) continue;  // the centre tap's deviations are exactly zero
                 const float2 g2 = f2(args.g[d], args.g[d]);
                 const float2 ab = __ffma2_rn(c, neg1, M.XY[yy][xx + d]);
                 const float2 gab = __fmul2_rn(g2, ab);
@@ -571,8 +598,9 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
             const float vx = b2.x - b1.x * b1.x, vy = b2.y - b1.y * b1.y,
                         cxy = b11 - b1.x * b1.y;
             const float ux = c.x + a1[q].x, uy = c.y + a1[q].y;
-            const float ssim = ((2.f * ux * uy + C1) * (2.f * cxy + C2)) /
-                               ((ux * ux + uy * uy + C1) * (vx + vy + C2));
+            // the denominator lies in [C1 C2, 2^33): the fast quotient is within 2 ulp
+            const float ssim = __fdividef((2.f * ux * uy + C1) * (2.f * cxy + C2),
+                                          (ux * ux + uy * uy + C1) * (vx + vy + C2));
             const float qv = ssim > 0.f ? ssim : 0.f;
             float wk = 0.f;
             if (x < w && y < h) {
@@ -602,12 +630,15 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int x = x0 + tx, y = y0 + ty0 + 8 * q;
-                if (x < w && y < h) oy[(size_t)y * w + x] = M.Ns[ty0 + 8 * q][tx] / M.Ds[ty0 + 8 * q][tx];
+                // D holds the reference's own weight (at least exp(-k/4)) and at most
+                // nsrc + 1: the fast quotient is within 2 ulp
+                if (x < w && y < h)
+                    oy[(size_t)y * w + x] = __fdividef(M.Ns[ty0 + 8 * q][tx], M.Ds[ty0 + 8 * q][tx]);
             }
             if (c_ok) {
                 const size_t o = (size_t)cy * cw + cx;
-                ou[o] = cnu / cden;
-                ov[o] = cnv / cden;
+                ou[o] = __fdividef(cnu, cden);
+                ov[o] = __fdividef(cnv, cden);
             }
         }
         __syncthreads();  // the staging buffer and the sums are reused by the next unit
@@ -686,6 +717,8 @@ static MergeStackDev merge_stack(const uint8_t* ref_y, const uint8_t* ref_u, con
         fsum += (double)a.g[d];
     }
     a.gsum = (float)fsum;
+    a.s0 = 0.f;
+    for (int d = 0; d <= 2 * kSsimRadius; d++) a.s0 = std::fma(a.g[d], a.gsum, a.s0);
     a.we_k = (float)(1.0 / (2.0 * we_sigma * we_sigma));
     bool async_ok = (w % 32) == 0;  // 16-byte rows for u8 luma and chroma planes
     auto al = [](const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; };
@@ -702,6 +735,7 @@ static MergeStackDev merge_stack(const uint8_t* ref_y, const uint8_t* ref_u, con
     D.w = w;
     D.h = h;
     D.tiles_x = (w + kTile - 1) / kTile;
+    D.inv_tiles_x = 1.f / (float)D.tiles_x;
     D.item_begin = 0;
     D.async_ok = async_ok ? 1 : 0;
     return D;

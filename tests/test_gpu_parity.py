@@ -329,6 +329,19 @@ def test_flow_full_size(hd, orc, five_mp):
     _flow_case(hd, orc, five_mp, cfg(32, 6))
 
 
+@pytest.mark.parametrize("w,h,T,R", [(96, 1928, 16, 4), (80, 1000, 16, 4), (64, 4200, 16, 4),
+                                     (48, 17, 8, 2)])
+def test_flow_column_pass_shapes(hd, orc, w, h, T, R):
+    """Heights that exercise the column pass's 64-row tiles and its carry chain: 1928 rows
+    end in a tile of 8 rows, 1000 rows in one of 40, 4200 rows make 66 tiles per column
+    (three rounds of the chain's 32-tile scan, carried across rounds), 17 rows are one
+    tile of which most rows lie below the frame."""
+    from paper_1504_01441_b300 import synth
+    spec = synth.StackSpec(w, h, ratios=((4, 1),), noise_sigma=1.0, field_amp=3.0, movers=0,
+                           chroma=False, n_blobs=max(4, w * h // 4000), n_rects=2)
+    _flow_case(hd, orc, synth.make_stack(spec, 23), cfg(T, R, grid_half=min(4, T // 2 - 1)))
+
+
 def test_flow_propagate_full_mode(hd, orc, vga):
     _flow_case(hd, orc, vga, cfg(propagate_full=1))
 
