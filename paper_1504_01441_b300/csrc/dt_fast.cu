@@ -361,16 +361,28 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
         if (!empty) {
         float v[3][LM];
         float wl[LM + 1];
+        // warps whose segments and their links all lie inside the row skip the frame tests
+        const int wp = tid >> 5;
+        if (wp > 0 && (32 * wp + 32) * LM < w) {
 #pragma unroll
-        for (int i = 0; i < LM; i++) {
-            const int x = x0 + i;
-            const bool in = x < w;
-            v[0][i] = in ? s0[x] : 0.f;
-            v[1][i] = in ? s1[x] : 0.f;
-            v[2][i] = in ? s2[x] : 0.f;
-            wl[i] = (in && x > 0) ? lut[absdiff(g[x], g[x - 1])] : 0.f;
-        }
-        {
+            for (int i = 0; i < LM; i++) {
+                const int x = x0 + i;
+                v[0][i] = s0[x];
+                v[1][i] = s1[x];
+                v[2][i] = s2[x];
+                wl[i] = lut[absdiff(g[x], g[x - 1])];
+            }
+            wl[LM] = lut[absdiff(g[x0 + LM], g[x0 + LM - 1])];
+        } else {
+#pragma unroll
+            for (int i = 0; i < LM; i++) {
+                const int x = x0 + i;
+                const bool in = x < w;
+                v[0][i] = in ? s0[x] : 0.f;
+                v[1][i] = in ? s1[x] : 0.f;
+                v[2][i] = in ? s2[x] : 0.f;
+                wl[i] = (in && x > 0) ? lut[absdiff(g[x], g[x - 1])] : 0.f;
+            }
             const int x = x0 + LM;
             wl[LM] = (x < w) ? lut[absdiff(g[x], g[x - 1])] : 0.f;
         }
@@ -442,6 +454,129 @@ __device__ __forceinline__ Aff4 compose4(const Aff4& f, const Aff4& s)
                 fmaf(s.A, f.B3, s.B3)};
 }
 
+// One 8-row segment of a column tile in registers: rows r0 + sg*8 + i of column
+// `lane`; plane k of the tile at P + k*kTR*kTW (rows of kTW floats); G row j is global
+// row r0 - 1 + j. kInterior: every row of the tile and the row after it lie inside the
+// frame (0 < r0 and r0 + kTR < h), so no element needs the frame tests.
+template <bool kInterior>
+__device__ __forceinline__ void tile_seg_load(const float* P, const uint8_t* G, const float* lut,
+                                              int sg, int lane, int r0, int h,
+                                              float (&v)[3][kTLS], float (&wl)[kTLS + 1])
+{
+#pragma unroll
+    for (int i = 0; i < kTLS; i++) {
+        const int rr = sg * kTLS + i, r = r0 + rr;
+        const bool in = kInterior || r < h;
+        v[0][i] = in ? P[(0 * kTR + rr) * kTW + lane] : 0.f;
+        v[1][i] = in ? P[(1 * kTR + rr) * kTW + lane] : 0.f;
+        v[2][i] = in ? P[(2 * kTR + rr) * kTW + lane] : 0.f;
+        const float l = lut[absdiff(G[(rr + 1) * kTW + lane], G[rr * kTW + lane])];
+        wl[i] = (kInterior || (r > 0 && r < h)) ? l : 0.f;
+    }
+    const int rr = sg * kTLS + kTLS, r = r0 + rr;
+    const float l = lut[absdiff(G[(rr + 1) * kTW + lane], G[rr * kTW + lane])];
+    wl[kTLS] = (kInterior || r < h) ? l : 0.f;
+}
+
+// Phase A on one tile (all threads): the tile's nine values of column `lane`,
+// out[k * ostride] = A_f, B_f[3] (written by the last segment's warp) and K0[3], Q, S
+// (by the first segment's warp). `agg` is free again on return.
+__device__ __forceinline__ void tile_maps(float (&v)[3][kTLS], const float (&wl)[kTLS + 1],
+                                          Aff4 (*agg)[kTW], int sg, int lane, bool colok,
+                                          float* out, size_t ostride)
+{
+    const Aff m = sweep_fwd<kTLS>(v, wl, kTLS);
+    agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
+    __syncthreads();
+    Aff pre{1.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < sg; q++) {
+        const Aff4 a = agg[q][lane];
+        pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+    }
+    if (sg == kTSeg - 1 && colok) {
+        const Aff f = compose(pre, m);
+        out[0 * ostride] = f.A;
+        out[1 * ostride] = f.B0;
+        out[2 * ostride] = f.B1;
+        out[3 * ostride] = f.B2;
+    }
+    carry_fwd<kTLS>(v, wl, kTLS, pre);  // v = J0
+    float pv[kTLS];
+    float lp = pre.A;
+#pragma unroll
+    for (int i = 0; i < kTLS; i++) {
+        lp *= wl[i];
+        pv[i] = lp;
+    }
+    __syncthreads();
+    float k0 = 0.f, k1 = 0.f, k2 = 0.f, k3 = 0.f, A = 1.f;
+#pragma unroll
+    for (int i = kTLS - 1; i >= 0; i--) {
+        const float wt = wl[i + 1];
+        k0 = fmaf(wt, k0 - v[0][i], v[0][i]);
+        k1 = fmaf(wt, k1 - v[1][i], v[1][i]);
+        k2 = fmaf(wt, k2 - v[2][i], v[2][i]);
+        k3 = fmaf(wt, k3 - pv[i], pv[i]);
+        A *= wt;
+    }
+    agg[sg][lane] = Aff4{A, k0, k1, k2, k3};
+    __syncthreads();
+    if (sg == 0 && colok) {
+        Aff4 suf{1.f, 0.f, 0.f, 0.f, 0.f};
+        for (int q = kTSeg - 1; q > 0; q--) suf = compose4(suf, agg[q][lane]);
+        const Aff4 t4 = compose4(suf, agg[0][lane]);
+        out[4 * ostride] = t4.B0;
+        out[5 * ostride] = t4.B1;
+        out[6 * ostride] = t4.B2;
+        out[7 * ostride] = t4.B3;
+        out[8 * ostride] = t4.A;
+    }
+    __syncthreads();  // agg is reused by the next tile
+}
+
+// Phase C on one tile (all threads): the sweeps again from the exact carries
+// cr = {c[3] entering at the top, c'[3] entering at the bottom}; the results replace the
+// tile's rows in shared memory (the flow u, v in planes 0 and 1 on the final pass: the
+// sums over N, which is at least flow_eps = 1e-20 there, so the fast quotient is within
+// 2 ulp).
+__device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl)[kTLS + 1],
+                                           Aff4 (*agg)[kTW], int sg, int lane, const float (&cr)[6],
+                                           float* P, int final_pass, float flow_eps)
+{
+    Aff m = sweep_fwd<kTLS>(v, wl, kTLS);
+    agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
+    __syncthreads();
+    Aff pre = Aff{0.f, cr[0], cr[1], cr[2]};  // zero carries outside the image
+    for (int q = 0; q < sg; q++) {
+        const Aff4 a = agg[q][lane];
+        pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+    }
+    carry_fwd<kTLS>(v, wl, kTLS, pre);
+    __syncthreads();
+    m = sweep_bwd<kTLS>(v, wl, kTLS);
+    agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
+    __syncthreads();
+    Aff suf = Aff{0.f, cr[3], cr[4], cr[5]};
+    for (int q = kTSeg - 1; q > sg; q--) {
+        const Aff4 a = agg[q][lane];
+        suf = compose(suf, Aff{a.A, a.B0, a.B1, a.B2});
+    }
+    carry_bwd<kTLS>(v, wl, kTLS, suf);
+#pragma unroll
+    for (int i = 0; i < kTLS; i++) {
+        const int rr = sg * kTLS + i;
+        if (final_pass) {
+            const bool okn = v[2][i] >= flow_eps;
+            P[(0 * kTR + rr) * kTW + lane] = okn ? __fdividef(v[0][i], v[2][i]) : 0.f;
+            P[(1 * kTR + rr) * kTW + lane] = okn ? __fdividef(v[1][i], v[2][i]) : 0.f;
+        } else {
+            P[(0 * kTR + rr) * kTW + lane] = v[0][i];
+            P[(1 * kTR + rr) * kTW + lane] = v[1][i];
+            P[(2 * kTR + rr) * kTW + lane] = v[2][i];
+        }
+    }
+}
+
 // Persistent, double-buffered tile pass over items i = tile * ntx + strip.
 // kApply = false: phase A (tile maps to agg_out); true: phase C (apply carries, store).
 template <bool kApply>
@@ -508,101 +643,17 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
         float* P = reinterpret_cast<float*>(smt + b * kTileBuf);
         const uint8_t* G = smt + b * kTileBuf + 3 * kTR * kTW * 4;
         const int x0 = (item % ntx) * kTW, tile = item / ntx, r0 = tile * kTR;
-        // registers: rows r0 + sg*8 + i of column x0 + lane; G row j is global row r0-1+j
         float v[3][kTLS], wl[kTLS + 1];
-#pragma unroll
-        for (int i = 0; i < kTLS; i++) {
-            const int rr = sg * kTLS + i, r = r0 + rr;
-            const bool in = r < h;
-            v[0][i] = in ? P[(0 * kTR + rr) * kTW + lane] : 0.f;
-            v[1][i] = in ? P[(1 * kTR + rr) * kTW + lane] : 0.f;
-            v[2][i] = in ? P[(2 * kTR + rr) * kTW + lane] : 0.f;
-            wl[i] = (r > 0 && r < h) ? lut[absdiff(G[(rr + 1) * kTW + lane], G[rr * kTW + lane])] : 0.f;
-        }
-        {
-            const int rr = sg * kTLS + kTLS, r = r0 + rr;
-            wl[kTLS] = (r < h) ? lut[absdiff(G[(rr + 1) * kTW + lane], G[rr * kTW + lane])] : 0.f;
-        }
-        const bool colok = x0 + lane < w;
-        const size_t ao = (size_t)(x0 + lane) * kAgg * ntile + tile;  // agg[x][k][t]
-        Aff m = sweep_fwd<kTLS>(v, wl, kTLS);
-        agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
-        __syncthreads();
+        if (r0 > 0 && r0 + kTR < h)
+            tile_seg_load<true>(P, G, lut, sg, lane, r0, h, v, wl);
+        else
+            tile_seg_load<false>(P, G, lut, sg, lane, r0, h, v, wl);
         if (!kApply) {
-            Aff pre{1.f, 0.f, 0.f, 0.f};
-            for (int q = 0; q < sg; q++) {
-                const Aff4 a = agg[q][lane];
-                pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
-            }
-            if (sg == kTSeg - 1 && colok) {
-                const Aff f = compose(pre, m);
-                agg_out[ao + 0 * ntile] = f.A;
-                agg_out[ao + 1 * ntile] = f.B0;
-                agg_out[ao + 2 * ntile] = f.B1;
-                agg_out[ao + 3 * ntile] = f.B2;
-            }
-            carry_fwd<kTLS>(v, wl, kTLS, pre);  // v = J0
-            float pv[kTLS];
-            float lp = pre.A;
-#pragma unroll
-            for (int i = 0; i < kTLS; i++) {
-                lp *= wl[i];
-                pv[i] = lp;
-            }
-            __syncthreads();
-            float k0 = 0.f, k1 = 0.f, k2 = 0.f, k3 = 0.f, A = 1.f;
-#pragma unroll
-            for (int i = kTLS - 1; i >= 0; i--) {
-                const float wt = wl[i + 1];
-                k0 = fmaf(wt, k0 - v[0][i], v[0][i]);
-                k1 = fmaf(wt, k1 - v[1][i], v[1][i]);
-                k2 = fmaf(wt, k2 - v[2][i], v[2][i]);
-                k3 = fmaf(wt, k3 - pv[i], pv[i]);
-                A *= wt;
-            }
-            agg[sg][lane] = Aff4{A, k0, k1, k2, k3};
-            __syncthreads();
-            if (sg == 0 && colok) {
-                Aff4 suf{1.f, 0.f, 0.f, 0.f, 0.f};
-                for (int q = kTSeg - 1; q > 0; q--) suf = compose4(suf, agg[q][lane]);
-                const Aff4 t4 = compose4(suf, agg[0][lane]);
-                agg_out[ao + 4 * ntile] = t4.B0;
-                agg_out[ao + 5 * ntile] = t4.B1;
-                agg_out[ao + 6 * ntile] = t4.B2;
-                agg_out[ao + 7 * ntile] = t4.B3;
-                agg_out[ao + 8 * ntile] = t4.A;
-            }
-            __syncthreads();  // agg reused by the next item
+            const bool colok = x0 + lane < w;
+            tile_maps(v, wl, agg, sg, lane, colok, agg_out + (size_t)(x0 + lane) * kAgg * ntile + tile,
+                      (size_t)ntile);
         } else {
-            Aff pre = Aff{0.f, cr[0], cr[1], cr[2]};  // zero carries outside the image
-            for (int q = 0; q < sg; q++) {
-                const Aff4 a = agg[q][lane];
-                pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
-            }
-            carry_fwd<kTLS>(v, wl, kTLS, pre);
-            __syncthreads();
-            m = sweep_bwd<kTLS>(v, wl, kTLS);
-            agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
-            __syncthreads();
-            Aff suf = Aff{0.f, cr[3], cr[4], cr[5]};
-            for (int q = kTSeg - 1; q > sg; q--) {
-                const Aff4 a = agg[q][lane];
-                suf = compose(suf, Aff{a.A, a.B0, a.B1, a.B2});
-            }
-            carry_bwd<kTLS>(v, wl, kTLS, suf);
-#pragma unroll
-            for (int i = 0; i < kTLS; i++) {
-                const int rr = sg * kTLS + i;
-                if (final_pass) {
-                    const bool okn = v[2][i] >= flow_eps;
-                    P[(0 * kTR + rr) * kTW + lane] = okn ? v[0][i] / v[2][i] : 0.f;
-                    P[(1 * kTR + rr) * kTW + lane] = okn ? v[1][i] / v[2][i] : 0.f;
-                } else {
-                    P[(0 * kTR + rr) * kTW + lane] = v[0][i];
-                    P[(1 * kTR + rr) * kTW + lane] = v[1][i];
-                    P[(2 * kTR + rr) * kTW + lane] = v[2][i];
-                }
-            }
+            tile_apply(v, wl, agg, sg, lane, cr, P, final_pass, flow_eps);
             fence_async_smem();
             __syncthreads();  // also: agg reads of this item are done
             if (tid == 0) {
