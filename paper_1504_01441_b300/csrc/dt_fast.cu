@@ -49,7 +49,7 @@ __device__ __forceinline__ Aff shfl_aff(const Aff& a, int d)
                __shfl_down_sync(0xffffffffu, a.B1, d), __shfl_down_sync(0xffffffffu, a.B2, d)};
 }
 
-__device__ __forceinline__ int absdiff(int a, int b) { return a > b ? a - b : b - a; }
+__device__ __forceinline__ int absdiff(int a, int b) { return (int)__sad(a, b, 0u); }
 
 // ---------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -225,11 +225,16 @@ __device__ __forceinline__ Aff seg_scan(Aff mine, Aff (*tot)[kCols], int col)
     if (kUp ? (sl == 0) : (sl == nseg - 1)) exc = Aff{1.f, 0.f, 0.f, 0.f};
     if (kUp ? (sl == nseg - 1) : (sl == 0)) tot[warp][col] = inc;
     __syncthreads();
+    // unrolled and predicated: the warps' maps are all loaded before the chain
     Aff pre{1.f, 0.f, 0.f, 0.f};
     if (kUp) {
-        for (int k = 0; k < warp; k++) pre = compose(pre, tot[k][col]);
+#pragma unroll
+        for (int k = 0; k < kWarps - 1; k++)
+            if (k < warp) pre = compose(pre, tot[k][col]);
     } else {
-        for (int k = kWarps - 1; k > warp; k--) pre = compose(pre, tot[k][col]);
+#pragma unroll
+        for (int k = kWarps - 1; k > 0; k--)
+            if (k > warp) pre = compose(pre, tot[k][col]);
     }
     __syncthreads();
     return compose(pre, exc);
@@ -489,9 +494,12 @@ __device__ __forceinline__ void tile_maps(float (&v)[3][kTLS], const float (&wl)
     agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
     __syncthreads();
     Aff pre{1.f, 0.f, 0.f, 0.f};
-    for (int q = 0; q < sg; q++) {
-        const Aff4 a = agg[q][lane];
-        pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+#pragma unroll
+    for (int q = 0; q < kTSeg - 1; q++) {
+        if (q < sg) {
+            const Aff4 a = agg[q][lane];
+            pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+        }
     }
     if (sg == kTSeg - 1 && colok) {
         const Aff f = compose(pre, m);
@@ -523,6 +531,7 @@ __device__ __forceinline__ void tile_maps(float (&v)[3][kTLS], const float (&wl)
     __syncthreads();
     if (sg == 0 && colok) {
         Aff4 suf{1.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
         for (int q = kTSeg - 1; q > 0; q--) suf = compose4(suf, agg[q][lane]);
         const Aff4 t4 = compose4(suf, agg[0][lane]);
         out[4 * ostride] = t4.B0;
@@ -547,9 +556,12 @@ __device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl
     agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
     __syncthreads();
     Aff pre = Aff{0.f, cr[0], cr[1], cr[2]};  // zero carries outside the image
-    for (int q = 0; q < sg; q++) {
-        const Aff4 a = agg[q][lane];
-        pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+#pragma unroll
+    for (int q = 0; q < kTSeg - 1; q++) {
+        if (q < sg) {
+            const Aff4 a = agg[q][lane];
+            pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+        }
     }
     carry_fwd<kTLS>(v, wl, kTLS, pre);
     __syncthreads();
@@ -557,9 +569,12 @@ __device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl
     agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
     __syncthreads();
     Aff suf = Aff{0.f, cr[3], cr[4], cr[5]};
-    for (int q = kTSeg - 1; q > sg; q--) {
-        const Aff4 a = agg[q][lane];
-        suf = compose(suf, Aff{a.A, a.B0, a.B1, a.B2});
+#pragma unroll
+    for (int q = kTSeg - 1; q > 0; q--) {
+        if (q > sg) {
+            const Aff4 a = agg[q][lane];
+            suf = compose(suf, Aff{a.A, a.B0, a.B1, a.B2});
+        }
     }
     carry_bwd<kTLS>(v, wl, kTLS, suf);
 #pragma unroll
