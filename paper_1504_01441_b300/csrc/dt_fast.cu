@@ -683,7 +683,8 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
 
 // One warp per column; lane = tile (32 tiles per round, carried across rounds):
 // forward carries by an exclusive shuffle scan of the maps (A_f, B_f), then the
-// backward carries by a reverse exclusive scan of (S, K0 + Q c).
+// backward carries by a reverse exclusive scan of (S, K0 + Q c). Columns of at most
+// 32 tiles (frames up to 2,048 rows) take one round from registers.
 __global__ void __launch_bounds__(256) k_dt_cols_chain(const float* __restrict__ agg, int w,
                                                       int ntile, float* __restrict__ car)
 {
@@ -691,6 +692,42 @@ __global__ void __launch_bounds__(256) k_dt_cols_chain(const float* __restrict__
     if (x >= w) return;
     const float* ag = agg + (size_t)x * kAgg * ntile;  // ag[k * ntile + t]
     float* ca = car + (size_t)x * kCar * ntile;         // ca[k * ntile + t]
+    if (ntile <= 32) {
+        // one round: the nine values of each tile loaded together, and the forward
+        // carries kept in registers for the backward scan
+        const int t = lane;
+        const bool in = t < ntile;
+        float a[kAgg];
+#pragma unroll
+        for (int k = 0; k < kAgg; k++) a[k] = in ? __ldg(ag + k * ntile + t) : 0.f;
+        const Aff id{1.f, 0.f, 0.f, 0.f};
+        Aff inc = in ? Aff{a[0], a[1], a[2], a[3]} : id;
+        for (int d = 1; d < 32; d <<= 1) {
+            const Aff q = shfl_aff<true>(inc, d);
+            if (lane >= d) inc = compose(q, inc);
+        }
+        Aff exc = shfl_aff<true>(inc, 1);
+        if (lane == 0) exc = id;
+        const Aff c = compose(id, exc);
+        inc = in ? Aff{a[8], fmaf(a[7], c.B0, a[4]), fmaf(a[7], c.B1, a[5]), fmaf(a[7], c.B2, a[6])}
+                 : id;
+        for (int d = 1; d < 32; d <<= 1) {
+            const Aff q = shfl_aff<false>(inc, d);
+            if (lane + d < 32) inc = compose(q, inc);
+        }
+        exc = shfl_aff<false>(inc, 1);
+        if (lane == 31) exc = id;
+        const Aff cb = compose(id, exc);
+        if (in) {
+            ca[t] = c.B0;
+            ca[ntile + t] = c.B1;
+            ca[2 * ntile + t] = c.B2;
+            ca[3 * ntile + t] = cb.B0;
+            ca[4 * ntile + t] = cb.B1;
+            ca[5 * ntile + t] = cb.B2;
+        }
+        return;
+    }
     Aff run{1.f, 0.f, 0.f, 0.f};  // maps of the tiles before this round
     for (int t0 = 0; t0 < ntile; t0 += 32) {
         const int t = t0 + lane;
