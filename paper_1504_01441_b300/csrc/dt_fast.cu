@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
 //     at the tile's top row as a function of both carries,
 //     K_top = K0 + Q c + S c' (c: forward carry entering at the top, c': backward
 //     carry entering at the bottom; Q because the backward pass is linear in J =
-//     J0 + P c);
+//     J0 + P c): each segment's own map, folded over the tile's segments;
 //  B) one thread per column chains the carries down and up the tiles;
 //  C) every tile recomputes its sweeps with the exact carries and stores.
 // Tiles never wait on one another; phase C re-reads the tile from L2.
@@ -453,11 +453,6 @@ struct Aff4 {
     float A, B0, B1, B2, B3;
 };
 
-__device__ __forceinline__ Aff4 compose4(const Aff4& f, const Aff4& s)
-{
-    return Aff4{s.A * f.A, fmaf(s.A, f.B0, s.B0), fmaf(s.A, f.B1, s.B1), fmaf(s.A, f.B2, s.B2),
-                fmaf(s.A, f.B3, s.B3)};
-}
 
 // One 8-row segment of a column tile in registers: rows r0 + sg*8 + i of column
 // `lane`; plane k of the tile at P + k*kTR*kTW (rows of kTW floats); G row j is global
@@ -483,41 +478,52 @@ __device__ __forceinline__ void tile_seg_load(const float* P, const uint8_t* G, 
     wl[kTLS] = (kInterior || r < h) ? l : 0.f;
 }
 
-// Phase A on one tile (all threads): the tile's nine values of column `lane`,
-// out[k * ostride] = A_f, B_f[3] (written by the last segment's warp) and K0[3], Q, S
-// (by the first segment's warp). `agg` is free again on return.
-__device__ __forceinline__ void tile_maps(float (&v)[3][kTLS], const float (&wl)[kTLS + 1],
-                                          Aff4 (*agg)[kTW], int sg, int lane, bool colok,
-                                          float* out, size_t ostride)
+// Nine values of a row range of one column, as functions of the carries entering it:
+// forward J_bottom = A c + B (c: J of the row above the range); backward K_top = K0 + Q c +
+// S c' (c': K of the row below). fold(u, d) joins a range u with the range d below it:
+// A = Ad Au, B = Ad Bu + Bd, K0 = K0u + Su (K0d + Qd Bu), Q = Qu + Su Qd Au, S = Su Sd.
+struct Map9 {
+    float A, B[3], K0[3], Q, S;
+};
+
+__device__ __forceinline__ Map9 fold(const Map9& u, const Map9& d)
 {
-    const Aff m = sweep_fwd<kTLS>(v, wl, kTLS);
-    agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
-    __syncthreads();
-    Aff pre{1.f, 0.f, 0.f, 0.f};
+    Map9 r;
+    r.A = d.A * u.A;
 #pragma unroll
-    for (int q = 0; q < kTSeg - 1; q++) {
-        if (q < sg) {
-            const Aff4 a = agg[q][lane];
-            pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
-        }
+    for (int p = 0; p < 3; p++) {
+        r.B[p] = fmaf(d.A, u.B[p], d.B[p]);
+        r.K0[p] = fmaf(u.S, fmaf(d.Q, u.B[p], d.K0[p]), u.K0[p]);
     }
-    if (sg == kTSeg - 1 && colok) {
-        const Aff f = compose(pre, m);
-        out[0 * ostride] = f.A;
-        out[1 * ostride] = f.B0;
-        out[2 * ostride] = f.B1;
-        out[3 * ostride] = f.B2;
-    }
-    carry_fwd<kTLS>(v, wl, kTLS, pre);  // v = J0
-    float pv[kTLS];
-    float lp = pre.A;
+    r.Q = fmaf(u.S * d.Q, u.A, u.Q);
+    r.S = u.S * d.S;
+    return r;
+}
+
+// Phase A on one tile (all threads): each 8-row segment's own Map9 (both sweeps from
+// zero carries, with the derivative of the backward sweep in the forward carry carried
+// along); the first segment's warp folds the eight, top to bottom, into the tile's nine
+// values of column `lane`, out[k * ostride] in Map9 order. seg ([9][kTSeg][kTW] floats)
+// is free again on return.
+__device__ __forceinline__ void tile_maps(float (&v)[3][kTLS], const float (&wl)[kTLS + 1],
+                                          float* seg, int sg, int lane, bool colok, float* out,
+                                          size_t ostride)
+{
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f, A = 1.f;
+    float pv[kTLS];  // d J / d c: products of the links from the segment's top
 #pragma unroll
     for (int i = 0; i < kTLS; i++) {
-        lp *= wl[i];
-        pv[i] = lp;
+        const float wt = wl[i];
+        y0 = fmaf(wt, y0 - v[0][i], v[0][i]);
+        y1 = fmaf(wt, y1 - v[1][i], v[1][i]);
+        y2 = fmaf(wt, y2 - v[2][i], v[2][i]);
+        A *= wt;
+        pv[i] = A;
+        v[0][i] = y0;
+        v[1][i] = y1;
+        v[2][i] = y2;
     }
-    __syncthreads();
-    float k0 = 0.f, k1 = 0.f, k2 = 0.f, k3 = 0.f, A = 1.f;
+    float k0 = 0.f, k1 = 0.f, k2 = 0.f, k3 = 0.f, S = 1.f;
 #pragma unroll
     for (int i = kTLS - 1; i >= 0; i--) {
         const float wt = wl[i + 1];
@@ -525,22 +531,33 @@ __device__ __forceinline__ void tile_maps(float (&v)[3][kTLS], const float (&wl)
         k1 = fmaf(wt, k1 - v[1][i], v[1][i]);
         k2 = fmaf(wt, k2 - v[2][i], v[2][i]);
         k3 = fmaf(wt, k3 - pv[i], pv[i]);
-        A *= wt;
+        S *= wt;
     }
-    agg[sg][lane] = Aff4{A, k0, k1, k2, k3};
+    const float mv[9] = {A, y0, y1, y2, k0, k1, k2, k3, S};
+#pragma unroll
+    for (int k = 0; k < 9; k++) seg[(k * kTSeg + sg) * kTW + lane] = mv[k];
     __syncthreads();
     if (sg == 0 && colok) {
-        Aff4 suf{1.f, 0.f, 0.f, 0.f, 0.f};
+        auto at = [&](int q) {
+            const float* p = seg + q * kTW + lane;
+            return Map9{p[0], {p[kTSeg * kTW], p[2 * kTSeg * kTW], p[3 * kTSeg * kTW]},
+                        {p[4 * kTSeg * kTW], p[5 * kTSeg * kTW], p[6 * kTSeg * kTW]},
+                        p[7 * kTSeg * kTW], p[8 * kTSeg * kTW]};
+        };
+        Map9 m = at(0);
 #pragma unroll
-        for (int q = kTSeg - 1; q > 0; q--) suf = compose4(suf, agg[q][lane]);
-        const Aff4 t4 = compose4(suf, agg[0][lane]);
-        out[4 * ostride] = t4.B0;
-        out[5 * ostride] = t4.B1;
-        out[6 * ostride] = t4.B2;
-        out[7 * ostride] = t4.B3;
-        out[8 * ostride] = t4.A;
+        for (int q = 1; q < kTSeg; q++) m = fold(m, at(q));
+        out[0 * ostride] = m.A;
+        out[1 * ostride] = m.B[0];
+        out[2 * ostride] = m.B[1];
+        out[3 * ostride] = m.B[2];
+        out[4 * ostride] = m.K0[0];
+        out[5 * ostride] = m.K0[1];
+        out[6 * ostride] = m.K0[2];
+        out[7 * ostride] = m.Q;
+        out[8 * ostride] = m.S;
     }
-    __syncthreads();  // agg is reused by the next tile
+    __syncthreads();  // seg is reused by the next tile
 }
 
 // Phase C on one tile (all threads): the sweeps again from the exact carries
@@ -603,7 +620,9 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
 {
     extern __shared__ __align__(1024) uint8_t smt[];
     __shared__ float lut[256];
-    __shared__ Aff4 agg[kTSeg][kTW];
+    // segment maps: [9][kTSeg][kTW] floats in phase A, Aff4 [kTSeg][kTW] in phase C
+    __shared__ __align__(16) float segbuf[kApply ? kTSeg * kTW * 5 : kTSeg * kTW * kAgg];
+    Aff4 (*agg)[kTW] = reinterpret_cast<Aff4 (*)[kTW]>(segbuf);
     __shared__ __align__(8) uint64_t bar[2];
     const int tid = threadIdx.x, lane = tid & 31, sg = tid >> 5;
     for (int i = tid; i < 256; i += blockDim.x) lut[i] = lut_in.w[i];
@@ -665,8 +684,8 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
             tile_seg_load<false>(P, G, lut, sg, lane, r0, h, v, wl);
         if (!kApply) {
             const bool colok = x0 + lane < w;
-            tile_maps(v, wl, agg, sg, lane, colok, agg_out + (size_t)(x0 + lane) * kAgg * ntile + tile,
-                      (size_t)ntile);
+            tile_maps(v, wl, segbuf, sg, lane, colok,
+                      agg_out + (size_t)(x0 + lane) * kAgg * ntile + tile, (size_t)ntile);
         } else {
             tile_apply(v, wl, agg, sg, lane, cr, P, final_pass, flow_eps);
             fence_async_smem();
