@@ -297,6 +297,7 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
         if (tid == 0) {
             float* B = sm + b * kBuf;
             const size_t row = (size_t)y * ppitch;
+            fence_async_smem();  // earlier reads of the buffer come before the copy's writes
             mbar_expect(&bar[b], bytes);
             if (!kSparse) {
                 bulk_load(B, P0 + row, ppitch * 4, &bar[b]);
@@ -561,10 +562,10 @@ __device__ __forceinline__ void tile_maps(float (&v)[3][kTLS], const float (&wl)
 }
 
 // Phase C on one tile (all threads): the sweeps again from the exact carries
-// cr = {c[3] entering at the top, c'[3] entering at the bottom}; the results replace the
-// tile's rows in shared memory (the flow u, v in planes 0 and 1 on the final pass: the
-// sums over N, which is at least flow_eps = 1e-20 there, so the fast quotient is within
-// 2 ulp).
+// cr = {c[3] entering at the top, c'[3] entering at the bottom}; the results go to the
+// output planes P in shared memory, once the store that last read them has drained (the
+// flow u, v in planes 0 and 1 on the final pass: the sums over N, which is at least
+// flow_eps = 1e-20 there, so the fast quotient is within 2 ulp).
 __device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl)[kTLS + 1],
                                            Aff4 (*agg)[kTW], int sg, int lane, const float (&cr)[6],
                                            float* P, int final_pass, float flow_eps)
@@ -584,6 +585,7 @@ __device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl
     __syncthreads();
     m = sweep_bwd<kTLS>(v, wl, kTLS);
     agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
+    if (threadIdx.x == 0) bulk_wait_read();  // the output buffer's previous store has left it
     __syncthreads();
     Aff suf = Aff{0.f, cr[3], cr[4], cr[5]};
 #pragma unroll
@@ -609,8 +611,12 @@ __device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl
     }
 }
 
-// Persistent, double-buffered tile pass over items i = tile * ntx + strip.
-// kApply = false: phase A (tile maps to agg_out); true: phase C (apply carries, store).
+// Persistent tile pass over items i = tile * ntx + strip. An item's tile lands in the
+// input buffer; once every thread holds its segment in registers, the next item's copy is
+// issued into the same buffer, so the copy overlaps the item's arithmetic.
+// kApply = false: phase A (tile maps to agg_out). kApply = true: phase C (apply the
+// carries); the results go out through a second buffer, whose previous store has had the
+// item's arithmetic to drain before the buffer is written again.
 template <bool kApply>
 __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMaps maps, int w,
                                                    int h, int ntx, int ntile, DtLut lut_in,
@@ -618,41 +624,35 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
                                                    const float* __restrict__ car, int final_pass,
                                                    float flow_eps, int* err)
 {
-    extern __shared__ __align__(1024) uint8_t smt[];
+    extern __shared__ __align__(1024) uint8_t smt[];  // input tile, then (phase C) output planes
     __shared__ float lut[256];
     // segment maps: [9][kTSeg][kTW] floats in phase A, Aff4 [kTSeg][kTW] in phase C
     __shared__ __align__(16) float segbuf[kApply ? kTSeg * kTW * 5 : kTSeg * kTW * kAgg];
     Aff4 (*agg)[kTW] = reinterpret_cast<Aff4 (*)[kTW]>(segbuf);
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x, lane = tid & 31, sg = tid >> 5;
     for (int i = tid; i < 256; i += blockDim.x) lut[i] = lut_in.w[i];
-    if (tid == 0) {
-        mbar_init(&bar[0]);
-        mbar_init(&bar[1]);
-    }
+    if (tid == 0) mbar_init(&bar);
     __syncthreads();
+    float* P = reinterpret_cast<float*>(smt);
+    const uint8_t* G = smt + 3 * kTR * kTW * 4;
+    float* Q = reinterpret_cast<float*>(smt + kTileBuf);
     const int nitems = ntx * ntile;
-    auto issue = [&](int item, int b) {
+    auto issue = [&](int item) {
         if (tid == 0) {
-            float* P = reinterpret_cast<float*>(smt + b * kTileBuf);
-            uint8_t* G = smt + b * kTileBuf + 3 * kTR * kTW * 4;
             const int x0 = (item % ntx) * kTW, r0 = (item / ntx) * kTR;
-            mbar_expect(&bar[b], 3u * kTR * kTW * 4u + kGRows * kTW);
-            for (int k = 0; k < 3; k++) tma_load_2d(P + k * kTR * kTW, &maps.in[k], x0, r0, &bar[b]);
-            tma_load_2d(G, &maps.guide, x0, r0 - 1, &bar[b]);
+            // the threads' reads of the buffer (ordered before this by a barrier) come
+            // before the copy's writes into it
+            fence_async_smem();
+            mbar_expect(&bar, 3u * kTR * kTW * 4u + kGRows * kTW);
+            for (int k = 0; k < 3; k++) tma_load_2d(P + k * kTR * kTW, &maps.in[k], x0, r0, &bar);
+            tma_load_2d(smt + 3 * kTR * kTW * 4, &maps.guide, x0, r0 - 1, &bar);
         }
     };
-    uint32_t ph0 = 0, ph1 = 0;
+    uint32_t ph = 0;
     int item = blockIdx.x;
-    if (item < nitems) issue(item, 0);
-    for (int k = 0; item < nitems; item += gridDim.x, k++) {
-        const int b = k & 1;
-        const int nx = item + gridDim.x;
-        if (nx < nitems) {
-            if (kApply && tid == 0) bulk_wait_read();  // the store of item k-1 left buffer 1-b
-            if (!kApply) __syncthreads();             // all threads are done reading buffer 1-b
-            issue(nx, 1 - b);
-        }
+    if (item < nitems) issue(item);
+    for (; item < nitems; item += gridDim.x) {
         // phase C: this item's six carries (written by the chain kernel), loaded before
         // the wait for the tile so that their latency overlaps it
         float cr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -664,35 +664,35 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
                 for (int q = 0; q < 6; q++) cr[q] = __ldg(car + c0 + (size_t)q * ntile);
             }
         }
-        const bool ok = __syncthreads_and(mbar_wait(&bar[b], b ? ph1 : ph0));
-        if (b) ph1 ^= 1u; else ph0 ^= 1u;
+        const bool ok = __syncthreads_and(mbar_wait(&bar, ph));
+        ph ^= 1u;
         if (!ok) {
             if (tid == 0) {
                 atomicExch(err, 1);
-                mbar_wait(&bar[1 - b], b ? ph0 : ph1);
+                mbar_wait(&bar, ph ^ 1u);  // no copy may land after the CTA has left
                 bulk_wait_read();
             }
             return;
         }
-        float* P = reinterpret_cast<float*>(smt + b * kTileBuf);
-        const uint8_t* G = smt + b * kTileBuf + 3 * kTR * kTW * 4;
         const int x0 = (item % ntx) * kTW, tile = item / ntx, r0 = tile * kTR;
         float v[3][kTLS], wl[kTLS + 1];
         if (r0 > 0 && r0 + kTR < h)
             tile_seg_load<true>(P, G, lut, sg, lane, r0, h, v, wl);
         else
             tile_seg_load<false>(P, G, lut, sg, lane, r0, h, v, wl);
+        __syncthreads();  // every thread holds its segment: the input buffer is free
+        if (item + (int)gridDim.x < nitems) issue(item + gridDim.x);
         if (!kApply) {
             const bool colok = x0 + lane < w;
             tile_maps(v, wl, segbuf, sg, lane, colok,
                       agg_out + (size_t)(x0 + lane) * kAgg * ntile + tile, (size_t)ntile);
         } else {
-            tile_apply(v, wl, agg, sg, lane, cr, P, final_pass, flow_eps);
+            tile_apply(v, wl, agg, sg, lane, cr, Q, final_pass, flow_eps);
             fence_async_smem();
             __syncthreads();  // also: agg reads of this item are done
             if (tid == 0) {
                 const int np = final_pass ? 2 : 3;
-                for (int q = 0; q < np; q++) tma_store_2d(&maps.out[q], x0, r0, P + q * kTR * kTW);
+                for (int q = 0; q < np; q++) tma_store_2d(&maps.out[q], x0, r0, Q + q * kTR * kTW);
                 bulk_commit();
             }
         }
@@ -858,19 +858,28 @@ int sm_count()
 void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int final_pass,
                        float eps, float* agg, float* car, int* err, cudaStream_t s)
 {
-    const size_t smem = 2 * (size_t)kTileBuf;
-    ensure_smem((const void*)k_dt_tiles<false>, smem);
-    ensure_smem((const void*)k_dt_tiles<true>, smem);
+    // phase A holds one tile; phase C one tile and one tile's output planes
+    const size_t smem_a = (size_t)kTileBuf, smem_c = (size_t)kTileBuf + 3 * kTR * kTW * 4;
+    ensure_smem((const void*)k_dt_tiles<false>, smem_a);
+    ensure_smem((const void*)k_dt_tiles<true>, smem_c);
     const int ntx = (w + kTW - 1) / kTW, ntile = (h + kTR - 1) / kTR;
     const int nitems = ntx * ntile;
-    const int grid = nitems < 3 * sm_count() ? nitems : 3 * sm_count();
+    auto grid_of = [&](const void* fn, size_t smem) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTNT, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        const int cap = per_sm * sm_count();
+        return nitems < cap ? nitems : cap;
+    };
     note_launch();
-    k_dt_tiles<false><<<grid, kTNT, smem, s>>>(maps, w, h, ntx, ntile, lut, agg, car, 0, eps, err);
+    k_dt_tiles<false><<<grid_of((const void*)k_dt_tiles<false>, smem_a), kTNT, smem_a, s>>>(
+        maps, w, h, ntx, ntile, lut, agg, car, 0, eps, err);
     note_launch();
     k_dt_cols_chain<<<(w + 7) / 8, 256, 0, s>>>(agg, w, ntile, car);
     note_launch();
-    k_dt_tiles<true><<<grid, kTNT, smem, s>>>(maps, w, h, ntx, ntile, lut, agg, car, final_pass,
-                                             eps, err);
+    k_dt_tiles<true><<<grid_of((const void*)k_dt_tiles<true>, smem_c), kTNT, smem_c, s>>>(
+        maps, w, h, ntx, ntile, lut, agg, car, final_pass, eps, err);
 }
 
 template <int LM>
