@@ -506,10 +506,16 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
                 M.Wk[ly][tx] = de;
             }
         }
-        for (int i = tid; i < kIn * kIn; i += 256) {
-            const int yy = i / kIn, xx = i - yy * kIn;
-            const float zy = S.Ys[yy][xx + 3];
-            M.XY[yy][xx] = f2((float)S.Rn[yy][xx + 11], norm_map(s, s.clip_sign ? fabsf(zy) : zy));
+        // two neighbours per step (rows have an even length, so a pair never straddles two
+        // rows), stored as one 16-byte write
+        static_assert(kIn % 2 == 0, "XY pairs");
+        for (int i = tid; i < kIn * kIn / 2; i += 256) {
+            const int yy = i / (kIn / 2), xx = 2 * (i - yy * (kIn / 2));
+            const float za = S.Ys[yy][xx + 3], zb = S.Ys[yy][xx + 4];
+            const float na = norm_map(s, s.clip_sign ? fabsf(za) : za);
+            const float nb = norm_map(s, s.clip_sign ? fabsf(zb) : zb);
+            *reinterpret_cast<float4*>(&M.XY[yy][xx]) =
+                make_float4((float)S.Rn[yy][xx + 11], na, (float)S.Rn[yy][xx + 12], nb);
         }
         __syncthreads();
         if (k == 0) {
