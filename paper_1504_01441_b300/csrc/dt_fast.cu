@@ -450,11 +450,6 @@ struct ColMaps {
 constexpr int kGRows = kTR + 2;
 constexpr int kTileBuf = (3 * kTR * kTW * 4 + kGRows * kTW + 1023) / 1024 * 1024;  // bytes
 
-struct Aff4 {
-    float A, B0, B1, B2, B3;
-};
-
-
 // One 8-row segment of a column tile in registers: rows r0 + sg*8 + i of column
 // `lane`; plane k of the tile at P + k*kTR*kTW (rows of kTW floats); G row j is global
 // row r0 - 1 + j. kInterior: every row of the tile and the row after it lie inside the
@@ -567,32 +562,30 @@ __device__ __forceinline__ void tile_maps(float (&v)[3][kTLS], const float (&wl)
 // flow u, v in planes 0 and 1 on the final pass: the sums over N, which is at least
 // flow_eps = 1e-20 there, so the fast quotient is within 2 ulp).
 __device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl)[kTLS + 1],
-                                           Aff4 (*agg)[kTW], int sg, int lane, const float (&cr)[6],
+                                           Aff (*agg)[kTW], int sg, int lane, const float (&cr)[6],
                                            float* P, int final_pass, float flow_eps)
 {
     Aff m = sweep_fwd<kTLS>(v, wl, kTLS);
-    agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
+    agg[sg][lane] = m;
     __syncthreads();
     Aff pre = Aff{0.f, cr[0], cr[1], cr[2]};  // zero carries outside the image
 #pragma unroll
     for (int q = 0; q < kTSeg - 1; q++) {
         if (q < sg) {
-            const Aff4 a = agg[q][lane];
-            pre = compose(pre, Aff{a.A, a.B0, a.B1, a.B2});
+            pre = compose(pre, agg[q][lane]);
         }
     }
     carry_fwd<kTLS>(v, wl, kTLS, pre);
     __syncthreads();
     m = sweep_bwd<kTLS>(v, wl, kTLS);
-    agg[sg][lane] = Aff4{m.A, m.B0, m.B1, m.B2, 0.f};
+    agg[sg][lane] = m;
     if (threadIdx.x == 0) bulk_wait_read();  // the output buffer's previous store has left it
     __syncthreads();
     Aff suf = Aff{0.f, cr[3], cr[4], cr[5]};
 #pragma unroll
     for (int q = kTSeg - 1; q > 0; q--) {
         if (q > sg) {
-            const Aff4 a = agg[q][lane];
-            suf = compose(suf, Aff{a.A, a.B0, a.B1, a.B2});
+            suf = compose(suf, agg[q][lane]);
         }
     }
     carry_bwd<kTLS>(v, wl, kTLS, suf);
@@ -626,9 +619,9 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
 {
     extern __shared__ __align__(1024) uint8_t smt[];  // input tile, then (phase C) output planes
     __shared__ float lut[256];
-    // segment maps: [9][kTSeg][kTW] floats in phase A, Aff4 [kTSeg][kTW] in phase C
-    __shared__ __align__(16) float segbuf[kApply ? kTSeg * kTW * 5 : kTSeg * kTW * kAgg];
-    Aff4 (*agg)[kTW] = reinterpret_cast<Aff4 (*)[kTW]>(segbuf);
+    // segment maps: [9][kTSeg][kTW] floats in phase A, Aff [kTSeg][kTW] in phase C
+    __shared__ __align__(16) float segbuf[kTSeg * kTW * (kApply ? 4 : kAgg)];
+    Aff (*agg)[kTW] = reinterpret_cast<Aff (*)[kTW]>(segbuf);
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x, lane = tid & 31, sg = tid >> 5;
     for (int i = tid; i < 256; i += blockDim.x) lut[i] = lut_in.w[i];
@@ -864,21 +857,25 @@ void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int 
     ensure_smem((const void*)k_dt_tiles<true>, smem_c);
     const int ntx = (w + kTW - 1) / kTW, ntile = (h + kTR - 1) / kTR;
     const int nitems = ntx * ntile;
-    auto grid_of = [&](const void* fn, size_t smem) {
+    // persistent grids of the resident CTAs, at most 4 (phase A) and 3 (phase C) per SM:
+    // five phase-A CTAs (at 48 registers) or four phase-C CTAs made the batch faster but the
+    // flow replayed alone slower (195-197 against 187-191 us)
+    auto grid_of = [&](const void* fn, size_t smem, int most) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTNT, smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
+        if (per_sm > most) per_sm = most;
         const int cap = per_sm * sm_count();
         return nitems < cap ? nitems : cap;
     };
     note_launch();
-    k_dt_tiles<false><<<grid_of((const void*)k_dt_tiles<false>, smem_a), kTNT, smem_a, s>>>(
+    k_dt_tiles<false><<<grid_of((const void*)k_dt_tiles<false>, smem_a, 4), kTNT, smem_a, s>>>(
         maps, w, h, ntx, ntile, lut, agg, car, 0, eps, err);
     note_launch();
     k_dt_cols_chain<<<(w + 7) / 8, 256, 0, s>>>(agg, w, ntile, car);
     note_launch();
-    k_dt_tiles<true><<<grid_of((const void*)k_dt_tiles<true>, smem_c), kTNT, smem_c, s>>>(
+    k_dt_tiles<true><<<grid_of((const void*)k_dt_tiles<true>, smem_c, 3), kTNT, smem_c, s>>>(
         maps, w, h, ntx, ntile, lut, agg, car, final_pass, eps, err);
 }
 
