@@ -316,6 +316,34 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def time_train_step(torch, hdrreg, theta, dev, stream, steps=10):
+    """One training step of the predictor in the library's kernels: forward, backward and
+    Adam on 64 crops of 64 x 64 x 2 quarter-resolution inputs (256 x 256 full), averaged
+    over `steps` steps after 3 untimed ones. -> ms per step."""
+    net = hdrreg.Predictor(64, 64, 64, theta.cpu().numpy(), device=dev)
+    x = torch.empty((64, 64, 64, 2), dtype=torch.bfloat16, device=dev).uniform_(-1, 1)
+    label = torch.zeros((64, net.ho, net.wo, 2), dtype=torch.float32, device=dev)
+    valid = torch.ones((64, net.ho, net.wo), dtype=torch.uint8, device=dev)
+
+    def train_step():
+        net.forward(x, stream=stream)
+        net.backward(x, label, valid, stream=stream)
+        net.adam(1e-4, stream=stream)
+    for _ in range(3):
+        train_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        train_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+TRAIN_STEP = "64 crops of 64x64x2 quarter-resolution inputs (256x256 full): forward, backward, Adam"
+
+
 def measure_learned(torch, hdrreg, synth, stacks, frames, p, dev, args):
     """Same batch through the fused path with the learned level-0 search, at the default
     operating point (refine 1, fallback above 1.5 x the median plain cost) and, if
@@ -378,6 +406,9 @@ def measure_learned(torch, hdrreg, synth, stacks, frames, p, dev, args):
     out["weights"] = ("paper_1504_01441_b300/predictor_theta.npy (python -m "
                       "paper_1504_01441_b300.learned)")
     out["plain_ssd_offsets_per_tile"] = (2 * p.radius + 1) ** 2
+    out["train_step_ms"] = round(time_train_step(torch, hdrreg, theta, dev,
+                                                 torch.cuda.Stream(device=dev)), 3)
+    out["train_step"] = TRAIN_STEP
     # the headline fields of the learned leg: the default point
     out.update({k: out["default"][k] for k in ("value", "unit", "fallback_rate",
                                                  "epe_vs_plain_px", "meets_0.5px_vs_plain")})
@@ -959,25 +990,7 @@ def run_scale12(args):
     torch.cuda.synchronize()
     ms_e2e = a.elapsed_time(b) / K
     del host
-    # one training step: 64 crops of 64 x 64 quarter-resolution pixels (256 x 256 full)
-    net = hdrreg.Predictor(64, 64, 64, theta.cpu().numpy(), device=dev)
-    x = torch.empty((64, 64, 64, 2), dtype=torch.bfloat16, device=dev).uniform_(-1, 1)
-    label = torch.zeros((64, net.ho, net.wo, 2), dtype=torch.float32, device=dev)
-    valid = torch.ones((64, net.ho, net.wo), dtype=torch.uint8, device=dev)
-
-    def train_step():
-        net.forward(x, stream=stream)
-        net.backward(x, label, valid, stream=stream)
-        net.adam(1e-4, stream=stream)
-    for _ in range(3):
-        train_step()
-    torch.cuda.synchronize()
-    a.record(stream)
-    for _ in range(10):
-        train_step()
-    b.record(stream)
-    torch.cuda.synchronize()
-    train_ms = a.elapsed_time(b) / 10
+    train_ms = time_train_step(torch, hdrreg, theta, dev, stream)
     out_mpix = n * w * h / 1e6
     d = legs["default"]
     cpu = None
@@ -1017,8 +1030,7 @@ def run_scale12(args):
                     "ms_per_step": round(ms_e2e, 3),
                     "api": "hdrreg_register_merge_host, default operating point"},
             "train_step_ms": round(train_ms, 3),
-            "train_step": "64 crops of 64x64x2 quarter-resolution inputs (256x256 full): "
-                          "forward, backward, Adam",
+            "train_step": TRAIN_STEP,
             "gpu_launches": launches, "clocks": clk_sum, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
