@@ -531,24 +531,41 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
         }
         // Row pass: moments of each 11-tap row segment about its own centre pixel
         // (a = x - x_c, b = y - y_c): M1 = sum g (a, b), M2 = sum g (a^2, b^2), M11 = sum g a b.
-        for (int i = tid; i < kIn * kTile; i += 256) {
-            const int yy = i / kTile, xx = i % kTile;
-            const float2 c = M.XY[yy][xx + kHalo];
-            float2 m1 = f2(0.f, 0.f), m2 = f2(0.f, 0.f);
-            float m11 = 0.f;
+        // Two neighbouring segments per step share one 12-element window, read as six
+        // 16-byte loads; each keeps its own sums in tap order.
+        static_assert(kTile % 2 == 0 && 2 * kHalo + 2 == 12, "row pass window");
+        for (int i = tid; i < kIn * kTile / 2; i += 256) {
+            const int yy = i / (kTile / 2), xx = 2 * (i - yy * (kTile / 2));
+            float2 r[12];
+            const float4* src = reinterpret_cast<const float4*>(&M.XY[yy][xx]);
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                const float4 t = src[q];
+                r[2 * q] = f2(t.x, t.y);
+                r[2 * q + 1] = f2(t.z, t.w);
+            }
+            const float2 c0 = r[kHalo], c1 = r[kHalo + 1];
+            float2 m1a = f2(0.f, 0.f), m2a = f2(0.f, 0.f), m1b = f2(0.f, 0.f), m2b = f2(0.f, 0.f);
+            float m11a = 0.f, m11b = 0.f;
 #pragma unroll
             for (int d = 0; d <= 2 * kHalo; d++) {
                 if (d == kHalo) continue;  // the centre tap's deviations are exactly zero
                 const float2 g2 = f2(args.g[d], args.g[d]);
-                const float2 ab = __ffma2_rn(c, neg1, M.XY[yy][xx + d]);
-                const float2 gab = __fmul2_rn(g2, ab);
-                m1 = __fadd2_rn(m1, gab);
-                m2 = __ffma2_rn(gab, ab, m2);
-                m11 = fmaf(gab.x, ab.y, m11);
+                const float2 aba = __ffma2_rn(c0, neg1, r[d]);
+                const float2 abb = __ffma2_rn(c1, neg1, r[d + 1]);
+                const float2 gaba = __fmul2_rn(g2, aba);
+                const float2 gabb = __fmul2_rn(g2, abb);
+                m1a = __fadd2_rn(m1a, gaba);
+                m1b = __fadd2_rn(m1b, gabb);
+                m2a = __ffma2_rn(gaba, aba, m2a);
+                m2b = __ffma2_rn(gabb, abb, m2b);
+                m11a = fmaf(gaba.x, aba.y, m11a);
+                m11b = fmaf(gabb.x, abb.y, m11b);
             }
-            M.H1[yy][xx] = m1;
-            M.H2[yy][xx] = m2;
-            M.H11[yy][xx] = m11;
+            *reinterpret_cast<float4*>(&M.H1[yy][xx]) = make_float4(m1a.x, m1a.y, m1b.x, m1b.y);
+            *reinterpret_cast<float4*>(&M.H2[yy][xx]) = make_float4(m2a.x, m2a.y, m2b.x, m2b.y);
+            M.H11[yy][xx] = m11a;
+            M.H11[yy][xx + 1] = m11b;
         }
         __syncthreads();
         // Column pass: a thread takes four consecutive output rows 4 ty0 .. 4 ty0 + 3 of
