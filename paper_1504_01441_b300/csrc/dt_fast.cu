@@ -649,13 +649,12 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
         // phase C: this item's six carries (written by the chain kernel), loaded before
         // the wait for the tile so that their latency overlaps it
         float cr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (kApply) {
+        if (kApply) {  // car[tile][q][x]: one 128-byte line per warp and carry
             const int xc = (item % ntx) * kTW + lane, tc = item / ntx;
-            if (xc < w) {
-                const size_t c0 = (size_t)xc * kCar * ntile + tc;
+            const size_t wp = (size_t)ntx * kTW;
+            const size_t c0 = (size_t)tc * kCar * wp + xc;
 #pragma unroll
-                for (int q = 0; q < 6; q++) cr[q] = __ldg(car + c0 + (size_t)q * ntile);
-            }
+            for (int q = 0; q < 6; q++) cr[q] = __ldg(car + c0 + (size_t)q * wp);
         }
         const bool ok = __syncthreads_and(mbar_wait(&bar, ph));
         ph ^= 1u;
@@ -676,9 +675,10 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
         __syncthreads();  // every thread holds its segment: the input buffer is free
         if (item + (int)gridDim.x < nitems) issue(item + gridDim.x);
         if (!kApply) {
-            const bool colok = x0 + lane < w;
-            tile_maps(v, wl, segbuf, sg, lane, colok,
-                      agg_out + (size_t)(x0 + lane) * kAgg * ntile + tile, (size_t)ntile);
+            // agg[tile][k][x]: one 128-byte line per warp and value
+            const size_t wp = (size_t)ntx * kTW;
+            tile_maps(v, wl, segbuf, sg, lane, true,
+                      agg_out + (size_t)tile * kAgg * wp + x0 + lane, wp);
         } else {
             tile_apply(v, wl, agg, sg, lane, cr, Q, final_pass, flow_eps);
             fence_async_smem();
@@ -693,26 +693,21 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
     if (kApply && tid == 0) bulk_wait_read();
 }
 
-// One warp per column; lane = tile (32 tiles per round, carried across rounds):
-// forward carries by an exclusive shuffle scan of the maps (A_f, B_f), then the
-// backward carries by a reverse exclusive scan of (S, K0 + Q c). Columns of at most
-// 32 tiles (frames up to 2,048 rows) take one round from registers.
-__global__ void __launch_bounds__(256) k_dt_cols_chain(const float* __restrict__ agg, int w,
-                                                      int ntile, float* __restrict__ car)
+// The carry chain of one column, one warp, lane = tile (32 tiles per round, carried across
+// rounds): forward carries by an exclusive shuffle scan of the maps (A_f, B_f), then the
+// backward carries by a reverse exclusive scan of (S, K0 + Q c). ag(k, t) reads value k of
+// tile t's map, ca(k, t) is carry k of tile t (c[3], then c'[3]). Columns of at most 32
+// tiles (frames up to 2,048 rows) take one round from registers.
+template <typename AG, typename CA>
+__device__ __forceinline__ void column_chain(int ntile, int lane, AG ag, CA ca)
 {
-    const int x = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (x >= w) return;
-    const float* ag = agg + (size_t)x * kAgg * ntile;  // ag[k * ntile + t]
-    float* ca = car + (size_t)x * kCar * ntile;         // ca[k * ntile + t]
+    const Aff id{1.f, 0.f, 0.f, 0.f};
     if (ntile <= 32) {
-        // one round: the nine values of each tile loaded together, and the forward
-        // carries kept in registers for the backward scan
         const int t = lane;
         const bool in = t < ntile;
         float a[kAgg];
 #pragma unroll
-        for (int k = 0; k < kAgg; k++) a[k] = in ? __ldg(ag + k * ntile + t) : 0.f;
-        const Aff id{1.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < kAgg; k++) a[k] = in ? ag(k, t) : 0.f;
         Aff inc = in ? Aff{a[0], a[1], a[2], a[3]} : id;
         for (int d = 1; d < 32; d <<= 1) {
             const Aff q = shfl_aff<true>(inc, d);
@@ -731,44 +726,43 @@ __global__ void __launch_bounds__(256) k_dt_cols_chain(const float* __restrict__
         if (lane == 31) exc = id;
         const Aff cb = compose(id, exc);
         if (in) {
-            ca[t] = c.B0;
-            ca[ntile + t] = c.B1;
-            ca[2 * ntile + t] = c.B2;
-            ca[3 * ntile + t] = cb.B0;
-            ca[4 * ntile + t] = cb.B1;
-            ca[5 * ntile + t] = cb.B2;
+            ca(0, t) = c.B0;
+            ca(1, t) = c.B1;
+            ca(2, t) = c.B2;
+            ca(3, t) = cb.B0;
+            ca(4, t) = cb.B1;
+            ca(5, t) = cb.B2;
         }
         return;
     }
-    Aff run{1.f, 0.f, 0.f, 0.f};  // maps of the tiles before this round
+    Aff run = id;  // maps of the tiles before this round
     for (int t0 = 0; t0 < ntile; t0 += 32) {
         const int t = t0 + lane;
-        const Aff m = t < ntile ? Aff{ag[t], ag[ntile + t], ag[2 * ntile + t], ag[3 * ntile + t]}
-                                : Aff{1.f, 0.f, 0.f, 0.f};
+        const Aff m = t < ntile ? Aff{ag(0, t), ag(1, t), ag(2, t), ag(3, t)} : id;
         Aff inc = m;
         for (int d = 1; d < 32; d <<= 1) {
             const Aff q = shfl_aff<true>(inc, d);
             if (lane >= d) inc = compose(q, inc);
         }
         Aff exc = shfl_aff<true>(inc, 1);
-        if (lane == 0) exc = Aff{1.f, 0.f, 0.f, 0.f};
+        if (lane == 0) exc = id;
         const Aff c = compose(run, exc);
         if (t < ntile) {
-            ca[t] = c.B0;
-            ca[ntile + t] = c.B1;
-            ca[2 * ntile + t] = c.B2;
+            ca(0, t) = c.B0;
+            ca(1, t) = c.B1;
+            ca(2, t) = c.B2;
         }
         run = compose(run, Aff{__shfl_sync(0xffffffffu, inc.A, 31), __shfl_sync(0xffffffffu, inc.B0, 31),
                                __shfl_sync(0xffffffffu, inc.B1, 31), __shfl_sync(0xffffffffu, inc.B2, 31)});
     }
-    run = Aff{1.f, 0.f, 0.f, 0.f};  // maps of the tiles after this round, from the bottom
+    run = id;  // maps of the tiles after this round, from the bottom
     for (int rd = (ntile + 31) / 32 - 1; rd >= 0; rd--) {
         const int t = rd * 32 + lane;
-        Aff m{1.f, 0.f, 0.f, 0.f};
+        Aff m = id;
         if (t < ntile) {
-            const float Q = ag[7 * ntile + t];
-            m = Aff{ag[8 * ntile + t], fmaf(Q, ca[t], ag[4 * ntile + t]),
-                    fmaf(Q, ca[ntile + t], ag[5 * ntile + t]), fmaf(Q, ca[2 * ntile + t], ag[6 * ntile + t])};
+            const float Q = ag(7, t);
+            m = Aff{ag(8, t), fmaf(Q, ca(0, t), ag(4, t)), fmaf(Q, ca(1, t), ag(5, t)),
+                    fmaf(Q, ca(2, t), ag(6, t))};
         }
         Aff inc = m;
         for (int d = 1; d < 32; d <<= 1) {
@@ -776,16 +770,66 @@ __global__ void __launch_bounds__(256) k_dt_cols_chain(const float* __restrict__
             if (lane + d < 32) inc = compose(q, inc);
         }
         Aff exc = shfl_aff<false>(inc, 1);
-        if (lane == 31) exc = Aff{1.f, 0.f, 0.f, 0.f};
+        if (lane == 31) exc = id;
         const Aff c = compose(run, exc);
         if (t < ntile) {
-            ca[3 * ntile + t] = c.B0;
-            ca[4 * ntile + t] = c.B1;
-            ca[5 * ntile + t] = c.B2;
+            ca(3, t) = c.B0;
+            ca(4, t) = c.B1;
+            ca(5, t) = c.B2;
         }
         run = compose(run, Aff{__shfl_sync(0xffffffffu, inc.A, 0), __shfl_sync(0xffffffffu, inc.B0, 0),
                                __shfl_sync(0xffffffffu, inc.B1, 0), __shfl_sync(0xffffffffu, inc.B2, 0)});
     }
+}
+
+// The maps and carries live as agg[t][k][x] and car[t][k][x], so that the tile passes move
+// them as whole 128-byte lines. One CTA of 32 warps per 32-column strip: the strip's maps
+// come in as whole lines into shared memory ([k][t][33], padded against bank conflicts),
+// each warp chains one column there, and the carries leave as whole lines.
+constexpr int kChainPad = 33;
+constexpr size_t kChainSmemMax = 200 * 1024;
+
+size_t chain_smem(int ntile) { return (size_t)(kAgg + kCar) * ntile * kChainPad * 4; }
+
+constexpr int kChainNT = 32 * kTW;
+
+__global__ void __launch_bounds__(kChainNT) k_dt_cols_chain(const float* __restrict__ agg, int w,
+                                                           int ntile, float* __restrict__ car)
+{
+    extern __shared__ float cs[];
+    float* M = cs;                                   // M[(k * ntile + t) * kChainPad + c]
+    float* C = cs + (size_t)kAgg * ntile * kChainPad;  // C[(k * ntile + t) * kChainPad + c]
+    const size_t wp = (size_t)((w + kTW - 1) / kTW * kTW);
+    const int x0 = blockIdx.x * kTW, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < ntile * kAgg; r += kTW) {
+        const int t = r / kAgg, k = r - t * kAgg;
+        M[(k * ntile + t) * kChainPad + lane] = __ldg(agg + ((size_t)t * kAgg + k) * wp + x0 + lane);
+    }
+    __syncthreads();
+    {
+        const int c = warp;
+        column_chain(ntile, lane,
+                     [&](int k, int t) { return M[(k * ntile + t) * kChainPad + c]; },
+                     [&](int k, int t) -> float& { return C[(k * ntile + t) * kChainPad + c]; });
+    }
+    __syncthreads();
+    for (int r = warp; r < ntile * kCar; r += kTW) {
+        const int t = r / kCar, k = r - t * kCar;
+        car[((size_t)t * kCar + k) * wp + x0 + lane] = C[(k * ntile + t) * kChainPad + lane];
+    }
+}
+
+// The same chain for columns too tall for the strip's maps to fit shared memory: one
+// warp per column, each lane reading its own tile's values from global memory.
+__global__ void __launch_bounds__(256) k_dt_cols_chain_tall(const float* __restrict__ agg, int w,
+                                                           int ntile, float* __restrict__ car)
+{
+    const size_t wp = (size_t)((w + kTW - 1) / kTW * kTW);
+    const int x = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (x >= (int)wp) return;
+    column_chain(ntile, lane,
+                 [&](int k, int t) { return __ldg(agg + ((size_t)t * kAgg + k) * wp + x); },
+                 [&](int k, int t) -> float& { return car[((size_t)t * kCar + k) * wp + x]; });
 }
 
 // ------------------------------------------------------------- host side
@@ -873,7 +917,13 @@ void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int 
     k_dt_tiles<false><<<grid_of((const void*)k_dt_tiles<false>, smem_a, 4), kTNT, smem_a, s>>>(
         maps, w, h, ntx, ntile, lut, agg, car, 0, eps, err);
     note_launch();
-    k_dt_cols_chain<<<(w + 7) / 8, 256, 0, s>>>(agg, w, ntile, car);
+    const size_t cs = chain_smem(ntile);
+    if (cs <= kChainSmemMax) {
+        ensure_smem((const void*)k_dt_cols_chain, cs);
+        k_dt_cols_chain<<<ntx, kChainNT, cs, s>>>(agg, w, ntile, car);
+    } else {
+        k_dt_cols_chain_tall<<<(ntx * kTW + 7) / 8, 256, 0, s>>>(agg, w, ntile, car);
+    }
     note_launch();
     k_dt_tiles<true><<<grid_of((const void*)k_dt_tiles<true>, smem_c, 3), kTNT, smem_c, s>>>(
         maps, w, h, ntx, ntile, lut, agg, car, final_pass, eps, err);
