@@ -430,9 +430,12 @@ __global__ void __launch_bounds__(kRowNT, LM <= 17 ? 3 : 1) k_dt_rows_pipe(float
 //     K_top = K0 + Q c + S c' (c: forward carry entering at the top, c': backward
 //     carry entering at the bottom; Q because the backward pass is linear in J =
 //     J0 + P c): each segment's own map, folded over the tile's segments;
-//  B) one thread per column chains the carries down and up the tiles;
+//  B) per column, the carries down and up its tiles (one warp per column, one CTA
+//     per 32-column strip);
 //  C) every tile recomputes its sweeps with the exact carries and stores.
-// Tiles never wait on one another; phase C re-reads the tile from L2.
+// Tiles never wait on one another; phase C re-reads the tile (partly from L2). The
+// maps and carries are stored [tile][value][column], so phases A and C move them as
+// whole 128-byte lines.
 constexpr int kTW = 32;
 constexpr int kTSeg = 8;
 constexpr int kTLS = 8;
