@@ -298,7 +298,6 @@ struct MergeSmem {
     float2 H2[kIn][kTile];  // (sum g a^2, sum g b^2)
     float H11[kIn][kTile + 1];  // sum g a b
     float Wk[kTile][kTile + 1];
-    float Ns[kTile][kTile + 1], Ds[kTile][kTile + 1];
 };
 
 // Tile t of a row-major grid tiles_x wide: (t mod tiles_x, t / tiles_x) from the FP32
@@ -427,7 +426,7 @@ __device__ __forceinline__ int stack_of(const MergeBatch<NS>& B, int item)
 // i = blockIdx.x + j * gridDim.x, and within an item every source of its stack in order;
 // the next unit's inputs are staged (async copies) while the current one computes.
 template <int NS>
-__global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeBatch<NS> B)
+__global__ void __launch_bounds__(256, 3) k_merge(const __grid_constant__ MergeBatch<NS> B)
 {
     extern __shared__ __align__(16) uint8_t merge_smem[];
     MergeSmem& M = *reinterpret_cast<MergeSmem*>(merge_smem);
@@ -449,7 +448,10 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
                     D.async_ok);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+    // this thread's sums over the sources: chroma, and luma for rows 4 ty0 .. 4 ty0 + 3 of
+    // column tx (the rows its column pass computes)
     float cnu = 0.f, cnv = 0.f, cden = 0.f;
+    float ns_acc[4] = {0.f, 0.f, 0.f, 0.f}, ds_acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (;;) {
         // the unit after this one: the next source of the item, or the CTA's next item
         int nitem = item, nsi = si, nk = k + 1;
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
         if (k == 0) {  // the reference's own weights open the sums
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const int ly = ty0 + 8 * q;
+                const int ly = 4 * ty0 + q;
                 const int x = x0 + tx, y = y0 + ly;
                 float nu = 0.f, de = 0.f;
                 if (x < w && y < h) {
@@ -501,8 +503,8 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
                     de = well_exposed(z, args.we_k);
                     nu = de * z;
                 }
-                M.Ns[ly][tx] = nu;
-                M.Ds[ly][tx] = de;
+                ns_acc[q] = nu;
+                ds_acc[q] = de;
                 M.Wk[ly][tx] = de;
             }
         }
@@ -634,8 +636,8 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
                                      : (s.clip ? __ldg(s.clip + (size_t)y * w + x) != 0
                                                : (z <= 0.f || z >= 255.f));
                 wk = clipped ? 0.f : well_exposed(z, args.we_k) * qv;
-                M.Ns[ly][tx] = fmaf(wk, z * s.inv_ratio, M.Ns[ly][tx]);
-                M.Ds[ly][tx] += wk;
+                ns_acc[q] = fmaf(wk, z * s.inv_ratio, ns_acc[q]);
+                ds_acc[q] += wk;
                 if (q_out) q_out[(size_t)k * w * h + (size_t)y * w + x] = qv;
             }
             M.Wk[ly][tx] = wk;
@@ -652,11 +654,10 @@ __global__ void __launch_bounds__(256, 2) k_merge(const __grid_constant__ MergeB
         if (k == ns - 1) {
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const int x = x0 + tx, y = y0 + ty0 + 8 * q;
+                const int x = x0 + tx, y = y0 + 4 * ty0 + q;
                 // D holds the reference's own weight (at least exp(-k/4)) and at most
                 // nsrc + 1: the fast quotient is within 2 ulp
-                if (x < w && y < h)
-                    oy[(size_t)y * w + x] = __fdividef(M.Ns[ty0 + 8 * q][tx], M.Ds[ty0 + 8 * q][tx]);
+                if (x < w && y < h) oy[(size_t)y * w + x] = __fdividef(ns_acc[q], ds_acc[q]);
             }
             if (c_ok) {
                 const size_t o = (size_t)cy * cw + cx;
@@ -769,7 +770,7 @@ static int merge_grid(int nitems)
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return nitems < 2 * sms ? nitems : 2 * sms;
+    return nitems < 3 * sms ? nitems : 3 * sms;  // the resident CTAs: three per SM
 }
 
 void launch_merge(const uint8_t* ref_y, const uint8_t* ref_u, const uint8_t* ref_v, int w, int h,
