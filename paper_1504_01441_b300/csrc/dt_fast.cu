@@ -607,6 +607,16 @@ __device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl
     }
 }
 
+// Dynamic shared memory of the tile passes, bytes: the tile (planes + guide rows), the
+// output planes (phase C), the link table, the segment maps, the barrier.
+constexpr int kTileOut = (3 * kTR * kTW * 4 + kGRows * kTW + 127) / 128 * 128;
+template <bool kApply>
+constexpr int kTileLut = kApply ? kTileOut + 3 * kTR * kTW * 4 : kTileBuf;
+template <bool kApply>
+constexpr int kTileBar = kTileLut<kApply> + 256 * 4 + kTSeg * kTW * (kApply ? 4 : kAgg) * 4;
+template <bool kApply>
+constexpr int kTileSmem = kTileBar<kApply> + 8;
+
 // Persistent tile pass over items i = tile * ntx + strip. An item's tile lands in the
 // input buffer; once every thread holds its segment in registers, the next item's copy is
 // issued into the same buffer, so the copy overlaps the item's arithmetic.
@@ -620,19 +630,21 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
                                                    const float* __restrict__ car, int final_pass,
                                                    float flow_eps, int* err)
 {
-    extern __shared__ __align__(1024) uint8_t smt[];  // input tile, then (phase C) output planes
-    __shared__ float lut[256];
-    // segment maps: [9][kTSeg][kTW] floats in phase A, Aff [kTSeg][kTW] in phase C
-    __shared__ __align__(16) float segbuf[kTSeg * kTW * (kApply ? 4 : kAgg)];
+    // all in the dynamic block (tile_smem): the input tile; in phase C the output planes
+    // (128-byte aligned after the tile's bytes); the link table; the segment maps
+    // ([9][kTSeg][kTW] floats in phase A, Aff [kTSeg][kTW] in phase C); the barrier
+    extern __shared__ __align__(1024) uint8_t smt[];
+    float* lut = reinterpret_cast<float*>(smt + kTileLut<kApply>);
+    float* segbuf = lut + 256;
     Aff (*agg)[kTW] = reinterpret_cast<Aff (*)[kTW]>(segbuf);
-    __shared__ __align__(8) uint64_t bar;
+    uint64_t& bar = *reinterpret_cast<uint64_t*>(smt + kTileBar<kApply>);
     const int tid = threadIdx.x, lane = tid & 31, sg = tid >> 5;
     for (int i = tid; i < 256; i += blockDim.x) lut[i] = lut_in.w[i];
     if (tid == 0) mbar_init(&bar);
     __syncthreads();
     float* P = reinterpret_cast<float*>(smt);
     const uint8_t* G = smt + 3 * kTR * kTW * 4;
-    float* Q = reinterpret_cast<float*>(smt + kTileBuf);
+    float* Q = reinterpret_cast<float*>(smt + kTileOut);
     const int nitems = ntx * ntile;
     auto issue = [&](int item) {
         if (tid == 0) {
@@ -899,7 +911,7 @@ void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int 
                        float eps, float* agg, float* car, int* err, cudaStream_t s)
 {
     // phase A holds one tile; phase C one tile and one tile's output planes
-    const size_t smem_a = (size_t)kTileBuf, smem_c = (size_t)kTileBuf + 3 * kTR * kTW * 4;
+    const size_t smem_a = (size_t)kTileSmem<false>, smem_c = (size_t)kTileSmem<true>;
     ensure_smem((const void*)k_dt_tiles<false>, smem_a);
     ensure_smem((const void*)k_dt_tiles<true>, smem_c);
     const int ntx = (w + kTW - 1) / kTW, ntile = (h + kTR - 1) / kTR;
@@ -928,7 +940,7 @@ void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int 
         k_dt_cols_chain_tall<<<(ntx * kTW + 7) / 8, 256, 0, s>>>(agg, w, ntile, car);
     }
     note_launch();
-    k_dt_tiles<true><<<grid_of((const void*)k_dt_tiles<true>, smem_c, 3), kTNT, smem_c, s>>>(
+    k_dt_tiles<true><<<grid_of((const void*)k_dt_tiles<true>, smem_c, 4), kTNT, smem_c, s>>>(
         maps, w, h, ntx, ntile, lut, agg, car, final_pass, eps, err);
 }
 
