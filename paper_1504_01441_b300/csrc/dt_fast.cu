@@ -916,9 +916,9 @@ void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int 
     ensure_smem((const void*)k_dt_tiles<true>, smem_c);
     const int ntx = (w + kTW - 1) / kTW, ntile = (h + kTR - 1) / kTR;
     const int nitems = ntx * ntile;
-    // persistent grids of the resident CTAs, at most 4 (phase A) and 3 (phase C) per SM:
-    // five phase-A CTAs (at 48 registers) or four phase-C CTAs made the batch faster but the
-    // flow replayed alone slower (195-197 against 187-191 us)
+    // persistent grids of the resident CTAs, at most four per SM in both phases: five
+    // phase-A CTAs (at 48 registers) made the flow replayed alone faster (171 against
+    // 174 us) but the batch of many stacks on concurrent lanes slower
     auto grid_of = [&](const void* fn, size_t smem, int most) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTNT, smem) != cudaSuccess ||
