@@ -615,7 +615,9 @@ constexpr int kTileLut = kApply ? kTileOut + 3 * kTR * kTW * 4 : kTileBuf;
 template <bool kApply>
 constexpr int kTileBar = kTileLut<kApply> + 256 * 4 + kTSeg * kTW * (kApply ? 4 : kAgg) * 4;
 template <bool kApply>
-constexpr int kTileSmem = kTileBar<kApply> + 8;
+constexpr int kTileCar = kTileBar<kApply> + 16;  // phase C: the item's six carry lines
+template <bool kApply>
+constexpr int kTileSmem = kApply ? kTileCar<true> + kCar * kTW * 4 : kTileBar<false> + 8;
 
 // Persistent tile pass over items i = tile * ntx + strip. An item's tile lands in the
 // input buffer; once every thread holds its segment in registers, the next item's copy is
@@ -652,25 +654,21 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
             // the threads' reads of the buffer (ordered before this by a barrier) come
             // before the copy's writes into it
             fence_async_smem();
-            mbar_expect(&bar, 3u * kTR * kTW * 4u + kGRows * kTW);
+            mbar_expect(&bar, 3u * kTR * kTW * 4u + kGRows * kTW + (kApply ? kCar * kTW * 4u : 0u));
             for (int k = 0; k < 3; k++) tma_load_2d(P + k * kTR * kTW, &maps.in[k], x0, r0, &bar);
             tma_load_2d(smt + 3 * kTR * kTW * 4, &maps.guide, x0, r0 - 1, &bar);
+            if (kApply) {  // car[tile][q][x]: the item's six 128-byte lines, with the tile
+                const size_t wp = (size_t)ntx * kTW;
+                const float* c0 = car + (size_t)(item / ntx) * kCar * wp + x0;
+                for (int q = 0; q < kCar; q++)
+                    bulk_load(smt + kTileCar<kApply> + q * kTW * 4, c0 + (size_t)q * wp, kTW * 4, &bar);
+            }
         }
     };
     uint32_t ph = 0;
     int item = blockIdx.x;
     if (item < nitems) issue(item);
     for (; item < nitems; item += gridDim.x) {
-        // phase C: this item's six carries (written by the chain kernel), loaded before
-        // the wait for the tile so that their latency overlaps it
-        float cr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (kApply) {  // car[tile][q][x]: one 128-byte line per warp and carry
-            const int xc = (item % ntx) * kTW + lane, tc = item / ntx;
-            const size_t wp = (size_t)ntx * kTW;
-            const size_t c0 = (size_t)tc * kCar * wp + xc;
-#pragma unroll
-            for (int q = 0; q < 6; q++) cr[q] = __ldg(car + c0 + (size_t)q * wp);
-        }
         const bool ok = __syncthreads_and(mbar_wait(&bar, ph));
         ph ^= 1u;
         if (!ok) {
@@ -682,6 +680,14 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
             return;
         }
         const int x0 = (item % ntx) * kTW, tile = item / ntx, r0 = tile * kTR;
+        // phase C: this item's six carries (written by the chain kernel), arrived with the
+        // tile; read before the barrier that frees the buffers for the next item's copies
+        float cr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (kApply) {
+            const float* cs = reinterpret_cast<const float*>(smt + kTileCar<kApply>);
+#pragma unroll
+            for (int q = 0; q < 6; q++) cr[q] = cs[q * kTW + lane];
+        }
         float v[3][kTLS], wl[kTLS + 1];
         if (r0 > 0 && r0 + kTR < h)
             tile_seg_load<true>(P, G, lut, sg, lane, r0, h, v, wl);
