@@ -804,15 +804,16 @@ __device__ __forceinline__ void column_chain(int ntile, int lane, AG ag, CA ca)
 }
 
 // The maps and carries live as agg[t][k][x] and car[t][k][x], so that the tile passes move
-// them as whole 128-byte lines. One CTA of 32 warps per 32-column strip: the strip's maps
-// come in as whole lines into shared memory ([k][t][33], padded against bank conflicts),
-// each warp chains one column there, and the carries leave as whole lines.
-constexpr int kChainPad = 33;
-constexpr size_t kChainSmemMax = 200 * 1024;
+// them as whole 128-byte lines. One CTA of eight warps per eight columns: the columns' maps
+// come in as 32-byte sectors into shared memory ([k][t][9], padded against bank conflicts),
+// each warp chains one column there, and the carries leave the same way.
+constexpr int kChainCols = 8;
+constexpr int kChainPad = kChainCols + 1;
+constexpr size_t kChainSmemMax = 48 * 1024;  // columns of up to 91 tiles (5,800 rows)
 
 size_t chain_smem(int ntile) { return (size_t)(kAgg + kCar) * ntile * kChainPad * 4; }
 
-constexpr int kChainNT = 32 * kTW;
+constexpr int kChainNT = 32 * kChainCols;
 
 __global__ void __launch_bounds__(kChainNT) k_dt_cols_chain(const float* __restrict__ agg, int w,
                                                            int ntile, float* __restrict__ car)
@@ -821,10 +822,10 @@ __global__ void __launch_bounds__(kChainNT) k_dt_cols_chain(const float* __restr
     float* M = cs;                                   // M[(k * ntile + t) * kChainPad + c]
     float* C = cs + (size_t)kAgg * ntile * kChainPad;  // C[(k * ntile + t) * kChainPad + c]
     const size_t wp = (size_t)((w + kTW - 1) / kTW * kTW);
-    const int x0 = blockIdx.x * kTW, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = warp; r < ntile * kAgg; r += kTW) {
-        const int t = r / kAgg, k = r - t * kAgg;
-        M[(k * ntile + t) * kChainPad + lane] = __ldg(agg + ((size_t)t * kAgg + k) * wp + x0 + lane);
+    const int x0 = blockIdx.x * kChainCols, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < ntile * kAgg * kChainCols; e += kChainNT) {
+        const int r = e / kChainCols, c = e - r * kChainCols, t = r / kAgg, k = r - t * kAgg;
+        M[(k * ntile + t) * kChainPad + c] = __ldg(agg + ((size_t)t * kAgg + k) * wp + x0 + c);
     }
     __syncthreads();
     {
@@ -834,9 +835,9 @@ __global__ void __launch_bounds__(kChainNT) k_dt_cols_chain(const float* __restr
                      [&](int k, int t) -> float& { return C[(k * ntile + t) * kChainPad + c]; });
     }
     __syncthreads();
-    for (int r = warp; r < ntile * kCar; r += kTW) {
-        const int t = r / kCar, k = r - t * kCar;
-        car[((size_t)t * kCar + k) * wp + x0 + lane] = C[(k * ntile + t) * kChainPad + lane];
+    for (int e = threadIdx.x; e < ntile * kCar * kChainCols; e += kChainNT) {
+        const int r = e / kChainCols, c = e - r * kChainCols, t = r / kCar, k = r - t * kCar;
+        car[((size_t)t * kCar + k) * wp + x0 + c] = C[(k * ntile + t) * kChainPad + c];
     }
 }
 
@@ -941,7 +942,7 @@ void launch_cols_tiles(const ColMaps& maps, int w, int h, const DtLut& lut, int 
     const size_t cs = chain_smem(ntile);
     if (cs <= kChainSmemMax) {
         ensure_smem((const void*)k_dt_cols_chain, cs);
-        k_dt_cols_chain<<<ntx, kChainNT, cs, s>>>(agg, w, ntile, car);
+        k_dt_cols_chain<<<ntx * (kTW / kChainCols), kChainNT, cs, s>>>(agg, w, ntile, car);
     } else {
         k_dt_cols_chain_tall<<<(ntx * kTW + 7) / 8, 256, 0, s>>>(agg, w, ntile, car);
     }
