@@ -494,7 +494,7 @@ def measure_stages(torch, hdrreg, p, stack, dev, args, meta=None):
 
 # DRAM bytes of one flow call (2592 x 1944, 3 iterations, 13 launches): dram__bytes_read.sum
 # + dram__bytes_write.sum over the call's launches in one ncu capture (cold L2).
-FLOW_TRAFFIC = 553227264
+FLOW_TRAFFIC = 553611520
 
 
 def measure_search_alu(torch, hdrreg, stages, p, valid_tiles, dev):

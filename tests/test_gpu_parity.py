@@ -335,8 +335,8 @@ def test_flow_column_pass_shapes(hd, orc, w, h, T, R):
     """Heights that exercise the column pass's 64-row tiles and its carry chain: 1928 rows
     end in a tile of 8 rows, 1000 rows in one of 40, 4200 rows make 66 tiles per column
     (three rounds of the chain's 32-tile scan, carried across rounds), 17 rows are one
-    tile of which most rows lie below the frame, 6720 rows (105 tiles) are more than a
-    strip's maps in shared memory hold, so the chain reads them from global memory."""
+    tile of which most rows lie below the frame, 6720 rows (105 tiles) are more than the
+    chain's shared-memory form takes (91 tiles), so the chain reads them from global memory."""
     from paper_1504_01441_b300 import synth
     spec = synth.StackSpec(w, h, ratios=((4, 1),), noise_sigma=1.0, field_amp=3.0, movers=0,
                            chroma=False, n_blobs=max(4, w * h // 4000), n_rects=2)
