@@ -607,8 +607,10 @@ __device__ __forceinline__ void tile_apply(float (&v)[3][kTLS], const float (&wl
     }
 }
 
-// Dynamic shared memory of the tile passes, bytes: the tile (planes + guide rows), the
-// output planes (phase C), the link table, the segment maps, the barrier.
+// Dynamic shared memory of the tile passes, bytes. Phase A: the tile (planes + guide rows,
+// 1 KB-rounded), the link table, the segment maps, the barrier. Phase C, packed so that
+// four CTAs fit an SM: the tile, the output planes 128-byte aligned after its bytes, the
+// link table, the composition records, the barrier, the item's six carry lines.
 constexpr int kTileOut = (3 * kTR * kTW * 4 + kGRows * kTW + 127) / 128 * 128;
 template <bool kApply>
 constexpr int kTileLut = kApply ? kTileOut + 3 * kTR * kTW * 4 : kTileBuf;
@@ -632,9 +634,8 @@ __global__ void __launch_bounds__(kTNT) k_dt_tiles(const __grid_constant__ ColMa
                                                    const float* __restrict__ car, int final_pass,
                                                    float flow_eps, int* err)
 {
-    // all in the dynamic block (tile_smem): the input tile; in phase C the output planes
-    // (128-byte aligned after the tile's bytes); the link table; the segment maps
-    // ([9][kTSeg][kTW] floats in phase A, Aff [kTSeg][kTW] in phase C); the barrier
+    // all in the dynamic block (kTileSmem bytes, laid out above): the segment maps are
+    // [9][kTSeg][kTW] floats in phase A and Aff [kTSeg][kTW] in phase C
     extern __shared__ __align__(1024) uint8_t smt[];
     float* lut = reinterpret_cast<float*>(smt + kTileLut<kApply>);
     float* segbuf = lut + 256;
