@@ -6,8 +6,9 @@
 // homography is evaluated as a displacement H(p) - p from FP32 coefficients
 // prepared once per CTA in binary64, so the bilinear fraction is computed from
 // small numbers (no 2600-px absolute coordinates in FP32).
-// Merge: one CTA per 32x32 luma tile with a 5-pixel halo staged in shared
-// memory; the five Gaussian moments are separable (row pass, column pass). To
+// Merge: persistent CTAs (three per SM) walk 32x32 luma tiles, each with a 5-pixel
+// halo staged in shared memory; the five Gaussian moments are separable (row pass,
+// column pass). To
 // avoid the FP32 cancellation of E[x^2] - mu^2, each row segment's moments are
 // taken about its own centre pixel and the column pass re-centres them exactly
 // onto the output pixel, so flat windows only ever sum small numbers. The two
@@ -424,7 +425,9 @@ __device__ __forceinline__ int stack_of(const MergeBatch<NS>& B, int item)
 
 // Persistent CTAs over (tile, source) units: items (tiles of any stack of the launch)
 // i = blockIdx.x + j * gridDim.x, and within an item every source of its stack in order;
-// the next unit's inputs are staged (async copies) while the current one computes.
+// the next unit's inputs are staged (async copies) while the current one computes. Three
+// CTAs fit an SM: 80 registers a thread (the launch bound) and 74 KB of shared memory,
+// each thread keeping its four output rows' luma sums in registers.
 template <int NS>
 __global__ void __launch_bounds__(256, 3) k_merge(const __grid_constant__ MergeBatch<NS> B)
 {
